@@ -1,0 +1,26 @@
+"""The seeded generators are deterministic and produce the workload shapes."""
+import numpy as np
+
+from workloads import config1, tiny_pair, template_half, margin_for
+
+
+def test_config1_deterministic_and_shaped():
+    a = config1()
+    b = config1()
+    np.testing.assert_array_equal(a.ref, b.ref)
+    np.testing.assert_array_equal(a.sen, b.sen)
+    np.testing.assert_array_equal(a.points, b.points)
+    assert a.ref.shape == (512, 512) and a.ref.dtype == np.float32
+    assert a.points.shape == (100, 2)
+    assert 0.0 <= a.ref.min() and a.ref.max() <= 1.0
+    sx, sy = a.meta["shift"]
+    assert -8 <= sx <= 8 and -8 <= sy <= 8
+    lo, hi = margin_for(a.m, a.R)
+    assert np.all(a.points >= lo) and np.all(a.points < 512 - hi)
+
+
+def test_tiny_pair_and_half():
+    p = tiny_pair(3, 70, 83, 9, 4, 12)
+    assert p.ref.shape == (70, 83)
+    assert len(p.points) <= 12
+    assert template_half(9) == 4 and template_half(10) == 5
