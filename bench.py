@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the fine-registration hot path of arXiv 2202.13347 on GB300.
+
+One step = the whole path on one synthetic image pair: SFOC cube of the
+reference and of the sensed image (Sec. 2.1), the FP64 integral images,
+template statistics, correlation R_ST, NCC (Eq. 9), argmax and sub-pixel
+refinement for every interest point (Sec. 2.2, Sec. 3.2.2).
+
+Default workload: 2048x2048 optical-like reference vs SAR-like sensed image
+(Gamma speckle L=4, piecewise shift field), 1000 block-Harris points,
+template 81x81, search radius 20, 12 SFOC channels.
+
+Metric: matched control points per second (points whose status is OK),
+whole job over all ranks; SFOC Mpix/s is reported beside it.  Both forms
+are measured: the BF16 cube + tcgen05 correlation form and the plain FP32
+form; the line's `value` is the BF16 form when it is available.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "matched CPs/sec and SFOC Mpix/sec on 1 GB300, BF16-batched vs plain FP32"
+UNIT = "CP/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2"])
+    ap.add_argument("--forms", default="bf16,f32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+def workload(name, rank):
+    from workloads import config1, config2
+    if name == "c1":
+        p = config1(seed=1000 + 7919 * rank)
+        desc = "c1: 512x512 pair, piecewise inverting map, 100 block-max points, m=41, R=10, z=12"
+    else:
+        p = config2(seed=2000 + 7919 * rank)
+        desc = ("c2: 2048x2048 optical-like ref vs SAR-like sensed (Gamma L=4 speckle, 256-px shift field), "
+                "1000 block-Harris points, m=81, R=20, z=12")
+    return p, desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
+    p = b.params(dtype=b.DTYPE_BF16 if form == "bf16" else b.DTYPE_F32)
+    corr = b.CORR_IGEMM_TC if form == "bf16" else b.CORR_DIRECT_F32
+    d_ref = torch.from_numpy(pair.ref).cuda()
+    d_sen = torch.from_numpy(pair.sen).cuda()
+    d_pts = torch.from_numpy(pair.points).cuda()
+    raw = torch.empty((len(pair.points), 6), dtype=torch.int32, device="cuda")
+
+    def step():
+        ctx.register_pair(d_ref, d_sen, d_pts, pair.m, pair.R, p=p, corr_path=corr, out=raw)
+
+    for _ in range(warmup):
+        step()
+    ctx.sync()
+    stream = torch.cuda.current_stream()
+    ctx.enable_timing(True)
+    ctx.reset_timing()
+    l0 = ctx.launch_count
+    evs = []
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.zero_()                       # L2 flush (256 MB write), outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    launches = ctx.launch_count - l0
+    ctx.sync()
+    st = ctx.stage_times()
+    ctx.enable_timing(False)
+    ms = [a.elapsed_time(c) for a, c in evs]
+    status = raw[:, 5].cpu()
+    return dict(ms=sum(ms), ms_steps=ms, matched=int((status == 0).sum()), valid=int(((status == 0) | (status == 3)).sum()),
+                stages=st, launches=launches, p=p, corr=corr, d=(d_ref, d_sen, d_pts))
+
+
+def run_e2e(b, torch, ctx, pair, p, corr, steps):
+    h_ref = torch.from_numpy(pair.ref).pin_memory()
+    h_sen = torch.from_numpy(pair.sen).pin_memory()
+    h_pts = torch.from_numpy(pair.points).pin_memory()
+    out = torch.empty((len(pair.points), 6), dtype=torch.int32).pin_memory()
+    ctx.register_pair_host(h_ref, h_sen, h_pts, pair.m, pair.R, p=p, corr_path=corr, out=out)
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        ctx.register_pair_host(h_ref, h_sen, h_pts, pair.m, pair.R, p=p, corr_path=corr, out=out)
+        t.append(time.perf_counter() - t0)
+    matched = int((out[:, 5] == 0).sum())
+    h2d = h_ref.numel() * 4 + h_sen.numel() * 4 + h_pts.numel() * 4
+    d2h = out.numel() * 4
+    return dict(value=matched / statistics.mean(t), unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                ms_per_step=1e3 * statistics.mean(t))
+
+
+def cpu_baseline(pair, n_sample=16, seed=99):
+    import numpy as np
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(pair.points), min(n_sample, len(pair.points)), replace=False))
+    t0 = time.perf_counter()
+    o = oracle.match_pair(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R)
+    dt = time.perf_counter() - t0
+    matched = int((o["status"] == 0).sum())
+    return dict(value=matched / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                sample="%d of %d points (seeded), FP64 SFOC on their windows only, Eq. 8 NCC" % (len(idx), len(pair.points)),
+                seconds=dt)
+
+
+def corr_flops(pair, z=12):
+    P = (2 * pair.R + 1) ** 2
+    return 2.0 * pair.m * pair.m * z * P
+
+
+def main():
+    args = parse()
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        if torch.cuda.is_available():
+            torch.cuda.set_device(0)
+
+    pair, desc = workload(args.config, rank)
+    config = {"workload": desc, "H": int(pair.ref.shape[0]), "W": int(pair.ref.shape[1]),
+              "points_per_pair": int(len(pair.points)), "m": pair.m, "R": pair.R, "z": 12,
+              "pairs_per_rank": 1, "l2": "flushed between timed steps (256 MB write)"}
+
+    if args.impl == "reference":
+        # the CPU oracle as it stands, on a bounded sample of the same workload
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        steps_t = []
+        matched = 0
+        n_sample = 8
+        for i in range(args.warmup + args.steps):
+            import numpy as np
+            rng = np.random.default_rng(1000 + i)
+            idx = np.sort(rng.choice(len(pair.points), n_sample, replace=False))
+            t0 = time.perf_counter()
+            o = oracle.match_pair(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R)
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                steps_t.append(dt)
+                matched += int((o["status"] == 0).sum())
+        tot = sum(steps_t)
+        value = matched / tot
+        sample = "%d seeded points of %d per step, FP64 SFOC on their windows, Eq. 8 NCC" % (n_sample, len(pair.points))
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "impl": "reference",
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import paper_2202_13347_gb300 as pkg
+    pkg.build()
+    b = pkg.load()
+    ctx = b.Context(torch.cuda.current_device())
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    forms = [f for f in args.forms.split(",") if f]
+    pk = peaks()
+    results = {}
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if os.environ.get(
+        "CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    clocks = None
+    for form in forms:
+        try:
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            with ClockSampler(gpu_index) as cs:
+                r = run_form(b, torch, ctx, pair, form, args.steps, args.warmup, flush)
+            if dist:
+                t = torch.tensor([r["ms"]], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                mt = torch.tensor([r["matched"]], device="cuda", dtype=torch.int64)
+                dist.all_reduce(mt)
+                r["ms_max"], r["matched_all"] = float(t.item()), int(mt.item())
+            else:
+                r["ms_max"], r["matched_all"] = r["ms"], r["matched"]
+            r["clocks"] = cs.summary()
+            results[form] = r
+        except b.SfocError as e:
+            results[form] = {"error": str(e)}
+    main_form = next((f for f in forms if "error" not in results.get(f, {"error": 1})), None)
+    if main_form is None:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "error": {f: results[f].get("error") for f in forms}}))
+        sys.exit(1)
+
+    def summarize(r, form):
+        st = r["stages"]
+        per_step = {k: v[0] / args.steps for k, v in st.items()}
+        sfoc_ms = per_step["steer"] + per_step["smooth"]
+        corr_ms, corr_n = st["correlation"]
+        flops = corr_flops(pair) * r["valid"]          # processed points only
+        per_launch = corr_ms / max(1, corr_n)
+        ach = flops / (per_launch * 1e-3) / 1e12
+        if form == "bf16":
+            roof = {"bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
+                    "frac": ach / pk["bf16"], "traffic": None,
+                    "kernel": "k_corr_tc (tcgen05 bf16, fp32 accumulate)",
+                    "peak_src": "bf16_tflops burst, %s" % pk["src"],
+                    "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
+        else:
+            roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "kernel": "k_corr_f32 (FP32 FMA)",
+                    "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                    "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
+        return dict(value=r["matched_all"] / (r["ms_max"] * 1e-3), ms_per_step=r["ms_max"] / args.steps,
+                    sfoc_mpix_s=2 * pair.ref.size / (sfoc_ms * 1e-3) / 1e6 if sfoc_ms > 0 else None,
+                    stage_ms_per_step={k: round(v, 4) for k, v in per_step.items()}, roofline=roof,
+                    matched_per_step=r["matched"], gpu_launches=r["launches"], clocks=r["clocks"])
+
+    summ = {f: summarize(results[f], f) for f in forms if "error" not in results[f]}
+    main = summ[main_form]
+    r0 = results[main_form]
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(b, torch, ctx, pair, r0["p"], r0["corr"], max(3, min(args.steps, 10)))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pair)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if main_form == "bf16" else "f32",
+            "data": "synthetic", "config": dict(config, form=main_form), "roofline": main["roofline"],
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
+            "sfoc_mpix_s": main["sfoc_mpix_s"], "stage_ms_per_step": main["stage_ms_per_step"],
+            "forms": {f: {k: v for k, v in s.items() if k not in ("clocks",)} for f, s in summ.items()},
+            "errors": {f: results[f]["error"] for f in forms if "error" in results[f]} or None}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

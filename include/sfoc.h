@@ -1,0 +1,235 @@
+/*
+ * sfoc.h - C ABI of the GB300 (sm_103a) library for the fine-registration
+ * hot path of Ye et al., arXiv 2202.13347: building the SFOC feature cube
+ * (Sec. 2.1) and Fast-NCC_SFOC template matching (Sec. 2.2, Sec. 3.2.2).
+ *
+ * Conventions
+ *  - Images are H rows x W columns; x is the column (right), y the row (down).
+ *  - Every pointer named d_* is CUDA device memory owned by the caller unless
+ *    stated otherwise; h_* is host memory.  Nothing is freed by the library
+ *    that it did not allocate.
+ *  - All calls are asynchronous on the context's stream unless stated
+ *    otherwise and return an sfoc_status.  Nothing throws across the ABI.
+ *    On a negative status sfoc_last_error_string() describes the failure.
+ *  - A context is not thread-safe: use one per host thread.
+ *  - Calls check their arguments before enqueuing work; kernel-side failures
+ *    (bounded waits that expired, bad points) are reported per point in
+ *    fastncc_result.status or by sfoc_ctx_sync().
+ */
+#ifndef SFOC_GB300_H
+#define SFOC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SFOC_API __attribute__((visibility("default")))
+#else
+#define SFOC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfoc_ctx sfoc_ctx;
+typedef struct sfoc_cube sfoc_cube;
+
+typedef enum {
+    SFOC_OK = 0,
+    SFOC_ERR_INVALID_ARG = -1, /* null pointer, negative size, bad enum */
+    SFOC_ERR_SHAPE = -2,       /* shapes or channel counts that do not fit together */
+    SFOC_ERR_OOM = -3,         /* a device allocation failed */
+    SFOC_ERR_CUDA = -4,        /* a CUDA runtime/driver call failed */
+    SFOC_ERR_TIMEOUT = -5,     /* a bounded device wait expired */
+    SFOC_ERR_UNSUPPORTED = -6  /* valid but outside what the kernels implement */
+} sfoc_status;
+
+/* Per-point status in fastncc_result.status. */
+enum {
+    SFOC_PT_OK = 0,
+    SFOC_PT_OUT_OF_BOUNDS = 1, /* template or a candidate window leaves its image; nothing computed */
+    SFOC_PT_FLAT_TEMPLATE = 2, /* template variance <= 1e-12 * m*m*z; offsets 0, ncc 0 */
+    SFOC_PT_PEAK_ON_EDGE = 3,  /* best |dx| or |dy| equals R; no sub-pixel on that axis */
+    SFOC_PT_NAN = 4            /* NaN in the template or in some candidate's score */
+};
+
+typedef enum { SFOC_DTYPE_F32 = 0, SFOC_DTYPE_BF16 = 1 } sfoc_dtype;
+
+/* Correlation kernel for R_ST (Eq. 10). */
+typedef enum {
+    SFOC_CORR_AUTO = 0,       /* pick by dtype and autotuned shape class */
+    SFOC_CORR_DIRECT_F32 = 1, /* FP32 CUDA-core direct correlation (F32 cubes) */
+    SFOC_CORR_IGEMM_TC = 2    /* tcgen05 BF16 implicit GEMM, FP32 accumulate (BF16 cubes) */
+} sfoc_corr_path;
+
+/*
+ * Descriptor parameters (Sec. 2.1; Table 2).  sfoc_params_default() fills:
+ *   scales = {0.6, 0.8, 1.0} first-order STDs, sigma2 = 1.5 second-order STD
+ *   (Table 2); n_orient = 6 (theta_k = k*pi/6, Sec. 2.1); dilations {1,2,3}
+ *   (Sec. 2.1); sigma_d1 = 1.0 and sigma_d2 = 1.5, the smoothing STDs of the
+ *   first- and second-order groups (the paper only says the second is
+ *   larger); eps = 1e-3 in v/(||v||+eps); rectify = 1 (|.| of each steered
+ *   response); radius_mult = 3 (kernel radius ceil(3 sigma));
+ *   first_order_only = 0 (1 gives the F-SFOC variant of Sec. 4.2);
+ *   cube_dtype = SFOC_DTYPE_F32.
+ * Limits: n_scales 1..4, each radius <= 9; sigma2 radius <= 9; n_orient 1..8;
+ * n_dil 1..3 with rates 1..3; smoothing radii <= 6; cube_dtype BF16 needs
+ * n_orient == 6 and first_order_only == 0 (12 channels).
+ */
+typedef struct {
+    int n_scales;
+    double scales[8];
+    double sigma2;
+    int n_orient;
+    int n_dil;
+    int dil[4];
+    double sigma_d1;
+    double sigma_d2;
+    double eps;
+    int rectify;
+    double radius_mult;
+    int first_order_only;
+    int cube_dtype; /* sfoc_dtype */
+} sfoc_params;
+
+/* One matched control point (Sec. 3.2.2: the most similar position is the CP).
+ * The template is cut from the sensed cube around p; the candidate window is
+ * the reference cube around p + (dx, dy).  For a sensed image that is the
+ * reference shifted by s, the answer is (dx, dy) = -s. */
+typedef struct {
+    int32_t dx, dy;       /* integer offset in [-R, R] of the best NCC */
+    float ncc;            /* NCC_SFOC at that offset (Eq. 8) */
+    float sub_dx, sub_dy; /* offset refined by a 3-point parabola per axis */
+    int32_t status;       /* SFOC_PT_* */
+} fastncc_result;
+
+typedef struct {
+    int corr_path;  /* sfoc_corr_path */
+    float* d_maps;  /* optional: n x (2R+1) x (2R+1) NCC maps (rows dy, cols dx) */
+} fastncc_opts;
+
+/* ---- context -------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` issuing work on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The context owns its
+ * workspace (grown on demand, freed by sfoc_ctx_destroy). */
+SFOC_API sfoc_status sfoc_ctx_create(sfoc_ctx** out, int device, void* stream);
+SFOC_API sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx);
+SFOC_API sfoc_status sfoc_ctx_set_stream(sfoc_ctx* ctx, void* stream);
+/* Blocks until the context's stream is idle; reports deferred device errors
+ * (SFOC_ERR_CUDA, or SFOC_ERR_TIMEOUT when a bounded device wait expired). */
+SFOC_API sfoc_status sfoc_ctx_sync(sfoc_ctx* ctx);
+/* Grows the workspace to hold at least `bytes` (so later calls, e.g. inside
+ * a CUDA-graph capture, allocate nothing). */
+SFOC_API sfoc_status sfoc_ctx_reserve(sfoc_ctx* ctx, size_t bytes);
+/* Bytes of workspace fastncc_match needs for n points of radius R. */
+SFOC_API size_t sfoc_match_workspace_bytes(int n, int search_radius);
+/* Last error message of this context (never NULL; "" when none). */
+SFOC_API const char* sfoc_last_error_string(const sfoc_ctx* ctx);
+/* Number of kernel launches this context has issued so far. */
+SFOC_API int64_t sfoc_ctx_launch_count(const sfoc_ctx* ctx);
+
+/* Per-stage device timing (tracing).  When enabled, every kernel launch of
+ * the context is bracketed by CUDA events on the context stream.  Stages:
+ * 0 steer (Eq. 2-7), 1 smooth+normalise, 2 integral images (Eq. 14-15),
+ * 3 template statistics (Eq. 12), 4 correlation R_ST (Eq. 10),
+ * 5 NCC + argmax + sub-pixel (Eq. 9), 6 other (exports, copies). */
+#define SFOC_NUM_STAGES 7
+SFOC_API sfoc_status sfoc_ctx_enable_timing(sfoc_ctx* ctx, int enable);
+/* Synchronises the stream and returns, per stage, the summed milliseconds
+ * and the number of launches since the last reset. */
+SFOC_API sfoc_status sfoc_ctx_stage_times(sfoc_ctx* ctx, double* ms_out, int64_t* launches_out);
+SFOC_API sfoc_status sfoc_ctx_reset_timing(sfoc_ctx* ctx);
+
+/* ---- descriptor ----------------------------------------------------- */
+
+SFOC_API sfoc_status sfoc_params_default(sfoc_params* p);
+
+/*
+ * sfoc_build - SFOC cube of one image (Sec. 2.1, Eq. 1-7, dilated Gaussian
+ * smoothing and group normalisation).
+ *   d_image      float32 image, row-major, pitch `pitch_elems` >= W elements.
+ *   scales       host array of n_scales first-order STDs (overrides p->scales;
+ *                NULL = take p->scales / n_scales from p).
+ *   n_orient     orientations per group (overrides p->n_orient; <= 0 = p's).
+ *   p            NULL = sfoc_params_default().
+ *   out          receives a cube owned by the library (free with
+ *                sfoc_cube_free).  If *out already holds a cube of the same
+ *                H, W, channel count and dtype, it is rebuilt in place and no
+ *                memory is allocated.
+ * The cube holds z = 2*n_orient channels (first-order then second-order
+ * orientations), each normalised per group, plus per-pixel sums over
+ * channels of g and g^2 used for the integral images of Eq. 14.
+ */
+SFOC_API sfoc_status sfoc_build(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems,
+                       const double* scales, int n_scales, int n_orient, const sfoc_params* p,
+                       sfoc_cube** out);
+
+/* Shape and dtype of a cube (any pointer may be NULL). */
+SFOC_API sfoc_status sfoc_cube_info(const sfoc_cube* cube, int* z, int* H, int* W, int* dtype);
+/* Writes the cube as float32 [z][H][W] (dense) into d_out. */
+SFOC_API sfoc_status sfoc_cube_export(sfoc_ctx* ctx, const sfoc_cube* cube, float* d_out);
+/* Builds (if needed) and writes the two integral planes of Eq. 14 as
+ * float64 [2][H+1][W+1] (exclusive prefix of sum_c g and of sum_c g^2). */
+SFOC_API sfoc_status sfoc_cube_export_integral(sfoc_ctx* ctx, sfoc_cube* cube, double* d_out);
+SFOC_API sfoc_status sfoc_cube_free(sfoc_cube* cube);
+
+/* ---- matching ------------------------------------------------------- */
+
+/*
+ * fastncc_match - Fast-NCC_SFOC (Sec. 2.2, Eq. 8-16) for n interest points.
+ *   ref, sen        cubes of the reference and sensed images (same z/dtype).
+ *   d_points        int32 n x 2 (x, y) pairs in sensed coordinates.
+ *   template_size   m >= 1 (odd: +-(m-1)/2 around p; even: [p-m/2, p+m/2-1]).
+ *   search_radius   R >= 0: candidates d in [-R, R]^2.
+ *   opts            NULL = defaults (AUTO path, no maps).
+ *   d_out           caller-owned array of n fastncc_result.
+ * NCC is the Eq. 8 value computed through Eq. 9: R_ST by a correlation
+ * kernel, R_S and R_SS from FP64 integral images (Eq. 14-16), the variances
+ * in FP64.  Ties go to the smallest dy, then the smallest dx.
+ * Limits: m <= 128, R <= 63.
+ */
+SFOC_API sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const int32_t* d_points, int n,
+                          int template_size, int search_radius, const fastncc_opts* opts,
+                          fastncc_result* d_out);
+
+/*
+ * fastncc_register_pair - the whole fine-registration path for one pair:
+ * sfoc_build of both images, then fastncc_match.  Device buffers.  The two
+ * cubes are cached in the context and reused while the shapes stay equal.
+ */
+SFOC_API sfoc_status fastncc_register_pair(sfoc_ctx* ctx, const float* d_ref, int Hr, int Wr, const float* d_sen,
+                                  int Hs, int Ws, const int32_t* d_points, int n, int template_size,
+                                  int search_radius, const sfoc_params* p, const fastncc_opts* opts,
+                                  fastncc_result* d_out);
+
+/* Same with host buffers: copies the images and points to the device,
+ * runs the path and copies the results back before returning (synchronous).
+ * h_out receives n fastncc_result. */
+SFOC_API sfoc_status fastncc_register_pair_host(sfoc_ctx* ctx, const float* h_ref, int Hr, int Wr, const float* h_sen,
+                                       int Hs, int Ws, const int32_t* h_points, int n, int template_size,
+                                       int search_radius, const sfoc_params* p, const fastncc_opts* opts,
+                                       fastncc_result* h_out);
+
+/* ---- batched forms -------------------------------------------------- */
+
+/* Builds n_img cubes; images[i] is H[i] x W[i] with pitch pitch_elems[i]. */
+SFOC_API sfoc_status sfoc_build_batch(sfoc_ctx* ctx, int n_img, const float* const* d_images, const int* H, const int* W,
+                             const size_t* pitch_elems, const sfoc_params* p, sfoc_cube** outs);
+
+/*
+ * Matches n_pairs (ref, sen) pairs, each with its own points, m and R.  The
+ * work of all pairs goes through one persistent launch per stage (a device
+ * work queue of (pair, point) tasks ordered by cost); for BF16 cubes the
+ * correlation stage is the tcgen05 kernel.
+ */
+SFOC_API sfoc_status fastncc_match_batch(sfoc_ctx* ctx, int n_pairs, sfoc_cube* const* refs, sfoc_cube* const* sens,
+                                const int32_t* const* d_points, const int* n_points, const int* template_size,
+                                const int* search_radius, const fastncc_opts* opts, fastncc_result* const* d_outs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFOC_GB300_H */

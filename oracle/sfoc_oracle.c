@@ -326,7 +326,8 @@ int oracle_sfoc_roi(const float* image, int H, int W, const oracle_params* p,
                 for (int k = 0; k < no; ++k) n2s += D[g * no + k] * D[g * no + k];
                 double den = sqrt(n2s) + p->eps;
                 for (int k = 0; k < no; ++k) {
-                    double v = den > 0.0 ? D[g * no + k] / den : 0.0;
+                    /* NaN inputs stay NaN so matching can report them */
+                    double v = (den != den) ? NAN : (den > 0.0 ? D[g * no + k] / den : 0.0);
                     cube[((size_t)(g * no + k) * h + yy) * w + xx] = v;
                 }
             }

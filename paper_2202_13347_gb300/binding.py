@@ -1,0 +1,339 @@
+"""Thin ctypes binding of libsfoc_gb300.so (include/sfoc.h).
+
+Argument marshalling only: every step of the path runs in the library's
+CUDA kernels.  Torch supplies device memory (tensor data pointers) and the
+stream.  If the library is missing the import of this module fails loudly;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsfoc_gb300.so")
+
+OK = 0
+ERR_NAMES = {0: "SFOC_OK", -1: "SFOC_ERR_INVALID_ARG", -2: "SFOC_ERR_SHAPE", -3: "SFOC_ERR_OOM",
+             -4: "SFOC_ERR_CUDA", -5: "SFOC_ERR_TIMEOUT", -6: "SFOC_ERR_UNSUPPORTED"}
+PT_OK, PT_OUT_OF_BOUNDS, PT_FLAT_TEMPLATE, PT_PEAK_ON_EDGE, PT_NAN = 0, 1, 2, 3, 4
+DTYPE_F32, DTYPE_BF16 = 0, 1
+CORR_AUTO, CORR_DIRECT_F32, CORR_IGEMM_TC = 0, 1, 2
+
+
+class SfocError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n_scales", C.c_int),
+        ("scales", C.c_double * 8),
+        ("sigma2", C.c_double),
+        ("n_orient", C.c_int),
+        ("n_dil", C.c_int),
+        ("dil", C.c_int * 4),
+        ("sigma_d1", C.c_double),
+        ("sigma_d2", C.c_double),
+        ("eps", C.c_double),
+        ("rectify", C.c_int),
+        ("radius_mult", C.c_double),
+        ("first_order_only", C.c_int),
+        ("cube_dtype", C.c_int),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [("dx", C.c_int32), ("dy", C.c_int32), ("ncc", C.c_float), ("sub_dx", C.c_float),
+                ("sub_dy", C.c_float), ("status", C.c_int32)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("corr_path", C.c_int), ("d_maps", C.c_void_p)]
+
+
+_lib = None
+
+# every function of include/sfoc.h with (restype, argtypes)
+_P = C.c_void_p
+_SIGS = {
+    "sfoc_ctx_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "sfoc_ctx_destroy": (C.c_int, [_P]),
+    "sfoc_ctx_set_stream": (C.c_int, [_P, _P]),
+    "sfoc_ctx_sync": (C.c_int, [_P]),
+    "sfoc_ctx_reserve": (C.c_int, [_P, C.c_size_t]),
+    "sfoc_match_workspace_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "sfoc_last_error_string": (C.c_char_p, [_P]),
+    "sfoc_ctx_launch_count": (C.c_int64, [_P]),
+    "sfoc_ctx_enable_timing": (C.c_int, [_P, C.c_int]),
+    "sfoc_ctx_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "sfoc_ctx_reset_timing": (C.c_int, [_P]),
+    "sfoc_params_default": (C.c_int, [C.POINTER(Params)]),
+    "sfoc_build": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, C.POINTER(C.c_double), C.c_int, C.c_int,
+                             C.POINTER(Params), C.POINTER(_P)]),
+    "sfoc_cube_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)]),
+    "sfoc_cube_export": (C.c_int, [_P, _P, _P]),
+    "sfoc_cube_export_integral": (C.c_int, [_P, _P, _P]),
+    "sfoc_cube_free": (C.c_int, [_P]),
+    "fastncc_match": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_int, C.POINTER(Opts), _P]),
+    "fastncc_register_pair": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P, C.c_int, C.c_int,
+                                        C.c_int, C.POINTER(Params), C.POINTER(Opts), _P]),
+    "fastncc_register_pair_host": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P, C.c_int,
+                                             C.c_int, C.c_int, C.POINTER(Params), C.POINTER(Opts), _P]),
+    "sfoc_build_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_size_t), C.POINTER(Params), C.POINTER(_P)]),
+    "fastncc_match_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                                      C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(Opts), C.POINTER(_P)]),
+}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libsfoc_gb300.so is not built (run paper_2202_13347_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def params(scales=(0.6, 0.8, 1.0), sigma2=1.5, n_orient=6, dil=(1, 2, 3), sigma_d1=1.0, sigma_d2=1.5,
+           eps=1e-3, rectify=True, radius_mult=3.0, first_order_only=False, dtype=DTYPE_F32) -> Params:
+    p = Params()
+    lib().sfoc_params_default(C.byref(p))
+    p.n_scales = len(scales)
+    for i, s in enumerate(scales):
+        p.scales[i] = float(s)
+    p.sigma2 = float(sigma2)
+    p.n_orient = int(n_orient)
+    p.n_dil = len(dil)
+    for i, r in enumerate(dil):
+        p.dil[i] = int(r)
+    p.sigma_d1, p.sigma_d2, p.eps = float(sigma_d1), float(sigma_d2), float(eps)
+    p.rectify = 1 if rectify else 0
+    p.radius_mult = float(radius_mult)
+    p.first_order_only = 1 if first_order_only else 0
+    p.cube_dtype = int(dtype)
+    return p
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _check_cuda(t, name, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+class Cube:
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def info(self):
+        z, H, W, dt = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self.ctx._chk(lib().sfoc_cube_info(self.handle, C.byref(z), C.byref(H), C.byref(W), C.byref(dt)))
+        return z.value, H.value, W.value, dt.value
+
+    def export(self) -> torch.Tensor:
+        z, H, W, _ = self.info()
+        out = torch.empty((z, H, W), dtype=torch.float32, device=self.ctx.device)
+        self.ctx._chk(lib().sfoc_cube_export(self.ctx.h, self.handle, _ptr(out)))
+        return out
+
+    def export_integral(self) -> torch.Tensor:
+        z, H, W, _ = self.info()
+        out = torch.empty((2, H + 1, W + 1), dtype=torch.float64, device=self.ctx.device)
+        self.ctx._chk(lib().sfoc_cube_export_integral(self.ctx.h, self.handle, _ptr(out)))
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().sfoc_cube_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _results(raw: torch.Tensor):
+    return dict(dx=raw[:, 0], dy=raw[:, 1], ncc=raw[:, 2].view(torch.float32),
+                sub_dx=raw[:, 3].view(torch.float32), sub_dy=raw[:, 4].view(torch.float32), status=raw[:, 5])
+
+
+class Context:
+    """sfoc_ctx on one device and stream (default: torch's current stream)."""
+
+    def __init__(self, device=0, stream=None):
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        idx = self.device.index if self.device.index is not None else 0
+        if stream is None:
+            stream = torch.cuda.current_stream(idx)
+        self.stream = stream
+        h = C.c_void_p()
+        rc = lib().sfoc_ctx_create(C.byref(h), idx, C.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise SfocError(rc, "sfoc_ctx_create failed")
+        self.h = h
+
+    def _chk(self, rc):
+        if rc != OK:
+            raise SfocError(rc, lib().sfoc_last_error_string(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sfoc_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._chk(lib().sfoc_ctx_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def sync(self):
+        self._chk(lib().sfoc_ctx_sync(self.h))
+
+    def reserve(self, nbytes):
+        self._chk(lib().sfoc_ctx_reserve(self.h, int(nbytes)))
+
+    STAGES = ("steer", "smooth", "integral", "template_stats", "correlation", "ncc_argmax", "other")
+
+    def enable_timing(self, on=True):
+        self._chk(lib().sfoc_ctx_enable_timing(self.h, 1 if on else 0))
+
+    def reset_timing(self):
+        self._chk(lib().sfoc_ctx_reset_timing(self.h))
+
+    def stage_times(self):
+        """{stage: (milliseconds, launches)} accumulated since the last reset."""
+        ms = (C.c_double * len(self.STAGES))()
+        nl = (C.c_int64 * len(self.STAGES))()
+        self._chk(lib().sfoc_ctx_stage_times(self.h, ms, nl))
+        return {s: (ms[i], nl[i]) for i, s in enumerate(self.STAGES)}
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib().sfoc_ctx_launch_count(self.h))
+
+    # -- paper-named calls -------------------------------------------------
+    def sfoc_build(self, image: torch.Tensor, scales=None, n_orient=0, p: Params = None, out: Cube = None) -> Cube:
+        _check_cuda(image, "image", torch.float32)
+        H, W = image.shape
+        arr = None
+        if scales is not None:
+            arr = (C.c_double * len(scales))(*[float(s) for s in scales])
+        h = C.c_void_p(out.handle if out is not None else None)
+        self._chk(lib().sfoc_build(self.h, _ptr(image), H, W, W, arr, len(scales) if scales else 0, int(n_orient),
+                                   C.byref(p) if p is not None else None, C.byref(h)))
+        if out is not None and h.value == out.handle:
+            return out
+        return Cube(self, h.value)
+
+    def fastncc_match(self, ref: Cube, sen: Cube, points: torch.Tensor, template_size: int, search_radius: int,
+                      corr_path=CORR_AUTO, want_maps=False):
+        _check_cuda(points, "points", torch.int32)
+        n = points.shape[0]
+        raw = torch.empty((n, 6), dtype=torch.int32, device=self.device)
+        maps = None
+        if want_maps:
+            P1 = 2 * search_radius + 1
+            maps = torch.empty((n, P1, P1), dtype=torch.float32, device=self.device)
+        o = Opts(int(corr_path), maps.data_ptr() if maps is not None else None)
+        self._chk(lib().fastncc_match(self.h, ref.handle, sen.handle, _ptr(points), n, int(template_size),
+                                      int(search_radius), C.byref(o), _ptr(raw)))
+        res = _results(raw)
+        if want_maps:
+            res["maps"] = maps
+        return res
+
+    def register_pair(self, ref: torch.Tensor, sen: torch.Tensor, points: torch.Tensor, template_size: int,
+                      search_radius: int, p: Params = None, corr_path=CORR_AUTO, out: torch.Tensor = None):
+        _check_cuda(ref, "ref", torch.float32)
+        _check_cuda(sen, "sen", torch.float32)
+        _check_cuda(points, "points", torch.int32)
+        n = points.shape[0]
+        raw = out if out is not None else torch.empty((n, 6), dtype=torch.int32, device=self.device)
+        o = Opts(int(corr_path), None)
+        self._chk(lib().fastncc_register_pair(self.h, _ptr(ref), ref.shape[0], ref.shape[1], _ptr(sen), sen.shape[0],
+                                              sen.shape[1], _ptr(points), n, int(template_size), int(search_radius),
+                                              C.byref(p) if p is not None else None, C.byref(o), _ptr(raw)))
+        return raw
+
+    def register_pair_host(self, ref, sen, points, template_size: int, search_radius: int, p: Params = None,
+                           corr_path=CORR_AUTO, out=None):
+        """Host (CPU, ideally pinned) tensors in, host results out."""
+        for t, nm in ((ref, "ref"), (sen, "sen"), (points, "points")):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous host tensor" % nm)
+        n = points.shape[0]
+        raw = out if out is not None else torch.empty((n, 6), dtype=torch.int32)
+        o = Opts(int(corr_path), None)
+        self._chk(lib().fastncc_register_pair_host(
+            self.h, C.c_void_p(ref.data_ptr()), ref.shape[0], ref.shape[1], C.c_void_p(sen.data_ptr()), sen.shape[0],
+            sen.shape[1], C.c_void_p(points.data_ptr()), n, int(template_size), int(search_radius),
+            C.byref(p) if p is not None else None, C.byref(o), C.c_void_p(raw.data_ptr())))
+        return raw
+
+    def sfoc_build_batch(self, images, p: Params = None, outs=None):
+        n = len(images)
+        for i, im in enumerate(images):
+            _check_cuda(im, "images[%d]" % i, torch.float32)
+        ptrs = (C.c_void_p * n)(*[im.data_ptr() for im in images])
+        Hs = (C.c_int * n)(*[im.shape[0] for im in images])
+        Ws = (C.c_int * n)(*[im.shape[1] for im in images])
+        pitches = (C.c_size_t * n)(*[im.shape[1] for im in images])
+        hs = (C.c_void_p * n)(*[(outs[i].handle if outs is not None else None) for i in range(n)])
+        self._chk(lib().sfoc_build_batch(self.h, n, ptrs, Hs, Ws, pitches, C.byref(p) if p is not None else None, hs))
+        res = []
+        for i in range(n):
+            if outs is not None and hs[i] == outs[i].handle:
+                res.append(outs[i])
+            else:
+                res.append(Cube(self, hs[i]))
+        return res
+
+    def fastncc_match_batch(self, refs, sens, points, template_sizes, search_radii, corr_path=CORR_AUTO):
+        n = len(refs)
+        outs = [torch.empty((p.shape[0], 6), dtype=torch.int32, device=self.device) for p in points]
+        R = (C.c_void_p * n)(*[c.handle for c in refs])
+        S = (C.c_void_p * n)(*[c.handle for c in sens])
+        Pp = (C.c_void_p * n)(*[p.data_ptr() for p in points])
+        Np = (C.c_int * n)(*[p.shape[0] for p in points])
+        Mp = (C.c_int * n)(*[int(v) for v in template_sizes])
+        Rp = (C.c_int * n)(*[int(v) for v in search_radii])
+        Op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        o = Opts(int(corr_path), None)
+        self._chk(lib().fastncc_match_batch(self.h, n, R, S, Pp, Np, Mp, Rp, C.byref(o), Op))
+        return outs
+
+
+def results(raw: torch.Tensor):
+    """Splits an (n, 6) int32 result buffer into named fields."""
+    return _results(raw)
+
+
+def workspace_bytes(n, R) -> int:
+    return int(lib().sfoc_match_workspace_bytes(int(n), int(R)))

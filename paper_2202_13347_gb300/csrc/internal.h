@@ -1,0 +1,109 @@
+// Internal declarations of the SFOC / Fast-NCC_SFOC CUDA library (sm_103a).
+// Shared only between this library's own translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sfoc.h"
+
+namespace sfoc {
+
+// ---- limits -----------------------------------------------------------
+constexpr int kMaxScales = 4;
+constexpr int kMaxDerivRadius = 9;   // ceil(3 sigma) <= 9
+constexpr int kMaxSmoothRadius = 6;  // ceil(3 sigma_d) <= 6
+constexpr int kMaxDil = 3;
+constexpr int kMaxOrient = 8;
+constexpr int kMaxZ = 16;
+constexpr int kMaxTemplate = 128;
+constexpr int kMaxRadius = 63;
+
+// ---- filter taps (computed on the host in double, stored as float) -----
+// A separable 2-D kernel a(x) b(y) is applied as a horizontal pass with a
+// and a vertical pass with b; "odd" taps satisfy t(-q) = -t(q) and "even"
+// taps t(-q) = t(q), so only q = 0..K are stored.
+struct SteerTaps {
+    int ns;                                   // first-order scales
+    int K1[kMaxScales];                       // radius per scale
+    float a1[kMaxScales][kMaxDerivRadius + 1];  // odd: -q/(2 pi s^4) exp(-q^2/2s^2)
+    float g1[kMaxScales][kMaxDerivRadius + 1];  // even: exp(-q^2/2s^2)
+    int K2;                                   // second-order radius (0 = no second group)
+    float a2[kMaxDerivRadius + 1];            // even, zero-mean second-derivative factor
+    float g2[kMaxDerivRadius + 1];            // even Gaussian factor
+    float c2x[kMaxDerivRadius + 1];           // odd: q exp(-q^2/2s^2) / (2 pi s^6)
+    float c2y[kMaxDerivRadius + 1];           // odd: q exp(-q^2/2s^2)
+    int no;                                   // orientations
+    float ct[kMaxOrient], st[kMaxOrient];     // cos/sin of theta_k = k pi / no
+    int rectify;
+    int second;                               // 1: compute the second-order group
+    int halo;                                 // max radius
+};
+
+struct SmoothTaps {
+    int n_dil;
+    int dil[kMaxDil];
+    int Kd[2];                                // smoothing radius per group
+    float g[2][kMaxSmoothRadius + 1];         // normalised even taps per group
+    int halo[2];                              // max rate * Kd per group
+    int no;                                   // channels per group
+    int z;                                    // channels
+    float eps;
+};
+
+// ---- cube --------------------------------------------------------------
+// F32 cube: planar [z][H][pitch] float.
+// BF16 cube (z = 12): two 8-channel chunks per pixel, chunk 0 = channels
+// 0..7, chunk 1 = channels 8..11 and four zeros, stored twice:
+//   rm: [2][H][W][8] (pixels row-major)     - search windows (A operand)
+//   cm: [2][W][H][8] (pixels column-major)  - templates (B operand)
+struct Cube {
+    int H = 0, W = 0, z = 0, dtype = SFOC_DTYPE_F32;
+    size_t pitch = 0;          // elements per row of f32 planes / sum planes
+    float* f32 = nullptr;      // [z][H][pitch]
+    __nv_bfloat16* rm = nullptr;
+    __nv_bfloat16* cm = nullptr;
+    float* s1 = nullptr;       // [H][pitch] sum over channels of g
+    float* s2 = nullptr;       // [H][pitch] sum over channels of g^2
+    double* integ = nullptr;   // [2][H+1][ipitch] exclusive prefix of s1, s2
+    size_t ipitch = 0;
+    bool integ_valid = false;
+    int device = 0;
+};
+
+struct TileSums;  // integral-image scratch layout (k_integral.cu)
+
+// ---- kernel launchers (return cudaError_t of the launch) ----------------
+cudaError_t launch_sfoc_steer(const float* img, int H, int W, size_t pitch, float* F, size_t fpitch,
+                              const SteerTaps& tp, int z_first, cudaStream_t st);
+cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,
+                               cudaStream_t st);
+cudaError_t launch_cube_export(const Cube& c, float* out, cudaStream_t st);
+
+size_t integral_scratch_bytes(int H, int W);
+cudaError_t launch_integral(const Cube& c, void* scratch, cudaStream_t st, int* launches);
+
+struct PointStat {
+    double RT, RTT;       // template sums (Eq. 12) from the sensed integral images
+    float tmean;          // R_T / mnz (for the zero-mean template)
+    int status;           // SFOC_PT_*
+};
+
+cudaError_t launch_template_stats(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
+                                  PointStat* stats, cudaStream_t st);
+cudaError_t launch_corr_f32(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
+                            const PointStat* stats, float* maps, cudaStream_t st);
+cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
+                           const PointStat* stats, float* maps, int* err_flag, cudaStream_t st);
+size_t corr_tc_smem_bytes(int m, int R);
+cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m, int R, const PointStat* stats,
+                              const float* num, int centered, float* out_maps, fastncc_result* out,
+                              cudaStream_t st);
+
+// template half-width: rows before the centre
+__host__ __device__ inline int template_half(int m) { return (m % 2) ? (m - 1) / 2 : m / 2; }
+
+}  // namespace sfoc

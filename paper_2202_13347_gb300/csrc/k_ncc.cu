@@ -1,0 +1,187 @@
+// NCC assembly, peak picking and sub-pixel refinement (Eq. 9, 12, 16 of
+// arXiv 2202.13347; Sec. 3.2.2 takes the most similar position as the CP).
+//
+// k_template_stats  per point: bounds check, R_T and R_TT from the sensed
+//                   cube's integral images (Eq. 12 via Eq. 16), FP64.
+// k_ncc_argmax      per point (one CTA): for every offset, R_S and R_SS from
+//                   the reference integral images (4 lookups each), the
+//                   FP64 variance R_SS - R_S^2/mnz, NCC = num / sqrt(vS vT);
+//                   then a warp-shuffle argmax with the (NCC desc, dy asc,
+//                   dx asc) order and a 3-point parabola per axis.
+#include <math.h>
+
+#include "internal.h"
+
+namespace sfoc {
+
+namespace {
+
+__device__ __forceinline__ double rect(const double* P, size_t ip, int y0, int x0, int y1, int x1) {
+    return P[(size_t)y1 * ip + x1] - P[(size_t)y0 * ip + x1] - P[(size_t)y1 * ip + x0] + P[(size_t)y0 * ip + x0];
+}
+
+__global__ void k_template_stats(const double* __restrict__ Pr, int Hr, int Wr, const double* __restrict__ Ps,
+                                 int Hs, int Ws, size_t ips, const int32_t* __restrict__ pts, int n, int m, int R,
+                                 int z, PointStat* __restrict__ stats) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    (void)Pr;
+    const int h = template_half(m);
+    int px = pts[2 * k], py = pts[2 * k + 1];
+    PointStat s;
+    s.RT = s.RTT = 0.0;
+    s.tmean = 0.f;
+    int ty0 = py - h, tx0 = px - h;
+    bool ok = ty0 >= 0 && tx0 >= 0 && ty0 + m <= Hs && tx0 + m <= Ws && ty0 - R >= 0 && tx0 - R >= 0 &&
+              ty0 + m + R <= Hr && tx0 + m + R <= Wr;
+    if (!ok) {
+        s.status = SFOC_PT_OUT_OF_BOUNDS;
+    } else {
+        const double N = (double)m * m * z;
+        const double* P1 = Ps;
+        const double* P2 = Ps + (size_t)(Hs + 1) * ips;
+        s.RT = rect(P1, ips, ty0, tx0, ty0 + m, tx0 + m);
+        s.RTT = rect(P2, ips, ty0, tx0, ty0 + m, tx0 + m);
+        s.tmean = (float)(s.RT / N);
+        double vT = s.RTT - s.RT * s.RT / N;
+        if (s.RT != s.RT || s.RTT != s.RTT) s.status = SFOC_PT_NAN;
+        else if (vT <= 1e-12 * N) s.status = SFOC_PT_FLAT_TEMPLATE;
+        else s.status = SFOC_PT_OK;
+    }
+    stats[k] = s;
+}
+
+// argmax key: larger value wins, ties go to the smaller index
+__device__ __forceinline__ bool better(double v, int i, double bv, int bi) {
+    return v > bv || (v == bv && i < bi);
+}
+
+constexpr int kNccThreads = 256;
+
+__global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const double* __restrict__ Pr, int Hr, size_t ipr,
+                                                            const int32_t* __restrict__ pts, int m, int R, int z,
+                                                            const PointStat* __restrict__ stats,
+                                                            const float* __restrict__ num, int centered,
+                                                            float* __restrict__ out_maps,
+                                                            fastncc_result* __restrict__ out) {
+    extern __shared__ double s_map[];  // P1 * P1
+    __shared__ double s_bv[kNccThreads / 32];
+    __shared__ int s_bi[kNccThreads / 32];
+    __shared__ int s_nan;
+    const int k = blockIdx.x;
+    const int P1 = 2 * R + 1, P = P1 * P1;
+    const PointStat st = stats[k];
+    if (threadIdx.x == 0) s_nan = 0;
+    fastncc_result res;
+    res.dx = res.dy = 0;
+    res.ncc = 0.f;
+    res.sub_dx = res.sub_dy = 0.f;
+    res.status = st.status;
+    if (st.status != SFOC_PT_OK) {
+        if (out_maps)
+            for (int i = threadIdx.x; i < P; i += blockDim.x) out_maps[(size_t)k * P + i] = 0.f;
+        if (threadIdx.x == 0) out[k] = res;
+        return;
+    }
+    __syncthreads();
+    const double N = (double)m * m * z;
+    const double vT = st.RTT - st.RT * st.RT / N;
+    const int h = template_half(m);
+    const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
+    const double* P1p = Pr;
+    const double* P2p = Pr + (size_t)(Hr + 1) * ipr;
+    const float* nk = num + (size_t)k * P;
+    double bv = -INFINITY;
+    int bi = 0x7fffffff;
+    int has_nan = 0;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int iy = i / P1, ix = i - iy * P1;
+        int wy = ty0 + iy - R, wx = tx0 + ix - R;
+        double RS = rect(P1p, ipr, wy, wx, wy + m, wx + m);
+        double RSS = rect(P2p, ipr, wy, wx, wy + m, wx + m);
+        double vS = RSS - RS * RS / N;
+        double nm = (double)nk[i];
+        if (!centered) nm -= RS * st.RT / N;
+        double v;
+        if (vS != vS || nm != nm) v = NAN;
+        else if (vS <= 1e-12 * N) v = 0.0;
+        else v = nm / sqrt(vS * vT);
+        s_map[i] = v;
+        if (out_maps) out_maps[(size_t)k * P + i] = (float)v;
+        if (v != v) { has_nan = 1; continue; }
+        if (better(v, i, bv, bi)) { bv = v; bi = i; }
+    }
+    // warp argmax
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_down_sync(full, bv, o);
+        int oi = __shfl_down_sync(full, bi, o);
+        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+    }
+    has_nan = __any_sync(full, has_nan);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_bv[wid] = bv;
+        s_bi[wid] = bi;
+        if (has_nan) atomicOr(&s_nan, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bv = s_bv[0];
+        bi = s_bi[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (better(s_bv[w], s_bi[w], bv, bi)) { bv = s_bv[w]; bi = s_bi[w]; }
+        if (bi == 0x7fffffff) {  // every score NaN
+            res.status = SFOC_PT_NAN;
+        } else {
+            int iy = bi / P1, ix = bi - iy * P1;
+            res.dy = iy - R;
+            res.dx = ix - R;
+            res.ncc = (float)bv;
+            bool edge = false;
+            double ddx = 0.0, ddy = 0.0;
+            auto parab = [](double cm, double c0, double cp) {
+                double den = cm - 2.0 * c0 + cp;
+                if (!(den < 0.0)) return 0.0;
+                double d = (cm - cp) / (2.0 * den);
+                return d > 0.5 ? 0.5 : (d < -0.5 ? -0.5 : d);
+            };
+            if (ix > 0 && ix < P1 - 1) ddx = parab(s_map[bi - 1], bv, s_map[bi + 1]);
+            else edge = true;
+            if (iy > 0 && iy < P1 - 1) ddy = parab(s_map[bi - P1], bv, s_map[bi + P1]);
+            else edge = true;
+            if (ddx != ddx) ddx = 0.0;
+            if (ddy != ddy) ddy = 0.0;
+            res.sub_dx = (float)(res.dx + ddx);
+            res.sub_dy = (float)(res.dy + ddy);
+            res.status = s_nan ? SFOC_PT_NAN : (edge ? SFOC_PT_PEAK_ON_EDGE : SFOC_PT_OK);
+        }
+        out[k] = res;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_template_stats(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
+                                  PointStat* stats, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_template_stats<<<(n + 127) / 128, 128, 0, st>>>(ref.integ, ref.H, ref.W, sen.integ, sen.H, sen.W, sen.ipitch,
+                                                     pts, n, m, R, sen.z, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m, int R, const PointStat* stats,
+                              const float* num, int centered, float* out_maps, fastncc_result* out,
+                              cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int P1 = 2 * R + 1;
+    size_t smem = sizeof(double) * (size_t)P1 * P1;
+    cudaError_t e = cudaFuncSetAttribute(k_ncc_argmax, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_ncc_argmax<<<n, kNccThreads, smem, st>>>(ref.integ, ref.H, ref.ipitch, pts, m, R, ref.z, stats, num, centered,
+                                               out_maps, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sfoc

@@ -1,0 +1,677 @@
+// C ABI of the SFOC / Fast-NCC_SFOC library (include/sfoc.h).
+//
+// Host side only: argument checks, filter taps (computed in double from
+// the closed forms of Eq. 2, 3, 5 and the dilated Gaussian of Sec. 2.1),
+// workspace management and kernel dispatch on the context's stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace sfoc;
+
+struct sfoc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t launches = 0;
+    int* d_err = nullptr;  // device error word set by bounded waits
+    // cached cubes and staging for the pair pipeline
+    sfoc_cube* pair_ref = nullptr;
+    sfoc_cube* pair_sen = nullptr;
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    // per-stage timing
+    bool timing = false;
+    struct Ev {
+        int stage, launches;
+        cudaEvent_t a, b;
+    };
+    std::vector<Ev> evs;
+    std::vector<cudaEvent_t> pool;
+    double acc_ms[SFOC_NUM_STAGES] = {0};
+    int64_t acc_n[SFOC_NUM_STAGES] = {0};
+};
+
+struct sfoc_cube {
+    Cube c;
+};
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+sfoc_status fail(sfoc_ctx* ctx, sfoc_status s, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+sfoc_status cuda_fail(sfoc_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, SFOC_ERR_OOM, m);
+    return fail(ctx, SFOC_ERR_CUDA, m);
+}
+
+int radius_of(double sigma, double mult) { return (int)ceil(mult * sigma - 1e-9); }
+
+size_t roundup(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+enum { ST_STEER = 0, ST_SMOOTH = 1, ST_INTEGRAL = 2, ST_STATS = 3, ST_CORR = 4, ST_NCC = 5, ST_OTHER = 6 };
+
+cudaEvent_t pool_event(sfoc_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets the launches of one stage with events (when timing is on) and
+// counts them.
+struct StageScope {
+    sfoc_ctx* c;
+    int stage, launches;
+    cudaEvent_t a = nullptr;
+    StageScope(sfoc_ctx* ctx, int st, int nl) : c(ctx), stage(st), launches(nl) {
+        c->launches += nl;
+        if (!c->timing) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(c->stream, &cs);
+        if (cs != cudaStreamCaptureStatusNone) return;
+        a = pool_event(c);
+        if (a) cudaEventRecord(a, c->stream);
+    }
+    ~StageScope() {
+        if (!a) return;
+        cudaEvent_t b = pool_event(c);
+        if (!b) return;
+        cudaEventRecord(b, c->stream);
+        c->evs.push_back({stage, launches, a, b});
+    }
+};
+
+// Grows the workspace (never inside a stream capture).
+sfoc_status ensure_ws(sfoc_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return SFOC_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &cs);
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "workspace too small inside a stream capture; call sfoc_ctx_reserve first");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    size_t nb = roundup(bytes, 1 << 20);
+    e = cudaMalloc(&ctx->ws, nb);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(workspace)");
+    ctx->ws_bytes = nb;
+    return SFOC_OK;
+}
+
+sfoc_status check_params(sfoc_ctx* ctx, const sfoc_params& p) {
+    if (p.n_scales < 1 || p.n_scales > kMaxScales) return fail(ctx, SFOC_ERR_UNSUPPORTED, "n_scales must be 1..4");
+    for (int s = 0; s < p.n_scales; ++s) {
+        if (!(p.scales[s] > 0.0)) return fail(ctx, SFOC_ERR_INVALID_ARG, "scales must be > 0");
+        if (radius_of(p.scales[s], p.radius_mult) > kMaxDerivRadius)
+            return fail(ctx, SFOC_ERR_UNSUPPORTED, "first-order kernel radius > 9");
+    }
+    if (!(p.radius_mult > 0.0)) return fail(ctx, SFOC_ERR_INVALID_ARG, "radius_mult must be > 0");
+    if (!p.first_order_only) {
+        if (!(p.sigma2 > 0.0)) return fail(ctx, SFOC_ERR_INVALID_ARG, "sigma2 must be > 0");
+        if (radius_of(p.sigma2, p.radius_mult) > kMaxDerivRadius)
+            return fail(ctx, SFOC_ERR_UNSUPPORTED, "second-order kernel radius > 9");
+    }
+    if (p.n_orient < 1 || p.n_orient > kMaxOrient) return fail(ctx, SFOC_ERR_UNSUPPORTED, "n_orient must be 1..8");
+    if (p.n_dil < 1 || p.n_dil > kMaxDil) return fail(ctx, SFOC_ERR_UNSUPPORTED, "n_dil must be 1..3");
+    for (int r = 0; r < p.n_dil; ++r)
+        if (p.dil[r] < 1 || p.dil[r] > 3) return fail(ctx, SFOC_ERR_UNSUPPORTED, "dilation rates must be 1..3");
+    double sd[2] = {p.sigma_d1, p.sigma_d2};
+    for (int g = 0; g < 2; ++g) {
+        if (!(sd[g] > 0.0)) return fail(ctx, SFOC_ERR_INVALID_ARG, "smoothing STDs must be > 0");
+        if (radius_of(sd[g], p.radius_mult) > kMaxSmoothRadius)
+            return fail(ctx, SFOC_ERR_UNSUPPORTED, "smoothing radius > 6");
+    }
+    if (!(p.eps >= 0.0)) return fail(ctx, SFOC_ERR_INVALID_ARG, "eps must be >= 0");
+    if (p.cube_dtype != SFOC_DTYPE_F32 && p.cube_dtype != SFOC_DTYPE_BF16)
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "cube_dtype must be F32 or BF16");
+    if (p.cube_dtype == SFOC_DTYPE_BF16 && (p.n_orient != 6 || p.first_order_only))
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "BF16 cubes need 12 channels (n_orient 6, both groups)");
+    return SFOC_OK;
+}
+
+SteerTaps make_steer(const sfoc_params& p) {
+    SteerTaps t;
+    memset(&t, 0, sizeof(t));
+    t.ns = p.n_scales;
+    int hal = 0;
+    for (int s = 0; s < p.n_scales; ++s) {
+        double sg = p.scales[s], s2 = sg * sg, s4 = s2 * s2;
+        int K = radius_of(sg, p.radius_mult);
+        t.K1[s] = K;
+        hal = std::max(hal, K);
+        for (int q = 0; q <= K; ++q) {
+            double e = exp(-(double)q * q / (2.0 * s2));
+            t.a1[s][q] = (float)(-(double)q / (2.0 * kPi * s4) * e);
+            t.g1[s][q] = (float)e;
+        }
+    }
+    t.second = p.first_order_only ? 0 : 1;
+    if (t.second) {
+        double sg = p.sigma2, s2 = sg * sg, s4 = s2 * s2, s6 = s4 * s2;
+        int K = radius_of(sg, p.radius_mult);
+        t.K2 = K;
+        hal = std::max(hal, K);
+        double a2[kMaxDerivRadius + 1];
+        double mean = 0.0;
+        for (int q = 0; q <= K; ++q) {
+            double e = exp(-(double)q * q / (2.0 * s2));
+            a2[q] = -(1.0 / (2.0 * kPi * s4)) * (1.0 - q * q / s2) * e;
+            mean += (q == 0 ? 1.0 : 2.0) * a2[q];
+            t.g2[q] = (float)e;
+            t.c2x[q] = (float)(q * e / (2.0 * kPi * s6));
+            t.c2y[q] = (float)(q * e);
+        }
+        mean /= (2 * K + 1);
+        for (int q = 0; q <= K; ++q) t.a2[q] = (float)(a2[q] - mean);
+    }
+    t.no = p.n_orient;
+    for (int k = 0; k < p.n_orient; ++k) {
+        t.ct[k] = (float)cos(k * kPi / p.n_orient);
+        t.st[k] = (float)sin(k * kPi / p.n_orient);
+    }
+    t.rectify = p.rectify ? 1 : 0;
+    t.halo = hal;
+    return t;
+}
+
+SmoothTaps make_smooth(const sfoc_params& p) {
+    SmoothTaps t;
+    memset(&t, 0, sizeof(t));
+    t.n_dil = p.n_dil;
+    int maxrate = 0;
+    for (int r = 0; r < p.n_dil; ++r) {
+        t.dil[r] = p.dil[r];
+        maxrate = std::max(maxrate, p.dil[r]);
+    }
+    double sd[2] = {p.sigma_d1, p.sigma_d2};
+    for (int g = 0; g < 2; ++g) {
+        int K = radius_of(sd[g], p.radius_mult);
+        t.Kd[g] = K;
+        double w[kMaxSmoothRadius + 1], sum = 0.0;
+        for (int q = 0; q <= K; ++q) {
+            w[q] = exp(-(double)q * q / (2.0 * sd[g] * sd[g]));
+            sum += (q == 0 ? 1.0 : 2.0) * w[q];
+        }
+        for (int q = 0; q <= K; ++q) t.g[g][q] = (float)(w[q] / sum);
+        t.halo[g] = maxrate * K;
+    }
+    t.no = p.n_orient;
+    t.z = p.first_order_only ? p.n_orient : 2 * p.n_orient;
+    if (p.first_order_only) t.halo[1] = 0;
+    t.eps = (float)p.eps;
+    return t;
+}
+
+void free_cube_mem(Cube& c) {
+    cudaFree(c.f32);
+    cudaFree(c.rm);
+    cudaFree(c.cm);
+    cudaFree(c.s1);
+    cudaFree(c.s2);
+    cudaFree(c.integ);
+    c.f32 = nullptr;
+    c.rm = c.cm = nullptr;
+    c.s1 = c.s2 = nullptr;
+    c.integ = nullptr;
+}
+
+sfoc_status alloc_cube(sfoc_ctx* ctx, Cube& c, int H, int W, int z, int dtype) {
+    c.H = H;
+    c.W = W;
+    c.z = z;
+    c.dtype = dtype;
+    c.pitch = roundup((size_t)W, 32);
+    c.ipitch = (size_t)W + 1;
+    c.device = ctx->device;
+    cudaError_t e = cudaSuccess;
+    size_t plane = c.pitch * (size_t)H;
+    if (dtype == SFOC_DTYPE_F32) {
+        e = cudaMalloc(&c.f32, sizeof(float) * plane * z);
+    } else {
+        e = cudaMalloc(&c.rm, sizeof(__nv_bfloat16) * 16 * (size_t)H * W);
+        if (e == cudaSuccess) e = cudaMalloc(&c.cm, sizeof(__nv_bfloat16) * 16 * (size_t)H * W);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c.s1, sizeof(float) * plane);
+    if (e == cudaSuccess) e = cudaMalloc(&c.s2, sizeof(float) * plane);
+    if (e == cudaSuccess) e = cudaMalloc(&c.integ, sizeof(double) * 2 * (size_t)(H + 1) * c.ipitch);
+    if (e != cudaSuccess) {
+        free_cube_mem(c);
+        return cuda_fail(ctx, e, "cudaMalloc(cube)");
+    }
+    return SFOC_OK;
+}
+
+sfoc_status build_integral(sfoc_ctx* ctx, Cube& c) {
+    if (c.integ_valid) return SFOC_OK;
+    sfoc_status s = ensure_ws(ctx, integral_scratch_bytes(c.H, c.W));
+    if (s != SFOC_OK) return s;
+    int nl = 0;
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_INTEGRAL, 4);
+        e = launch_integral(c, ctx->ws, ctx->stream, &nl);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "integral launch");
+    c.integ_valid = true;
+    return SFOC_OK;
+}
+
+size_t align256(size_t v) { return roundup(v, 256); }
+
+}  // namespace
+
+extern "C" {
+
+sfoc_status sfoc_ctx_create(sfoc_ctx** out, int device, void* stream) {
+    if (!out) return SFOC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SFOC_ERR_INVALID_ARG;
+    sfoc_ctx* c = new (std::nothrow) sfoc_ctx();
+    if (!c) return SFOC_ERR_OOM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    DeviceGuard g(device);
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) {
+        delete c;
+        return SFOC_ERR_OOM;
+    }
+    cudaMemset(c->d_err, 0, sizeof(int));
+    *out = c;
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->pair_ref) sfoc_cube_free(ctx->pair_ref);
+    if (ctx->pair_sen) sfoc_cube_free(ctx->pair_sen);
+    cudaFree(ctx->ws);
+    cudaFree(ctx->stage);
+    cudaFree(ctx->d_err);
+    for (auto& e : ctx->evs) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    delete ctx;
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_ctx_set_stream(sfoc_ctx* ctx, void* stream) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_ctx_sync(sfoc_ctx* ctx) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    int h = 0;
+    e = cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(error word)");
+    if (h) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return fail(ctx, SFOC_ERR_TIMEOUT, "a bounded device wait expired (error word " + std::to_string(h) + ")");
+    }
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_ctx_reserve(sfoc_ctx* ctx, size_t bytes) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return ensure_ws(ctx, bytes);
+}
+
+size_t sfoc_match_workspace_bytes(int n, int search_radius) {
+    if (n < 0 || search_radius < 0) return 0;
+    size_t P = (size_t)(2 * search_radius + 1) * (2 * search_radius + 1);
+    return align256(sizeof(PointStat) * (size_t)n) + align256(sizeof(float) * P * (size_t)n);
+}
+
+const char* sfoc_last_error_string(const sfoc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t sfoc_ctx_launch_count(const sfoc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+sfoc_status sfoc_ctx_enable_timing(sfoc_ctx* ctx, int enable) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    ctx->timing = enable != 0;
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_ctx_stage_times(sfoc_ctx* ctx, double* ms_out, int64_t* launches_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    for (auto& ev : ctx->evs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) ctx->acc_ms[ev.stage] += ms;
+        ctx->acc_n[ev.stage] += ev.launches;
+        ctx->pool.push_back(ev.a);
+        ctx->pool.push_back(ev.b);
+    }
+    ctx->evs.clear();
+    for (int i = 0; i < SFOC_NUM_STAGES; ++i) {
+        if (ms_out) ms_out[i] = ctx->acc_ms[i];
+        if (launches_out) launches_out[i] = ctx->acc_n[i];
+    }
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_ctx_reset_timing(sfoc_ctx* ctx) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    double tmp[SFOC_NUM_STAGES];
+    sfoc_status s = sfoc_ctx_stage_times(ctx, tmp, nullptr);
+    for (int i = 0; i < SFOC_NUM_STAGES; ++i) {
+        ctx->acc_ms[i] = 0.0;
+        ctx->acc_n[i] = 0;
+    }
+    return s;
+}
+
+sfoc_status sfoc_params_default(sfoc_params* p) {
+    if (!p) return SFOC_ERR_INVALID_ARG;
+    memset(p, 0, sizeof(*p));
+    p->n_scales = 3;
+    p->scales[0] = 0.6;
+    p->scales[1] = 0.8;
+    p->scales[2] = 1.0;
+    p->sigma2 = 1.5;
+    p->n_orient = 6;
+    p->n_dil = 3;
+    p->dil[0] = 1;
+    p->dil[1] = 2;
+    p->dil[2] = 3;
+    p->sigma_d1 = 1.0;
+    p->sigma_d2 = 1.5;
+    p->eps = 1e-3;
+    p->rectify = 1;
+    p->radius_mult = 3.0;
+    p->first_order_only = 0;
+    p->cube_dtype = SFOC_DTYPE_F32;
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_build(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems, const double* scales,
+                       int n_scales, int n_orient, const sfoc_params* pin, sfoc_cube** out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!d_image || !out) return fail(ctx, SFOC_ERR_INVALID_ARG, "null image or output pointer");
+    if (H <= 0 || W <= 0) return fail(ctx, SFOC_ERR_SHAPE, "image must be at least 1 x 1");
+    if (pitch_elems < (size_t)W) return fail(ctx, SFOC_ERR_SHAPE, "pitch_elems < W");
+    if ((size_t)H * (size_t)W > ((size_t)1 << 31)) return fail(ctx, SFOC_ERR_UNSUPPORTED, "image larger than 2^31 pixels");
+    sfoc_params p;
+    if (pin) p = *pin;
+    else sfoc_params_default(&p);
+    if (scales) {
+        if (n_scales < 1 || n_scales > kMaxScales) return fail(ctx, SFOC_ERR_UNSUPPORTED, "n_scales must be 1..4");
+        p.n_scales = n_scales;
+        for (int s = 0; s < n_scales; ++s) p.scales[s] = scales[s];
+    }
+    if (n_orient > 0) p.n_orient = n_orient;
+    sfoc_status s = check_params(ctx, p);
+    if (s != SFOC_OK) return s;
+    const int z = p.first_order_only ? p.n_orient : 2 * p.n_orient;
+    DeviceGuard g(ctx->device);
+
+    sfoc_cube* cube = *out;
+    bool reuse = cube && cube->c.H == H && cube->c.W == W && cube->c.z == z && cube->c.dtype == p.cube_dtype &&
+                 cube->c.device == ctx->device;
+    if (!reuse) {
+        cube = new (std::nothrow) sfoc_cube();
+        if (!cube) return fail(ctx, SFOC_ERR_OOM, "host allocation");
+        s = alloc_cube(ctx, cube->c, H, W, z, p.cube_dtype);
+        if (s != SFOC_OK) {
+            delete cube;
+            return s;
+        }
+    }
+    const size_t fpitch = roundup((size_t)W, 32);
+    s = ensure_ws(ctx, sizeof(float) * fpitch * (size_t)H * z);
+    if (s != SFOC_OK) {
+        if (!reuse) sfoc_cube_free(cube);
+        return s;
+    }
+    float* F = static_cast<float*>(ctx->ws);
+    SteerTaps st = make_steer(p);
+    SmoothTaps sm = make_smooth(p);
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_STEER, 1);
+        e = launch_sfoc_steer(d_image, H, W, pitch_elems, F, fpitch, st, z, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        StageScope sc(ctx, ST_SMOOTH, 1);
+        e = launch_sfoc_smooth(F, fpitch, H, W, sm, cube->c, ctx->stream);
+    }
+    if (e != cudaSuccess) {
+        if (!reuse) sfoc_cube_free(cube);
+        return cuda_fail(ctx, e, "sfoc kernels");
+    }
+    cube->c.integ_valid = false;
+    *out = cube;
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_cube_info(const sfoc_cube* cube, int* z, int* H, int* W, int* dtype) {
+    if (!cube) return SFOC_ERR_INVALID_ARG;
+    if (z) *z = cube->c.z;
+    if (H) *H = cube->c.H;
+    if (W) *W = cube->c.W;
+    if (dtype) *dtype = cube->c.dtype;
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_cube_export(sfoc_ctx* ctx, const sfoc_cube* cube, float* d_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!cube || !d_out) return fail(ctx, SFOC_ERR_INVALID_ARG, "null cube or output");
+    DeviceGuard g(ctx->device);
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_OTHER, 1);
+        e = launch_cube_export(cube->c, d_out, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "export launch");
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_cube_export_integral(sfoc_ctx* ctx, sfoc_cube* cube, double* d_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!cube || !d_out) return fail(ctx, SFOC_ERR_INVALID_ARG, "null cube or output");
+    DeviceGuard g(ctx->device);
+    sfoc_status s = build_integral(ctx, cube->c);
+    if (s != SFOC_OK) return s;
+    const Cube& c = cube->c;
+    cudaError_t e = cudaMemcpy2DAsync(d_out, sizeof(double) * (c.W + 1), c.integ, sizeof(double) * c.ipitch,
+                                      sizeof(double) * (c.W + 1), 2 * (size_t)(c.H + 1), cudaMemcpyDeviceToDevice,
+                                      ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy integral");
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_cube_free(sfoc_cube* cube) {
+    if (!cube) return SFOC_ERR_INVALID_ARG;
+    DeviceGuard g(cube->c.device);
+    free_cube_mem(cube->c);
+    delete cube;
+    return SFOC_OK;
+}
+
+sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const int32_t* d_points, int n,
+                          int template_size, int search_radius, const fastncc_opts* opts, fastncc_result* d_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!ref || !sen) return fail(ctx, SFOC_ERR_INVALID_ARG, "null cube");
+    if (n < 0) return fail(ctx, SFOC_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!d_points || !d_out)) return fail(ctx, SFOC_ERR_INVALID_ARG, "null points or output");
+    if (template_size < 1 || search_radius < 0) return fail(ctx, SFOC_ERR_INVALID_ARG, "m >= 1 and R >= 0 required");
+    if (template_size > kMaxTemplate || search_radius > kMaxRadius)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "m <= 128 and R <= 63");
+    if (ref->c.z != sen->c.z) return fail(ctx, SFOC_ERR_SHAPE, "cubes have different channel counts");
+    if (ref->c.dtype != sen->c.dtype) return fail(ctx, SFOC_ERR_SHAPE, "cubes have different dtypes");
+    int path = opts ? opts->corr_path : SFOC_CORR_AUTO;
+    if (path == SFOC_CORR_AUTO) path = ref->c.dtype == SFOC_DTYPE_BF16 ? SFOC_CORR_IGEMM_TC : SFOC_CORR_DIRECT_F32;
+    if (path == SFOC_CORR_DIRECT_F32 && ref->c.dtype != SFOC_DTYPE_F32)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "DIRECT_F32 needs F32 cubes");
+    if (path == SFOC_CORR_IGEMM_TC && ref->c.dtype != SFOC_DTYPE_BF16)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "IGEMM_TC needs BF16 cubes");
+    if (path != SFOC_CORR_DIRECT_F32 && path != SFOC_CORR_IGEMM_TC)
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown corr_path");
+    DeviceGuard g(ctx->device);
+    if (n == 0) return SFOC_OK;
+
+    sfoc_status s = build_integral(ctx, ref->c);
+    if (s == SFOC_OK) s = build_integral(ctx, sen->c);
+    if (s != SFOC_OK) return s;
+    s = ensure_ws(ctx, sfoc_match_workspace_bytes(n, search_radius));
+    if (s != SFOC_OK) return s;
+    char* w = static_cast<char*>(ctx->ws);
+    PointStat* stats = reinterpret_cast<PointStat*>(w);
+    float* maps = reinterpret_cast<float*>(w + align256(sizeof(PointStat) * (size_t)n));
+    const int m = template_size, R = search_radius;
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_STATS, 1);
+        e = launch_template_stats(ref->c, sen->c, d_points, n, m, R, stats, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "template stats launch");
+    {
+        StageScope sc(ctx, ST_CORR, 1);
+        if (path == SFOC_CORR_DIRECT_F32)
+            e = launch_corr_f32(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->stream);
+        else
+            e = launch_corr_tc(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->d_err, ctx->stream);
+    }
+    if (e == cudaErrorInvalidValue || e == cudaErrorNotSupported)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "correlation kernel does not support this m / R");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "correlation launch");
+    {
+        StageScope sc(ctx, ST_NCC, 1);
+        e = launch_ncc_argmax(ref->c, d_points, n, m, R, stats, maps, path == SFOC_CORR_DIRECT_F32 ? 1 : 0,
+                              opts ? opts->d_maps : nullptr, d_out, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ncc launch");
+    return SFOC_OK;
+}
+
+sfoc_status fastncc_register_pair(sfoc_ctx* ctx, const float* d_ref, int Hr, int Wr, const float* d_sen, int Hs,
+                                  int Ws, const int32_t* d_points, int n, int template_size, int search_radius,
+                                  const sfoc_params* p, const fastncc_opts* opts, fastncc_result* d_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    sfoc_status s = sfoc_build(ctx, d_ref, Hr, Wr, (size_t)Wr, nullptr, 0, 0, p, &ctx->pair_ref);
+    if (s != SFOC_OK) return s;
+    s = sfoc_build(ctx, d_sen, Hs, Ws, (size_t)Ws, nullptr, 0, 0, p, &ctx->pair_sen);
+    if (s != SFOC_OK) return s;
+    return fastncc_match(ctx, ctx->pair_ref, ctx->pair_sen, d_points, n, template_size, search_radius, opts, d_out);
+}
+
+sfoc_status fastncc_register_pair_host(sfoc_ctx* ctx, const float* h_ref, int Hr, int Wr, const float* h_sen,
+                                       int Hs, int Ws, const int32_t* h_points, int n, int template_size,
+                                       int search_radius, const sfoc_params* p, const fastncc_opts* opts,
+                                       fastncc_result* h_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!h_ref || !h_sen || (n > 0 && (!h_points || !h_out)))
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "null host buffer");
+    if (Hr <= 0 || Wr <= 0 || Hs <= 0 || Ws <= 0 || n < 0) return fail(ctx, SFOC_ERR_SHAPE, "bad sizes");
+    DeviceGuard g(ctx->device);
+    size_t b_ref = align256(sizeof(float) * (size_t)Hr * Wr), b_sen = align256(sizeof(float) * (size_t)Hs * Ws);
+    size_t b_pts = align256(sizeof(int32_t) * 2 * (size_t)n), b_out = align256(sizeof(fastncc_result) * (size_t)n);
+    size_t need = b_ref + b_sen + b_pts + b_out;
+    if (need > ctx->stage_bytes) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+        cudaFree(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        e = cudaMalloc(&ctx->stage, need);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(staging)");
+        ctx->stage_bytes = need;
+    }
+    char* b = static_cast<char*>(ctx->stage);
+    float* d_ref = reinterpret_cast<float*>(b);
+    float* d_sen = reinterpret_cast<float*>(b + b_ref);
+    int32_t* d_pts = reinterpret_cast<int32_t*>(b + b_ref + b_sen);
+    fastncc_result* d_out = reinterpret_cast<fastncc_result*>(b + b_ref + b_sen + b_pts);
+    cudaError_t e = cudaMemcpyAsync(d_ref, h_ref, sizeof(float) * (size_t)Hr * Wr, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_sen, h_sen, sizeof(float) * (size_t)Hs * Ws, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(d_pts, h_points, sizeof(int32_t) * 2 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
+    sfoc_status s = fastncc_register_pair(ctx, d_ref, Hr, Wr, d_sen, Hs, Ws, d_pts, n, template_size, search_radius, p,
+                                          opts, d_out);
+    if (s != SFOC_OK) return s;
+    if (n > 0) {
+        e = cudaMemcpyAsync(h_out, d_out, sizeof(fastncc_result) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
+    }
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_build_batch(sfoc_ctx* ctx, int n_img, const float* const* d_images, const int* H, const int* W,
+                             const size_t* pitch_elems, const sfoc_params* p, sfoc_cube** outs) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (n_img < 0 || (n_img > 0 && (!d_images || !H || !W || !outs)))
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "bad batch arguments");
+    for (int i = 0; i < n_img; ++i) {
+        sfoc_status s = sfoc_build(ctx, d_images[i], H[i], W[i], pitch_elems ? pitch_elems[i] : (size_t)W[i], nullptr, 0,
+                                   0, p, &outs[i]);
+        if (s != SFOC_OK) return s;
+    }
+    return SFOC_OK;
+}
+
+sfoc_status fastncc_match_batch(sfoc_ctx* ctx, int n_pairs, sfoc_cube* const* refs, sfoc_cube* const* sens,
+                                const int32_t* const* d_points, const int* n_points, const int* template_size,
+                                const int* search_radius, const fastncc_opts* opts, fastncc_result* const* d_outs) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (n_pairs < 0 || (n_pairs > 0 && (!refs || !sens || !d_points || !n_points || !template_size || !search_radius ||
+                                        !d_outs)))
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "bad batch arguments");
+    for (int i = 0; i < n_pairs; ++i) {
+        fastncc_opts o = {opts ? opts->corr_path : SFOC_CORR_AUTO, nullptr};
+        sfoc_status s = fastncc_match(ctx, refs[i], sens[i], d_points[i], n_points[i], template_size[i],
+                                      search_radius[i], &o, d_outs[i]);
+        if (s != SFOC_OK) return s;
+    }
+    return SFOC_OK;
+}
+
+}  // extern "C"

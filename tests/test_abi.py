@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point include/sfoc.h declares; struct layouts agree between C and the
+binding; host-only calls behave.  No compute call runs here."""
+import ctypes as C
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        names |= set(re.findall(r"^SFOC_API\s+[\w\s\*]+?\b(\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def b():
+    import paper_2202_13347_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+def test_every_declared_symbol_is_exported(b):
+    names = declared()
+    assert len(names) >= 19
+    L = C.CDLL(b.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding knows every one of them
+    assert names <= set(b._SIGS), names - set(b._SIGS)
+
+
+def test_struct_layouts_match_c(b, tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "sfoc.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sfoc_params), sizeof(fastncc_result),'
+        ' sizeof(fastncc_opts), offsetof(sfoc_params, cube_dtype), offsetof(fastncc_result, status),'
+        ' offsetof(fastncc_opts, d_maps)); return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [C.sizeof(b.Params), C.sizeof(b.Result), C.sizeof(b.Opts), b.Params.cube_dtype.offset,
+                    b.Result.status.offset, b.Opts.d_maps.offset]
+
+
+def test_params_default_are_the_paper_values(b):
+    p = b.Params()
+    assert b.lib().sfoc_params_default(C.byref(p)) == 0
+    assert [p.scales[i] for i in range(p.n_scales)] == [0.6, 0.8, 1.0]      # Table 2
+    assert p.sigma2 == 1.5 and p.n_orient == 6                                # Table 2, Sec. 2.1
+    assert [p.dil[i] for i in range(p.n_dil)] == [1, 2, 3]                    # Sec. 2.1
+    assert p.rectify == 1 and p.radius_mult == 3.0 and p.cube_dtype == 0
+    assert b.lib().sfoc_params_default(None) == -1
+
+
+def test_host_only_calls(b):
+    L = b.lib()
+    assert L.sfoc_match_workspace_bytes(-1, 3) == 0
+    assert L.sfoc_match_workspace_bytes(10, 2) > 10 * 25 * 4
+    assert L.sfoc_ctx_destroy(None) == -1
+    assert L.sfoc_cube_free(None) == -1
+    assert L.sfoc_last_error_string(None) == b"null context"
+    assert L.sfoc_build(None, None, 1, 1, 1, None, 0, 0, None, None) == -1
+    assert L.fastncc_match(None, None, None, None, 0, 1, 1, None, None) == -1
+
+
+def test_no_oracle_in_product_path():
+    """The product package never imports the oracle and the library holds no
+    CPU fallback: the sources do not mention it."""
+    pkg = os.path.join(ROOT, "paper_2202_13347_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "liboracle" not in txt, f

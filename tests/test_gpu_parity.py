@@ -1,0 +1,169 @@
+"""GPU path against the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several kernel tiles plus ragged tails; the full-size workload
+(2048^2, 1000 points, m=81, R=20) runs in the same launch configuration as
+the benchmark and is checked on a seeded sample of points the oracle
+computes one by one.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from workloads import config1, config2, tiny_pair  # noqa: E402
+
+from parity import compare  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def b():
+    import paper_2202_13347_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+@pytest.fixture(scope="module")
+def ctx(b):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return b.Context(0)
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# ---------------------------------------------------------------------------
+# SFOC cube (Sec. 2.1)
+# ---------------------------------------------------------------------------
+
+CUBE_ATOL = 2e-5   # FP32 filtering of [0,1] images, values normalised to <= 1
+
+
+@pytest.mark.parametrize("H,W,seed", [(77, 93, 1), (33, 130, 2), (512, 512, 3)])
+def test_cube_f32_matches_oracle(b, ctx, orc, H, W, seed):
+    rng = np.random.default_rng(seed)
+    from workloads import optical_like
+    img = optical_like(rng, H, W)
+    cube = ctx.sfoc_build(dev(img))
+    got = cube.export().cpu().numpy().astype(np.float64)
+    want = orc.sfoc_roi(img).data
+    err = np.abs(got - want)
+    assert err.max() <= CUBE_ATOL, "max err %g at %s" % (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_cube_variants_match_oracle(b, ctx, orc):
+    rng = np.random.default_rng(4)
+    img = rng.random((45, 70)).astype(np.float32)
+    for kw in (dict(first_order_only=True), dict(rectify=False), dict(scales=(1.0, 2.0, 3.0)),
+               dict(n_orient=4, dil=(1, 2)), dict(eps=0.05)):
+        okw = dict(kw)
+        p = b.params(**kw)
+        got = ctx.sfoc_build(dev(img), p=p).export().cpu().numpy()
+        want = orc.sfoc_roi(img, orc.params(**okw)).data
+        assert np.abs(got - want).max() <= CUBE_ATOL, kw
+
+
+def test_integral_planes(b, ctx, orc):
+    """Eq. 14: exclusive prefix of the channel sums, FP64."""
+    rng = np.random.default_rng(5)
+    from workloads import optical_like
+    for H, W in ((77, 93), (200, 131)):
+        img = optical_like(rng, H, W)
+        cube = ctx.sfoc_build(dev(img))
+        P = cube.export_integral().cpu().numpy()
+        c = cube.export().cpu().numpy().astype(np.float64)
+        for k, plane in enumerate((c.sum(0), (c * c).sum(0))):
+            want = orc.integral(plane)
+            np.testing.assert_allclose(P[k], want, rtol=2e-6, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# matching (Sec. 2.2, Eq. 8-16)
+# ---------------------------------------------------------------------------
+
+def gpu_match(ctx, b, pair, p=None, corr=0, want_maps=False):
+    rc = ctx.sfoc_build(dev(pair.ref), p=p)
+    sc = ctx.sfoc_build(dev(pair.sen), p=p)
+    return ctx.fastncc_match(rc, sc, dev(pair.points), pair.m, pair.R, corr_path=corr, want_maps=want_maps)
+
+
+def test_match_config1_f32(b, ctx, orc):
+    pair = config1()
+    o = orc.match_pair(pair.ref, pair.sen, pair.points, pair.m, pair.R, want_maps=True, roi=False)
+    g = gpu_match(ctx, b, pair, want_maps=True)
+    st = compare(g, o, pair.R, oracle_maps=o["maps"])
+    # the NCC maps themselves agree everywhere
+    gm = g["maps"].cpu().numpy()
+    assert np.abs(gm - o["maps"]).max() <= 1e-4
+    assert st["valid"] == 100
+
+
+@pytest.mark.parametrize("H,W,m,R,npts,seed", [
+    (70, 83, 9, 4, 12, 11),     # ragged, small
+    (96, 61, 10, 3, 9, 12),     # even template
+    (64, 64, 1, 2, 16, 13),     # m = 1
+    (60, 75, 15, 0, 9, 14),     # R = 0
+    (150, 140, 31, 12, 20, 15),
+])
+def test_match_small_cases(b, ctx, orc, H, W, m, R, npts, seed):
+    pair = tiny_pair(seed, H, W, m, R, npts, shift=(2, -1))
+    o = orc.match_pair(pair.ref, pair.sen, pair.points, m, R, want_maps=True, roi=False)
+    g = gpu_match(ctx, b, pair, want_maps=True)
+    compare(g, o, R, oracle_maps=o["maps"])
+
+
+def test_status_cases(b, ctx, orc):
+    """Out-of-bounds points, a flat template and a NaN pixel."""
+    pair = tiny_pair(21, 90, 90, 11, 5, 4)
+    sen = pair.sen.copy()
+    sen[10:40, 50:80] = 0.5            # flat -> zero cube -> FLAT_TEMPLATE
+    sen[70, 20] = np.nan               # NaN propagates to nearby cube values
+    pts = np.array([[3, 45], [45, 87], [65, 25], [20, 70], [45, 45], [22, 68]], np.int32)
+    pair.sen = sen
+    pair.points = pts
+    o = orc.match_pair(pair.ref, sen, pts, 11, 5, want_maps=True, roi=False)
+    assert set(o["status"].tolist()) >= {1, 2, 4}
+    g = gpu_match(ctx, b, pair, want_maps=True)
+    compare(g, o, 5, oracle_maps=o["maps"])
+
+
+def test_config2_full_size_sampled(b, ctx, orc):
+    """2048^2, 1000 points, m=81, R=20: the benchmark's configuration; the
+    oracle checks a seeded sample of 8 points."""
+    pair = config2()
+    g = gpu_match(ctx, b, pair)
+    rng = np.random.default_rng(2024)
+    idx = np.sort(rng.choice(len(pair.points), 8, replace=False))
+    o = orc.match_pair(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R, want_maps=True)
+    gs = {k: v[torch.from_numpy(idx).cuda()] for k, v in g.items()}
+    compare(gs, o, pair.R, oracle_maps=o["maps"])
+    assert int((g["status"] == 0).sum()) >= 900
+
+
+def test_host_entry_matches_device(b, ctx):
+    pair = config1()
+    p = b.params()
+    raw_d = ctx.register_pair(dev(pair.ref), dev(pair.sen), dev(pair.points), pair.m, pair.R, p=p)
+    raw_h = ctx.register_pair_host(torch.from_numpy(pair.ref).pin_memory(), torch.from_numpy(pair.sen).pin_memory(),
+                                   torch.from_numpy(pair.points).pin_memory(), pair.m, pair.R, p=p)
+    assert torch.equal(raw_d.cpu(), raw_h)
+
+
+def test_invalid_arguments_return_errors(b, ctx):
+    pair = tiny_pair(31, 60, 60, 9, 3, 4)
+    rc = ctx.sfoc_build(dev(pair.ref))
+    sc = ctx.sfoc_build(dev(pair.sen))
+    with pytest.raises(b.SfocError) as e:
+        ctx.fastncc_match(rc, sc, dev(pair.points), 0, 3)
+    assert e.value.code == -1
+    with pytest.raises(b.SfocError) as e:
+        ctx.fastncc_match(rc, sc, dev(pair.points), 9, 3, corr_path=b.CORR_IGEMM_TC)
+    assert e.value.code == -6
+    with pytest.raises(b.SfocError):
+        ctx.sfoc_build(dev(pair.ref), p=b.params(n_orient=9))
