@@ -314,7 +314,7 @@ def main():
                     "kernel": "k_corr_f32 (FP32 FMA)",
                     "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                     "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
-        return dict(value=r["matched_all"] / (r["ms_max"] * 1e-3), ms_per_step=r["ms_max"] / args.steps,
+        return dict(value=r["matched_all"] * args.steps / (r["ms_max"] * 1e-3), ms_per_step=r["ms_max"] / args.steps,
                     sfoc_mpix_s=2 * pair.ref.size / (sfoc_ms * 1e-3) / 1e6 if sfoc_ms > 0 else None,
                     stage_ms_per_step={k: round(v, 4) for k, v in per_step.items()}, roofline=roof,
                     matched_per_step=r["matched"], gpu_launches=r["launches"], clocks=r["clocks"])

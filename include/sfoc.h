@@ -49,7 +49,7 @@ typedef enum {
 enum {
     SFOC_PT_OK = 0,
     SFOC_PT_OUT_OF_BOUNDS = 1, /* template or a candidate window leaves its image; nothing computed */
-    SFOC_PT_FLAT_TEMPLATE = 2, /* template variance <= 1e-12 * m*m*z; offsets 0, ncc 0 */
+    SFOC_PT_FLAT_TEMPLATE = 2, /* template variance <= 1e-6 * m*m*z; offsets 0, ncc 0 */
     SFOC_PT_PEAK_ON_EDGE = 3,  /* best |dx| or |dy| equals R; no sub-pixel on that axis */
     SFOC_PT_NAN = 4            /* NaN in the template or in some candidate's score */
 };

@@ -25,7 +25,8 @@
  *   (second group), radius ceil(3 sigma_d), rates {1,2,3}, results summed;
  *   per-pixel L2 normalisation of each group, v / (||v|| + eps);
  *   clamp-to-edge borders for every convolution;
- *   NCC := 0 where the window variance is <= 1e-12 * mnz;
+ *   a window (template) is flat when its variance is <= 1e-6 * mnz: NCC := 0
+ *   (FLAT_TEMPLATE); FP32 noise on a constant image stays near 1e-10 per value;
  *   argmax order (NCC desc, dy asc, dx asc); 3-point parabola per axis.
  */
 #include <math.h>
@@ -500,7 +501,7 @@ int oracle_match(const oracle_cube* ref, const oracle_cube* sen, const int32_t* 
                     double d = cube_at(sen, c, ty0 + i, tx0 + j) - tbar;
                     vT += d * d;
                 }
-        if (vT <= 1e-12 * N) { o->status = OR_FLAT_TEMPLATE; continue; }
+        if (vT <= 1e-6 * N) { o->status = OR_FLAT_TEMPLATE; continue; }
         double* lmap = map ? map : (double*)malloc(sizeof(double) * P1 * P1);
         for (int dy = -R; dy <= R; ++dy)
             for (int dx = -R; dx <= R; ++dx) {
@@ -520,7 +521,7 @@ int oracle_match(const oracle_cube* ref, const oracle_cube* sen, const int32_t* 
                         }
                 double v;
                 if (vS != vS || num != num) v = NAN;
-                else if (vS <= 1e-12 * N) v = 0.0;
+                else if (vS <= 1e-6 * N) v = 0.0;
                 else v = num / sqrt(vS * vT);
                 lmap[(dy + R) * P1 + (dx + R)] = v;
             }
@@ -605,7 +606,7 @@ int oracle_ncc_eq9_dft(const double* S, const double* T, int z, int m, int R, in
             double RSS = oracle_rect_sum(P2s, M, dy, dx, dy + m, dx + m);
             double vS = RSS - RS * RS / N;
             double num = RST - RS * RT / N;
-            map[dy * P1 + dx] = (vS <= 1e-12 * N) ? 0.0 : num / (sqrt(vS) * sqrt(vT));
+            map[dy * P1 + dx] = (vS <= 1e-6 * N) ? 0.0 : num / (sqrt(vS) * sqrt(vT));
         }
     free(accr); free(acci); free(sr); free(si); free(tr); free(ti);
     free(g1); free(g2); free(P1s); free(P2s);

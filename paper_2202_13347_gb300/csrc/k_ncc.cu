@@ -45,7 +45,7 @@ __global__ void k_template_stats(const double* __restrict__ Pr, int Hr, int Wr, 
         s.tmean = (float)(s.RT / N);
         double vT = s.RTT - s.RT * s.RT / N;
         if (s.RT != s.RT || s.RTT != s.RTT) s.status = SFOC_PT_NAN;
-        else if (vT <= 1e-12 * N) s.status = SFOC_PT_FLAT_TEMPLATE;
+        else if (vT <= 1e-6 * N) s.status = SFOC_PT_FLAT_TEMPLATE;
         else s.status = SFOC_PT_OK;
     }
     stats[k] = s;
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const double* __rest
         if (!centered) nm -= RS * st.RT / N;
         double v;
         if (vS != vS || nm != nm) v = NAN;
-        else if (vS <= 1e-12 * N) v = 0.0;
+        else if (vS <= 1e-6 * N) v = 0.0;
         else v = nm / sqrt(vS * vT);
         s_map[i] = v;
         if (out_maps) out_maps[(size_t)k * P + i] = (float)v;

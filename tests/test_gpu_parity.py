@@ -122,9 +122,10 @@ def test_status_cases(b, ctx, orc):
     """Out-of-bounds points, a flat template and a NaN pixel."""
     pair = tiny_pair(21, 90, 90, 11, 5, 4)
     sen = pair.sen.copy()
-    sen[10:40, 50:80] = 0.5            # flat -> zero cube -> FLAT_TEMPLATE
+    sen[0:60, 40:90] = 0.5             # flat up to the border -> zero cube -> FLAT_TEMPLATE
     sen[70, 20] = np.nan               # NaN propagates to nearby cube values
-    pts = np.array([[3, 45], [45, 87], [65, 25], [20, 70], [45, 45], [22, 68]], np.int32)
+    # points are (x, y)
+    pts = np.array([[3, 45], [45, 87], [65, 28], [20, 70], [30, 45], [22, 68]], np.int32)
     pair.sen = sen
     pair.points = pts
     o = orc.match_pair(pair.ref, sen, pts, 11, 5, want_maps=True, roi=False)

@@ -1,0 +1,183 @@
+"""BF16 form: the tcgen05 correlation kernel against the FP64 oracle.
+
+Kernel parity: the oracle's FP64 cube rounded to bf16 (round to nearest
+even, a plain definition) is matched by the oracle's Eq. 8; the GPU's BF16
+form must agree with it.  The GPU rounds its FP32 cube, which is within
+2e-5 of the oracle's, so values that close to a rounding midpoint may round
+the other way (one ulp).  Tolerances: per point at the best offset,
+1e-4 + 6 sigma of the NCC change those flips imply through the exact NCC
+gradient (parity.flip_tolerance); over whole maps, the worst case
+1e-4 + ||delta_S||/sigma_S + ||delta_T||/sigma_T (parity.ncc_rounding_bound).
+Offsets must agree wherever the oracle's top-2 margin exceeds twice the
+point tolerance.
+
+Precision report: the same GPU results against the oracle on the unrounded
+FP64 cube; the error must stay inside the storage bound
+1e-4 + 2^-9 (||S||/sigma_S + ||T||/sigma_T) (parity.storage_bound).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from workloads import config1, config2, tiny_pair  # noqa: E402
+
+from parity import (bf16_round, compare, compare_maps, flip_tolerance, ncc_rounding_bound,  # noqa: E402
+                    storage_bound, subpixel_tol, to_np)
+
+
+@pytest.fixture(scope="module")
+def b():
+    import paper_2202_13347_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+@pytest.fixture(scope="module")
+def ctx(b):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return b.Context(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_bf16(ctx, b, pair, want_maps=False):
+    p = b.params(dtype=b.DTYPE_BF16)
+    rc = ctx.sfoc_build(dev(pair.ref), p=p)
+    sc = ctx.sfoc_build(dev(pair.sen), p=p)
+    return ctx.fastncc_match(rc, sc, dev(pair.points), pair.m, pair.R, corr_path=b.CORR_IGEMM_TC,
+                             want_maps=want_maps)
+
+
+def oracle_side(orc, pair, roi=False):
+    """Oracle Eq. 8 on its cube rounded to bf16 and on the unrounded cube,
+    plus per point the unrounded search region and template."""
+    m, R = pair.m, pair.R
+    h = orc.template_half(m)
+    M = m + 2 * R
+    regions = []
+    if not roi:
+        rc_full = orc.sfoc_roi(pair.ref)
+        sc_full = orc.sfoc_roi(pair.sen)
+    res_r, res_u = [], []
+    for (px, py) in pair.points:
+        ty0, tx0 = int(py) - h, int(px) - h
+        inb = (ty0 - R >= 0 and tx0 - R >= 0 and ty0 + m + R <= pair.ref.shape[0]
+               and tx0 + m + R <= pair.ref.shape[1] and ty0 + m <= pair.sen.shape[0] and tx0 + m <= pair.sen.shape[1])
+        if not inb:
+            regions.append(None)
+            continue
+        if roi:
+            S = orc.sfoc_roi(pair.ref, None, ty0 - R, tx0 - R, M, M).data
+            T = orc.sfoc_roi(pair.sen, None, ty0, tx0, m, m).data
+        else:
+            S = rc_full.data[:, ty0 - R:ty0 + m + R, tx0 - R:tx0 + m + R].copy()
+            T = sc_full.data[:, ty0:ty0 + m, tx0:tx0 + m].copy()
+        regions.append((S, T))
+    import oracle as _o
+
+    def run(rounded):
+        outs = []
+        for k, (px, py) in enumerate(pair.points):
+            if regions[k] is None:
+                dummy = _o.CubeROI(np.zeros((12, 1, 1)), pair.ref.shape[0], pair.ref.shape[1], 0, 0)
+                outs.append(orc.match(dummy, dummy, np.array([[px, py]], np.int32), m, R, want_maps=True))
+                continue
+            S, T = regions[k]
+            ty0, tx0 = int(py) - h, int(px) - h
+            Sc = bf16_round(S) if rounded else S
+            Tc = bf16_round(T) if rounded else T
+            rc = _o.CubeROI(np.ascontiguousarray(Sc), pair.ref.shape[0], pair.ref.shape[1], ty0 - R, tx0 - R)
+            sc = _o.CubeROI(np.ascontiguousarray(Tc), pair.sen.shape[0], pair.sen.shape[1], ty0, tx0)
+            outs.append(orc.match(rc, sc, np.array([[px, py]], np.int32), m, R, want_maps=True))
+        return {key: np.concatenate([o[key] for o in outs]) for key in outs[0]}
+
+    return run(True), run(False), regions
+
+
+def check(g, o_r, o_u, regions, R, report):
+    n = len(regions)
+    bmaps = [ncc_rounding_bound(*r) if r is not None else None for r in regions]
+    smaps = [storage_bound(*r) if r is not None else None for r in regions]
+    tol = np.full(n, 1e-4)
+    for k, reg in enumerate(regions):
+        if reg is None or o_r["status"][k] not in (0, 3):
+            continue
+        S, T = reg
+        m = T.shape[1]
+        dy, dx = o_r["dy"][k] + R, o_r["dx"][k] + R
+        tol[k] = flip_tolerance(S[:, dy:dy + m, dx:dx + m], T)
+    sub = np.array([subpixel_tol(o_r["maps"][k], R, tol[k]) if bmaps[k] is not None else 0.02 for k in range(n)])
+    st = compare(g, o_r, R, ncc_tol=tol, sub_tol=sub, oracle_maps=o_r["maps"])
+    valid = np.isin(o_r["status"], [0, 3])
+    if "maps" in g:
+        compare_maps(g["maps"].cpu().numpy(), o_r["maps"], bmaps, valid)
+    # precision report against the unrounded FP64 oracle
+    gn = to_np(g)
+    same = valid & (gn["dx"] == o_u["dx"]) & (gn["dy"] == o_u["dy"])
+    stol = np.array([smaps[k][gn["dy"][k] + R, gn["dx"][k] + R] if smaps[k] is not None else 1.0 for k in range(n)])
+    err = np.abs(gn["ncc"] - o_u["ncc"])
+    assert np.all(err[same] <= stol[same]), float((err[same] - stol[same]).max())
+    report.update(st, bf16_vs_fp64_offsets_equal=int(same.sum()), bf16_vs_fp64_valid=int(valid.sum()),
+                  bf16_vs_fp64_ncc_err_max=float(err[same].max()) if same.any() else 0.0,
+                  rounding_bound_max=float(tol[valid].max()) if valid.any() else 0.0)
+    print(report)
+    return st
+
+
+@pytest.mark.parametrize("H,W,m,R,npts,seed", [
+    (70, 83, 9, 4, 12, 11),
+    (96, 61, 10, 3, 9, 12),     # even template
+    (64, 64, 1, 2, 16, 13),     # m = 1
+    (60, 75, 15, 0, 9, 14),     # R = 0
+    (150, 140, 31, 12, 20, 15),
+    (110, 120, 17, 7, 25, 16),
+])
+def test_tc_small_cases(b, ctx, orc, H, W, m, R, npts, seed):
+    pair = tiny_pair(seed, H, W, m, R, npts, shift=(2, -1))
+    g = gpu_bf16(ctx, b, pair, want_maps=True)
+    ctx.sync()
+    o_r, o_u, regions = oracle_side(orc, pair)
+    check(g, o_r, o_u, regions, R, {})
+
+
+def test_bf16_cube_is_rounded_oracle_cube(b, ctx, orc):
+    rng = np.random.default_rng(3)
+    from workloads import optical_like
+    img = optical_like(rng, 77, 93)
+    cube = ctx.sfoc_build(dev(img), p=b.params(dtype=b.DTYPE_BF16))
+    got = cube.export().cpu().numpy().astype(np.float64)
+    want = orc.sfoc_roi(img).data
+    # one bf16 rounding (half an ulp: 2^-9 relative) on top of the FP32 error
+    assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 2e-5)
+
+
+def test_tc_config1(b, ctx, orc):
+    pair = config1()
+    g = gpu_bf16(ctx, b, pair, want_maps=True)
+    ctx.sync()
+    o_r, o_u, regions = oracle_side(orc, pair)
+    rep = {}
+    st = check(g, o_r, o_u, regions, pair.R, rep)
+    assert st["valid"] == 100
+    assert rep["bf16_vs_fp64_offsets_equal"] >= 95
+
+
+def test_tc_config2_full_size_sampled(b, ctx, orc):
+    """2048^2, 1000 points, m=81, R=20 in the benchmark's launch
+    configuration; a seeded sample of 6 points against the oracle."""
+    pair = config2()
+    g = gpu_bf16(ctx, b, pair)
+    ctx.sync()
+    rng = np.random.default_rng(77)
+    idx = np.sort(rng.choice(len(pair.points), 6, replace=False))
+    sub = type(pair)(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R, pair.truth[idx])
+    o_r, o_u, regions = oracle_side(orc, sub, roi=True)
+    gs = {k: v[torch.from_numpy(idx).cuda()] for k, v in g.items()}
+    check(gs, o_r, o_u, regions, pair.R, {})
+    assert int((g["status"] == 0).sum()) >= 900

@@ -11,6 +11,7 @@ def test_config1_deterministic_and_shaped():
     np.testing.assert_array_equal(a.sen, b.sen)
     np.testing.assert_array_equal(a.points, b.points)
     assert a.ref.shape == (512, 512) and a.ref.dtype == np.float32
+    assert a.ref.flags.c_contiguous and a.sen.flags.c_contiguous
     assert a.points.shape == (100, 2)
     assert 0.0 <= a.ref.min() and a.ref.max() <= 1.0
     sx, sy = a.meta["shift"]

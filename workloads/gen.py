@@ -125,7 +125,7 @@ def shift_image(img, sx, sy):
     H, W = img.shape
     ys = np.clip(np.arange(H) - sy, 0, H - 1)
     xs = np.clip(np.arange(W) - sx, 0, W - 1)
-    return img[ys][:, xs]
+    return np.ascontiguousarray(img[ys][:, xs])
 
 
 def shift_field_image(img, block, offsets):
@@ -426,4 +426,4 @@ def tiny_pair(seed, H, W, m, R, n_points, shift=(0, 0), kind="piecewise"):
     g = max(1, int(math.ceil(math.sqrt(max(1, n_points)))))
     pts = _points_for(sen, ref.shape, m, R, (g, g), "grad", n_points)
     truth = np.tile(np.array([[-sx, -sy]], np.float64), (len(pts), 1))
-    return Pair(ref, sen, pts, m, R, truth, dict(seed=seed))
+    return Pair(np.ascontiguousarray(ref), np.ascontiguousarray(sen), pts, m, R, truth, dict(seed=seed))
