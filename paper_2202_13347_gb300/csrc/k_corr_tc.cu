@@ -2,35 +2,46 @@
 // GEMM with FP32 accumulation in tensor memory (sm_103a).
 //
 // Out[dy][dx] = sum_{c,y,u} S[c][y][u+dx] * T[c][y-dy][u]
-//   S: reference window (m+2R)^2 around p (cube rows/cols from p - h - R),
-//   T: template m^2 from the sensed cube (zero outside [0, m)^2).
-// As a GEMM D[r][n] = sum_k A[r][k] B[n][k] with
-//   r = dx (M = 128 rows, rows > 2R are discarded),
-//   n = 2R - dy (N = roundup(2R+1, 16) columns),
-//   k = (y, u, channel), 16 channels per instruction (12 + 4 zero pad).
-// Both operands are K-major, no swizzle: one "core matrix" row is the 16 B
+//   S: reference window (m+2R)^2 around p (rows/cols from p - h - R),
+//   T: template m^2 from the sensed cube, zero outside [0, m)^2.
+// GEMM form D[r][n] = sum_k A[r][k] B[n][k]:
+//   r = dx (M = 128 rows; rows > 2R are discarded),
+//   n = 2R - dy (N = roundup(2R+1, 16)),
+//   k = (y, u, channel); one instruction covers one (y, u) and 16 channels
+//   (12 + 4 zero pad) as two 8-channel chunks LBO apart.
+// Both operands are K-major without swizzle.  A core-matrix row is the 16 B
 // chunk of 8 channels of one pixel, so
-//   A row r  = window pixel (y, u + r)  -> in a row-major pixel layout the
-//              rows of A are consecutive 16 B chunks: a shift in dx is a
-//              16 B offset of the descriptor start address;
-//   B row n  = template pixel (y - 2R + n, u) -> in a column-major pixel
-//              layout consecutive n are consecutive 16 B chunks (Toeplitz
-//              along y by address arithmetic, no copies).
-// The two chunks of an instruction (channels 0-7 and 8-15) sit in two
-// planes, LBO apart; 8-row groups are SBO = 128 B apart.
+//   A row r = window pixel (y, u + r): in the row-major pixel layout rows are
+//             consecutive chunks, a shift in dx is a 16 B step of the
+//             descriptor start;
+//   B row n = template pixel (y - 2R + n, u): in the column-major layout
+//             consecutive n are consecutive chunks (Toeplitz along y through
+//             address arithmetic, no copies).
 //
-// Staging: per K stage (8 window rows x 16 template columns) the A slab
-// (8 x (16+2R) pixels) and the B slab (16 columns x (8+N-1) template rows)
-// are copied with cp.async (16 B, zero-fill outside the window/template)
-// into one of NB ring buffers.  One thread issues the MMAs of a stage and
-// commits them to that buffer's mbarrier; the buffer is refilled once that
-// barrier fires.  Persistent CTAs walk the points; the accumulator is read
-// back with tcgen05.ld and written as the numerator map of Eq. 9 (raw R_ST;
-// the NCC stage subtracts R_S R_T / mnz in FP64).
+// Data movement, per point:
+//   template column block (U columns x (m+2R+N-1) rows, i.e. the template
+//   plus the rows above and below it): TMA loads, then two warps zero the
+//   rows outside [0, m); reused for every window row of the point;
+//   window slab (8 rows x (U+2R) columns): one 4-D TMA load per K stage into
+//   a ring of NA buffers.
+// Warp roles (256 threads):
+//   warp 0 lane 0  TMA producer          warp 1 lane 0  MMA issuer
+//   warps 2-3      template zero rows    warps 4-7      TMEM drain + output
+// The MMAs of one K stage (8 window rows x U template columns) go to one of
+// two TMEM accumulators; the drain warps add it into FP32 registers with
+// round-to-nearest while the next stage runs.  (The tensor core truncates
+// as it accumulates: a single accumulator over ~10^4 MMAs biased R_ST by
+// about -5e-5 relative; per-stage partial sums keep that near 2e-6.)
+// Each MMA's N is trimmed to the 16-column band where the Toeplitz operand
+// is non-zero for its window row; the first MMA of a stage is full width so
+// that it initialises the whole accumulator.
 //
 // Every wait is bounded (about 2 s of %globaltimer); on expiry the CTA sets
-// the context's device error word, drains its copies, frees its TMEM and
-// returns.
+// the context's device error word, every role leaves its loop, the producer
+// waits (bounded) for its copies still in flight, TMEM is freed and the
+// kernel returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include "internal.h"
@@ -41,32 +52,40 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kY = 8;    // window rows per stage
-constexpr int kU = 16;   // template columns per stage
 constexpr int kM = 128;  // MMA M (dx rows)
 constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr unsigned long long kDrainNs = 200000000ull;
+constexpr int kMaxNA = 6;
 
 struct TcGeom {
-    int m, R, P1, Lw, Npad, AW, J, NB, tmem_cols, acc_stride;
-    int a_bytes, b_bytes, stage_bytes;  // per buffer (both channel chunks)
+    int m, R, P1, Lw, Npad, U, AW, JB, JS, NA, tmem_cols, acc_stride;
+    int a_bytes, b_bytes;   // one window slab / one template column block (both chunks)
+    int a_off, b_off;       // shared-memory offsets of the A ring and the B pair
+    int smem;               // dynamic shared memory used (incl. a 2 KB guard)
 };
 
-__host__ __device__ inline TcGeom tc_geom(int m, int R) {
+__host__ __device__ inline TcGeom tc_geom(int m, int R, int U) {
     TcGeom g;
     g.m = m;
     g.R = R;
     g.P1 = 2 * R + 1;
     g.Lw = m + 2 * R;
     g.Npad = (g.P1 + 15) / 16 * 16;
-    g.AW = kU + 2 * R;
-    g.J = kY + g.Npad - 1;
+    g.U = U;
+    g.AW = U + 2 * R;
+    g.JB = g.Lw + g.Npad - 1;
+    g.JS = (g.JB + 7) / 8 * 8;  // column stride: every TMA destination 128-byte aligned
     g.a_bytes = 2 * kY * g.AW * 16;
-    g.b_bytes = 2 * kU * g.J * 16;
-    g.stage_bytes = g.a_bytes + g.b_bytes;
-    int nb = (224 * 1024) / g.stage_bytes;
-    g.NB = nb > 4 ? 4 : nb;
-    g.acc_stride = (g.Npad + 31) / 32 * 32;  // second accumulator starts on a 32-column boundary
+    g.b_bytes = 2 * U * g.JS * 16;
+    const int budget = 224 * 1024 - 2048;
+    int na = (budget - 2 * g.b_bytes) / g.a_bytes;
+    g.NA = na > kMaxNA ? kMaxNA : na;
+    g.a_off = 0;
+    g.b_off = g.NA * g.a_bytes;
+    g.smem = g.b_off + 2 * g.b_bytes + 2048;
+    g.acc_stride = (g.Npad + 31) / 32 * 32;
     int c = 32;
-    while (c < 2 * g.acc_stride) c <<= 1;   // two accumulators
+    while (c < 2 * g.acc_stride) c <<= 1;
     g.tmem_cols = c;
     return g;
 }
@@ -97,7 +116,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; returns false (and sets *s_abort) when the limit expires.
+// Bounded wait; on expiry (or once another role aborted) returns false.
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* s_abort) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
@@ -111,15 +130,31 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* s_abort) {
     }
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+// Bounded wait that ignores the abort flag (used to let copies land).
+__device__ void mbar_wait_short(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer() - t0 > kDrainNs) return;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -163,34 +198,69 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Number of 16-column accumulator chunks a thread drains: warps w and w+4
-// share a 32-lane quarter and take alternate chunks.
-template <int NQ>
-__global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __nv_bfloat16* __restrict__ rm, int Hr, int Wr,
-                                                         const __nv_bfloat16* __restrict__ cm, int Hs, int Ws,
-                                                         const int32_t* __restrict__ pts, int n, int m, int R,
-                                                         const PointStat* __restrict__ stats,
-                                                         float* __restrict__ maps, int* __restrict__ err) {
+// Optional per-stage timestamps of CTA 0 (compiled in only when
+// SFOC_TC_TRACE is defined; rows: 0 window-slab TMA issued, 1 MMA waits
+// begin, 2 MMA issue begins, 3 MMA issue ends, 4 drain waits begin,
+// 5 drain done, 6 zero rows begin, 7 zero rows done).
+#ifdef SFOC_TC_TRACE
+__device__ unsigned long long g_tc_trace[8][8192];
+#define TC_TRACE(row, idx)                                           \
+    do {                                                             \
+        if (blockIdx.x == 0 && (idx) < 8192u) g_tc_trace[row][idx] = clock64(); \
+    } while (0)
+#else
+#define TC_TRACE(row, idx) \
+    do {                   \
+    } while (0)
+#endif
+
+// barrier slots
+enum {
+    BA_FULL = 0,
+    BA_EMPTY = kMaxNA,
+    BB_FULL = 2 * kMaxNA,
+    BB_READY = BB_FULL + 2,
+    BB_EMPTY = BB_READY + 2,
+    BACC_FULL = BB_EMPTY + 2,
+    BACC_EMPTY = BACC_FULL + 2,
+    NBAR = BACC_EMPTY + 2
+};
+
+// NQ = number of 16-column accumulator chunks (Npad / 16), UC = template
+// columns per column block (8, or 4 for the largest windows)
+template <int NQ, int UC>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_corr_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmB2, const int32_t* __restrict__ pts, int n, int m, int R,
+              const PointStat* __restrict__ stats, float* __restrict__ maps, int* __restrict__ err) {
+    constexpr int U = UC;
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t s_empty[4];     // MMAs of the stage in buffer b are complete
-    __shared__ __align__(8) uint64_t s_acc_free[2];  // accumulator a has been drained
+    __shared__ __align__(8) uint64_t s_bar[NBAR];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
 
-    const TcGeom g = tc_geom(m, R);
+    const TcGeom g = tc_geom(m, R, U);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
     const int h = template_half(m);
-    const int nyb = (g.Lw + kY - 1) / kY, nub = (m + kU - 1) / kU;
+    const int nyb = (g.Lw + kY - 1) / kY, nub = (m + U - 1) / U;
     const int T = nyb * nub;
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t idesc = idesc_bf16(kM, g.Npad);
-    const int nchunk = g.Npad / 16;
+    uint32_t bars = smem_u32(&s_bar[0]);
+    auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
 
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&s_empty[i]), 1);
-        for (int i = 0; i < 2; ++i) mbar_init(smem_u32(&s_acc_free[i]), kThreads / 32);
+        for (int i = 0; i < kMaxNA; ++i) {
+            mbar_init(bar(BA_FULL + i), 1);
+            mbar_init(bar(BA_EMPTY + i), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar(BB_FULL + i), 1);
+            mbar_init(bar(BB_READY + i), 2);    // the two zeroing warps
+            mbar_init(bar(BB_EMPTY + i), 1);
+            mbar_init(bar(BACC_FULL + i), 1);
+            mbar_init(bar(BACC_EMPTY + i), 4);  // the four drain warps
+        }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -205,200 +275,282 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __nv_bfloat16* __
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    uint32_t g_stage = 0;  // stages issued by this CTA so far (ring-buffer and accumulator phases)
-    bool aborted = false;
-    const size_t rplane = (size_t)Hr * Wr * 8, splane = (size_t)Ws * Hs * 8;
+    uint32_t gs = 0;        // K stages of this CTA so far
+    uint32_t gb = 0;        // template column blocks of this CTA so far
+    uint32_t a_issued = 0;  // producer: window slabs issued
+    uint32_t b_issued = 0;  // producer: column blocks issued
 
-    for (int k = blockIdx.x; k < n && !aborted; k += gridDim.x) {
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        if (*reinterpret_cast<volatile int*>(&s_abort)) break;
         const PointStat st = stats[k];
         if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
         const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
         const int wy0 = ty0 - R, wx0 = tx0 - R;
+        bool ok = true;
 
-        // loads stage s of this point into ring buffer gs % NB
-        auto load_stage = [&](int s, uint32_t gs) -> bool {
-            const uint32_t buf = gs % g.NB;
-            if (gs >= (uint32_t)g.NB) {
-                if (!mbar_wait(smem_u32(&s_empty[buf]), ((gs / g.NB) - 1) & 1, &s_abort)) return false;
-            }
-            const int yb = s / nub, ub = s - yb * nub;
-            const int y0 = yb * kY, u0 = ub * kU;
-            const uint32_t a_s = sbase + buf * g.stage_bytes;
-            const uint32_t b_s = a_s + g.a_bytes;
-            const int na = 2 * kY * g.AW;
-            for (int i = tid; i < na; i += kThreads) {
-                int cg = i / (kY * g.AW);
-                int rr = i - cg * kY * g.AW;
-                int yl = rr / g.AW, xl = rr - yl * g.AW;
-                int y = y0 + yl, x = u0 + xl;
-                bool v = y < g.Lw && x < g.Lw;
-                const __nv_bfloat16* src = v ? rm + cg * rplane + ((size_t)(wy0 + y) * Wr + (wx0 + x)) * 8 : rm;
-                cp_async16(a_s + i * 16, src, v);
-            }
-            const int nbk = 2 * kU * g.J;
-            for (int i = tid; i < nbk; i += kThreads) {
-                int cg = i / (kU * g.J);
-                int rr = i - cg * kU * g.J;
-                int ul = rr / g.J, jl = rr - ul * g.J;
-                int u = u0 + ul, j = y0 - 2 * R + jl;
-                bool v = u < m && j >= 0 && j < m;
-                const __nv_bfloat16* src = v ? cm + cg * splane + ((size_t)(tx0 + u) * Hs + (ty0 + j)) * 8 : cm;
-                cp_async16(b_s + i * 16, src, v);
-            }
-            return true;
-        };
-
-        // FP32 register sums of the per-stage accumulators (round to nearest):
-        // the tensor core's own accumulation truncates, so each hardware
-        // partial sum covers one stage only.
-        float acc[NQ][16];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-            for (int i = 0; i < 16; ++i) acc[q][i] = 0.f;
-
-        // drains the accumulator of global stage gs into acc[] and frees it
-        auto drain = [&](uint32_t gs) -> bool {
-            if (!mbar_wait(smem_u32(&s_empty[gs % g.NB]), (gs / g.NB) & 1, &s_abort)) return false;
-            tc_fence_after();
-            const uint32_t abase = tmem + ((uint32_t)(quarter * 32) << 16) + (gs & 1) * g.acc_stride;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int chunk = half + 2 * q;
-                if (chunk < nchunk) {
-                    float v[16];
-                    tmem_ld16(abase + chunk * 16, v);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) acc[q][i] += v[i];
+        if (warp == 0) {
+            // ---------------- TMA producer ----------------
+            if (lane == 0) {
+                for (int s = 0; s < T && ok; ++s) {
+                    const int ub = s / nyb, yb = s - ub * nyb;
+                    const uint32_t ga = gs + s;
+                    if (yb == 0) {
+                        const uint32_t gk = gb + ub, bb = gk & 1;
+                        if (gk >= 2) ok = mbar_wait(bar(BB_EMPTY + bb), ((gk >> 1) - 1) & 1, &s_abort);
+                        if (!ok) break;
+                        const uint32_t bdst = sbase + g.b_off + bb * g.b_bytes;
+                        mbar_expect_tx(bar(BB_FULL + bb), g.b_bytes);
+                        for (int cg = 0; cg < 2; ++cg)
+                            for (int ul = 0; ul < U; ++ul) {
+                                const uint32_t cdst = bdst + (cg * U + ul) * g.JS * 16;
+                                const int cx = tx0 + ub * U + ul, cy = ty0 - 2 * R;
+                                tma_load_4d(cdst, &tmB, 0, cy, cx, cg, bar(BB_FULL + bb));
+                                if (g.JS > 256) tma_load_4d(cdst + 256 * 16, &tmB2, 0, cy + 256, cx, cg, bar(BB_FULL + bb));
+                            }
+                        ++b_issued;
+                    }
+                    const uint32_t slot = ga % g.NA;
+                    if (ga >= (uint32_t)g.NA) ok = mbar_wait(bar(BA_EMPTY + slot), ((ga / g.NA) - 1) & 1, &s_abort);
+                    if (!ok) break;
+                    mbar_expect_tx(bar(BA_FULL + slot), g.a_bytes);
+                    tma_load_4d(sbase + g.a_off + slot * g.a_bytes, &tmA, 0, wx0 + ub * U, wy0 + yb * kY, 0,
+                                bar(BA_FULL + slot));
+                    TC_TRACE(0, ga);
+                    ++a_issued;
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_acc_free[gs & 1])) : "memory");
-            return true;
-        };
-
-        const uint32_t gbase = g_stage;
-        const int NB = g.NB;
-        for (int s = 0; s < NB - 1; ++s) {
-            if (s < T && !load_stage(s, gbase + s)) aborted = true;
-            cp_async_commit();
-        }
-        for (int c = 0; c < T; ++c) {
-            if (NB == 2) cp_async_wait<0>();
-            else if (NB == 3) cp_async_wait<1>();
-            else cp_async_wait<2>();
-            fence_proxy_async();
-            __syncthreads();
-            if (s_abort) aborted = true;
-            if (aborted) break;
-            const uint32_t gs = gbase + c;
-            if (tid == 0) {
-                // accumulator gs & 1 must have been drained (stage gs - 2)
-                bool ok = true;
-                if (gs >= 2) ok = mbar_wait(smem_u32(&s_acc_free[gs & 1]), ((gs >> 1) - 1) & 1, &s_abort);
-                if (ok) {
+        } else if (warp == 1) {
+            // ---------------- MMA issuer ----------------
+            if (lane == 0) {
+                const uint32_t a_lbo = kY * g.AW * 16, b_lbo = UC * g.JS * 16;
+                const uint32_t id_full = idesc_bf16(kM, g.Npad);
+                // non-zero band of B rows for window row y: j = y - 2R + n in [0, m),
+                // rounded out to 16 rows
+                auto n0_tab = [&](int y) {
+                    int nlo = 2 * R - y;
+                    nlo = nlo < 0 ? 0 : nlo;
+                    return (nlo / 16) * 16;
+                };
+                auto id_tab = [&](int y) {
+                    int nhi = m + 2 * R - y;
+                    nhi = nhi > g.Npad ? g.Npad : nhi;
+                    const int n1 = (nhi + 15) / 16 * 16;
+                    return idesc_bf16(kM, n1 - n0_tab(y));
+                };
+                for (int s = 0; s < T && ok; ++s) {
+                    const int ub = s / nyb, yb = s - ub * nyb;
+                    const uint32_t ga = gs + s, slot = ga % g.NA, acc = ga & 1;
+                    const uint32_t gk = gb + ub, bb = gk & 1;
+                    TC_TRACE(1, ga);
+                    if (yb == 0) ok = mbar_wait(bar(BB_READY + bb), (gk >> 1) & 1, &s_abort);
+                    if (ok) ok = mbar_wait(bar(BA_FULL + slot), (ga / g.NA) & 1, &s_abort);
+                    if (ok && ga >= 2) ok = mbar_wait(bar(BACC_EMPTY + acc), ((ga >> 1) - 1) & 1, &s_abort);
+                    if (!ok) break;
                     tc_fence_after();
-                    const uint32_t buf = gs % NB;
-                    const int yb = c / nub, ub = c - yb * nub;
-                    const int y0 = yb * kY, u0 = ub * kU;
-                    const uint32_t a_s = sbase + buf * g.stage_bytes;
-                    const uint32_t b_s = a_s + g.a_bytes;
-                    const uint32_t a_lbo = kY * g.AW * 16, b_lbo = kU * g.J * 16;
-                    const uint32_t dacc = tmem + (gs & 1) * g.acc_stride;
-                    uint32_t first = 1;
+                    TC_TRACE(2, ga);
+                    // descriptors advance in 16-byte units by plain integer adds
+                    const uint64_t da0 = smem_desc(sbase + g.a_off + slot * g.a_bytes, a_lbo, 128);
+                    const uint64_t db0 = smem_desc(sbase + g.b_off + bb * g.b_bytes, b_lbo, 128);
+                    const uint32_t dacc = tmem + acc * g.acc_stride;
+                    const int y0 = yb * kY, u0 = ub * UC;
+                    const int ulim = m - u0 < UC ? m - u0 : UC;
+                    const int ylim = g.Lw - y0 < kY ? g.Lw - y0 : kY;
+                    // first MMA of the stage: full width, overwrites the accumulator
+                    mma_bf16(dacc, da0, db0 + (uint64_t)y0, id_full, 0u);
+#pragma unroll
                     for (int yl = 0; yl < kY; ++yl) {
-                        if (y0 + yl >= g.Lw) break;
-                        for (int ul = 0; ul < kU; ++ul) {
-                            if (u0 + ul >= m) break;
-                            uint64_t da = smem_desc(a_s + (yl * g.AW + ul) * 16, a_lbo, 128);
-                            uint64_t db = smem_desc(b_s + (ul * g.J + yl) * 16, b_lbo, 128);
-                            mma_bf16(dacc, da, db, idesc, first ? 0u : 1u);
-                            first = 0;
+                        if (yl < ylim) {
+                            const int y = y0 + yl;
+                            const int n0 = yl == 0 ? 0 : n0_tab(y);
+                            const uint32_t id = yl == 0 ? id_full : id_tab(y);
+                            const uint64_t da = da0 + (uint64_t)(yl * g.AW);
+                            const uint64_t db = db0 + (uint64_t)(y + n0);
+                            const uint32_t dd = dacc + (uint32_t)n0;
+#pragma unroll
+                            for (int ul = 0; ul < UC; ++ul) {
+                                if ((yl > 0 || ul > 0) && ul < ulim)
+                                    mma_bf16(dd, da + (uint64_t)ul, db + (uint64_t)(ul * g.JS), id, 1u);
+                            }
                         }
                     }
-                    mma_commit(smem_u32(&s_empty[buf]));
+                    TC_TRACE(3, ga);
+                    mma_commit(bar(BA_EMPTY + slot));
+                    mma_commit(bar(BACC_FULL + acc));
+                    if (yb == nyb - 1) mma_commit(bar(BB_EMPTY + bb));
                 }
             }
-            // drain the previous stage while this one runs on the tensor cores
-            if (c >= 1 && !drain(gs - 1)) aborted = true;
-            const int s = c + NB - 1;
-            if (s < T && !aborted && !load_stage(s, gbase + s)) aborted = true;
-            cp_async_commit();
-        }
-        g_stage = gbase + T;
-        if (!aborted && T >= 1 && !drain(gbase + T - 1)) aborted = true;
-        __syncthreads();
-        if (s_abort) aborted = true;
-        if (aborted) break;
-        {
-            const int r = quarter * 32 + lane;  // dx
-            float* out = maps + (size_t)k * g.P1 * g.P1;
+        } else if (warp < 4) {
+            // ---------------- template zero rows ----------------
+            const int t = tid - 64;  // 0..63
+            for (int ub = 0; ub < nub && ok; ++ub) {
+                const uint32_t gk = gb + ub, bb = gk & 1;
+                ok = mbar_wait(bar(BB_FULL + bb), (gk >> 1) & 1, &s_abort);
+                if (!ok) break;
+                if (t == 0) TC_TRACE(6, gk);
+                uint8_t* b = smem + g.b_off + bb * g.b_bytes;
+                const int nz_lo = 2 * R;               // rows j < 0
+                const int nz_hi = g.JS - (m + 2 * R);  // rows j >= m, incl. the stride padding
+                const int per_col = nz_lo + nz_hi;
+                const int total = 2 * U * per_col;
+                for (int i = t; i < total; i += 64) {
+                    const int col = i / per_col, rr = i - col * per_col;
+                    const int jl = rr < nz_lo ? rr : m + 2 * R + (rr - nz_lo);
+                    *reinterpret_cast<uint4*>(b + ((size_t)col * g.JS + jl) * 16) = make_uint4(0, 0, 0, 0);
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(BB_READY + bb));
+                if (t == 0) TC_TRACE(7, gk);
+            }
+        } else {
+            // ---------------- TMEM drain + output ----------------
+            const int quarter = warp & 3;
+            float accr[NQ][16];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int chunk = half + 2 * q;
-                if (chunk < nchunk) {
+            for (int q = 0; q < NQ; ++q)
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        int nn = chunk * 16 + i;
-                        int dy = 2 * R - nn;
-                        if (r < g.P1 && dy >= 0) out[dy * g.P1 + r] = acc[q][i];
-                    }
+                for (int i = 0; i < 16; ++i) accr[q][i] = 0.f;
+            for (int s = 0; s < T && ok; ++s) {
+                const uint32_t ga = gs + s, acc = ga & 1;
+                if (warp == 4 && lane == 0) TC_TRACE(4, ga);
+                ok = mbar_wait(bar(BACC_FULL + acc), (ga >> 1) & 1, &s_abort);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t abase = tmem + ((uint32_t)(quarter * 32) << 16) + acc * g.acc_stride;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    float v[16];
+                    tmem_ld16(abase + q * 16, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) accr[q][i] += v[i];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(BACC_EMPTY + acc));
+                if (warp == 4 && lane == 0) TC_TRACE(5, ga);
+            }
+            if (ok) {
+                const int r = quarter * 32 + lane;  // dx
+                float* out = maps + (size_t)k * g.P1 * g.P1;
+                if (r < g.P1) {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int dy = 2 * R - (q * 16 + i);
+                            if (dy >= 0) out[dy * g.P1 + r] = accr[q][i];
+                        }
                 }
             }
         }
+        gs += T;
+        gb += nub;
+        if (!ok) atomicExch(&s_abort, 1);
     }
 
-    if (aborted || s_abort) {
-        if (tid == 0) atomicExch(err, 1);
+    if (warp == 0 && lane == 0 && *reinterpret_cast<volatile int*>(&s_abort)) {
+        // let every copy this CTA issued land before the CTA leaves
+        for (uint32_t i = 0; i < (uint32_t)g.NA && i < a_issued; ++i) {
+            const uint32_t ga = a_issued - 1 - i;
+            mbar_wait_short(bar(BA_FULL + ga % g.NA), (ga / g.NA) & 1);
+        }
+        for (uint32_t i = 0; i < 2 && i < b_issued; ++i) {
+            const uint32_t gk = b_issued - 1 - i;
+            mbar_wait_short(bar(BB_FULL + (gk & 1)), (gk >> 1) & 1);
+        }
     }
-    cp_async_wait_all();
     tc_fence_before();
     __syncthreads();
+    if (s_abort && tid == 0) atomicExch(err, 1);
     if (warp == 0) {
+        tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols)
                      : "memory");
     }
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 4-D bf16 view {8 channels, d1, d2, 2 chunks} of a chunked cube layout.
+bool make_map(CUtensorMap* map, const void* base, uint64_t d1, uint64_t d2, uint32_t b1, uint32_t b2, uint32_t b3) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {8, d1, d2, 2};
+    cuuint64_t strides[3] = {16, 16 * d1, 16 * d1 * d2};
+    cuuint32_t box[4] = {8, b1, b2, b3};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int pick_U(int m, int R) {
+    TcGeom g = tc_geom(m, R, 8);
+    if (g.NA >= 3) return 8;
+    return 4;
+}
+
 }  // namespace
 
-// The kernel always takes the whole opt-in shared memory of an SM (it runs
-// one CTA per SM): the ring buffers plus slack that keeps every descriptor
-// address inside the allocation.
-size_t corr_tc_smem_bytes(int m, int R) {
-    TcGeom g = tc_geom(m, R);
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    size_t need = (size_t)g.NB * g.stage_bytes + 1024;
-    size_t have = optin > 4096 ? (size_t)optin - 1024 : need;
-    return need > have ? need : have;
-}
+size_t corr_tc_smem_bytes(int m, int R) { return (size_t)tc_geom(m, R, pick_U(m, R)).smem; }
 
 cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
                            const PointStat* stats, float* maps, int* err_flag, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (ref.dtype != SFOC_DTYPE_BF16 || sen.dtype != SFOC_DTYPE_BF16 || ref.z != 12) return cudaErrorNotSupported;
     if (2 * R + 1 > kM || m > kMaxTemplate) return cudaErrorNotSupported;
-    TcGeom g = tc_geom(m, R);
-    if (g.NB < 2) return cudaErrorNotSupported;
-    size_t smem = corr_tc_smem_bytes(m, R);
-    cudaError_t e;
+    const int U = pick_U(m, R);
+    const TcGeom g = tc_geom(m, R, U);
+    if (g.NA < 2 || g.JS > 512 || g.AW > 256) return cudaErrorNotSupported;
+    // A: window slab, box {8, AW, 8 rows, 2 chunks} over rm = [2][H][W][8]
+    // B: one template column, box {8, rows, 1, 1} over cm = [2][W][H][8];
+    //    rows [0, 256) through tmB and [256, JS) through tmB2 when JS > 256
+    alignas(64) CUtensorMap tmA, tmB, tmB2;
+    const uint32_t brow = g.JS < 256 ? (uint32_t)g.JS : 256u;
+    const uint32_t brow2 = g.JS > 256 ? (uint32_t)(g.JS - 256) : 8u;
+    if (!make_map(&tmA, ref.rm, (uint64_t)ref.W, (uint64_t)ref.H, (uint32_t)g.AW, kY, 2)) return cudaErrorNotSupported;
+    if (!make_map(&tmB, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, brow, 1, 1)) return cudaErrorNotSupported;
+    if (!make_map(&tmB2, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, brow2, 1, 1)) return cudaErrorNotSupported;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = n < sms ? n : sms;
-    const int nq = (g.Npad / 16 + 1) / 2;
-#define SFOC_TC_CASE(NQ)                                                                                          \
-    e = cudaFuncSetAttribute(k_corr_tc<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);             \
-    if (e != cudaSuccess) return e;                                                                               \
-    k_corr_tc<NQ><<<grid, kThreads, smem, st>>>(ref.rm, ref.H, ref.W, sen.cm, sen.H, sen.W, pts, n, m, R, stats, \
-                                                maps, err_flag);
-    if (nq <= 1) { SFOC_TC_CASE(1) }
-    else if (nq <= 2) { SFOC_TC_CASE(2) }
-    else if (nq <= 3) { SFOC_TC_CASE(3) }
-    else { SFOC_TC_CASE(4) }
+    const int grid = n < sms ? n : sms;
+    const int nq = g.Npad / 16;
+    const size_t smem = (size_t)g.smem;
+    cudaError_t e;
+#define SFOC_TC_CASE(NQ, UC)                                                                               \
+    e = cudaFuncSetAttribute(k_corr_tc<NQ, UC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    if (e != cudaSuccess) return e;                                                                        \
+    k_corr_tc<NQ, UC><<<grid, kThreads, smem, st>>>(tmA, tmB, tmB2, pts, n, m, R, stats, maps, err_flag);
+#define SFOC_TC_NQ(UC)                  \
+    switch (nq) {                       \
+        case 1: SFOC_TC_CASE(1, UC) break; \
+        case 2: SFOC_TC_CASE(2, UC) break; \
+        case 3: SFOC_TC_CASE(3, UC) break; \
+        case 4: SFOC_TC_CASE(4, UC) break; \
+        case 5: SFOC_TC_CASE(5, UC) break; \
+        case 6: SFOC_TC_CASE(6, UC) break; \
+        case 7: SFOC_TC_CASE(7, UC) break; \
+        default: SFOC_TC_CASE(8, UC) break; \
+    }
+    if (U == 8) {
+        SFOC_TC_NQ(8)
+    } else {
+        SFOC_TC_NQ(4)
+    }
+#undef SFOC_TC_NQ
 #undef SFOC_TC_CASE
     return cudaGetLastError();
 }
