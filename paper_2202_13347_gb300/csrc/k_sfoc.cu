@@ -109,11 +109,74 @@ __global__ void __launch_bounds__(kThreads) k_sfoc_steer(const float* __restrict
     }
 }
 
-// Smoothing: per channel, load the F tile with the group's halo (clamped),
-// horizontal dilated passes for each rate into shared planes, vertical
-// passes summed over rates into s_D.  Then normalise each group per pixel.
-constexpr int kMaxSmoothHalo = kMaxDil * kMaxSmoothRadius;  // 18
+// Smoothing (Sec. 2.1): per channel, the F tile with the group's halo
+// (clamped) is staged in shared memory; the horizontal pass of each rate
+// runs register-blocked (a thread loads one row segment once and produces 8
+// outputs for every rate) into shared planes; the vertical pass runs
+// register-blocked too (8 rows of one column per thread) and sums the rates
+// in registers.  The six channels of a group stay in registers, are
+// normalised there and written out: F32 planar, or the bf16 chunks (chunk
+// g = the six channels of group g and two zeros) in both pixel orders,
+// plus the per-pixel sum planes.  Tiles are 32 columns x 64 rows.
+constexpr int kSTW = 32, kSTH = 64, kSRows = 8;
 
+template <int KD>
+__device__ __forceinline__ void smooth_channel(const float* __restrict__ Fk, size_t fpitch, int H, int W, int x0,
+                                               int y0, int hal, int n_dil, const int* s_dil, const float* t,
+                                               float* s_F, int FW, float* s_h, int HR, float (&Dk)[kSRows]) {
+    const int IW = kSTW + 2 * hal, IH = kSTH + 2 * hal;
+    __syncthreads();  // previous channel done with s_F / s_h
+    // load: 8 threads per row, 8 consecutive columns each
+    for (int rr = threadIdx.x >> 3; rr < IH; rr += kThreads >> 3) {
+        const int yy = clampi(y0 + rr - hal, 0, H - 1);
+        const float* row = Fk + (size_t)yy * fpitch;
+        const int cb = (threadIdx.x & 7) * 8;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int cc = cb + c;
+            if (cc < IW) s_F[rr * FW + cc] = __ldg(row + clampi(x0 + cc - hal, 0, W - 1));
+        }
+    }
+    __syncthreads();
+    // horizontal: task = (row, 8-column block); 4 blocks per row
+    for (int task = threadIdx.x; task < IH * 4; task += kThreads) {
+        const int rr = task >> 2, cb = (task & 3) * 8;
+        const float* x = s_F + rr * FW + cb;  // x[c + hal] is column cb + c
+        for (int ri = 0; ri < n_dil; ++ri) {
+            const int rate = s_dil[ri];
+            float o[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) o[c] = t[0] * x[c + hal];
+#pragma unroll
+            for (int q = 1; q <= KD; ++q) {
+                const float tq = t[q];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) o[c] = fmaf(tq, x[c + hal - q * rate] + x[c + hal + q * rate], o[c]);
+            }
+            float4* dst = reinterpret_cast<float4*>(s_h + (ri * HR + rr) * kSTW + cb);
+            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
+    }
+    __syncthreads();
+    // vertical: task = (column, 8-row block): 32 x 8 = 256 tasks
+    const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
+#pragma unroll
+    for (int j = 0; j < kSRows; ++j) Dk[j] = 0.f;
+    for (int ri = 0; ri < n_dil; ++ri) {
+        const int rate = s_dil[ri];
+        const float* x = s_h + (ri * HR + rb + hal) * kSTW + col;  // x[j * kSTW] is output row rb + j
+#pragma unroll
+        for (int j = 0; j < kSRows; ++j) {
+            float a = t[0] * x[j * kSTW];
+#pragma unroll
+            for (int q = 1; q <= KD; ++q) a = fmaf(t[q], x[(j - q * rate) * kSTW] + x[(j + q * rate) * kSTW], a);
+            Dk[j] += a;
+        }
+    }
+}
+
+template <int NO>
 __global__ void __launch_bounds__(kThreads) k_sfoc_smooth(const float* __restrict__ F, size_t fpitch,
                                                            size_t fplane, int H, int W, SmoothTaps tp,
                                                            float* __restrict__ c32, size_t cpitch, size_t cplane,
@@ -121,115 +184,85 @@ __global__ void __launch_bounds__(kThreads) k_sfoc_smooth(const float* __restric
                                                            __nv_bfloat16* __restrict__ cm,
                                                            float* __restrict__ s1, float* __restrict__ s2) {
     extern __shared__ float sm[];
+    __shared__ float s_tap[2][kMaxSmoothRadius + 1];  // taps in shared memory: no local copy of the params
+    __shared__ int s_dil[kMaxDil];
+    if (threadIdx.x < 2 * (kMaxSmoothRadius + 1)) {
+        const int gg = threadIdx.x / (kMaxSmoothRadius + 1), q = threadIdx.x % (kMaxSmoothRadius + 1);
+        s_tap[gg][q] = tp.g[gg][q];
+    }
+    if (threadIdx.x < kMaxDil) s_dil[threadIdx.x] = tp.dil[threadIdx.x];
     const int maxhal = max(tp.halo[0], tp.halo[1]);
-    const int FW = kTW + 2 * maxhal;
-    float* s_F = sm;                                  // (kTH + 2 maxhal) x FW
-    float* s_h = s_F + (kTH + 2 * maxhal) * FW;       // n_dil x (kTH + 2 maxhal) x kTW
-    float* s_D = s_h + tp.n_dil * (kTH + 2 * maxhal) * kTW;  // z x kTH x kTW
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-
-    for (int k = 0; k < tp.z; ++k) {
-        const int g = k < tp.no ? 0 : 1;
-        const int hal = tp.halo[g];
-        const int IW = kTW + 2 * hal, IH = kTH + 2 * hal;
-        const float* Fk = F + (size_t)k * fplane;
-        __syncthreads();  // previous channel done with s_F / s_h
-        for (int i = threadIdx.x; i < IH * IW; i += kThreads) {
-            int r = i / IW, c = i - r * IW;
-            int gy = clampi(y0 + r - hal, 0, H - 1), gx = clampi(x0 + c - hal, 0, W - 1);
-            s_F[r * FW + c] = __ldg(Fk + (size_t)gy * fpitch + gx);
-        }
-        __syncthreads();
-        const float* t = tp.g[g];
-        const int Kd = tp.Kd[g];
-        for (int i = threadIdx.x; i < IH * kTW; i += kThreads) {
-            int r = i / kTW, c = i - r * kTW;
-            const float* x = s_F + r * FW + c + hal;
-            for (int ri = 0; ri < tp.n_dil; ++ri) {
-                const int rate = tp.dil[ri];
-                float acc = t[0] * x[0];
-#pragma unroll
-                for (int q = 1; q <= kMaxSmoothRadius; ++q)
-                    if (q <= Kd) acc = fmaf(t[q], x[-q * rate] + x[q * rate], acc);
-                s_h[(ri * (kTH + 2 * maxhal) + r) * kTW + c] = acc;
-            }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < kTH * kTW; i += kThreads) {
-            int r = i / kTW, c = i - r * kTW;
-            float acc = 0.f;
-            for (int ri = 0; ri < tp.n_dil; ++ri) {
-                const int rate = tp.dil[ri];
-                const float* x = s_h + (ri * (kTH + 2 * maxhal) + r + hal) * kTW + c;
-                float a = t[0] * x[0];
-#pragma unroll
-                for (int q = 1; q <= kMaxSmoothRadius; ++q)
-                    if (q <= Kd) a = fmaf(t[q], x[-q * rate * kTW] + x[q * rate * kTW], a);
-                acc += a;
-            }
-            s_D[(k * kTH + r) * kTW + c] = acc;
-        }
-    }
-    __syncthreads();
-
-    // group normalisation, per pixel; values stay in s_D (rounded to bf16
-    // when the cube is bf16, so the sum planes describe the stored values)
+    const int FW = kSTW + 2 * maxhal + 8;  // + slack: the 8-wide load blocks may overrun IW
+    const int HR = kSTH + 2 * maxhal;
+    float* s_F = sm;                       // HR x FW
+    float* s_h = s_F + HR * FW;            // n_dil x HR x kSTW
+    const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH;
+    const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
+    const int gx = x0 + col;
     const bool bf = rm != nullptr;
-    for (int i = threadIdx.x; i < kTH * kTW; i += kThreads) {
-        int r = i / kTW, c = i - r * kTW;
-        int gy = y0 + r, gx = x0 + c;
-        float a1 = 0.f, a2 = 0.f;
-        const int ng = tp.z / tp.no;
-        for (int g = 0; g < ng; ++g) {
-            float n2 = 0.f;
-            for (int k = 0; k < tp.no; ++k) {
-                float v = s_D[((g * tp.no + k) * kTH + r) * kTW + c];
-                n2 = fmaf(v, v, n2);
-            }
-            float inv = 1.f / (sqrtf(n2) + tp.eps);
-            if (!(sqrtf(n2) + tp.eps > 0.f)) inv = 0.f;
-            for (int k = 0; k < tp.no; ++k) {
-                float* p = &s_D[((g * tp.no + k) * kTH + r) * kTW + c];
-                float v = *p * inv;
-                if (bf) v = __bfloat162float(__float2bfloat16_rn(v));
-                *p = v;
-                a1 += v;
-                a2 = fmaf(v, v, a2);
+    const int no = NO > 0 ? NO : tp.no;
+    const int ng = tp.z / no;
+    constexpr int KO = NO > 0 ? NO : kMaxOrient;
+
+    float a1[kSRows], a2[kSRows];
+#pragma unroll
+    for (int j = 0; j < kSRows; ++j) a1[j] = a2[j] = 0.f;
+
+    for (int g = 0; g < ng; ++g) {
+        const int hal = g ? tp.halo[1] : tp.halo[0];
+        const int Kd = g ? tp.Kd[1] : tp.Kd[0];
+        const float* t = s_tap[g];
+        float D[KO][kSRows];
+#pragma unroll
+        for (int k = 0; k < KO; ++k) {
+            if (k >= no) break;
+            const float* Fk = F + (size_t)(g * no + k) * fplane;
+            switch (Kd) {
+                case 1: smooth_channel<1>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
+                case 2: smooth_channel<2>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
+                case 3: smooth_channel<3>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
+                case 4: smooth_channel<4>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
+                case 5: smooth_channel<5>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
+                default: smooth_channel<6>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
             }
         }
-        if (gy < H && gx < W) {
-            s1[(size_t)gy * cpitch + gx] = a1;
-            s2[(size_t)gy * cpitch + gx] = a2;
-            if (c32)
-                for (int k = 0; k < tp.z; ++k) c32[(size_t)k * cplane + (size_t)gy * cpitch + gx] = s_D[(k * kTH + r) * kTW + c];
+        // group normalisation in registers; write this group
+#pragma unroll
+        for (int j = 0; j < kSRows; ++j) {
+            float n2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < KO; ++k)
+                if (k < no) n2 = fmaf(D[k][j], D[k][j], n2);
+            const float den = sqrtf(n2) + tp.eps;
+            const float inv = den > 0.f ? 1.f / den : 0.f;  // NaN stays NaN through D * inv
+            const int gy = y0 + rb + j;
+            const bool in = gy < H && gx < W;
+            __align__(16) __nv_bfloat16 ch[8];
+#pragma unroll
+            for (int k = 0; k < KO; ++k) {
+                if (k >= no) break;
+                float v = (den > 0.f || den != den) ? D[k][j] * inv : 0.f;
+                if (bf) v = __bfloat162float(__float2bfloat16_rn(v));
+                a1[j] += v;
+                a2[j] = fmaf(v, v, a2[j]);
+                if (k < 8) ch[k] = __float2bfloat16_rn(v);
+                if (c32 && in) c32[(size_t)(g * no + k) * cplane + (size_t)gy * cpitch + gx] = v;
+            }
+            if (NO == 6 && bf && in) {
+                ch[6] = ch[7] = __float2bfloat16_rn(0.f);
+                const size_t npx = (size_t)H * W;
+                const size_t pix = (size_t)gy * W + gx, cpx = (size_t)gx * H + gy;
+                *reinterpret_cast<uint4*>(rm + ((size_t)g * npx + pix) * 8) = *reinterpret_cast<uint4*>(ch);
+                *reinterpret_cast<uint4*>(cm + ((size_t)g * npx + cpx) * 8) = *reinterpret_cast<uint4*>(ch);
+            }
         }
     }
-    if (!bf) return;
-    __syncthreads();
-    // bf16 chunked layouts: chunk 0 = channels 0..7, chunk 1 = 8..11 + zeros
-    auto pack = [&](int r, int c, int chunk) -> uint4 {
-        __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            int k = chunk * 8 + j;
-            v[j] = __float2bfloat16_rn(k < tp.z ? s_D[(k * kTH + r) * kTW + c] : 0.f);
-        }
-        return *reinterpret_cast<uint4*>(v);
-    };
-    for (int i = threadIdx.x; i < 2 * kTH * kTW; i += kThreads) {
-        int chunk = i / (kTH * kTW);
-        int j = i - chunk * kTH * kTW;
-        {   // row-major: consecutive threads -> consecutive x
-            int r = j / kTW, c = j - r * kTW;
-            int gy = y0 + r, gx = x0 + c;
-            if (gy < H && gx < W)
-                *reinterpret_cast<uint4*>(rm + (((size_t)chunk * H + gy) * W + gx) * 8) = pack(r, c, chunk);
-        }
-        {   // column-major: consecutive threads -> consecutive y
-            int c = j / kTH, r = j - c * kTH;
-            int gy = y0 + r, gx = x0 + c;
-            if (gy < H && gx < W)
-                *reinterpret_cast<uint4*>(cm + (((size_t)chunk * W + gx) * H + gy) * 8) = pack(r, c, chunk);
+    for (int j = 0; j < kSRows; ++j) {
+        const int gy = y0 + rb + j;
+        if (gy < H && gx < W) {
+            s1[(size_t)gy * cpitch + gx] = a1[j];
+            s2[(size_t)gy * cpitch + gx] = a2[j];
         }
     }
 }
@@ -239,7 +272,7 @@ __global__ void k_cube_export_bf16(const __nv_bfloat16* __restrict__ rm, int H, 
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n * z; i += (size_t)gridDim.x * blockDim.x) {
         int k = (int)(i / n);
         size_t p = i - (size_t)k * n;
-        int chunk = k / 8, j = k % 8;
+        int chunk = k / 6, j = k % 6;  // chunk g = the six channels of group g + two zeros
         out[i] = __bfloat162float(rm[((size_t)chunk * n + p) * 8 + j]);
     }
 }
@@ -272,13 +305,22 @@ cudaError_t launch_sfoc_steer(const float* img, int H, int W, size_t pitch, floa
 cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,
                                cudaStream_t st) {
     const int maxhal = tp.halo[0] > tp.halo[1] ? tp.halo[0] : tp.halo[1];
-    const int IH = kTH + 2 * maxhal, IW = kTW + 2 * maxhal;
-    size_t smem = sizeof(float) * ((size_t)IH * IW + (size_t)tp.n_dil * IH * kTW + (size_t)tp.z * kTH * kTW);
-    cudaError_t e = cudaFuncSetAttribute(k_sfoc_smooth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
-    k_sfoc_smooth<<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
-                                                c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+    const int HR = kSTH + 2 * maxhal, FW = kSTW + 2 * maxhal + 8;
+    size_t smem = sizeof(float) * ((size_t)HR * FW + (size_t)tp.n_dil * HR * kSTW);
+    dim3 grid((W + kSTW - 1) / kSTW, (H + kSTH - 1) / kSTH);
+    cudaError_t e;
+    if (tp.no == 6) {
+        e = cudaFuncSetAttribute(k_sfoc_smooth<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sfoc_smooth<6><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
+                                                       c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+    } else {
+        if (c.rm) return cudaErrorNotSupported;  // bf16 layouts need 12 channels
+        e = cudaFuncSetAttribute(k_sfoc_smooth<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sfoc_smooth<0><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
+                                                       c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+    }
     return cudaGetLastError();
 }
 
