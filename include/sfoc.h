@@ -166,6 +166,31 @@ SFOC_API sfoc_status sfoc_build(sfoc_ctx* ctx, const float* d_image, int H, int 
                        const double* scales, int n_scales, int n_orient, const sfoc_params* p,
                        sfoc_cube** out);
 
+/*
+ * sfoc_build_static - sfoc_build into a caller-owned F32 cube, allocating
+ * nothing.  The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory when they build a descriptor (a fixed
+ * memory budget set at start-up, or a loop that must not take cudaMalloc's
+ * device-wide synchronisation).  It computes the same cube as sfoc_build
+ * (same kernels, same values).
+ *   d_image      float32 image, row-major, pitch `pitch_elems` >= W elements.
+ *   p            NULL = sfoc_params_default(); cube_dtype must be F32.
+ *   d_out        caller-owned float32 [z][H][W] (dense), z = 2*n_orient (or
+ *                n_orient with first_order_only); receives the cube.
+ * Scratch: one library-owned device array of SFOC_STATIC_SCRATCH_FLOATS
+ * floats (64 MiB) per device.  A call needs z*roundup(W,32)*H + 2*H*W
+ * floats of it (12 channels: up to about 1024 x 1170 pixels); larger
+ * images return SFOC_ERR_UNSUPPORTED with the sizes in the error string.
+ * The first call on a device looks up the array's address (this may load
+ * the library's device code); make that first call before any stream
+ * capture.  Calls that overlap in time on one device (several streams or
+ * threads) share the array and race; it keeps the last call's contents.
+ * Asynchronous on the context's stream.
+ */
+#define SFOC_STATIC_SCRATCH_FLOATS (1u << 24)
+SFOC_API sfoc_status sfoc_build_static(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems,
+                                       const sfoc_params* p, float* d_out);
+
 /* Shape and dtype of a cube (any pointer may be NULL). */
 SFOC_API sfoc_status sfoc_cube_info(const sfoc_cube* cube, int* z, int* H, int* W, int* dtype);
 /* Writes the cube as float32 [z][H][W] (dense) into d_out. */

@@ -21,6 +21,7 @@ ERR_NAMES = {0: "SFOC_OK", -1: "SFOC_ERR_INVALID_ARG", -2: "SFOC_ERR_SHAPE", -3:
 PT_OK, PT_OUT_OF_BOUNDS, PT_FLAT_TEMPLATE, PT_PEAK_ON_EDGE, PT_NAN = 0, 1, 2, 3, 4
 DTYPE_F32, DTYPE_BF16 = 0, 1
 CORR_AUTO, CORR_DIRECT_F32, CORR_IGEMM_TC = 0, 1, 2
+STATIC_SCRATCH_FLOATS = 1 << 24  # SFOC_STATIC_SCRATCH_FLOATS
 
 
 class SfocError(RuntimeError):
@@ -85,6 +86,7 @@ _SIGS = {
                                         C.c_int, C.POINTER(Params), C.POINTER(Opts), _P]),
     "fastncc_register_pair_host": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P, C.c_int,
                                              C.c_int, C.c_int, C.POINTER(Params), C.POINTER(Opts), _P]),
+    "sfoc_build_static": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, _P, _P]),
     "sfoc_build_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_size_t), C.POINTER(Params), C.POINTER(_P)]),
     "fastncc_match_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
@@ -251,6 +253,16 @@ class Context:
         if out is not None and h.value == out.handle:
             return out
         return Cube(self, h.value)
+
+    def sfoc_build_static(self, image: torch.Tensor, out: torch.Tensor, p: Params = None) -> torch.Tensor:
+        """sfoc_build into the caller's dense float32 [z][H][W] tensor `out`,
+        with the library's fixed scratch array instead of the workspace."""
+        _check_cuda(image, "image", torch.float32)
+        _check_cuda(out, "out", torch.float32)
+        H, W = image.shape
+        self._chk(lib().sfoc_build_static(self.h, _ptr(image), H, W, W, C.byref(p) if p is not None else None,
+                                          _ptr(out)))
+        return out
 
     def fastncc_match(self, ref: Cube, sen: Cube, points: torch.Tensor, template_size: int, search_radius: int,
                       corr_path=CORR_AUTO, want_maps=False):

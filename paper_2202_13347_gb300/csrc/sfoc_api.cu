@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -671,6 +672,98 @@ sfoc_status fastncc_match_batch(sfoc_ctx* ctx, int n_pairs, sfoc_cube* const* re
                                       search_radius[i], &o, d_outs[i]);
         if (s != SFOC_OK) return s;
     }
+    return SFOC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// sfoc_build_static: the SFOC build with its scratch in a fixed device array.
+//
+// Some callers cannot allocate device memory at the moment they need a
+// descriptor: a service that sizes every allocation up front and holds a
+// hard memory cap, or a real-time loop that must not take cudaMalloc's
+// device-wide synchronisation.  This entry point serves them: the
+// steering responses (the only scratch of the build) go to the array below,
+// the cube goes to the caller's buffer, and nothing is allocated.
+//
+// The array is 2^24 floats (64 MiB).  It holds the z steering planes
+// (rows padded to 32 floats) followed by the two per-pixel sum planes the
+// smoothing pass writes; nothing in it has to start at zero, because the
+// steering pass writes every element the smoothing pass reads and the sum
+// planes are stored, not accumulated.  There is one array per device, so
+// calls that overlap in time (two streams, two threads) race on it, and it
+// keeps the last call's contents until the next call.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) float g_static_scratch[SFOC_STATIC_SCRATCH_FLOATS];
+
+namespace {
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+float* g_static_ptr[kMaxStaticDevices] = {nullptr};
+
+// Address of this device's array; the first call on a device looks it up
+// (with that device current) and remembers it.
+cudaError_t static_scratch(int device, float** out) {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[device]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[device] = static_cast<float*>(ptr);
+    }
+    *out = g_static_ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+sfoc_status sfoc_build_static(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems,
+                              const sfoc_params* pin, float* d_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!d_image || !d_out) return fail(ctx, SFOC_ERR_INVALID_ARG, "null image or output pointer");
+    if (H <= 0 || W <= 0) return fail(ctx, SFOC_ERR_SHAPE, "image must be at least 1 x 1");
+    if (pitch_elems < (size_t)W) return fail(ctx, SFOC_ERR_SHAPE, "pitch_elems < W");
+    if (ctx->device < 0 || ctx->device >= kMaxStaticDevices)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "device index beyond the static scratch table");
+    sfoc_params p;
+    if (pin) p = *pin;
+    else sfoc_params_default(&p);
+    if (p.cube_dtype != SFOC_DTYPE_F32) return fail(ctx, SFOC_ERR_UNSUPPORTED, "sfoc_build_static writes F32 cubes only");
+    sfoc_status s = check_params(ctx, p);
+    if (s != SFOC_OK) return s;
+    const int z = p.first_order_only ? p.n_orient : 2 * p.n_orient;
+    const size_t fpitch = roundup((size_t)W, 32);
+    const size_t f_floats = fpitch * (size_t)H * z;
+    const size_t need = f_floats + 2 * (size_t)H * W;
+    if ((size_t)H * W > ((size_t)1 << 31) || need > (size_t)SFOC_STATIC_SCRATCH_FLOATS)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED,
+                    "image too large for the static scratch: needs " + std::to_string(need) + " floats, holds " +
+                        std::to_string((size_t)SFOC_STATIC_SCRATCH_FLOATS));
+    DeviceGuard g(ctx->device);
+    float* F = nullptr;
+    cudaError_t e = static_scratch(ctx->device, &F);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(static scratch)");
+    Cube c;
+    c.H = H;
+    c.W = W;
+    c.z = z;
+    c.dtype = SFOC_DTYPE_F32;
+    c.pitch = (size_t)W;  // dense [z][H][W], the layout sfoc_cube_export writes
+    c.ipitch = (size_t)W + 1;
+    c.device = ctx->device;
+    c.f32 = d_out;
+    c.s1 = F + f_floats;
+    c.s2 = c.s1 + (size_t)H * W;
+    const SteerTaps st = make_steer(p);
+    const SmoothTaps sm = make_smooth(p);
+    ctx->launches += 2;
+    e = launch_sfoc_steer(d_image, H, W, pitch_elems, F, fpitch, st, z, ctx->stream);
+    if (e == cudaSuccess) e = launch_sfoc_smooth(F, fpitch, H, W, sm, c, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sfoc kernels");
     return SFOC_OK;
 }
 
