@@ -60,7 +60,9 @@ typedef enum { SFOC_DTYPE_F32 = 0, SFOC_DTYPE_BF16 = 1 } sfoc_dtype;
 typedef enum {
     SFOC_CORR_AUTO = 0,       /* pick by dtype and autotuned shape class */
     SFOC_CORR_DIRECT_F32 = 1, /* FP32 CUDA-core direct correlation (F32 cubes) */
-    SFOC_CORR_IGEMM_TC = 2    /* tcgen05 BF16 implicit GEMM, FP32 accumulate (BF16 cubes) */
+    SFOC_CORR_IGEMM_TC = 2,   /* tcgen05 BF16 implicit GEMM, FP32 accumulate (BF16 cubes):
+                               * column form when m + 2R <= 128, else Toeplitz form */
+    SFOC_CORR_TC_TOEPLITZ = 3 /* the Toeplitz form of the tcgen05 kernel for any m, R */
 } sfoc_corr_path;
 
 /*

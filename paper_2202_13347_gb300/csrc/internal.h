@@ -97,7 +97,7 @@ cudaError_t launch_template_stats(const Cube& ref, const Cube& sen, const int32_
 cudaError_t launch_corr_f32(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
                             const PointStat* stats, float* maps, cudaStream_t st);
 cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                           const PointStat* stats, float* maps, int* err_flag, cudaStream_t st);
+                           const PointStat* stats, float* maps, int* err_flag, int form, cudaStream_t st);
 size_t corr_tc_smem_bytes(int m, int R);
 cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m, int R, const PointStat* stats,
                               const float* num, int centered, float* out_maps, fastncc_result* out,

@@ -469,6 +469,450 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Column form (window at most 128 rows tall).
+//
+// For a group of G offsets dx = d0 .. d0+G-1, TMEM accumulator g holds
+//   D_g[y][i] = sum_{u, c} S[c][y][u + dx] T[c][i][u]
+// with M = window row y (128 rows), N = template row i (m rounded up to 16)
+// and K = (template column u, 16 channels): one MMA per (dx, u).  Then
+//   Out[dy][dx] = sum_{i < m} D_g[i + dy][i],
+// a sum along a diagonal, done by the drain warps through shared memory.
+// Template rows i >= m (image rows below the template, or the copy's zero
+// fill) only reach accumulator columns i >= m, which no diagonal sum reads,
+// so they need no clearing.  Per point this issues (2R+1) m MMAs of
+// N = roundup(m, 16) instead of the (m+2R) m narrow MMAs of the Toeplitz form.
+//
+// Operands come from the column-major pixel layout (cm) in slabs of kColQ
+// image columns, one 4-D tensor copy each ({8 channels, rows, kColQ
+// columns, 2 chunks}): every copy request costs a fixed ~200 cycles of the
+// copy engine, so few large requests matter more than exact extents.
+//   template slab s of a group: template columns 8s .. 8s+7, Npad rows;
+//   window slab b of a group:   window columns d0 + 8b .. d0 + 8b + 7, Bw
+//                               rows (Bw = m + 2R rounded up to 8, <= 128).
+// Columns and rows past the region are loaded too (or zero filled past the
+// image) and never reach a used accumulator entry; MMA rows past Bw read
+// further bytes of shared memory and only feed accumulator rows that the
+// diagonal sums never use.
+// The issuer works in stages of kColQ template columns: it waits once for
+// the stage's slabs, then issues the stage's kColQ x G MMAs as straight code
+// from precomputed descriptors (control flow between tcgen05.mma
+// instructions costs far more issue time than integer work) and commits
+// once.  A relay warp turns each stage commit into the releases of the
+// stage's slabs.  Each accumulator spans m MMAs, so the tensor core's
+// truncating accumulation stays small.
+// ---------------------------------------------------------------------------
+constexpr int kColMaxG = 16;
+constexpr int kColQ = 8;   // template columns per stage and columns per slab
+constexpr int kColMaxWS = 5;
+constexpr int kColMaxTS = 3;
+// Stage-done barriers.  The issuer can run at most TS stages ahead of the
+// relay (a template slab is reused only after the relay freed it), so with
+// more barriers than that no barrier completes twice before the relay has
+// seen the first phase.
+constexpr int kColNS = 8;
+constexpr int kColDB = 6;  // TMEM chunks of 16 columns per drain load batch
+
+struct ColGeom {
+    int m, R, P1, Lw, Bw, Npad, G;
+    int WS, TS;                // window / template slab ring sizes
+    int ws_bytes, ts_bytes;    // slab sizes
+    int t_off, w_off, bk_off;  // shared-memory offsets
+    int part_off;              // partial diagonal sums: 2 x 128 floats
+    int bk_stride;             // band buffer row stride in floats (odd: no bank conflicts)
+    int smem;
+};
+
+__host__ __device__ inline ColGeom col_geom(int m, int R) {
+    ColGeom c;
+    c.m = m;
+    c.R = R;
+    c.P1 = 2 * R + 1;
+    c.Lw = m + 2 * R;
+    c.Bw = (c.Lw + 7) / 8 * 8;
+    c.Bw = c.Bw > kM ? kM : c.Bw;
+    c.Npad = (m + 15) / 16 * 16;
+    int G = 512 / c.Npad;
+    G = G > c.P1 ? c.P1 : G;
+    c.G = G > kColMaxG ? kColMaxG : G;
+    c.WS = (kColQ + c.G - 1 + kColQ - 1) / kColQ + 2;  // slabs one stage reads, plus two in flight
+    c.TS = kColMaxTS;
+    c.ws_bytes = 2 * kColQ * c.Bw * 16;
+    c.ts_bytes = 2 * kColQ * c.Npad * 16;
+    c.t_off = 0;
+    c.w_off = c.TS * c.ts_bytes;
+    c.bk_stride = c.m | 1;
+    c.bk_off = c.w_off + c.WS * c.ws_bytes;
+    c.part_off = c.bk_off + ((c.P1 * c.bk_stride + 32) * 4 + 127) / 128 * 128;  // + 32 dummy slots
+    // an MMA on the last window slab may read up to 2048 - 16 Bw bytes past it
+    c.smem = c.part_off + 2 * 128 * 4 + (2048 - 16 * c.Bw);
+    if (c.smem > 225 * 1024) {  // drop the third template slab (static shared memory needs the rest)
+        c.TS = 2;
+        c.w_off -= c.ts_bytes;
+        c.bk_off -= c.ts_bytes;
+        c.part_off -= c.ts_bytes;
+        c.smem -= c.ts_bytes;
+    }
+    // one CTA per SM: the CTA allocates all 512 TMEM columns
+    c.smem = c.smem < 120 * 1024 ? 120 * 1024 : c.smem;
+    return c;
+}
+
+enum {
+    CB_WFULL = 0,
+    CB_WEMPTY = kColMaxWS,
+    CB_TFULL = 2 * kColMaxWS,
+    CB_TEMPTY = CB_TFULL + kColMaxTS,
+    CB_STG = CB_TEMPTY + kColMaxTS,
+    CB_AFULL = CB_STG + kColNS,
+    CB_AEMPTY,
+    CB_FIN,
+    CB_N
+};
+
+template <int G>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_corr_tc_col(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmT,
+                  const int32_t* __restrict__ pts, int n, int m, int R, const PointStat* __restrict__ stats,
+                  float* __restrict__ maps, int* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_bar[CB_N];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ int s_go;
+
+    const ColGeom g = col_geom(m, R);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int h = template_half(m);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bars = smem_u32(&s_bar[0]);
+    auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
+
+    if (tid == 0) {
+        for (int i = 0; i < g.WS; ++i) {
+            mbar_init(bar(CB_WFULL + i), 1);
+            mbar_init(bar(CB_WEMPTY + i), 1);
+        }
+        for (int i = 0; i < g.TS; ++i) {
+            mbar_init(bar(CB_TFULL + i), 1);
+            mbar_init(bar(CB_TEMPTY + i), 1);
+        }
+        for (int i = 0; i < kColNS; ++i) mbar_init(bar(CB_STG + i), 1);
+        mbar_init(bar(CB_AFULL), 1);
+        mbar_init(bar(CB_AEMPTY), 4);  // the four drain warps
+        mbar_init(bar(CB_FIN), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    // per-CTA running counts (window slabs, template slabs = stages, groups),
+    // advanced identically by every role
+    uint32_t wsc = 0, tsc = 0, grp = 0;
+    uint32_t w_issued = 0, t_issued = 0, mma_issued = 0;
+    const int nstage = (m + kColQ - 1) / kColQ;  // stages (template slabs) per group
+
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        if (*reinterpret_cast<volatile int*>(&s_abort)) break;
+        const PointStat st = stats[k];
+        if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
+        const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
+        const int wy0 = ty0 - R, wx0 = tx0 - R;
+        bool ok = true;
+        if (warp == 0) {
+            // ---------------- TMA producer ----------------
+            if (lane == 0) {
+                uint32_t wv = wsc, tv = tsc;
+                for (int d0 = 0; d0 < g.P1 && ok; d0 += G) {
+                    const int Gg = g.P1 - d0 < G ? g.P1 - d0 : G;
+                    const int nws = (m + Gg - 1 + kColQ - 1) / kColQ;
+                    int wl = 0;  // window slabs of the group loaded
+                    for (int s = 0; s < nstage && ok; ++s) {
+                        {  // template slab s
+                            const uint32_t slot = tv % g.TS;
+                            if (tv >= (uint32_t)g.TS)
+                                ok = mbar_wait(bar(CB_TEMPTY + slot), ((tv / g.TS) - 1) & 1, &s_abort);
+                            if (!ok) break;
+                            mbar_expect_tx(bar(CB_TFULL + slot), (uint32_t)g.ts_bytes);
+                            tma_load_4d(sbase + g.t_off + slot * g.ts_bytes, &tmT, 0, ty0, tx0 + s * kColQ, 0,
+                                        bar(CB_TFULL + slot));
+                            ++tv;
+                            ++t_issued;
+                        }
+                        // window slabs up to the last one stage s reads
+                        int last = (s * kColQ + kColQ - 1 + Gg - 1) / kColQ;
+                        last = last > nws - 1 ? nws - 1 : last;
+                        if (s == nstage - 1) last = nws - 1;
+                        while (ok && wl <= last) {
+                            const uint32_t slot = wv % g.WS;
+                            if (wv >= (uint32_t)g.WS)
+                                ok = mbar_wait(bar(CB_WEMPTY + slot), ((wv / g.WS) - 1) & 1, &s_abort);
+                            if (!ok) break;
+                            mbar_expect_tx(bar(CB_WFULL + slot), (uint32_t)g.ws_bytes);
+                            tma_load_4d(sbase + g.w_off + slot * g.ws_bytes, &tmW, 0, wy0, wx0 + d0 + wl * kColQ, 0,
+                                        bar(CB_WFULL + slot));
+                            ++wv;
+                            ++w_issued;
+                            ++wl;
+                        }
+                    }
+                }
+            }
+        } else if (warp == 1) {
+            // ---------------- MMA issuer ----------------
+            if (lane == 0) {
+                const uint32_t idesc = idesc_bf16(kM, g.Npad);
+                const uint32_t wcol = (uint32_t)g.Bw;    // window column stride in 16-byte units
+                const uint32_t tcol = (uint32_t)g.Npad;  // template column stride in 16-byte units
+                const uint64_t da_base = smem_desc(sbase + g.w_off, kColQ * g.Bw * 16u, 128);
+                const uint64_t db_base = smem_desc(sbase + g.t_off, kColQ * g.Npad * 16u, 128);
+                const uint32_t w_step = (uint32_t)g.ws_bytes >> 4, t_step = (uint32_t)g.ts_bytes >> 4;
+                uint32_t dD[G];
+#pragma unroll
+                for (int gi = 0; gi < G; ++gi) dD[gi] = tmem + (uint32_t)(gi * g.Npad);
+                constexpr int kSpan = (kColQ + G - 2) / kColQ + 1;  // window slabs one stage reads
+                uint32_t wv = wsc, tv = tsc, gg = grp;
+                for (int d0 = 0; d0 < g.P1 && ok; d0 += G, ++gg) {
+                    const int Gg = g.P1 - d0 < G ? g.P1 - d0 : G;
+                    const int nws = (m + Gg - 1 + kColQ - 1) / kColQ;
+                    if (gg >= 1) ok = mbar_wait(bar(CB_AEMPTY), (gg - 1) & 1, &s_abort);
+                    if (!ok) break;
+                    tc_fence_after();  // the drain's TMEM reads come before these MMAs
+                    int ww = 0;  // window slabs of the group waited for
+                    for (int s = 0; s < nstage && ok; ++s, ++tv) {
+                        const int u0 = s * kColQ;
+                        const int nq = m - u0 < kColQ ? m - u0 : kColQ;
+                        TC_TRACE(0, tv);
+                        const uint32_t tslot = tv % g.TS;
+                        ok = mbar_wait(bar(CB_TFULL + tslot), (tv / g.TS) & 1, &s_abort);
+                        int last = (u0 + nq - 1 + Gg - 1) / kColQ;
+                        last = last > nws - 1 ? nws - 1 : last;
+                        while (ok && ww <= last) {
+                            const uint32_t wi = wv + (uint32_t)ww;
+                            ok = mbar_wait(bar(CB_WFULL + wi % g.WS), (wi / g.WS) & 1, &s_abort);
+                            ++ww;
+                        }
+                        if (!ok) break;
+                        // descriptors: window slab s + e (e < kSpan), template slab tslot
+                        uint64_t dW[kSpan];
+#pragma unroll
+                        for (int e = 0; e < kSpan; ++e) dW[e] = da_base + (uint64_t)(((wv + s + e) % g.WS) * w_step);
+                        const uint64_t dT = db_base + (uint64_t)(tslot * t_step);
+                        const uint32_t acc0 = u0 > 0 ? 1u : 0u;
+                        TC_TRACE(1, tv);
+                        if (nq == kColQ && Gg == G) {
+#pragma unroll
+                            for (int q = 0; q < kColQ; ++q)
+#pragma unroll
+                                for (int gi = 0; gi < G; ++gi)
+                                    mma_bf16(dD[gi], dW[(q + gi) / kColQ] + (uint64_t)(((q + gi) % kColQ) * wcol),
+                                             dT + (uint64_t)(q * tcol), idesc, q > 0 ? 1u : acc0);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < kColQ; ++q)
+                                if (q < nq) {
+#pragma unroll
+                                    for (int gi = 0; gi < G; ++gi)
+                                        if (gi < Gg)
+                                            mma_bf16(dD[gi],
+                                                     dW[(q + gi) / kColQ] + (uint64_t)(((q + gi) % kColQ) * wcol),
+                                                     dT + (uint64_t)(q * tcol), idesc, q > 0 ? 1u : acc0);
+                                }
+                        }
+                        mma_issued += (uint32_t)(nq * Gg);
+                        if (s == nstage - 1) mma_commit(bar(CB_AFULL));
+                        mma_commit(bar(CB_STG + tv % kColNS));
+                        TC_TRACE(2, tv);
+                    }
+                    wv += (uint32_t)nws;
+                }
+            }
+        } else if (warp == 2) {
+            // ---------------- slab release relay ----------------
+            if (lane == 0) {
+                uint32_t wv = wsc, tv = tsc;
+                for (int d0 = 0; d0 < g.P1 && ok; d0 += G) {
+                    const int Gg = g.P1 - d0 < G ? g.P1 - d0 : G;
+                    const int nws = (m + Gg - 1 + kColQ - 1) / kColQ;
+                    for (int s = 0; s < nstage && ok; ++s, ++tv) {
+                        ok = mbar_wait(bar(CB_STG + tv % kColNS), (tv / kColNS) & 1, &s_abort);
+                        if (!ok) break;
+                        // template slab s; window slab s (its last reader is
+                        // stage s); at the group's end every remaining slab
+                        mbar_arrive(bar(CB_TEMPTY + tv % g.TS));
+                        const int hi = s == nstage - 1 ? nws : s + 1;
+                        for (int b = s; b < hi; ++b) mbar_arrive(bar(CB_WEMPTY + (wv + (uint32_t)b) % g.WS));
+                        TC_TRACE(3, tv);
+                    }
+                    wv += (uint32_t)nws;
+                }
+            }
+        } else if (warp >= 4) {
+            // ---------------- drain: diagonal sums ----------------
+            // Thread t holds accumulator row y = t (its TMEM lane) and stores
+            // the band entries D[y][c], 0 <= y - c < 2R+1, c < m, skewed into
+            // bk[y - c][c]; then nparts threads per dy sum row dy of bk.
+            const int t = tid - 128;
+            const int quarter = warp & 3;
+            const int y = quarter * 32 + lane;
+            const int Sb = g.bk_stride;
+            int nparts = 128 / g.P1;
+            nparts = nparts > 4 ? 4 : nparts;
+            const int dy = t % g.P1, part = t / g.P1;
+            const int c0 = part * m / nparts, c1 = (part + 1) * m / nparts;
+            // 16-column chunks that hold band entries of this warp's rows
+            int clo = quarter * 32 - 2 * R;
+            clo = clo < 0 ? 0 : clo / 16;
+            int chi = quarter * 32 + 31;
+            chi = chi > m - 1 ? m - 1 : chi;
+            chi = chi / 16;
+            float* bk = reinterpret_cast<float*>(smem + g.bk_off);
+            const int dummy = g.P1 * Sb + lane;  // per-lane slot for entries outside the band
+            float* pbuf = reinterpret_cast<float*>(smem + g.part_off);
+            float* out = maps + (size_t)k * g.P1 * g.P1;
+            const uint32_t lbase = tmem + ((uint32_t)(quarter * 32) << 16);
+            uint32_t gg = grp;
+            for (int d0 = 0; d0 < g.P1 && ok; d0 += G, ++gg) {
+                const int Gg = g.P1 - d0 < G ? g.P1 - d0 : G;
+                // one thread takes the bounded wait; the named barrier below
+                // is then reached by all four warps in bounded time
+                if (t == 0) {
+                    TC_TRACE(4, gg);
+                    s_go = mbar_wait(bar(CB_AFULL), gg & 1, &s_abort) ? 1 : 0;
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                ok = s_go != 0;
+                if (!ok) break;
+                mbar_wait(bar(CB_AFULL), gg & 1, &s_abort);  // completed already: acquire for this thread
+                tc_fence_after();
+                for (int gi = 0; gi < Gg; ++gi) {
+                    // the band chunks of this warp's rows, kColDB at a time:
+                    // one batch of loads and one wait per batch (the load
+                    // latency is paid once per batch)
+                    for (int cb = clo; cb <= chi; cb += kColDB) {
+                        uint32_t r[kColDB * 16];
+#pragma unroll
+                        for (int k2 = 0; k2 < kColDB; ++k2) {
+                            if (cb + k2 <= chi) {
+                                asm volatile(
+                                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                                    "%12,%13,%14,%15}, [%16];"
+                                    : "=r"(r[k2 * 16 + 0]), "=r"(r[k2 * 16 + 1]), "=r"(r[k2 * 16 + 2]),
+                                      "=r"(r[k2 * 16 + 3]), "=r"(r[k2 * 16 + 4]), "=r"(r[k2 * 16 + 5]),
+                                      "=r"(r[k2 * 16 + 6]), "=r"(r[k2 * 16 + 7]), "=r"(r[k2 * 16 + 8]),
+                                      "=r"(r[k2 * 16 + 9]), "=r"(r[k2 * 16 + 10]), "=r"(r[k2 * 16 + 11]),
+                                      "=r"(r[k2 * 16 + 12]), "=r"(r[k2 * 16 + 13]), "=r"(r[k2 * 16 + 14]),
+                                      "=r"(r[k2 * 16 + 15])
+                                    : "r"(lbase + (uint32_t)(gi * g.Npad + (cb + k2) * 16)));
+                            }
+                        }
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (gi == Gg - 1 && cb + kColDB > chi) {  // every accumulator read: the next group may start
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(bar(CB_AEMPTY));
+                        }
+                        // band entries to bk[y - col][col]; the others to this
+                        // lane's dummy slot (no branches: the store always runs)
+#pragma unroll
+                        for (int k2 = 0; k2 < kColDB; ++k2) {
+                            if (cb + k2 <= chi) {
+                                const int col0 = (cb + k2) * 16;
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    const int col = col0 + j, d = y - col;
+                                    const bool in = (unsigned)d < (unsigned)g.P1 && col < m;
+                                    bk[in ? d * Sb + col : dummy] = __uint_as_float(r[k2 * 16 + j]);
+                                }
+                            }
+                        }
+                    }
+                    if (clo > chi && gi == Gg - 1) {  // a warp without band entries still releases TMEM
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(bar(CB_AEMPTY));
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (gi > 0 && t < g.P1) {  // finish offset d0 + gi - 1
+                        const float* pb = pbuf + ((gi - 1) & 1) * 128;
+                        float sum = 0.f;
+                        for (int p = 0; p < nparts; ++p) sum += pb[p * g.P1 + t];
+                        out[t * g.P1 + d0 + gi - 1] = sum;
+                    }
+                    if (part < nparts) {  // eight independent chains keep the loads in flight
+                        float sa[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) sa[e] = 0.f;
+                        const float* row = bk + dy * Sb;
+                        int c = c0;
+                        for (; c + 8 <= c1; c += 8) {
+                            float v[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) v[e] = row[c + e];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) sa[e] += v[e];
+                        }
+#pragma unroll
+                        for (int e = 0; e < 7; ++e)
+                            if (c + e < c1) sa[e] += row[c + e];
+                        pbuf[(gi & 1) * 128 + part * g.P1 + dy] =
+                            ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                }
+                if (t < g.P1) {  // finish offset d0 + Gg - 1
+                    const float* pb = pbuf + ((Gg - 1) & 1) * 128;
+                    float sum = 0.f;
+                    for (int p = 0; p < nparts; ++p) sum += pb[p * g.P1 + t];
+                    out[t * g.P1 + d0 + Gg - 1] = sum;
+                }
+                if (t == 0) TC_TRACE(5, gg);
+            }
+        }
+        for (int d0 = 0; d0 < g.P1; d0 += G) {
+            const int Gg = g.P1 - d0 < G ? g.P1 - d0 : G;
+            wsc += (uint32_t)((m + Gg - 1 + kColQ - 1) / kColQ);
+            tsc += (uint32_t)nstage;
+            ++grp;
+        }
+        if (!ok) atomicExch(&s_abort, 1);
+    }
+
+    if (*reinterpret_cast<volatile int*>(&s_abort)) {
+        if (warp == 0 && lane == 0) {  // let every copy in flight land
+            for (uint32_t i = 0; i < (uint32_t)g.WS && i < w_issued; ++i) {
+                const uint32_t wi = w_issued - 1 - i;
+                mbar_wait_short(bar(CB_WFULL + wi % g.WS), (wi / g.WS) & 1);
+            }
+            for (uint32_t i = 0; i < (uint32_t)g.TS && i < t_issued; ++i) {
+                const uint32_t ti = t_issued - 1 - i;
+                mbar_wait_short(bar(CB_TFULL + ti % g.TS), (ti / g.TS) & 1);
+            }
+        }
+        if (warp == 1 && lane == 0 && mma_issued > 0) {  // and every MMA issued
+            mma_commit(bar(CB_FIN));
+            mbar_wait_short(bar(CB_FIN), 0);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort && tid == 0) atomicExch(err, 1);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -507,10 +951,50 @@ int pick_U(int m, int R) {
 size_t corr_tc_smem_bytes(int m, int R) { return (size_t)tc_geom(m, R, pick_U(m, R)).smem; }
 
 cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                           const PointStat* stats, float* maps, int* err_flag, cudaStream_t st) {
+                           const PointStat* stats, float* maps, int* err_flag, int form, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (ref.dtype != SFOC_DTYPE_BF16 || sen.dtype != SFOC_DTYPE_BF16 || ref.z != 12) return cudaErrorNotSupported;
     if (2 * R + 1 > kM || m > kMaxTemplate) return cudaErrorNotSupported;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (m + 2 * R <= kM && form != 1) {
+        const ColGeom c = col_geom(m, R);
+        // window slab: box {8, Bw rows, 8 columns, 2 chunks}; template slab: {8, Npad, 8, 2}
+        alignas(64) CUtensorMap tmW, tmT;
+        if (!make_map(&tmW, ref.cm, (uint64_t)ref.H, (uint64_t)ref.W, (uint32_t)c.Bw, kColQ, 2) ||
+            !make_map(&tmT, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, (uint32_t)c.Npad, kColQ, 2))
+            return cudaErrorNotSupported;
+        const int grid = n < sms ? n : sms;
+        cudaError_t e = cudaErrorNotSupported;
+#define SFOC_COL_CASE(GV)                                                                                     \
+    case GV:                                                                                                  \
+        e = cudaFuncSetAttribute(k_corr_tc_col<GV>, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);     \
+        if (e != cudaSuccess) return e;                                                                       \
+        k_corr_tc_col<GV><<<grid, kThreads, c.smem, st>>>(tmW, tmT, pts, n, m, R, stats, maps, err_flag);     \
+        return cudaGetLastError();
+        switch (c.G) {
+            SFOC_COL_CASE(1)
+            SFOC_COL_CASE(2)
+            SFOC_COL_CASE(3)
+            SFOC_COL_CASE(4)
+            SFOC_COL_CASE(5)
+            SFOC_COL_CASE(6)
+            SFOC_COL_CASE(7)
+            SFOC_COL_CASE(8)
+            SFOC_COL_CASE(9)
+            SFOC_COL_CASE(10)
+            SFOC_COL_CASE(11)
+            SFOC_COL_CASE(12)
+            SFOC_COL_CASE(13)
+            SFOC_COL_CASE(14)
+            SFOC_COL_CASE(15)
+            SFOC_COL_CASE(16)
+            default: break;
+        }
+#undef SFOC_COL_CASE
+        return e;
+    }
     const int U = pick_U(m, R);
     const TcGeom g = tc_geom(m, R, U);
     if (g.NA < 2 || g.JS > 512 || g.AW > 256) return cudaErrorNotSupported;
@@ -523,9 +1007,6 @@ cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts,
     if (!make_map(&tmA, ref.rm, (uint64_t)ref.W, (uint64_t)ref.H, (uint32_t)g.AW, kY, 2)) return cudaErrorNotSupported;
     if (!make_map(&tmB, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, brow, 1, 1)) return cudaErrorNotSupported;
     if (!make_map(&tmB2, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, brow2, 1, 1)) return cudaErrorNotSupported;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = n < sms ? n : sms;
     const int nq = g.Npad / 16;
     const size_t smem = (size_t)g.smem;

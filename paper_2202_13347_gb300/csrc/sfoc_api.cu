@@ -549,9 +549,9 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
     if (path == SFOC_CORR_AUTO) path = ref->c.dtype == SFOC_DTYPE_BF16 ? SFOC_CORR_IGEMM_TC : SFOC_CORR_DIRECT_F32;
     if (path == SFOC_CORR_DIRECT_F32 && ref->c.dtype != SFOC_DTYPE_F32)
         return fail(ctx, SFOC_ERR_UNSUPPORTED, "DIRECT_F32 needs F32 cubes");
-    if (path == SFOC_CORR_IGEMM_TC && ref->c.dtype != SFOC_DTYPE_BF16)
-        return fail(ctx, SFOC_ERR_UNSUPPORTED, "IGEMM_TC needs BF16 cubes");
-    if (path != SFOC_CORR_DIRECT_F32 && path != SFOC_CORR_IGEMM_TC)
+    if ((path == SFOC_CORR_IGEMM_TC || path == SFOC_CORR_TC_TOEPLITZ) && ref->c.dtype != SFOC_DTYPE_BF16)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
+    if (path != SFOC_CORR_DIRECT_F32 && path != SFOC_CORR_IGEMM_TC && path != SFOC_CORR_TC_TOEPLITZ)
         return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown corr_path");
     DeviceGuard g(ctx->device);
     if (n == 0) return SFOC_OK;
@@ -576,7 +576,8 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
         if (path == SFOC_CORR_DIRECT_F32)
             e = launch_corr_f32(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->stream);
         else
-            e = launch_corr_tc(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->d_err, ctx->stream);
+            e = launch_corr_tc(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->d_err,
+                               path == SFOC_CORR_TC_TOEPLITZ ? 1 : 0, ctx->stream);
     }
     if (e == cudaErrorInvalidValue || e == cudaErrorNotSupported)
         return fail(ctx, SFOC_ERR_UNSUPPORTED, "correlation kernel does not support this m / R");

@@ -46,12 +46,12 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def gpu_bf16(ctx, b, pair, want_maps=False):
+def gpu_bf16(ctx, b, pair, want_maps=False, path=None):
     p = b.params(dtype=b.DTYPE_BF16)
     rc = ctx.sfoc_build(dev(pair.ref), p=p)
     sc = ctx.sfoc_build(dev(pair.sen), p=p)
-    return ctx.fastncc_match(rc, sc, dev(pair.points), pair.m, pair.R, corr_path=b.CORR_IGEMM_TC,
-                             want_maps=want_maps)
+    return ctx.fastncc_match(rc, sc, dev(pair.points), pair.m, pair.R,
+                             corr_path=b.CORR_IGEMM_TC if path is None else path, want_maps=want_maps)
 
 
 def oracle_side(orc, pair, roi=False):
@@ -130,16 +130,35 @@ def check(g, o_r, o_u, regions, R, report):
     return st
 
 
-@pytest.mark.parametrize("H,W,m,R,npts,seed", [
+SMALL = [
     (70, 83, 9, 4, 12, 11),
     (96, 61, 10, 3, 9, 12),     # even template
     (64, 64, 1, 2, 16, 13),     # m = 1
     (60, 75, 15, 0, 9, 14),     # R = 0
     (150, 140, 31, 12, 20, 15),
     (110, 120, 17, 7, 25, 16),
-])
-def test_tc_small_cases(b, ctx, orc, H, W, m, R, npts, seed):
+    (190, 200, 64, 31, 8, 17),  # m + 2R = 126: column form, 4 offsets per group
+]
+
+
+@pytest.mark.parametrize("form", ["auto", "toeplitz"])
+@pytest.mark.parametrize("H,W,m,R,npts,seed", SMALL)
+def test_tc_small_cases(b, ctx, orc, H, W, m, R, npts, seed, form):
+    """Both tensor-core forms on the same inputs: the column form (chosen
+    when m + 2R <= 128) and the Toeplitz form."""
     pair = tiny_pair(seed, H, W, m, R, npts, shift=(2, -1))
+    g = gpu_bf16(ctx, b, pair, want_maps=True, path=b.CORR_TC_TOEPLITZ if form == "toeplitz" else None)
+    ctx.sync()
+    o_r, o_u, regions = oracle_side(orc, pair)
+    check(g, o_r, o_u, regions, R, {})
+
+
+@pytest.mark.parametrize("H,W,m,R,npts,seed", [
+    (230, 240, 61, 35, 8, 18),   # m + 2R = 131: Toeplitz form under the default path
+    (200, 190, 101, 14, 6, 19),  # m + 2R = 129
+])
+def test_tc_wide_windows(b, ctx, orc, H, W, m, R, npts, seed):
+    pair = tiny_pair(seed, H, W, m, R, npts, shift=(-3, 2))
     g = gpu_bf16(ctx, b, pair, want_maps=True)
     ctx.sync()
     o_r, o_u, regions = oracle_side(orc, pair)
@@ -157,9 +176,10 @@ def test_bf16_cube_is_rounded_oracle_cube(b, ctx, orc):
     assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 2e-5)
 
 
-def test_tc_config1(b, ctx, orc):
+@pytest.mark.parametrize("form", ["auto", "toeplitz"])
+def test_tc_config1(b, ctx, orc, form):
     pair = config1()
-    g = gpu_bf16(ctx, b, pair, want_maps=True)
+    g = gpu_bf16(ctx, b, pair, want_maps=True, path=b.CORR_TC_TOEPLITZ if form == "toeplitz" else None)
     ctx.sync()
     o_r, o_u, regions = oracle_side(orc, pair)
     rep = {}
