@@ -484,16 +484,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 // N = roundup(m, 16) instead of the (m+2R) m narrow MMAs of the Toeplitz form.
 //
 // Operands come from the column-major pixel layout (cm) in slabs of kColQ
-// image columns, one 4-D tensor copy each ({8 channels, rows, kColQ
-// columns, 2 chunks}): every copy request costs a fixed ~200 cycles of the
-// copy engine, so few large requests matter more than exact extents.
-//   template slab s of a group: template columns 8s .. 8s+7, Npad rows;
-//   window slab b of a group:   window columns d0 + 8b .. d0 + 8b + 7, Bw
-//                               rows (Bw = m + 2R rounded up to 8, <= 128).
-// Columns and rows past the region are loaded too (or zero filled past the
-// image) and never reach a used accumulator entry; MMA rows past Bw read
-// further bytes of shared memory and only feed accumulator rows that the
-// diagonal sums never use.
+// image columns, one 4-D tensor copy each.  The copy engine moves about one
+// innermost-dimension row per cycle, so the map's innermost dimension is 8
+// consecutive pixels of one 8-channel chunk (128 contiguous bytes), its
+// second dimension the pixel row with a 16-byte stride, traversed with an
+// element stride of 8: a box row is then 8 pixels starting at any row.
+//   template slab s of a group: template columns 8s .. 8s+7, roundup(m, 8)
+//                               rows each;
+//   window slab b of a group:   window columns d0 + 8b .. d0 + 8b + 7,
+//                               roundup(m + 2R, 8) rows each.
+// Columns past the region are loaded too (or zero filled past the image);
+// rows past the region read on into the next image column (the cube buffers
+// carry padding for the last one).  None of it reaches a used accumulator
+// entry: an MMA reads 128 window rows and roundup(m, 16) template rows from
+// a column's start, and rows past the region only feed accumulator rows
+// y >= m + 2R or columns i >= m, which no diagonal sum reads.
 // The issuer works in stages of kColQ template columns: it waits once for
 // the stage's slabs, then issues the stage's kColQ x G MMAs as straight code
 // from precomputed descriptors (control flow between tcgen05.mma
@@ -511,14 +516,19 @@ constexpr int kColMaxTS = 3;
 // more barriers than that no barrier completes twice before the relay has
 // seen the first phase.
 constexpr int kColNS = 8;
-constexpr int kColDB = 6;  // TMEM chunks of 16 columns per drain load batch
+constexpr int kColDB = 4;  // TMEM chunks of 16 columns per drain load batch
+// 12 warps: 0 TMA producer, 1 MMA issuer, 2 release relay, 3 idle,
+// 4..11 drain (two teams of four, one warp per TMEM lane quarter each)
+constexpr int kColThreads = 384;
+constexpr int kColDrain = 256;
 
 struct ColGeom {
-    int m, R, P1, Lw, Bw, Npad, G;
+    int m, R, P1, Lw, Npad, G;
+    int wrows, trows;          // rows loaded per window / template column (multiples of 8)
     int WS, TS;                // window / template slab ring sizes
     int ws_bytes, ts_bytes;    // slab sizes
     int t_off, w_off, bk_off;  // shared-memory offsets
-    int part_off;              // partial diagonal sums: 2 x 128 floats
+    int part_off;              // partial diagonal sums: 2 x 256 floats
     int bk_stride;             // band buffer row stride in floats (odd: no bank conflicts)
     int smem;
 };
@@ -529,23 +539,24 @@ __host__ __device__ inline ColGeom col_geom(int m, int R) {
     c.R = R;
     c.P1 = 2 * R + 1;
     c.Lw = m + 2 * R;
-    c.Bw = (c.Lw + 7) / 8 * 8;
-    c.Bw = c.Bw > kM ? kM : c.Bw;
     c.Npad = (m + 15) / 16 * 16;
     int G = 512 / c.Npad;
     G = G > c.P1 ? c.P1 : G;
     c.G = G > kColMaxG ? kColMaxG : G;
     c.WS = (kColQ + c.G - 1 + kColQ - 1) / kColQ + 2;  // slabs one stage reads, plus two in flight
     c.TS = kColMaxTS;
-    c.ws_bytes = 2 * kColQ * c.Bw * 16;
-    c.ts_bytes = 2 * kColQ * c.Npad * 16;
+    c.wrows = (c.Lw + 7) / 8 * 8;
+    c.trows = (m + 7) / 8 * 8;
+    c.ws_bytes = 2 * kColQ * c.wrows * 16;
+    c.ts_bytes = 2 * kColQ * c.trows * 16;
     c.t_off = 0;
     c.w_off = c.TS * c.ts_bytes;
     c.bk_stride = c.m | 1;
     c.bk_off = c.w_off + c.WS * c.ws_bytes;
     c.part_off = c.bk_off + ((c.P1 * c.bk_stride + 32) * 4 + 127) / 128 * 128;  // + 32 dummy slots
-    // an MMA on the last window slab may read up to 2048 - 16 Bw bytes past it
-    c.smem = c.part_off + 2 * 128 * 4 + (2048 - 16 * c.Bw);
+    // an MMA on the last window slab may read up to 2048 - 16 wrows bytes
+    // past it (template slabs are followed by the window slabs)
+    c.smem = c.part_off + 2 * kColDrain * 4 + (2048 - 16 * c.wrows);
     if (c.smem > 225 * 1024) {  // drop the third template slab (static shared memory needs the rest)
         c.TS = 2;
         c.w_off -= c.ts_bytes;
@@ -571,7 +582,7 @@ enum {
 };
 
 template <int G>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kColThreads, 1)
     k_corr_tc_col(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmT,
                   const int32_t* __restrict__ pts, int n, int m, int R, const PointStat* __restrict__ stats,
                   float* __restrict__ maps, int* __restrict__ err) {
@@ -600,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int i = 0; i < kColNS; ++i) mbar_init(bar(CB_STG + i), 1);
         mbar_init(bar(CB_AFULL), 1);
-        mbar_init(bar(CB_AEMPTY), 4);  // the four drain warps
+        mbar_init(bar(CB_AEMPTY), kColDrain / 32);  // every drain warp
         mbar_init(bar(CB_FIN), 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -672,44 +683,54 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---------------- MMA issuer ----------------
             if (lane == 0) {
                 const uint32_t idesc = idesc_bf16(kM, g.Npad);
-                const uint32_t wcol = (uint32_t)g.Bw;    // window column stride in 16-byte units
-                const uint32_t tcol = (uint32_t)g.Npad;  // template column stride in 16-byte units
-                const uint64_t da_base = smem_desc(sbase + g.w_off, kColQ * g.Bw * 16u, 128);
-                const uint64_t db_base = smem_desc(sbase + g.t_off, kColQ * g.Npad * 16u, 128);
+                const uint32_t wcol = (uint32_t)g.wrows;  // window column stride in 16-byte units
+                const uint32_t tcol = (uint32_t)g.trows;  // template column stride in 16-byte units
+                const uint64_t da_base = smem_desc(sbase + g.w_off, kColQ * g.wrows * 16u, 128);
+                const uint64_t db_base = smem_desc(sbase + g.t_off, kColQ * g.trows * 16u, 128);
                 const uint32_t w_step = (uint32_t)g.ws_bytes >> 4, t_step = (uint32_t)g.ts_bytes >> 4;
                 uint32_t dD[G];
 #pragma unroll
                 for (int gi = 0; gi < G; ++gi) dD[gi] = tmem + (uint32_t)(gi * g.Npad);
                 constexpr int kSpan = (kColQ + G - 2) / kColQ + 1;  // window slabs one stage reads
-                uint32_t wv = wsc, tv = tsc, gg = grp;
+                uint32_t stg = tsc % kColNS;                         // stage-done barrier of the next stage
+                // ring positions kept as running slot / parity pairs (no
+                // divisions on the issue path)
+                uint32_t gg = grp, tvt = tsc;                        // tvt: stage count (tracing)
+                uint32_t ts = tsc % g.TS, tph = (tsc / g.TS) & 1;  // template slab of the next stage
+                uint32_t ws = wsc % g.WS, wph = (wsc / g.WS) & 1;  // window slab 0 of the current group
                 for (int d0 = 0; d0 < g.P1 && ok; d0 += G, ++gg) {
                     const int Gg = g.P1 - d0 < G ? g.P1 - d0 : G;
                     const int nws = (m + Gg - 1 + kColQ - 1) / kColQ;
                     if (gg >= 1) ok = mbar_wait(bar(CB_AEMPTY), (gg - 1) & 1, &s_abort);
                     if (!ok) break;
                     tc_fence_after();  // the drain's TMEM reads come before these MMAs
-                    int ww = 0;  // window slabs of the group waited for
-                    for (int s = 0; s < nstage && ok; ++s, ++tv) {
+                    uint32_t nws_slot = ws, nws_ph = wph;  // next window slab to wait for
+                    int ww = 0;                            // window slabs of the group waited for
+                    uint32_t wcur = ws;                    // slot of window slab s
+                    for (int s = 0; s < nstage && ok; ++s) {
                         const int u0 = s * kColQ;
                         const int nq = m - u0 < kColQ ? m - u0 : kColQ;
-                        TC_TRACE(0, tv);
-                        const uint32_t tslot = tv % g.TS;
-                        ok = mbar_wait(bar(CB_TFULL + tslot), (tv / g.TS) & 1, &s_abort);
+                        TC_TRACE(0, tvt);
+                        ok = mbar_wait(bar(CB_TFULL + ts), tph, &s_abort);
                         int last = (u0 + nq - 1 + Gg - 1) / kColQ;
                         last = last > nws - 1 ? nws - 1 : last;
                         while (ok && ww <= last) {
-                            const uint32_t wi = wv + (uint32_t)ww;
-                            ok = mbar_wait(bar(CB_WFULL + wi % g.WS), (wi / g.WS) & 1, &s_abort);
+                            ok = mbar_wait(bar(CB_WFULL + nws_slot), nws_ph, &s_abort);
+                            if (++nws_slot == (uint32_t)g.WS) { nws_slot = 0; nws_ph ^= 1u; }
                             ++ww;
                         }
                         if (!ok) break;
-                        // descriptors: window slab s + e (e < kSpan), template slab tslot
+                        // descriptors: window slabs s .. s+kSpan-1, template slab ts
                         uint64_t dW[kSpan];
 #pragma unroll
-                        for (int e = 0; e < kSpan; ++e) dW[e] = da_base + (uint64_t)(((wv + s + e) % g.WS) * w_step);
-                        const uint64_t dT = db_base + (uint64_t)(tslot * t_step);
+                        for (int e = 0; e < kSpan; ++e) {
+                            uint32_t sl = wcur + (uint32_t)e;
+                            if (sl >= (uint32_t)g.WS) sl -= (uint32_t)g.WS;
+                            dW[e] = da_base + (uint64_t)(sl * w_step);
+                        }
+                        const uint64_t dT = db_base + (uint64_t)(ts * t_step);
                         const uint32_t acc0 = u0 > 0 ? 1u : 0u;
-                        TC_TRACE(1, tv);
+                        TC_TRACE(1, tvt);
                         if (nq == kColQ && Gg == G) {
 #pragma unroll
                             for (int q = 0; q < kColQ; ++q)
@@ -731,10 +752,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         mma_issued += (uint32_t)(nq * Gg);
                         if (s == nstage - 1) mma_commit(bar(CB_AFULL));
-                        mma_commit(bar(CB_STG + tv % kColNS));
-                        TC_TRACE(2, tv);
+                        mma_commit(bar(CB_STG + stg));
+                        if (++stg == (uint32_t)kColNS) stg = 0;
+                        TC_TRACE(2, tvt);
+                        ++tvt;
+                        if (++ts == (uint32_t)g.TS) { ts = 0; tph ^= 1u; }
+                        if (++wcur == (uint32_t)g.WS) wcur = 0;
                     }
-                    wv += (uint32_t)nws;
+                    // the next group's window slab 0 follows this group's last slab
+                    for (int b2 = 0; b2 < nws; ++b2)
+                        if (++ws == (uint32_t)g.WS) { ws = 0; wph ^= 1u; }
                 }
             }
         } else if (warp == 2) {
@@ -759,23 +786,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         } else if (warp >= 4) {
             // ---------------- drain: diagonal sums ----------------
-            // Thread t holds accumulator row y = t (its TMEM lane) and stores
-            // the band entries D[y][c], 0 <= y - c < 2R+1, c < m, skewed into
-            // bk[y - c][c]; then nparts threads per dy sum row dy of bk.
-            const int t = tid - 128;
+            // Thread t holds accumulator row y (its TMEM lane) and stores the
+            // band entries D[y][c], 0 <= y - c < 2R+1, c < m, skewed into
+            // bk[y - c][c]; the two teams split each warp's 16-column chunks.
+            // Then nparts threads per dy sum row dy of bk.
+            const int t = tid - 128;  // 0 .. kColDrain-1
+            const int team = (warp - 4) >> 2;
             const int quarter = warp & 3;
             const int y = quarter * 32 + lane;
             const int Sb = g.bk_stride;
-            int nparts = 128 / g.P1;
-            nparts = nparts > 4 ? 4 : nparts;
+            int nparts = kColDrain / g.P1;
+            nparts = nparts > 8 ? 8 : nparts;
             const int dy = t % g.P1, part = t / g.P1;
             const int c0 = part * m / nparts, c1 = (part + 1) * m / nparts;
-            // 16-column chunks that hold band entries of this warp's rows
+            // 16-column chunks that hold band entries of this warp's rows,
+            // split between the teams
             int clo = quarter * 32 - 2 * R;
             clo = clo < 0 ? 0 : clo / 16;
             int chi = quarter * 32 + 31;
             chi = chi > m - 1 ? m - 1 : chi;
             chi = chi / 16;
+            {
+                const int nch = chi - clo + 1, h0 = (nch + 1) / 2;
+                if (team == 0) chi = clo + h0 - 1;
+                else clo = clo + h0;
+            }
             float* bk = reinterpret_cast<float*>(smem + g.bk_off);
             const int dummy = g.P1 * Sb + lane;  // per-lane slot for entries outside the band
             float* pbuf = reinterpret_cast<float*>(smem + g.part_off);
@@ -785,20 +820,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int d0 = 0; d0 < g.P1 && ok; d0 += G, ++gg) {
                 const int Gg = g.P1 - d0 < G ? g.P1 - d0 : G;
                 // one thread takes the bounded wait; the named barrier below
-                // is then reached by all four warps in bounded time
+                // is then reached by every drain warp in bounded time
                 if (t == 0) {
                     TC_TRACE(4, gg);
                     s_go = mbar_wait(bar(CB_AFULL), gg & 1, &s_abort) ? 1 : 0;
                 }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"r"(kColDrain) : "memory");
                 ok = s_go != 0;
                 if (!ok) break;
                 mbar_wait(bar(CB_AFULL), gg & 1, &s_abort);  // completed already: acquire for this thread
                 tc_fence_after();
                 for (int gi = 0; gi < Gg; ++gi) {
-                    // the band chunks of this warp's rows, kColDB at a time:
-                    // one batch of loads and one wait per batch (the load
-                    // latency is paid once per batch)
+                    // this warp's chunks, kColDB at a time: one batch of loads
+                    // and one wait per batch (the load latency is paid once)
                     for (int cb = clo; cb <= chi; cb += kColDB) {
                         uint32_t r[kColDB * 16];
 #pragma unroll
@@ -842,9 +876,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(bar(CB_AEMPTY));
                     }
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    asm volatile("bar.sync 1, %0;" ::"r"(kColDrain) : "memory");
                     if (gi > 0 && t < g.P1) {  // finish offset d0 + gi - 1
-                        const float* pb = pbuf + ((gi - 1) & 1) * 128;
+                        const float* pb = pbuf + ((gi - 1) & 1) * kColDrain;
                         float sum = 0.f;
                         for (int p = 0; p < nparts; ++p) sum += pb[p * g.P1 + t];
                         out[t * g.P1 + d0 + gi - 1] = sum;
@@ -865,13 +899,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int e = 0; e < 7; ++e)
                             if (c + e < c1) sa[e] += row[c + e];
-                        pbuf[(gi & 1) * 128 + part * g.P1 + dy] =
+                        pbuf[(gi & 1) * kColDrain + part * g.P1 + dy] =
                             ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
                     }
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    asm volatile("bar.sync 1, %0;" ::"r"(kColDrain) : "memory");
                 }
                 if (t < g.P1) {  // finish offset d0 + Gg - 1
-                    const float* pb = pbuf + ((Gg - 1) & 1) * 128;
+                    const float* pb = pbuf + ((Gg - 1) & 1) * kColDrain;
                     float sum = 0.f;
                     for (int p = 0; p < nparts; ++p) sum += pb[p * g.P1 + t];
                     out[t * g.P1 + d0 + Gg - 1] = sum;
@@ -940,6 +974,26 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t d1, uint64_t d2, uint
     return r == CUDA_SUCCESS;
 }
 
+// 4-D bf16 view of a column-major chunked cube [2][W][H][8] whose innermost
+// dimension is 8 pixels x 8 channels (128 contiguous bytes) and whose second
+// dimension is the pixel row (16-byte stride) traversed with stride 8: a
+// box {64, rows, cols, 2} loads, per column and chunk, `rows` consecutive
+// pixels from any start row as rows/8 runs of 128 bytes.  The last run of
+// a column may read up to 7 pixels past the column (the cube buffers are
+// padded for the last column).
+bool make_map_rows8(CUtensorMap* map, const void* base, uint64_t H, uint64_t W, uint32_t rows, uint32_t cols) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {64, H, W, 2};
+    cuuint64_t strides[3] = {16, 16 * H, 16 * H * W};
+    cuuint32_t box[4] = {64, rows, cols, 2};
+    cuuint32_t es[4] = {1, 8, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 int pick_U(int m, int R) {
     TcGeom g = tc_geom(m, R, 8);
     if (g.NA >= 3) return 8;
@@ -960,10 +1014,10 @@ cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (m + 2 * R <= kM && form != 1) {
         const ColGeom c = col_geom(m, R);
-        // window slab: box {8, Bw rows, 8 columns, 2 chunks}; template slab: {8, Npad, 8, 2}
+        // slabs of 8 columns x 2 chunks, rows in 128-byte runs of 8 pixels
         alignas(64) CUtensorMap tmW, tmT;
-        if (!make_map(&tmW, ref.cm, (uint64_t)ref.H, (uint64_t)ref.W, (uint32_t)c.Bw, kColQ, 2) ||
-            !make_map(&tmT, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, (uint32_t)c.Npad, kColQ, 2))
+        if (!make_map_rows8(&tmW, ref.cm, (uint64_t)ref.H, (uint64_t)ref.W, (uint32_t)c.wrows, kColQ) ||
+            !make_map_rows8(&tmT, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, (uint32_t)c.trows, kColQ))
             return cudaErrorNotSupported;
         const int grid = n < sms ? n : sms;
         cudaError_t e = cudaErrorNotSupported;
@@ -971,7 +1025,7 @@ cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts,
     case GV:                                                                                                  \
         e = cudaFuncSetAttribute(k_corr_tc_col<GV>, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);     \
         if (e != cudaSuccess) return e;                                                                       \
-        k_corr_tc_col<GV><<<grid, kThreads, c.smem, st>>>(tmW, tmT, pts, n, m, R, stats, maps, err_flag);     \
+        k_corr_tc_col<GV><<<grid, kColThreads, c.smem, st>>>(tmW, tmT, pts, n, m, R, stats, maps, err_flag);  \
         return cudaGetLastError();
         switch (c.G) {
             SFOC_COL_CASE(1)

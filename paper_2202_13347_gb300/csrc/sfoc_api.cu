@@ -262,8 +262,10 @@ sfoc_status alloc_cube(sfoc_ctx* ctx, Cube& c, int H, int W, int z, int dtype) {
     if (dtype == SFOC_DTYPE_F32) {
         e = cudaMalloc(&c.f32, sizeof(float) * plane * z);
     } else {
-        e = cudaMalloc(&c.rm, sizeof(__nv_bfloat16) * 16 * (size_t)H * W);
-        if (e == cudaSuccess) e = cudaMalloc(&c.cm, sizeof(__nv_bfloat16) * 16 * (size_t)H * W);
+        // + 256 bytes: copies in 128-byte runs of pixels may read up to 112
+        // bytes past the last column
+        e = cudaMalloc(&c.rm, sizeof(__nv_bfloat16) * 16 * (size_t)H * W + 256);
+        if (e == cudaSuccess) e = cudaMalloc(&c.cm, sizeof(__nv_bfloat16) * 16 * (size_t)H * W + 256);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c.s1, sizeof(float) * plane);
     if (e == cudaSuccess) e = cudaMalloc(&c.s2, sizeof(float) * plane);
