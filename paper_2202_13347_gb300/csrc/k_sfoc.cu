@@ -23,6 +23,16 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Row stride (floats) of the smoothing input tile: room for the tile, its
+// halo and the 8-wide load blocks' overrun, a multiple of 4 floats (float4
+// rows) with an odd number of float4s, so that the two rows a quarter-warp
+// reads in the horizontal pass fall in different banks.
+__host__ __device__ inline int smooth_row_stride(int maxhal) {
+    int fw = (32 + 2 * maxhal + 8 + 3) / 4 * 4;
+    if ((fw / 4) % 2 == 0) fw += 4;
+    return fw;
+}
+
 // even taps: t0 x[0] + sum_q t[q] (x[-q] + x[+q]); `x` points at the centre, stride s
 __device__ __forceinline__ float conv_even(const float* x, int s, const float* t, int K) {
     float acc = t[0] * x[0];
@@ -176,47 +186,110 @@ __device__ __forceinline__ void smooth_channel(const float* __restrict__ Fk, siz
     }
 }
 
-template <int NO>
-__global__ void __launch_bounds__(kThreads) k_sfoc_smooth(const float* __restrict__ F, size_t fpitch,
-                                                           size_t fplane, int H, int W, SmoothTaps tp,
-                                                           float* __restrict__ c32, size_t cpitch, size_t cplane,
-                                                           __nv_bfloat16* __restrict__ rm,
-                                                           __nv_bfloat16* __restrict__ cm,
-                                                           float* __restrict__ s1, float* __restrict__ s2) {
-    extern __shared__ float sm[];
-    __shared__ float s_tap[2][kMaxSmoothRadius + 1];  // taps in shared memory: no local copy of the params
-    __shared__ int s_dil[kMaxDil];
-    if (threadIdx.x < 2 * (kMaxSmoothRadius + 1)) {
-        const int gg = threadIdx.x / (kMaxSmoothRadius + 1), q = threadIdx.x % (kMaxSmoothRadius + 1);
-        s_tap[gg][q] = tp.g[gg][q];
+// The paper's dilation rates 1, 2, 3 at compile time: every thread loads
+// its input span into registers once (float4 rows in the horizontal pass,
+// one column in the vertical pass) and applies all three rates from there,
+// instead of reading shared memory once per tap and rate.  Same arithmetic,
+// same order of operations per output as smooth_channel.
+template <int KD>
+__device__ __forceinline__ void smooth_channel_123(const float* __restrict__ Fk, size_t fpitch, int H, int W, int x0,
+                                                   int y0, const float* t, float* s_F, int FW, float* s_h, int HR,
+                                                   float (&Dk)[kSRows]) {
+    constexpr int hal = 3 * KD;
+    constexpr int IW = kSTW + 2 * hal, IH = kSTH + 2 * hal;
+    __syncthreads();  // previous channel done with s_F / s_h (and, at the start, the taps are written)
+    float tq[KD + 1];
+#pragma unroll
+    for (int q = 0; q <= KD; ++q) tq[q] = t[q];
+    for (int rr = threadIdx.x >> 3; rr < IH; rr += kThreads >> 3) {
+        const int yy = clampi(y0 + rr - hal, 0, H - 1);
+        const float* row = Fk + (size_t)yy * fpitch;
+        const int cb = (threadIdx.x & 7) * 8;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int cc = cb + c;
+            if (cc < IW) s_F[rr * FW + cc] = __ldg(row + clampi(x0 + cc - hal, 0, W - 1));
+        }
     }
-    if (threadIdx.x < kMaxDil) s_dil[threadIdx.x] = tp.dil[threadIdx.x];
-    const int maxhal = max(tp.halo[0], tp.halo[1]);
-    const int FW = kSTW + 2 * maxhal + 8;  // + slack: the 8-wide load blocks may overrun IW
-    const int HR = kSTH + 2 * maxhal;
-    float* s_F = sm;                       // HR x FW
-    float* s_h = s_F + HR * FW;            // n_dil x HR x kSTW
-    const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH;
+    __syncthreads();
+    // horizontal: task = (row, 8-column block); inputs cb .. cb + 8 + 2 hal
+    constexpr int NV = (8 + 2 * hal + 3) / 4;
+    for (int task = threadIdx.x; task < IH * 4; task += kThreads) {
+        const int rr = task >> 2, cb = (task & 3) * 8;
+        const float4* x4 = reinterpret_cast<const float4*>(s_F + rr * FW + cb);
+        float in[NV * 4];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float4 f = x4[v];
+            in[4 * v] = f.x;
+            in[4 * v + 1] = f.y;
+            in[4 * v + 2] = f.z;
+            in[4 * v + 3] = f.w;
+        }
+#pragma unroll
+        for (int r = 1; r <= 3; ++r) {
+            float o[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float a = tq[0] * in[hal + c];
+#pragma unroll
+                for (int q = 1; q <= KD; ++q) a = fmaf(tq[q], in[hal + c - q * r] + in[hal + c + q * r], a);
+                o[c] = a;
+            }
+            float4* dst = reinterpret_cast<float4*>(s_h + ((r - 1) * HR + rr) * kSTW + cb);
+            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
+    }
+    __syncthreads();
+    // vertical: task = (column, 8-row block)
+    const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
+#pragma unroll
+    for (int j = 0; j < kSRows; ++j) Dk[j] = 0.f;
+#pragma unroll
+    for (int r = 1; r <= 3; ++r) {
+        constexpr int kMaxSpan = kSRows + 2 * KD * 3;
+        const int span = kSRows + 2 * KD * r;
+        const float* x = s_h + ((r - 1) * HR + rb + hal - KD * r) * kSTW + col;
+        float in[kMaxSpan];
+#pragma unroll
+        for (int i = 0; i < kMaxSpan; ++i)
+            if (i < span) in[i] = x[i * kSTW];
+#pragma unroll
+        for (int j = 0; j < kSRows; ++j) {
+            float a = tq[0] * in[KD * r + j];
+#pragma unroll
+            for (int q = 1; q <= KD; ++q) a = fmaf(tq[q], in[KD * r + j - q * r] + in[KD * r + j + q * r], a);
+            Dk[j] += a;
+        }
+    }
+}
+
+// One group of `no` channels: smooth each channel (KDG > 0: radius KDG and
+// the rates 1, 2, 3 at compile time; KDG == 0: radius and rates at run
+// time), normalise the group in registers and write it out, and add its
+// values to the per-pixel sums a1 (g) and a2 (g^2).
+template <int NO, int KDG>
+__device__ __forceinline__ void smooth_group(int g, const float* __restrict__ F, size_t fpitch, size_t fplane, int H,
+                                             int W, const SmoothTaps& tp, const int* s_dil, const float* t,
+                                             float* s_F, int FW, float* s_h, int HR, int x0, int y0,
+                                             float* __restrict__ c32, size_t cpitch, size_t cplane,
+                                             __nv_bfloat16* __restrict__ rm, __nv_bfloat16* __restrict__ cm,
+                                             float (&a1)[kSRows], float (&a2)[kSRows]) {
+    constexpr int KO = NO > 0 ? NO : kMaxOrient;
+    const int no = NO > 0 ? NO : tp.no;
+    const bool bf = rm != nullptr;
     const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
     const int gx = x0 + col;
-    const bool bf = rm != nullptr;
-    const int no = NO > 0 ? NO : tp.no;
-    const int ng = tp.z / no;
-    constexpr int KO = NO > 0 ? NO : kMaxOrient;
-
-    float a1[kSRows], a2[kSRows];
+    float D[KO][kSRows];
 #pragma unroll
-    for (int j = 0; j < kSRows; ++j) a1[j] = a2[j] = 0.f;
-
-    for (int g = 0; g < ng; ++g) {
-        const int hal = g ? tp.halo[1] : tp.halo[0];
-        const int Kd = g ? tp.Kd[1] : tp.Kd[0];
-        const float* t = s_tap[g];
-        float D[KO][kSRows];
-#pragma unroll
-        for (int k = 0; k < KO; ++k) {
-            if (k >= no) break;
-            const float* Fk = F + (size_t)(g * no + k) * fplane;
+    for (int k = 0; k < KO; ++k) {
+        if (k >= no) break;
+        const float* Fk = F + (size_t)(g * no + k) * fplane;
+        if constexpr (KDG > 0) {
+            smooth_channel_123<KDG>(Fk, fpitch, H, W, x0, y0, t, s_F, FW, s_h, HR, D[k]);
+        } else {
+            const int hal = tp.halo[g], Kd = tp.Kd[g];
             switch (Kd) {
                 case 1: smooth_channel<1>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
                 case 2: smooth_channel<2>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
@@ -226,36 +299,81 @@ __global__ void __launch_bounds__(kThreads) k_sfoc_smooth(const float* __restric
                 default: smooth_channel<6>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
             }
         }
-        // group normalisation in registers; write this group
+    }
+    // group normalisation in registers; write this group
 #pragma unroll
-        for (int j = 0; j < kSRows; ++j) {
-            float n2 = 0.f;
+    for (int j = 0; j < kSRows; ++j) {
+        float n2 = 0.f;
 #pragma unroll
-            for (int k = 0; k < KO; ++k)
-                if (k < no) n2 = fmaf(D[k][j], D[k][j], n2);
-            const float den = sqrtf(n2) + tp.eps;
-            const float inv = den > 0.f ? 1.f / den : 0.f;  // NaN stays NaN through D * inv
-            const int gy = y0 + rb + j;
-            const bool in = gy < H && gx < W;
-            __align__(16) __nv_bfloat16 ch[8];
+        for (int k = 0; k < KO; ++k)
+            if (k < no) n2 = fmaf(D[k][j], D[k][j], n2);
+        const float den = sqrtf(n2) + tp.eps;
+        const float inv = den > 0.f ? 1.f / den : 0.f;  // NaN stays NaN through D * inv
+        const int gy = y0 + rb + j;
+        const bool in = gy < H && gx < W;
+        __align__(16) __nv_bfloat16 ch[8];
 #pragma unroll
-            for (int k = 0; k < KO; ++k) {
-                if (k >= no) break;
-                float v = (den > 0.f || den != den) ? D[k][j] * inv : 0.f;
-                if (bf) v = __bfloat162float(__float2bfloat16_rn(v));
-                a1[j] += v;
-                a2[j] = fmaf(v, v, a2[j]);
-                if (k < 8) ch[k] = __float2bfloat16_rn(v);
-                if (c32 && in) c32[(size_t)(g * no + k) * cplane + (size_t)gy * cpitch + gx] = v;
-            }
-            if (NO == 6 && bf && in) {
-                ch[6] = ch[7] = __float2bfloat16_rn(0.f);
-                const size_t npx = (size_t)H * W;
-                const size_t pix = (size_t)gy * W + gx, cpx = (size_t)gx * H + gy;
-                *reinterpret_cast<uint4*>(rm + ((size_t)g * npx + pix) * 8) = *reinterpret_cast<uint4*>(ch);
-                *reinterpret_cast<uint4*>(cm + ((size_t)g * npx + cpx) * 8) = *reinterpret_cast<uint4*>(ch);
-            }
+        for (int k = 0; k < KO; ++k) {
+            if (k >= no) break;
+            float v = (den > 0.f || den != den) ? D[k][j] * inv : 0.f;
+            if (bf) v = __bfloat162float(__float2bfloat16_rn(v));
+            a1[j] += v;
+            a2[j] = fmaf(v, v, a2[j]);
+            if (k < 8) ch[k] = __float2bfloat16_rn(v);
+            if (c32 && in) c32[(size_t)(g * no + k) * cplane + (size_t)gy * cpitch + gx] = v;
         }
+        if (NO == 6 && bf && in) {
+            ch[6] = ch[7] = __float2bfloat16_rn(0.f);
+            const size_t npx = (size_t)H * W;
+            const size_t pix = (size_t)gy * W + gx, cpx = (size_t)gx * H + gy;
+            *reinterpret_cast<uint4*>(rm + ((size_t)g * npx + pix) * 8) = *reinterpret_cast<uint4*>(ch);
+            *reinterpret_cast<uint4*>(cm + ((size_t)g * npx + cpx) * 8) = *reinterpret_cast<uint4*>(ch);
+        }
+    }
+}
+
+// KD1, KD2 > 0: the paper's dilation rates 1, 2, 3 with smoothing radii KD1
+// (first-order group) and KD2 (second-order group) at compile time, so the
+// kernel holds only the code it runs and fits two CTAs per SM; KD1 == 0:
+// any radii and rates at run time.
+template <int NO, int KD1, int KD2>
+__global__ void __launch_bounds__(kThreads, KD1 > 0 ? 2 : 1)
+    k_sfoc_smooth(const float* __restrict__ F, size_t fpitch, size_t fplane, int H, int W, SmoothTaps tp,
+                  float* __restrict__ c32, size_t cpitch, size_t cplane, __nv_bfloat16* __restrict__ rm,
+                  __nv_bfloat16* __restrict__ cm, float* __restrict__ s1, float* __restrict__ s2) {
+    extern __shared__ float sm[];
+    __shared__ float s_tap[2][kMaxSmoothRadius + 1];  // taps in shared memory: no local copy of the params
+    __shared__ int s_dil[kMaxDil];
+    if (threadIdx.x < 2 * (kMaxSmoothRadius + 1)) {
+        const int gg = threadIdx.x / (kMaxSmoothRadius + 1), q = threadIdx.x % (kMaxSmoothRadius + 1);
+        s_tap[gg][q] = tp.g[gg][q];
+    }
+    if (threadIdx.x < kMaxDil) s_dil[threadIdx.x] = tp.dil[threadIdx.x];
+    const int maxhal = max(tp.halo[0], tp.halo[1]);
+    const int FW = smooth_row_stride(maxhal);
+    const int HR = kSTH + 2 * maxhal;
+    float* s_F = sm;             // HR x FW
+    float* s_h = s_F + HR * FW;  // n_dil x HR x kSTW
+    const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH;
+    const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
+    const int gx = x0 + col;
+    const int no = NO > 0 ? NO : tp.no;
+    const int ng = tp.z / no;
+
+    float a1[kSRows], a2[kSRows];
+#pragma unroll
+    for (int j = 0; j < kSRows; ++j) a1[j] = a2[j] = 0.f;
+
+    if constexpr (KD1 > 0) {
+        smooth_group<NO, KD1>(0, F, fpitch, fplane, H, W, tp, s_dil, s_tap[0], s_F, FW, s_h, HR, x0, y0, c32, cpitch,
+                              cplane, rm, cm, a1, a2);
+        if (ng > 1)
+            smooth_group<NO, KD2>(1, F, fpitch, fplane, H, W, tp, s_dil, s_tap[1], s_F, FW, s_h, HR, x0, y0, c32,
+                                  cpitch, cplane, rm, cm, a1, a2);
+    } else {
+        for (int g = 0; g < ng; ++g)
+            smooth_group<NO, 0>(g, F, fpitch, fplane, H, W, tp, s_dil, s_tap[g], s_F, FW, s_h, HR, x0, y0, c32,
+                                cpitch, cplane, rm, cm, a1, a2);
     }
 #pragma unroll
     for (int j = 0; j < kSRows; ++j) {
@@ -305,21 +423,32 @@ cudaError_t launch_sfoc_steer(const float* img, int H, int W, size_t pitch, floa
 cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,
                                cudaStream_t st) {
     const int maxhal = tp.halo[0] > tp.halo[1] ? tp.halo[0] : tp.halo[1];
-    const int HR = kSTH + 2 * maxhal, FW = kSTW + 2 * maxhal + 8;
+    const int HR = kSTH + 2 * maxhal, FW = smooth_row_stride(maxhal);
     size_t smem = sizeof(float) * ((size_t)HR * FW + (size_t)tp.n_dil * HR * kSTW);
     dim3 grid((W + kSTW - 1) / kSTW, (H + kSTH - 1) / kSTH);
     cudaError_t e;
-    if (tp.no == 6) {
-        e = cudaFuncSetAttribute(k_sfoc_smooth<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool paper = tp.no == 6 && tp.z == 12 && tp.n_dil == 3 && tp.dil[0] == 1 && tp.dil[1] == 2 &&
+                       tp.dil[2] == 3 && tp.Kd[0] == 3 && tp.Kd[1] == 5;
+    if (paper) {  // sigma_d 1.0 / 1.5 with rates 1, 2, 3 (Sec. 2.1)
+        auto kern = k_sfoc_smooth<6, 3, 5>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        k_sfoc_smooth<6><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
-                                                       c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+        kern<<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
+                                           c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+    } else if (tp.no == 6) {
+        e = cudaFuncSetAttribute(k_sfoc_smooth<6, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sfoc_smooth<6, 0, 0><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
+                                                             c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
     } else {
         if (c.rm) return cudaErrorNotSupported;  // bf16 layouts need 12 channels
-        e = cudaFuncSetAttribute(k_sfoc_smooth<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sfoc_smooth<0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_sfoc_smooth<0><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
-                                                       c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+        k_sfoc_smooth<0, 0, 0><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
+                                                             c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
     }
     return cudaGetLastError();
 }
