@@ -193,8 +193,26 @@ SFOC_API sfoc_status sfoc_build(sfoc_ctx* ctx, const float* d_image, int H, int 
 SFOC_API sfoc_status sfoc_build_static(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems,
                                        const sfoc_params* p, float* d_out);
 
+/*
+ * sfoc_build_u16 - sfoc_build of a 16-bit image: each sample v is taken as
+ * the intensity v / 65535 (in float32, correctly rounded) while the tile is
+ * loaded, so no converted copy of the image is made.  Same cube, params and
+ * ownership rules as sfoc_build (the scales come from p).
+ */
+SFOC_API sfoc_status sfoc_build_u16(sfoc_ctx* ctx, const uint16_t* d_image, int H, int W, size_t pitch_elems,
+                                    const sfoc_params* p, sfoc_cube** out);
+
 /* Shape and dtype of a cube (any pointer may be NULL). */
 SFOC_API sfoc_status sfoc_cube_info(const sfoc_cube* cube, int* z, int* H, int* W, int* dtype);
+/*
+ * Device view of a cube's values (any pointer may be NULL; the data stay
+ * owned by the cube and valid until it is rebuilt or freed):
+ *   F32 cube:  *d_data = float [z][H][pitch] (planar, pitch in elements);
+ *   BF16 cube: *d_data = bf16 [z/6][H][W][8] (chunk g = the six channels of
+ *              group g then two zeros, pixels row-major), *pitch = W.
+ */
+SFOC_API sfoc_status sfoc_cube_view(const sfoc_cube* cube, void** d_data, int* z, int* H, int* W, size_t* pitch,
+                                    int* dtype);
 /* Writes the cube as float32 [z][H][W] (dense) into d_out. */
 SFOC_API sfoc_status sfoc_cube_export(sfoc_ctx* ctx, const sfoc_cube* cube, float* d_out);
 /* Builds (if needed) and writes the two integral planes of Eq. 14 as
@@ -246,10 +264,10 @@ SFOC_API sfoc_status sfoc_build_batch(sfoc_ctx* ctx, int n_img, const float* con
                              const size_t* pitch_elems, const sfoc_params* p, sfoc_cube** outs);
 
 /*
- * Matches n_pairs (ref, sen) pairs, each with its own points, m and R.  The
- * work of all pairs goes through one persistent launch per stage (a device
- * work queue of (pair, point) tasks ordered by cost); for BF16 cubes the
- * correlation stage is the tcgen05 kernel.
+ * Matches n_pairs (ref, sen) pairs, each with its own points, m and R, in
+ * order on the context stream (fastncc_match per pair, opts->corr_path for
+ * every pair; per-pair maps are not returned).  Stops at the first pair
+ * that fails and returns its status.
  */
 SFOC_API sfoc_status fastncc_match_batch(sfoc_ctx* ctx, int n_pairs, sfoc_cube* const* refs, sfoc_cube* const* sens,
                                 const int32_t* const* d_points, const int* n_points, const int* template_size,

@@ -86,6 +86,9 @@ _SIGS = {
                                         C.c_int, C.POINTER(Params), C.POINTER(Opts), _P]),
     "fastncc_register_pair_host": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, C.c_int, C.c_int, _P, C.c_int,
                                              C.c_int, C.c_int, C.POINTER(Params), C.POINTER(Opts), _P]),
+    "sfoc_build_u16": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, _P, C.POINTER(_P)]),
+    "sfoc_cube_view": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "sfoc_build_static": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, _P, _P]),
     "sfoc_build_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_size_t), C.POINTER(Params), C.POINTER(_P)]),
@@ -157,6 +160,14 @@ class Cube:
         out = torch.empty((z, H, W), dtype=torch.float32, device=self.ctx.device)
         self.ctx._chk(lib().sfoc_cube_export(self.ctx.h, self.handle, _ptr(out)))
         return out
+
+    def view(self):
+        """(device address, z, H, W, pitch, dtype) of the cube's own values
+        (sfoc_cube_view); the memory stays owned by the cube."""
+        d, z, H, W, pitch, dt = C.c_void_p(), C.c_int(), C.c_int(), C.c_int(), C.c_size_t(), C.c_int()
+        self.ctx._chk(lib().sfoc_cube_view(self.handle, C.byref(d), C.byref(z), C.byref(H), C.byref(W),
+                                           C.byref(pitch), C.byref(dt)))
+        return d.value, z.value, H.value, W.value, pitch.value, dt.value
 
     def export_integral(self) -> torch.Tensor:
         z, H, W, _ = self.info()
@@ -250,6 +261,20 @@ class Context:
         h = C.c_void_p(out.handle if out is not None else None)
         self._chk(lib().sfoc_build(self.h, _ptr(image), H, W, W, arr, len(scales) if scales else 0, int(n_orient),
                                    C.byref(p) if p is not None else None, C.byref(h)))
+        if out is not None and h.value == out.handle:
+            return out
+        return Cube(self, h.value)
+
+    def sfoc_build_u16(self, image: torch.Tensor, p: Params = None, out: Cube = None) -> Cube:
+        """sfoc_build of a uint16 image (intensity = value / 65535); torch has
+        no uint16 arithmetic, so `image` is passed as an int16 tensor holding
+        the same bits."""
+        if not (image.is_cuda and image.dtype == torch.int16 and image.is_contiguous()):
+            raise ValueError("image must be a contiguous CUDA int16 tensor holding uint16 bits")
+        H, W = image.shape
+        h = C.c_void_p(out.handle if out is not None else None)
+        self._chk(lib().sfoc_build_u16(self.h, _ptr(image), H, W, W, C.byref(p) if p is not None else None,
+                                       C.byref(h)))
         if out is not None and h.value == out.handle:
             return out
         return Cube(self, h.value)

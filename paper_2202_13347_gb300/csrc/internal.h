@@ -79,6 +79,8 @@ struct TileSums;  // integral-image scratch layout (k_integral.cu)
 // ---- kernel launchers (return cudaError_t of the launch) ----------------
 cudaError_t launch_sfoc_steer(const float* img, int H, int W, size_t pitch, float* F, size_t fpitch,
                               const SteerTaps& tp, int z_first, cudaStream_t st);
+cudaError_t launch_sfoc_steer(const uint16_t* img, int H, int W, size_t pitch, float* F, size_t fpitch,
+                              const SteerTaps& tp, int z_first, cudaStream_t st);
 cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,
                                cudaStream_t st);
 cudaError_t launch_cube_export(const Cube& c, float* out, cudaStream_t st);

@@ -51,9 +51,15 @@ __device__ __forceinline__ float conv_odd(const float* x, int s, const float* t,
     return acc;
 }
 
-__global__ void __launch_bounds__(kThreads) k_sfoc_steer(const float* __restrict__ img, int H, int W,
-                                                          size_t pitch, float* __restrict__ F, size_t fpitch,
-                                                          size_t fplane, SteerTaps tp) {
+// image samples to intensities: float as is; uint16 scaled to [0, 1] by
+// v / 65535 (correctly rounded division)
+__device__ __forceinline__ float to_unit(float v) { return v; }
+__device__ __forceinline__ float to_unit(uint16_t v) { return (float)v / 65535.f; }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_sfoc_steer(const T* __restrict__ img, int H, int W, size_t pitch,
+                                                          float* __restrict__ F, size_t fpitch, size_t fplane,
+                                                          SteerTaps tp) {
     extern __shared__ float sm[];
     const int hal = tp.halo;
     const int IW = kTW + 2 * hal, IH = kTH + 2 * hal;
@@ -65,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_sfoc_steer(const float* __restrict
     for (int i = threadIdx.x; i < IH * IW; i += kThreads) {
         int r = i / IW, c = i - r * IW;
         int gy = clampi(y0 + r - hal, 0, H - 1), gx = clampi(x0 + c - hal, 0, W - 1);
-        s_img[i] = __ldg(img + (size_t)gy * pitch + gx);
+        s_img[i] = to_unit(__ldg(img + (size_t)gy * pitch + gx));
     }
     __syncthreads();
 
@@ -405,19 +411,30 @@ __global__ void k_cube_export_f32(const float* __restrict__ c32, int H, int W, i
     }
 }
 
-}  // namespace
-
-cudaError_t launch_sfoc_steer(const float* img, int H, int W, size_t pitch, float* F, size_t fpitch,
-                              const SteerTaps& tp, int /*z_first*/, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_steer_any(const T* img, int H, int W, size_t pitch, float* F, size_t fpitch, const SteerTaps& tp,
+                             cudaStream_t st) {
     const int hal = tp.halo;
     const int IH = kTH + 2 * hal, IW = kTW + 2 * hal;
     const int np = 2 * tp.ns + (tp.second ? 3 : 0);
     size_t smem = sizeof(float) * ((size_t)IH * IW + (size_t)np * IH * kTW);
-    cudaError_t e = cudaFuncSetAttribute(k_sfoc_steer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_sfoc_steer<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
-    k_sfoc_steer<<<grid, kThreads, smem, st>>>(img, H, W, pitch, F, fpitch, fpitch * (size_t)H, tp);
+    k_sfoc_steer<T><<<grid, kThreads, smem, st>>>(img, H, W, pitch, F, fpitch, fpitch * (size_t)H, tp);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sfoc_steer(const float* img, int H, int W, size_t pitch, float* F, size_t fpitch,
+                              const SteerTaps& tp, int /*z_first*/, cudaStream_t st) {
+    return launch_steer_any(img, H, W, pitch, F, fpitch, tp, st);
+}
+
+cudaError_t launch_sfoc_steer(const uint16_t* img, int H, int W, size_t pitch, float* F, size_t fpitch,
+                              const SteerTaps& tp, int /*z_first*/, cudaStream_t st) {
+    return launch_steer_any(img, H, W, pitch, F, fpitch, tp, st);
 }
 
 cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,

@@ -296,6 +296,71 @@ size_t align256(size_t v) { return roundup(v, 256); }
 
 }  // namespace
 
+namespace {
+
+template <typename T>
+sfoc_status build_cube(sfoc_ctx* ctx, const T* d_image, int H, int W, size_t pitch_elems, const double* scales,
+                       int n_scales, int n_orient, const sfoc_params* pin, sfoc_cube** out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!d_image || !out) return fail(ctx, SFOC_ERR_INVALID_ARG, "null image or output pointer");
+    if (H <= 0 || W <= 0) return fail(ctx, SFOC_ERR_SHAPE, "image must be at least 1 x 1");
+    if (pitch_elems < (size_t)W) return fail(ctx, SFOC_ERR_SHAPE, "pitch_elems < W");
+    if ((size_t)H * (size_t)W > ((size_t)1 << 31)) return fail(ctx, SFOC_ERR_UNSUPPORTED, "image larger than 2^31 pixels");
+    sfoc_params p;
+    if (pin) p = *pin;
+    else sfoc_params_default(&p);
+    if (scales) {
+        if (n_scales < 1 || n_scales > kMaxScales) return fail(ctx, SFOC_ERR_UNSUPPORTED, "n_scales must be 1..4");
+        p.n_scales = n_scales;
+        for (int s = 0; s < n_scales; ++s) p.scales[s] = scales[s];
+    }
+    if (n_orient > 0) p.n_orient = n_orient;
+    sfoc_status s = check_params(ctx, p);
+    if (s != SFOC_OK) return s;
+    const int z = p.first_order_only ? p.n_orient : 2 * p.n_orient;
+    DeviceGuard g(ctx->device);
+
+    sfoc_cube* cube = *out;
+    bool reuse = cube && cube->c.H == H && cube->c.W == W && cube->c.z == z && cube->c.dtype == p.cube_dtype &&
+                 cube->c.device == ctx->device;
+    if (!reuse) {
+        cube = new (std::nothrow) sfoc_cube();
+        if (!cube) return fail(ctx, SFOC_ERR_OOM, "host allocation");
+        s = alloc_cube(ctx, cube->c, H, W, z, p.cube_dtype);
+        if (s != SFOC_OK) {
+            delete cube;
+            return s;
+        }
+    }
+    const size_t fpitch = roundup((size_t)W, 32);
+    s = ensure_ws(ctx, sizeof(float) * fpitch * (size_t)H * z);
+    if (s != SFOC_OK) {
+        if (!reuse) sfoc_cube_free(cube);
+        return s;
+    }
+    float* F = static_cast<float*>(ctx->ws);
+    SteerTaps st = make_steer(p);
+    SmoothTaps sm = make_smooth(p);
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_STEER, 1);
+        e = launch_sfoc_steer(d_image, H, W, pitch_elems, F, fpitch, st, z, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        StageScope sc(ctx, ST_SMOOTH, 1);
+        e = launch_sfoc_smooth(F, fpitch, H, W, sm, cube->c, ctx->stream);
+    }
+    if (e != cudaSuccess) {
+        if (!reuse) sfoc_cube_free(cube);
+        return cuda_fail(ctx, e, "sfoc kernels");
+    }
+    cube->c.integ_valid = false;
+    *out = cube;
+    return SFOC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 sfoc_status sfoc_ctx_create(sfoc_ctx** out, int device, void* stream) {
@@ -434,62 +499,12 @@ sfoc_status sfoc_params_default(sfoc_params* p) {
 
 sfoc_status sfoc_build(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems, const double* scales,
                        int n_scales, int n_orient, const sfoc_params* pin, sfoc_cube** out) {
-    if (!ctx) return SFOC_ERR_INVALID_ARG;
-    if (!d_image || !out) return fail(ctx, SFOC_ERR_INVALID_ARG, "null image or output pointer");
-    if (H <= 0 || W <= 0) return fail(ctx, SFOC_ERR_SHAPE, "image must be at least 1 x 1");
-    if (pitch_elems < (size_t)W) return fail(ctx, SFOC_ERR_SHAPE, "pitch_elems < W");
-    if ((size_t)H * (size_t)W > ((size_t)1 << 31)) return fail(ctx, SFOC_ERR_UNSUPPORTED, "image larger than 2^31 pixels");
-    sfoc_params p;
-    if (pin) p = *pin;
-    else sfoc_params_default(&p);
-    if (scales) {
-        if (n_scales < 1 || n_scales > kMaxScales) return fail(ctx, SFOC_ERR_UNSUPPORTED, "n_scales must be 1..4");
-        p.n_scales = n_scales;
-        for (int s = 0; s < n_scales; ++s) p.scales[s] = scales[s];
-    }
-    if (n_orient > 0) p.n_orient = n_orient;
-    sfoc_status s = check_params(ctx, p);
-    if (s != SFOC_OK) return s;
-    const int z = p.first_order_only ? p.n_orient : 2 * p.n_orient;
-    DeviceGuard g(ctx->device);
+    return build_cube(ctx, d_image, H, W, pitch_elems, scales, n_scales, n_orient, pin, out);
+}
 
-    sfoc_cube* cube = *out;
-    bool reuse = cube && cube->c.H == H && cube->c.W == W && cube->c.z == z && cube->c.dtype == p.cube_dtype &&
-                 cube->c.device == ctx->device;
-    if (!reuse) {
-        cube = new (std::nothrow) sfoc_cube();
-        if (!cube) return fail(ctx, SFOC_ERR_OOM, "host allocation");
-        s = alloc_cube(ctx, cube->c, H, W, z, p.cube_dtype);
-        if (s != SFOC_OK) {
-            delete cube;
-            return s;
-        }
-    }
-    const size_t fpitch = roundup((size_t)W, 32);
-    s = ensure_ws(ctx, sizeof(float) * fpitch * (size_t)H * z);
-    if (s != SFOC_OK) {
-        if (!reuse) sfoc_cube_free(cube);
-        return s;
-    }
-    float* F = static_cast<float*>(ctx->ws);
-    SteerTaps st = make_steer(p);
-    SmoothTaps sm = make_smooth(p);
-    cudaError_t e;
-    {
-        StageScope sc(ctx, ST_STEER, 1);
-        e = launch_sfoc_steer(d_image, H, W, pitch_elems, F, fpitch, st, z, ctx->stream);
-    }
-    if (e == cudaSuccess) {
-        StageScope sc(ctx, ST_SMOOTH, 1);
-        e = launch_sfoc_smooth(F, fpitch, H, W, sm, cube->c, ctx->stream);
-    }
-    if (e != cudaSuccess) {
-        if (!reuse) sfoc_cube_free(cube);
-        return cuda_fail(ctx, e, "sfoc kernels");
-    }
-    cube->c.integ_valid = false;
-    *out = cube;
-    return SFOC_OK;
+sfoc_status sfoc_build_u16(sfoc_ctx* ctx, const uint16_t* d_image, int H, int W, size_t pitch_elems,
+                           const sfoc_params* p, sfoc_cube** out) {
+    return build_cube(ctx, d_image, H, W, pitch_elems, nullptr, 0, 0, p, out);
 }
 
 sfoc_status sfoc_cube_info(const sfoc_cube* cube, int* z, int* H, int* W, int* dtype) {
@@ -498,6 +513,18 @@ sfoc_status sfoc_cube_info(const sfoc_cube* cube, int* z, int* H, int* W, int* d
     if (H) *H = cube->c.H;
     if (W) *W = cube->c.W;
     if (dtype) *dtype = cube->c.dtype;
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_cube_view(const sfoc_cube* cube, void** d_data, int* z, int* H, int* W, size_t* pitch, int* dtype) {
+    if (!cube) return SFOC_ERR_INVALID_ARG;
+    const Cube& c = cube->c;
+    if (d_data) *d_data = c.dtype == SFOC_DTYPE_BF16 ? static_cast<void*>(c.rm) : static_cast<void*>(c.f32);
+    if (z) *z = c.z;
+    if (H) *H = c.H;
+    if (W) *W = c.W;
+    if (pitch) *pitch = c.dtype == SFOC_DTYPE_BF16 ? (size_t)c.W : c.pitch;
+    if (dtype) *dtype = c.dtype;
     return SFOC_OK;
 }
 

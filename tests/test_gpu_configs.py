@@ -1,0 +1,112 @@
+"""The batched workload (c4) and the 10000^2 workload (c5) against the oracle.
+
+c4: pairs of different sizes, radiometric maps, m in {41, 61, 81, 101} and
+R in [10, 40], built and matched through the batched entry points
+(sfoc_build_batch, fastncc_match_batch), F32 and BF16 forms; the oracle
+checks a seeded sample of points per pair.
+c5: the 10000^2 pair at full size, the 16-bit reference read through
+sfoc_build_u16; 10000 points, m = 101, R = 40 (the BF16 form takes the
+Toeplitz tensor-core kernel since m + 2R > 128); the oracle checks a seeded
+sample of points.  Tolerances as in the other parity tests.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from workloads import config4, config5  # noqa: E402
+
+from parity import bf16_check, bf16_oracle_side, compare  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def b():
+    import paper_2202_13347_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+@pytest.fixture(scope="module")
+def ctx(b):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return b.Context(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def sample(pair, k, seed):
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(pair.points), min(k, len(pair.points)), replace=False))
+    return idx, type(pair)(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R, pair.truth[idx])
+
+
+@pytest.fixture(scope="module")
+def c4():
+    # 16 of the 64 pairs at a quarter of the side lengths and point counts
+    return config4(n_pairs=16, scale=0.25)
+
+
+def test_config4_batched_f32(b, ctx, orc, c4):
+    refs = ctx.sfoc_build_batch([dev(p.ref) for p in c4])
+    sens = ctx.sfoc_build_batch([dev(p.sen) for p in c4])
+    outs = ctx.fastncc_match_batch(refs, sens, [dev(p.points) for p in c4], [p.m for p in c4], [p.R for p in c4],
+                                   corr_path=b.CORR_DIRECT_F32)
+    ctx.sync()
+    for k, pair in enumerate(c4):
+        g = b.results(outs[k])
+        idx, sub = sample(pair, 3, 400 + k)
+        o = orc.match_pair(sub.ref, sub.sen, sub.points, sub.m, sub.R, want_maps=True)
+        gi = {key: v[torch.from_numpy(idx).cuda()] for key, v in g.items()}
+        compare(gi, o, pair.R, oracle_maps=o["maps"])
+
+
+def test_config4_batched_bf16(b, ctx, orc, c4):
+    p = b.params(dtype=b.DTYPE_BF16)
+    refs = ctx.sfoc_build_batch([dev(pp.ref) for pp in c4], p=p)
+    sens = ctx.sfoc_build_batch([dev(pp.sen) for pp in c4], p=p)
+    outs = ctx.fastncc_match_batch(refs, sens, [dev(pp.points) for pp in c4], [pp.m for pp in c4],
+                                   [pp.R for pp in c4], corr_path=b.CORR_IGEMM_TC)
+    ctx.sync()
+    for k, pair in enumerate(c4):
+        g = b.results(outs[k])
+        idx, sub = sample(pair, 2, 500 + k)
+        o_r, o_u, regions = bf16_oracle_side(orc, sub, roi=True)
+        gi = {key: v[torch.from_numpy(idx).cuda()] for key, v in g.items()}
+        bf16_check(gi, o_r, o_u, regions, pair.R, {})
+
+
+@pytest.fixture(scope="module")
+def c5():
+    return config5()
+
+
+def test_config5_full_size_sampled(b, ctx, orc, c5):
+    pair = c5
+    ref16 = pair.meta["ref_u16"]
+    bits = torch.from_numpy(ref16.view(np.int16)).cuda()
+    pts = dev(pair.points)
+    idx, sub = sample(pair, 6, 5005)
+    sel = torch.from_numpy(idx).cuda()
+    # F32 form
+    rc = ctx.sfoc_build_u16(bits)
+    sc = ctx.sfoc_build(dev(pair.sen))
+    g = ctx.fastncc_match(rc, sc, pts, pair.m, pair.R, corr_path=b.CORR_DIRECT_F32)
+    ctx.sync()
+    o = orc.match_pair(sub.ref, sub.sen, sub.points, sub.m, sub.R, want_maps=True)
+    compare({k: v[sel] for k, v in g.items()}, o, pair.R, oracle_maps=o["maps"])
+    assert int((g["status"] == 0).sum()) >= 0.5 * len(pair.points)
+    rc.free()
+    sc.free()
+    # BF16 form (Toeplitz tensor-core kernel: m + 2R = 181)
+    p = b.params(dtype=b.DTYPE_BF16)
+    rc = ctx.sfoc_build_u16(bits, p=p)
+    sc = ctx.sfoc_build(dev(pair.sen), p=p)
+    g = ctx.fastncc_match(rc, sc, pts, pair.m, pair.R, corr_path=b.CORR_IGEMM_TC)
+    ctx.sync()
+    o_r, o_u, regions = bf16_oracle_side(orc, sub, roi=True)
+    bf16_check({k: v[sel] for k, v in g.items()}, o_r, o_u, regions, pair.R, {})

@@ -168,3 +168,47 @@ def test_invalid_arguments_return_errors(b, ctx):
     assert e.value.code == -6
     with pytest.raises(b.SfocError):
         ctx.sfoc_build(dev(pair.ref), p=b.params(n_orient=9))
+
+
+def test_u16_input_matches_scaled_float(b, ctx, orc):
+    """sfoc_build_u16: a 16-bit image is read as v / 65535 (the input step
+    of the 10000^2 workload); the cube equals the oracle's on the FP64
+    scaled image and the GPU cube of the float32 image v / 65535."""
+    rng = np.random.default_rng(21)
+    from workloads import optical_like
+    img16 = np.round(optical_like(rng, 83, 97) * 65535.0).astype(np.uint16)
+    bits = torch.from_numpy(img16.view(np.int16)).cuda()
+    cube16 = ctx.sfoc_build_u16(bits)
+    f = (img16.astype(np.float32) / np.float32(65535.0)).astype(np.float32)
+    cubef = ctx.sfoc_build(torch.from_numpy(f).cuda())
+    got16 = cube16.export().cpu().numpy()
+    gotf = cubef.export().cpu().numpy()
+    np.testing.assert_array_equal(got16, gotf)
+    want = orc.sfoc_roi(img16.astype(np.float64) / 65535.0).data
+    np.testing.assert_allclose(got16, want, rtol=0, atol=2e-5)
+
+
+def test_cube_view_layouts(b, ctx):
+    rng = np.random.default_rng(22)
+    from workloads import optical_like
+    img = torch.from_numpy(optical_like(rng, 40, 52)).cuda()
+    for dt in (b.DTYPE_F32, b.DTYPE_BF16):
+        cube = ctx.sfoc_build(img, p=b.params(dtype=dt))
+        addr, z, H, W, pitch, dtype = cube.view()
+        assert (z, H, W, dtype) == (12, 40, 52, dt) and addr
+        exp = cube.export()
+        ctx.sync()
+
+        class _View:  # zero-copy tensor over the viewed device memory
+            def __init__(self, shape, typestr):
+                self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (addr, False),
+                                                 "version": 3}
+
+        if dt == b.DTYPE_F32:
+            raw = torch.as_tensor(_View((z, H, pitch), "<f4"), device="cuda")
+            assert torch.equal(raw[:, :, :W], exp)
+        else:
+            raw = torch.as_tensor(_View((2, H, W, 8), "<i2"), device="cuda").view(torch.bfloat16)
+            chans = torch.cat([raw[0, :, :, :6], raw[1, :, :, :6]], dim=-1).permute(2, 0, 1).float()
+            assert torch.equal(chans, exp)
+            assert torch.all(raw[:, :, :, 6:] == 0)

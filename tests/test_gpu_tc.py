@@ -24,8 +24,7 @@ torch = pytest.importorskip("torch")
 
 from workloads import config1, config2, tiny_pair  # noqa: E402
 
-from parity import (bf16_round, compare, compare_maps, flip_tolerance, ncc_rounding_bound,  # noqa: E402
-                    storage_bound, subpixel_tol, to_np)
+from parity import bf16_check as check, bf16_oracle_side as oracle_side  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -52,82 +51,6 @@ def gpu_bf16(ctx, b, pair, want_maps=False, path=None):
     sc = ctx.sfoc_build(dev(pair.sen), p=p)
     return ctx.fastncc_match(rc, sc, dev(pair.points), pair.m, pair.R,
                              corr_path=b.CORR_IGEMM_TC if path is None else path, want_maps=want_maps)
-
-
-def oracle_side(orc, pair, roi=False):
-    """Oracle Eq. 8 on its cube rounded to bf16 and on the unrounded cube,
-    plus per point the unrounded search region and template."""
-    m, R = pair.m, pair.R
-    h = orc.template_half(m)
-    M = m + 2 * R
-    regions = []
-    if not roi:
-        rc_full = orc.sfoc_roi(pair.ref)
-        sc_full = orc.sfoc_roi(pair.sen)
-    res_r, res_u = [], []
-    for (px, py) in pair.points:
-        ty0, tx0 = int(py) - h, int(px) - h
-        inb = (ty0 - R >= 0 and tx0 - R >= 0 and ty0 + m + R <= pair.ref.shape[0]
-               and tx0 + m + R <= pair.ref.shape[1] and ty0 + m <= pair.sen.shape[0] and tx0 + m <= pair.sen.shape[1])
-        if not inb:
-            regions.append(None)
-            continue
-        if roi:
-            S = orc.sfoc_roi(pair.ref, None, ty0 - R, tx0 - R, M, M).data
-            T = orc.sfoc_roi(pair.sen, None, ty0, tx0, m, m).data
-        else:
-            S = rc_full.data[:, ty0 - R:ty0 + m + R, tx0 - R:tx0 + m + R].copy()
-            T = sc_full.data[:, ty0:ty0 + m, tx0:tx0 + m].copy()
-        regions.append((S, T))
-    import oracle as _o
-
-    def run(rounded):
-        outs = []
-        for k, (px, py) in enumerate(pair.points):
-            if regions[k] is None:
-                dummy = _o.CubeROI(np.zeros((12, 1, 1)), pair.ref.shape[0], pair.ref.shape[1], 0, 0)
-                outs.append(orc.match(dummy, dummy, np.array([[px, py]], np.int32), m, R, want_maps=True))
-                continue
-            S, T = regions[k]
-            ty0, tx0 = int(py) - h, int(px) - h
-            Sc = bf16_round(S) if rounded else S
-            Tc = bf16_round(T) if rounded else T
-            rc = _o.CubeROI(np.ascontiguousarray(Sc), pair.ref.shape[0], pair.ref.shape[1], ty0 - R, tx0 - R)
-            sc = _o.CubeROI(np.ascontiguousarray(Tc), pair.sen.shape[0], pair.sen.shape[1], ty0, tx0)
-            outs.append(orc.match(rc, sc, np.array([[px, py]], np.int32), m, R, want_maps=True))
-        return {key: np.concatenate([o[key] for o in outs]) for key in outs[0]}
-
-    return run(True), run(False), regions
-
-
-def check(g, o_r, o_u, regions, R, report):
-    n = len(regions)
-    bmaps = [ncc_rounding_bound(*r) if r is not None else None for r in regions]
-    smaps = [storage_bound(*r) if r is not None else None for r in regions]
-    tol = np.full(n, 1e-4)
-    for k, reg in enumerate(regions):
-        if reg is None or o_r["status"][k] not in (0, 3):
-            continue
-        S, T = reg
-        m = T.shape[1]
-        dy, dx = o_r["dy"][k] + R, o_r["dx"][k] + R
-        tol[k] = flip_tolerance(S[:, dy:dy + m, dx:dx + m], T)
-    sub = np.array([subpixel_tol(o_r["maps"][k], R, tol[k]) if bmaps[k] is not None else 0.02 for k in range(n)])
-    st = compare(g, o_r, R, ncc_tol=tol, sub_tol=sub, oracle_maps=o_r["maps"])
-    valid = np.isin(o_r["status"], [0, 3])
-    if "maps" in g:
-        compare_maps(g["maps"].cpu().numpy(), o_r["maps"], bmaps, valid)
-    # precision report against the unrounded FP64 oracle
-    gn = to_np(g)
-    same = valid & (gn["dx"] == o_u["dx"]) & (gn["dy"] == o_u["dy"])
-    stol = np.array([smaps[k][gn["dy"][k] + R, gn["dx"][k] + R] if smaps[k] is not None else 1.0 for k in range(n)])
-    err = np.abs(gn["ncc"] - o_u["ncc"])
-    assert np.all(err[same] <= stol[same]), float((err[same] - stol[same]).max())
-    report.update(st, bf16_vs_fp64_offsets_equal=int(same.sum()), bf16_vs_fp64_valid=int(valid.sum()),
-                  bf16_vs_fp64_ncc_err_max=float(err[same].max()) if same.any() else 0.0,
-                  rounding_bound_max=float(tol[valid].max()) if valid.any() else 0.0)
-    print(report)
-    return st
 
 
 SMALL = [
