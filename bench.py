@@ -182,8 +182,8 @@ def run_e2e(b, torch, ctx, pair, p, corr, steps):
     matched = int((out[:, 5] == 0).sum())
     h2d = h_ref.numel() * 4 + h_sen.numel() * 4 + h_pts.numel() * 4
     d2h = out.numel() * 4
-    return dict(value=matched / statistics.mean(t), unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
-                ms_per_step=1e3 * statistics.mean(t))
+    return dict(ms=1e3 * sum(t), steps=steps, matched=matched, unit=UNIT, h2d_bytes_per_step=h2d,
+                d2h_bytes_per_step=d2h)
 
 
 def cpu_baseline(pair, n_sample=16, seed=99):
@@ -199,6 +199,23 @@ def cpu_baseline(pair, n_sample=16, seed=99):
     return dict(value=matched / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
                 sample="%d of %d points (seeded), FP64 SFOC on their windows only, Eq. 8 NCC" % (len(idx), len(pair.points)),
                 seconds=dt)
+
+
+def reduce_over_ranks(dist, torch, ms, matched, device):
+    """Whole-job figures of one timed region: the slowest rank's time (max)
+    and the points matched by all ranks (sum).  `dist` None = one rank."""
+    if dist is None:
+        return float(ms), int(matched)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([int(matched)], dtype=torch.int64, device=device)
+    dist.all_reduce(n)
+    return float(t.item()), int(n.item())
+
+
+def job_value(matched_all, steps, ms_max):
+    """Matched control points per second over the whole job."""
+    return matched_all * steps / (ms_max * 1e-3)
 
 
 def corr_flops(pair, z=12):
@@ -276,14 +293,7 @@ def main():
             torch.cuda.synchronize()
             with ClockSampler(gpu_index) as cs:
                 r = run_form(b, torch, ctx, pair, form, args.steps, args.warmup, flush)
-            if dist:
-                t = torch.tensor([r["ms"]], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                mt = torch.tensor([r["matched"]], device="cuda", dtype=torch.int64)
-                dist.all_reduce(mt)
-                r["ms_max"], r["matched_all"] = float(t.item()), int(mt.item())
-            else:
-                r["ms_max"], r["matched_all"] = r["ms"], r["matched"]
+            r["ms_max"], r["matched_all"] = reduce_over_ranks(dist, torch, r["ms"], r["matched"], "cuda")
             r["clocks"] = cs.summary()
             results[form] = r
         except b.SfocError as e:
@@ -314,7 +324,7 @@ def main():
                     "kernel": "k_corr_f32 (FP32 FMA)",
                     "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                     "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
-        return dict(value=r["matched_all"] * args.steps / (r["ms_max"] * 1e-3), ms_per_step=r["ms_max"] / args.steps,
+        return dict(value=job_value(r["matched_all"], args.steps, r["ms_max"]), ms_per_step=r["ms_max"] / args.steps,
                     sfoc_mpix_s=2 * pair.ref.size / (sfoc_ms * 1e-3) / 1e6 if sfoc_ms > 0 else None,
                     stage_ms_per_step={k: round(v, 4) for k, v in per_step.items()}, roofline=roof,
                     matched_per_step=r["matched"], gpu_launches=r["launches"], clocks=r["clocks"])
@@ -324,7 +334,12 @@ def main():
     r0 = results[main_form]
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(b, torch, ctx, pair, r0["p"], r0["corr"], max(3, min(args.steps, 10)))
+        r = run_e2e(b, torch, ctx, pair, r0["p"], r0["corr"], max(3, min(args.steps, 10)))
+        if dist:
+            dist.barrier()
+        ms_max, matched_all = reduce_over_ranks(dist, torch, r["ms"], r["matched"] * r["steps"], "cuda")
+        e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=r["h2d_bytes_per_step"],
+                   d2h_bytes_per_step=r["d2h_bytes_per_step"], ms_per_step=ms_max / r["steps"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pair)
