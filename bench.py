@@ -35,6 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "matched CPs/sec and SFOC Mpix/sec on 1 GB300, BF16-batched vs plain FP32"
 UNIT = "CP/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+# DRAM bytes (read + write) per launch of each form's correlation kernel on
+# the 2048x2048 workload, from one ncu capture of the kernel as it stands
+# (profiles/k_corr_tc_col_c2_2048.md, profiles/k_corr_f32_c2_2048.md); to be
+# retaken whenever the kernel changes.
+CORR_TRAFFIC_C2 = {"bf16": 272.4e6, "f32": 429.8e6}
 
 
 def parse():
@@ -312,15 +317,17 @@ def main():
         flops = corr_flops(pair) * r["valid"]          # processed points only
         per_launch = corr_ms / max(1, corr_n)
         ach = flops / (per_launch * 1e-3) / 1e12
+        traffic = CORR_TRAFFIC_C2.get(form) if args.config == "c2" else None
         if form == "bf16":
             roof = {"bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
-                    "frac": ach / pk["bf16"], "traffic": None,
-                    "kernel": "k_corr_tc (tcgen05 bf16, fp32 accumulate)",
+                    "frac": ach / pk["bf16"], "traffic": traffic,
+                    "kernel": "k_corr_tc_col (tcgen05 bf16, fp32 accumulate)" if pair.m + 2 * pair.R <= 128
+                    else "k_corr_tc (Toeplitz form, tcgen05 bf16, fp32 accumulate)",
                     "peak_src": "bf16_tflops burst, %s" % pk["src"],
                     "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
         else:
             roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
                     "kernel": "k_corr_f32 (FP32 FMA)",
                     "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                     "work": "2*m^2*z*(2R+1)^2 flop per processed point"}

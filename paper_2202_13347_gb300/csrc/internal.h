@@ -56,10 +56,12 @@ struct SmoothTaps {
 
 // ---- cube --------------------------------------------------------------
 // F32 cube: planar [z][H][pitch] float.
-// BF16 cube (z = 12): two 8-channel chunks per pixel, chunk 0 = channels
-// 0..7, chunk 1 = channels 8..11 and four zeros, stored twice:
-//   rm: [2][H][W][8] (pixels row-major)     - search windows (A operand)
-//   cm: [2][W][H][8] (pixels column-major)  - templates (B operand)
+// BF16 cube (z = 12): two 8-channel chunks per pixel, chunk g = the six
+// channels of group g and two zeros, stored twice:
+//   rm: [2][H][W][8] (pixels row-major)     - Toeplitz-form windows
+//   cm: [2][W][H][8] (pixels column-major)  - templates; column-form windows
+// Both buffers carry 256 bytes of padding past the end (copies in 128-byte
+// runs of pixels may read up to 7 pixels past the last column).
 struct Cube {
     int H = 0, W = 0, z = 0, dtype = SFOC_DTYPE_F32;
     size_t pitch = 0;          // elements per row of f32 planes / sum planes
