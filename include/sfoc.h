@@ -216,7 +216,10 @@ SFOC_API sfoc_status sfoc_cube_view(const sfoc_cube* cube, void** d_data, int* z
 /* Writes the cube as float32 [z][H][W] (dense) into d_out. */
 SFOC_API sfoc_status sfoc_cube_export(sfoc_ctx* ctx, const sfoc_cube* cube, float* d_out);
 /* Builds (if needed) and writes the two integral planes of Eq. 14 as
- * float64 [2][H+1][W+1] (exclusive prefix of sum_c g and of sum_c g^2). */
+ * float64 [2][H+1][W+1] (exclusive prefix of sum_c g and of sum_c g^2).
+ * The library keeps them as exact sums of the per-pixel values rounded to
+ * multiples of 2^-28; an entry whose prefix rectangle holds a non-finite
+ * value is NaN.  Uses the context workspace (4 bytes per entry). */
 SFOC_API sfoc_status sfoc_cube_export_integral(sfoc_ctx* ctx, sfoc_cube* cube, double* d_out);
 SFOC_API sfoc_status sfoc_cube_free(sfoc_cube* cube);
 

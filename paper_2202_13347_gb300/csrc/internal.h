@@ -70,7 +70,7 @@ struct Cube {
     __nv_bfloat16* cm = nullptr;
     float* s1 = nullptr;       // [H][pitch] sum over channels of g
     float* s2 = nullptr;       // [H][pitch] sum over channels of g^2
-    double* integ = nullptr;   // [2][H+1][ipitch] exclusive prefix of s1, s2
+    unsigned long long* integ = nullptr;  // [2][H+1][ipitch] exclusive prefix of s1, s2 in units of 2^-28
     size_t ipitch = 0;
     bool integ_valid = false;
     int device = 0;
@@ -87,8 +87,21 @@ cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, cons
                                cudaStream_t st);
 cudaError_t launch_cube_export(const Cube& c, float* out, cudaStream_t st);
 
+// Integral planes in fixed point: a value v counts as round(v * 2^28), sums
+// are 64-bit integers modulo 2^64 (window differences exact).  Valid window
+// sums stay below 2^45: at most 128^2 pixels of |s1| <= 2 sqrt(8) < 5.7 (two
+// unit-norm groups of at most 8 channels) or s2 <= 2, i.e. < 2^44.6 units.
+// A non-finite value enters as kIntNonFinite, so a window sum >= 2^45 holds
+// one (windows of up to 2^17 such values still fit below 2^63).
+constexpr float kIntScale = 268435456.f;                  // 2^28
+constexpr long long kIntNonFinite = 1ll << 46;
+constexpr long long kIntNonFiniteMin = 1ll << 45;
+__host__ __device__ inline double int_units_to_double(long long v) { return (double)v * (1.0 / 268435456.0); }
+
 size_t integral_scratch_bytes(int H, int W);
 cudaError_t launch_integral(const Cube& c, void* scratch, cudaStream_t st, int* launches);
+size_t integral_export_scratch_bytes(int H, int W);
+cudaError_t launch_integral_export(const Cube& c, void* scratch, double* out, cudaStream_t st);
 
 struct PointStat {
     double RT, RTT;       // template sums (Eq. 12) from the sensed integral images

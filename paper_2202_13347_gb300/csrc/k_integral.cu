@@ -1,10 +1,16 @@
-// Integral feature images (Eq. 14-16 of arXiv 2202.13347) in FP64.
+// Integral feature images (Eq. 14-16 of arXiv 2202.13347), exact.
 //
 // The two channel-summed planes s1 = sum_c g and s2 = sum_c g^2 of a cube
 // are turned into exclusive prefix planes P[y][x] = sum over rows < y and
 // columns < x, of size (H+1) x (W+1), so any window sum costs four lookups
-// (Eq. 16).  Window sums of up to 10^8 pixels lose too much in FP32, hence
-// FP64 everywhere here.
+// (Eq. 16).  Each pixel value is rounded once to a multiple of 2^-28 and
+// the prefixes are integer sums in 64 bits, so every window sum is exact
+// (its only error is the per-pixel rounding, at most 2^-29 per pixel) and
+// no floating-point adds are needed: GB300's FP64 rate is a small fraction
+// of its FP32 and integer rates.  The sums wrap modulo 2^64, which leaves
+// window differences exact.  A non-finite value enters as 2^46; window
+// sums of valid values stay below 2^45 (see internal.h), so a window sum at
+// or above 2^45 marks a window with a non-finite value.
 //
 // Three steps over 64 x 64 tiles:
 //   k_int_tilesums  per tile: column sums and row sums (reads s1, s2 once)
@@ -12,6 +18,8 @@
 //                   above (left), then a scan along the line
 //   k_int_final     per tile: local 2-D prefix + the grid-line values
 // HBM traffic is ~8 B/px read twice + 16 B/px written.
+#include <math.h>
+
 #include "internal.h"
 
 namespace sfoc {
@@ -19,13 +27,19 @@ namespace sfoc {
 namespace {
 
 constexpr int kT = 64;
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 quant(float v) {
+    if (!isfinite(v)) return (u64)kIntNonFinite;
+    return (u64)__float2ll_rn(v * kIntScale);
+}
 
 struct IntLayout {
     int H, W, nty, ntx;
-    double* colsum;  // [2][nty][W]   column sums per tile row (then exclusive prefix over tile rows)
-    double* rowsum;  // [2][ntx][H]   row sums per tile column (then exclusive prefix over tile columns)
-    double* top;     // [2][nty][W+1] P[y0(ty)][x]
-    double* left;    // [2][ntx][H+1] P[y][x0(tx)]
+    u64* colsum;  // [2][nty][W]   column sums per tile row (then exclusive prefix over tile rows)
+    u64* rowsum;  // [2][ntx][H]   row sums per tile column (then exclusive prefix over tile columns)
+    u64* top;     // [2][nty][W+1] P[y0(ty)][x]
+    u64* left;    // [2][ntx][H+1] P[y][x0(tx)]
 };
 
 IntLayout layout(int H, int W, void* scratch) {
@@ -34,7 +48,7 @@ IntLayout layout(int H, int W, void* scratch) {
     L.W = W;
     L.nty = (H + kT - 1) / kT;
     L.ntx = (W + kT - 1) / kT;
-    double* p = static_cast<double*>(scratch);
+    u64* p = static_cast<u64*>(scratch);
     L.colsum = p;
     p += 2 * (size_t)L.nty * W;
     L.rowsum = p;
@@ -47,7 +61,7 @@ IntLayout layout(int H, int W, void* scratch) {
 
 __global__ void __launch_bounds__(256) k_int_tilesums(const float* __restrict__ s1, const float* __restrict__ s2,
                                                        size_t pitch, IntLayout L) {
-    __shared__ double t[kT][kT + 1];
+    __shared__ u64 t[kT][kT + 1];
     const int ty = blockIdx.y, tx = blockIdx.x;
     const int y0 = ty * kT, x0 = tx * kT;
     for (int p = 0; p < 2; ++p) {
@@ -56,16 +70,16 @@ __global__ void __launch_bounds__(256) k_int_tilesums(const float* __restrict__ 
         for (int i = threadIdx.x; i < kT * kT; i += 256) {
             int r = i / kT, c = i % kT;
             int y = y0 + r, x = x0 + c;
-            t[r][c] = (y < L.H && x < L.W) ? (double)s[(size_t)y * pitch + x] : 0.0;
+            t[r][c] = (y < L.H && x < L.W) ? quant(s[(size_t)y * pitch + x]) : 0ull;
         }
         __syncthreads();
         const int role = threadIdx.x / kT, j = threadIdx.x % kT;  // roles 0,1: columns; 2,3: rows (half each)
         if (role == 0) {
-            double acc = 0.0;
+            u64 acc = 0;
             for (int r = 0; r < kT; ++r) acc += t[r][j];
             if (x0 + j < L.W) L.colsum[((size_t)p * L.nty + ty) * L.W + x0 + j] = acc;
         } else if (role == 1) {
-            double acc = 0.0;
+            u64 acc = 0;
             for (int c = 0; c < kT; ++c) acc += t[j][c];
             if (y0 + j < L.H) L.rowsum[((size_t)p * L.ntx + tx) * L.H + y0 + j] = acc;
         }
@@ -78,20 +92,20 @@ __global__ void k_int_carry(IntLayout L) {
     size_t ncol = 2 * (size_t)L.W, nrow = 2 * (size_t)L.H;
     if (i < ncol) {
         int p = (int)(i / L.W), x = (int)(i % L.W);
-        double run = 0.0;
+        u64 run = 0;
         for (int ty = 0; ty < L.nty; ++ty) {
-            double* q = &L.colsum[((size_t)p * L.nty + ty) * L.W + x];
-            double v = *q;
+            u64* q = &L.colsum[((size_t)p * L.nty + ty) * L.W + x];
+            u64 v = *q;
             *q = run;
             run += v;
         }
     } else if (i < ncol + nrow) {
         i -= ncol;
         int p = (int)(i / L.H), y = (int)(i % L.H);
-        double run = 0.0;
+        u64 run = 0;
         for (int tx = 0; tx < L.ntx; ++tx) {
-            double* q = &L.rowsum[((size_t)p * L.ntx + tx) * L.H + y];
-            double v = *q;
+            u64* q = &L.rowsum[((size_t)p * L.ntx + tx) * L.H + y];
+            u64 v = *q;
             *q = run;
             run += v;
         }
@@ -99,34 +113,34 @@ __global__ void k_int_carry(IntLayout L) {
 }
 
 // Block-wide exclusive scan of n values: out[0] = 0, out[k] = sum in[0..k-1].
-__device__ void block_scan_excl(const double* in, double* out, int n) {
-    __shared__ double warp_tot[32];
-    __shared__ double carry;
-    if (threadIdx.x == 0) carry = 0.0;
+__device__ void block_scan_excl(const u64* in, u64* out, int n) {
+    __shared__ u64 warp_tot[32];
+    __shared__ u64 carry;
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int base = 0; base < n + 1; base += blockDim.x) {
         int k = base + threadIdx.x;      // out index
-        double v = (k >= 1 && k - 1 < n) ? in[k - 1] : 0.0;
+        u64 v = (k >= 1 && k - 1 < n) ? in[k - 1] : 0ull;
         // inclusive warp scan
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            double u = __shfl_up_sync(0xffffffffu, v, o);
+            u64 u = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += u;
         }
         if (lane == 31) warp_tot[wid] = v;
         __syncthreads();
         if (wid == 0) {
-            double w = lane < nw ? warp_tot[lane] : 0.0;
+            u64 w = lane < nw ? warp_tot[lane] : 0ull;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                double u = __shfl_up_sync(0xffffffffu, w, o);
+                u64 u = __shfl_up_sync(0xffffffffu, w, o);
                 if (lane >= o) w += u;
             }
             if (lane < nw) warp_tot[lane] = w;  // inclusive over warps
         }
         __syncthreads();
-        double off = carry + (wid > 0 ? warp_tot[wid - 1] : 0.0);
+        u64 off = carry + (wid > 0 ? warp_tot[wid - 1] : 0ull);
         if (k <= n) out[k] = v + off;
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry = off + v;
@@ -148,33 +162,32 @@ __global__ void __launch_bounds__(256) k_int_lines(IntLayout L) {
 }
 
 __global__ void __launch_bounds__(256) k_int_final(const float* __restrict__ s1, const float* __restrict__ s2,
-                                                    size_t pitch, IntLayout L, double* __restrict__ P,
-                                                    size_t ipitch) {
-    __shared__ double t[kT][kT + 1];
+                                                    size_t pitch, IntLayout L, u64* __restrict__ P, size_t ipitch) {
+    __shared__ u64 t[kT][kT + 1];
     const int ty = blockIdx.y, tx = blockIdx.x, p = blockIdx.z;
     const int y0 = ty * kT, x0 = tx * kT;
     const float* s = p ? s2 : s1;
-    double* Pp = P + (size_t)p * (L.H + 1) * ipitch;
+    u64* Pp = P + (size_t)p * (L.H + 1) * ipitch;
     for (int i = threadIdx.x; i < kT * kT; i += 256) {
         int r = i / kT, c = i % kT;
         int y = y0 + r, x = x0 + c;
-        t[r][c] = (y < L.H && x < L.W) ? (double)s[(size_t)y * pitch + x] : 0.0;
+        t[r][c] = (y < L.H && x < L.W) ? quant(s[(size_t)y * pitch + x]) : 0ull;
     }
     __syncthreads();
-    // row prefix (64 rows, 4 threads per row would need shuffles; one thread per row is fine: 64 adds)
+    // row prefix, then column prefix (one thread per row / column: 64 integer adds)
     if (threadIdx.x < kT) {
-        double a = 0.0;
+        u64 a = 0;
         for (int c = 0; c < kT; ++c) { a += t[threadIdx.x][c]; t[threadIdx.x][c] = a; }
     }
     __syncthreads();
     if (threadIdx.x < kT) {
-        double a = 0.0;
+        u64 a = 0;
         for (int r = 0; r < kT; ++r) { a += t[r][threadIdx.x]; t[r][threadIdx.x] = a; }
     }
     __syncthreads();
-    const double* top = &L.top[((size_t)p * L.nty + ty) * (L.W + 1)];
-    const double* left = &L.left[((size_t)p * L.ntx + tx) * (L.H + 1)];
-    const double corner = top[x0];
+    const u64* top = &L.top[((size_t)p * L.nty + ty) * (L.W + 1)];
+    const u64* left = &L.left[((size_t)p * L.ntx + tx) * (L.H + 1)];
+    const u64 corner = top[x0];
     for (int i = threadIdx.x; i < kT * kT; i += 256) {
         int r = i / kT, c = i % kT;
         int y = y0 + r, x = x0 + c;
@@ -183,18 +196,69 @@ __global__ void __launch_bounds__(256) k_int_final(const float* __restrict__ s1,
     // zero first row / column
     if (ty == 0)
         for (int c = threadIdx.x; c < kT; c += 256)
-            if (x0 + c < L.W) Pp[x0 + c + 1] = 0.0;
+            if (x0 + c < L.W) Pp[x0 + c + 1] = 0;
     if (tx == 0)
         for (int r = threadIdx.x; r < kT; r += 256)
-            if (y0 + r < L.H) Pp[(size_t)(y0 + r + 1) * ipitch] = 0.0;
-    if (tx == 0 && ty == 0 && threadIdx.x == 0) Pp[0] = 0.0;
+            if (y0 + r < L.H) Pp[(size_t)(y0 + r + 1) * ipitch] = 0;
+    if (tx == 0 && ty == 0 && threadIdx.x == 0) Pp[0] = 0;
+}
+
+// ---- FP64 export: the prefix planes as doubles, NaN where the prefix
+// rectangle holds a non-finite value (counted here, outside the hot path)
+__global__ void k_nf_rows(const float* __restrict__ s1, const float* __restrict__ s2, size_t pitch, int H, int W,
+                          int* __restrict__ C) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * H) return;
+    const int p = i / H, y = i - p * H;
+    const float* s = (p ? s2 : s1) + (size_t)y * pitch;
+    int* row = C + ((size_t)p * (H + 1) + y + 1) * (W + 1);
+    int run = 0;
+    row[0] = 0;
+    for (int x = 0; x < W; ++x) {
+        run += isfinite(s[x]) ? 0 : 1;
+        row[x + 1] = run;
+    }
+}
+
+__global__ void k_nf_cols(int H, int W, int* __restrict__ C) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * (W + 1)) return;
+    const int p = i / (W + 1), x = i - p * (W + 1);
+    int* c = C + (size_t)p * (H + 1) * (W + 1) + x;
+    c[0] = 0;
+    int run = 0;
+    for (int y = 1; y <= H; ++y) {
+        run += c[(size_t)y * (W + 1)];
+        c[(size_t)y * (W + 1)] = run;
+    }
+}
+
+__global__ void k_int_to_f64(const u64* __restrict__ P, size_t ipitch, const int* __restrict__ C, int H, int W,
+                             double* __restrict__ out) {
+    const size_t n = 2 * (size_t)(H + 1) * (W + 1);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t pr = i / (W + 1);
+        const int x = (int)(i - pr * (W + 1));
+        const double v = (double)(long long)P[pr * ipitch + x] * (1.0 / kIntScale);
+        out[i] = C[i] ? NAN : v;
+    }
 }
 
 }  // namespace
 
+size_t integral_export_scratch_bytes(int H, int W) { return sizeof(int) * 2 * (size_t)(H + 1) * (W + 1); }
+
+cudaError_t launch_integral_export(const Cube& c, void* scratch, double* out, cudaStream_t st) {
+    int* C = static_cast<int*>(scratch);
+    k_nf_rows<<<(2 * c.H + 127) / 128, 128, 0, st>>>(c.s1, c.s2, c.pitch, c.H, c.W, C);
+    k_nf_cols<<<(2 * (c.W + 1) + 127) / 128, 128, 0, st>>>(c.H, c.W, C);
+    k_int_to_f64<<<152 * 8, 256, 0, st>>>(c.integ, c.ipitch, C, c.H, c.W, out);
+    return cudaGetLastError();
+}
+
 size_t integral_scratch_bytes(int H, int W) {
     size_t nty = (H + kT - 1) / kT, ntx = (W + kT - 1) / kT;
-    return sizeof(double) * (2 * nty * W + 2 * ntx * H + 2 * nty * (W + 1) + 2 * ntx * (H + 1));
+    return sizeof(u64) * (2 * nty * W + 2 * ntx * H + 2 * nty * (W + 1) + 2 * ntx * (H + 1));
 }
 
 cudaError_t launch_integral(const Cube& c, void* scratch, cudaStream_t st, int* launches) {

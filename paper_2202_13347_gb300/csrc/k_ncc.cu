@@ -2,12 +2,16 @@
 // arXiv 2202.13347; Sec. 3.2.2 takes the most similar position as the CP).
 //
 // k_template_stats  per point: bounds check, R_T and R_TT from the sensed
-//                   cube's integral images (Eq. 12 via Eq. 16), FP64.
+//                   cube's integral images (Eq. 12 via Eq. 16).
 // k_ncc_argmax      per point (one CTA): for every offset, R_S and R_SS from
-//                   the reference integral images (4 lookups each), the
-//                   FP64 variance R_SS - R_S^2/mnz, NCC = num / sqrt(vS vT);
-//                   then a warp-shuffle argmax with the (NCC desc, dy asc,
-//                   dx asc) order and a 3-point parabola per axis.
+//                   the reference integral images (4 lookups each, exact
+//                   64-bit fixed point), the variance R_SS - R_S^2/mnz and
+//                   the numerator in FP64 (the only steps that cancel), then
+//                   NCC = num / sqrt(vS vT) in FP32; a warp-shuffle argmax
+//                   with the (NCC desc, dy asc, dx asc) order and a 3-point
+//                   parabola per axis.  GB300 runs FP64 at a small fraction
+//                   of its FP32 rate, so FP64 is kept to a few operations
+//                   per offset.
 #include <math.h>
 
 #include "internal.h"
@@ -16,11 +20,15 @@ namespace sfoc {
 
 namespace {
 
-__device__ __forceinline__ double rect(const double* P, size_t ip, int y0, int x0, int y1, int x1) {
-    return P[(size_t)y1 * ip + x1] - P[(size_t)y0 * ip + x1] - P[(size_t)y1 * ip + x0] + P[(size_t)y0 * ip + x0];
+typedef unsigned long long u64;
+
+// window sum (Eq. 16) in 2^-28 units; exact (the planes wrap modulo 2^64)
+__device__ __forceinline__ long long rect(const u64* P, size_t ip, int y0, int x0, int y1, int x1) {
+    return (long long)(P[(size_t)y1 * ip + x1] - P[(size_t)y0 * ip + x1] - P[(size_t)y1 * ip + x0] +
+                       P[(size_t)y0 * ip + x0]);
 }
 
-__global__ void k_template_stats(const double* __restrict__ Pr, int Hr, int Wr, const double* __restrict__ Ps,
+__global__ void k_template_stats(const u64* __restrict__ Pr, int Hr, int Wr, const u64* __restrict__ Ps,
                                  int Hs, int Ws, size_t ips, const int32_t* __restrict__ pts, int n, int m, int R,
                                  int z, PointStat* __restrict__ stats) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -38,34 +46,39 @@ __global__ void k_template_stats(const double* __restrict__ Pr, int Hr, int Wr, 
         s.status = SFOC_PT_OUT_OF_BOUNDS;
     } else {
         const double N = (double)m * m * z;
-        const double* P1 = Ps;
-        const double* P2 = Ps + (size_t)(Hs + 1) * ips;
-        s.RT = rect(P1, ips, ty0, tx0, ty0 + m, tx0 + m);
-        s.RTT = rect(P2, ips, ty0, tx0, ty0 + m, tx0 + m);
-        s.tmean = (float)(s.RT / N);
-        double vT = s.RTT - s.RT * s.RT / N;
-        if (s.RT != s.RT || s.RTT != s.RTT) s.status = SFOC_PT_NAN;
-        else if (vT <= 1e-6 * N) s.status = SFOC_PT_FLAT_TEMPLATE;
-        else s.status = SFOC_PT_OK;
+        const u64* P1 = Ps;
+        const u64* P2 = Ps + (size_t)(Hs + 1) * ips;
+        const long long rt = rect(P1, ips, ty0, tx0, ty0 + m, tx0 + m);
+        const long long rtt = rect(P2, ips, ty0, tx0, ty0 + m, tx0 + m);
+        if (rt >= kIntNonFiniteMin || rtt >= kIntNonFiniteMin) {
+            s.RT = s.RTT = NAN;
+            s.status = SFOC_PT_NAN;
+        } else {
+            s.RT = int_units_to_double(rt);
+            s.RTT = int_units_to_double(rtt);
+            s.tmean = (float)(s.RT / N);
+            const double vT = s.RTT - s.RT * s.RT / N;
+            s.status = vT <= 1e-6 * N ? SFOC_PT_FLAT_TEMPLATE : SFOC_PT_OK;
+        }
     }
     stats[k] = s;
 }
 
 // argmax key: larger value wins, ties go to the smaller index
-__device__ __forceinline__ bool better(double v, int i, double bv, int bi) {
+__device__ __forceinline__ bool better(float v, int i, float bv, int bi) {
     return v > bv || (v == bv && i < bi);
 }
 
 constexpr int kNccThreads = 256;
 
-__global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const double* __restrict__ Pr, int Hr, size_t ipr,
+__global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const u64* __restrict__ Pr, int Hr, size_t ipr,
                                                             const int32_t* __restrict__ pts, int m, int R, int z,
                                                             const PointStat* __restrict__ stats,
                                                             const float* __restrict__ num, int centered,
                                                             float* __restrict__ out_maps,
                                                             fastncc_result* __restrict__ out) {
-    extern __shared__ double s_map[];  // P1 * P1
-    __shared__ double s_bv[kNccThreads / 32];
+    extern __shared__ float s_map[];  // P1 * P1
+    __shared__ float s_bv[kNccThreads / 32];
     __shared__ int s_bi[kNccThreads / 32];
     __shared__ int s_nan;
     const int k = blockIdx.x;
@@ -84,30 +97,34 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const double* __rest
         return;
     }
     __syncthreads();
-    const double N = (double)m * m * z;
-    const double vT = st.RTT - st.RT * st.RT / N;
+    const double N = (double)m * m * z, invN = 1.0 / N, flat = 1e-6 * N;
+    const float vTf = (float)(st.RTT - st.RT * st.RT * invN);
+    const double rt_n = st.RT * invN;
     const int h = template_half(m);
     const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
-    const double* P1p = Pr;
-    const double* P2p = Pr + (size_t)(Hr + 1) * ipr;
+    const u64* P1p = Pr;
+    const u64* P2p = Pr + (size_t)(Hr + 1) * ipr;
     const float* nk = num + (size_t)k * P;
-    double bv = -INFINITY;
+    float bv = -INFINITY;
     int bi = 0x7fffffff;
     int has_nan = 0;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        int iy = i / P1, ix = i - iy * P1;
-        int wy = ty0 + iy - R, wx = tx0 + ix - R;
-        double RS = rect(P1p, ipr, wy, wx, wy + m, wx + m);
-        double RSS = rect(P2p, ipr, wy, wx, wy + m, wx + m);
-        double vS = RSS - RS * RS / N;
-        double nm = (double)nk[i];
-        if (!centered) nm -= RS * st.RT / N;
-        double v;
-        if (vS != vS || nm != nm) v = NAN;
-        else if (vS <= 1e-6 * N) v = 0.0;
-        else v = nm / sqrt(vS * vT);
+        const int iy = i / P1, ix = i - iy * P1;
+        const int wy = ty0 + iy - R, wx = tx0 + ix - R;
+        const long long rs = rect(P1p, ipr, wy, wx, wy + m, wx + m);
+        const long long rss = rect(P2p, ipr, wy, wx, wy + m, wx + m);
+        const float n32 = nk[i];
+        float v;
+        if (rs >= kIntNonFiniteMin || rss >= kIntNonFiniteMin || n32 != n32) {
+            v = NAN;
+        } else {
+            const double RS = int_units_to_double(rs), RSS = int_units_to_double(rss);
+            const double vS = fma(-RS, RS * invN, RSS);
+            const double nm = centered ? (double)n32 : fma(-RS, rt_n, (double)n32);
+            v = vS <= flat ? 0.f : (float)nm / sqrtf((float)vS * vTf);
+        }
         s_map[i] = v;
-        if (out_maps) out_maps[(size_t)k * P + i] = (float)v;
+        if (out_maps) out_maps[(size_t)k * P + i] = v;
         if (v != v) { has_nan = 1; continue; }
         if (better(v, i, bv, bi)) { bv = v; bi = i; }
     }
@@ -115,7 +132,7 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const double* __rest
     const unsigned full = 0xffffffffu;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(full, bv, o);
+        float ov = __shfl_down_sync(full, bv, o);
         int oi = __shfl_down_sync(full, bi, o);
         if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
     }
@@ -141,7 +158,7 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const double* __rest
             res.ncc = (float)bv;
             bool edge = false;
             double ddx = 0.0, ddy = 0.0;
-            auto parab = [](double cm, double c0, double cp) {
+            auto parab = [](double cm, double c0, double cp) {  // from the FP32 map values
                 double den = cm - 2.0 * c0 + cp;
                 if (!(den < 0.0)) return 0.0;
                 double d = (cm - cp) / (2.0 * den);
@@ -176,7 +193,7 @@ cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m,
                               cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int P1 = 2 * R + 1;
-    size_t smem = sizeof(double) * (size_t)P1 * P1;
+    size_t smem = sizeof(float) * (size_t)P1 * P1;
     cudaError_t e = cudaFuncSetAttribute(k_ncc_argmax, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_ncc_argmax<<<n, kNccThreads, smem, st>>>(ref.integ, ref.H, ref.ipitch, pts, m, R, ref.z, stats, num, centered,

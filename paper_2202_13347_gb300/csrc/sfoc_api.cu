@@ -269,7 +269,7 @@ sfoc_status alloc_cube(sfoc_ctx* ctx, Cube& c, int H, int W, int z, int dtype) {
     }
     if (e == cudaSuccess) e = cudaMalloc(&c.s1, sizeof(float) * plane);
     if (e == cudaSuccess) e = cudaMalloc(&c.s2, sizeof(float) * plane);
-    if (e == cudaSuccess) e = cudaMalloc(&c.integ, sizeof(double) * 2 * (size_t)(H + 1) * c.ipitch);
+    if (e == cudaSuccess) e = cudaMalloc(&c.integ, sizeof(unsigned long long) * 2 * (size_t)(H + 1) * c.ipitch);
     if (e != cudaSuccess) {
         free_cube_mem(c);
         return cuda_fail(ctx, e, "cudaMalloc(cube)");
@@ -548,10 +548,14 @@ sfoc_status sfoc_cube_export_integral(sfoc_ctx* ctx, sfoc_cube* cube, double* d_
     sfoc_status s = build_integral(ctx, cube->c);
     if (s != SFOC_OK) return s;
     const Cube& c = cube->c;
-    cudaError_t e = cudaMemcpy2DAsync(d_out, sizeof(double) * (c.W + 1), c.integ, sizeof(double) * c.ipitch,
-                                      sizeof(double) * (c.W + 1), 2 * (size_t)(c.H + 1), cudaMemcpyDeviceToDevice,
-                                      ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy integral");
+    s = ensure_ws(ctx, integral_export_scratch_bytes(c.H, c.W));
+    if (s != SFOC_OK) return s;
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_OTHER, 3);
+        e = launch_integral_export(c, ctx->ws, d_out, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "integral export launch");
     return SFOC_OK;
 }
 
