@@ -197,29 +197,60 @@ __device__ __forceinline__ void smooth_channel(const float* __restrict__ Fk, siz
 // one column in the vertical pass) and applies all three rates from there,
 // instead of reading shared memory once per tap and rate.  Same arithmetic,
 // same order of operations per output as smooth_channel.
+// Input tile layout of the compile-time path: shared column j of a row holds
+// image column x0 - OFF + j, OFF = hal rounded up to 4, so every row starts
+// on a 16-byte boundary in global and shared memory.
+template <int HAL>
+struct TileGeom {
+    static constexpr int OFF = (HAL + 3) / 4 * 4;
+    static constexpr int NL = (OFF + kSTW + HAL + 3) / 4;  // float4 per row (covers the halo)
+    static constexpr int IH = kSTH + 2 * HAL;
+};
+
+// Asynchronous copy of one channel's input tile into shared memory, one
+// commit group per tile.  Interior tiles copy whole rows as 16-byte pieces;
+// tiles at the image border copy element by element with clamped indices.
+template <int HAL>
+__device__ __forceinline__ void tile_load_async(const float* __restrict__ Fk, size_t fpitch, int H, int W, int x0,
+                                                int y0, float* dst, int FW) {
+    using TG = TileGeom<HAL>;
+    const int xs = x0 - TG::OFF;
+    const bool interior = xs >= 0 && xs + 4 * TG::NL <= W && y0 - HAL >= 0 && y0 + kSTH + HAL <= H;
+    if (interior) {
+        const float* src0 = Fk + (size_t)(y0 - HAL) * fpitch + xs;
+        for (int i = threadIdx.x; i < TG::IH * TG::NL; i += kThreads) {
+            const int rr = i / TG::NL, v = i - rr * TG::NL;
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst + rr * FW + 4 * v);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src0 + (size_t)rr * fpitch + 4 * v)
+                         : "memory");
+        }
+    } else {
+        constexpr int IW = kSTW + 2 * HAL;
+        for (int i = threadIdx.x; i < TG::IH * IW; i += kThreads) {
+            const int rr = i / IW, cc = i - rr * IW;  // tile column cc = image column x0 - HAL + cc
+            const int yy = clampi(y0 + rr - HAL, 0, H - 1), xx = clampi(x0 + cc - HAL, 0, W - 1);
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst + rr * FW + (TG::OFF - HAL) + cc);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(Fk + (size_t)yy * fpitch + xx)
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One channel with the tile already in s_F (the caller waited for its copy
+// and synchronised the block).
 template <int KD>
-__device__ __forceinline__ void smooth_channel_123(const float* __restrict__ Fk, size_t fpitch, int H, int W, int x0,
-                                                   int y0, const float* t, float* s_F, int FW, float* s_h, int HR,
+__device__ __forceinline__ void smooth_channel_123(const float* t, const float* s_F, int FW, float* s_h, int HR,
                                                    float (&Dk)[kSRows]) {
     constexpr int hal = 3 * KD;
-    constexpr int IW = kSTW + 2 * hal, IH = kSTH + 2 * hal;
-    __syncthreads();  // previous channel done with s_F / s_h (and, at the start, the taps are written)
+    constexpr int IH = kSTH + 2 * hal;
     float tq[KD + 1];
 #pragma unroll
     for (int q = 0; q <= KD; ++q) tq[q] = t[q];
-    for (int rr = threadIdx.x >> 3; rr < IH; rr += kThreads >> 3) {
-        const int yy = clampi(y0 + rr - hal, 0, H - 1);
-        const float* row = Fk + (size_t)yy * fpitch;
-        const int cb = (threadIdx.x & 7) * 8;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int cc = cb + c;
-            if (cc < IW) s_F[rr * FW + cc] = __ldg(row + clampi(x0 + cc - hal, 0, W - 1));
-        }
-    }
-    __syncthreads();
-    // horizontal: task = (row, 8-column block); inputs cb .. cb + 8 + 2 hal
-    constexpr int NV = (8 + 2 * hal + 3) / 4;
+    // horizontal: task = (row, 8-column block); the block's inputs are
+    // shared columns cb + OFF - hal .. cb + OFF + 7 + hal
+    constexpr int OFF = TileGeom<hal>::OFF;
+    constexpr int NV = (OFF + 8 + hal + 3) / 4;
     for (int task = threadIdx.x; task < IH * 4; task += kThreads) {
         const int rr = task >> 2, cb = (task & 3) * 8;
         const float4* x4 = reinterpret_cast<const float4*>(s_F + rr * FW + cb);
@@ -237,9 +268,9 @@ __device__ __forceinline__ void smooth_channel_123(const float* __restrict__ Fk,
             float o[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                float a = tq[0] * in[hal + c];
+                float a = tq[0] * in[OFF + c];
 #pragma unroll
-                for (int q = 1; q <= KD; ++q) a = fmaf(tq[q], in[hal + c - q * r] + in[hal + c + q * r], a);
+                for (int q = 1; q <= KD; ++q) a = fmaf(tq[q], in[OFF + c - q * r] + in[OFF + c + q * r], a);
                 o[c] = a;
             }
             float4* dst = reinterpret_cast<float4*>(s_h + ((r - 1) * HR + rr) * kSTW + cb);
@@ -278,8 +309,8 @@ __device__ __forceinline__ void smooth_channel_123(const float* __restrict__ Fk,
 template <int NO, int KDG>
 __device__ __forceinline__ void smooth_group(int g, const float* __restrict__ F, size_t fpitch, size_t fplane, int H,
                                              int W, const SmoothTaps& tp, const int* s_dil, const float* t,
-                                             float* s_F, int FW, float* s_h, int HR, int x0, int y0,
-                                             float* __restrict__ c32, size_t cpitch, size_t cplane,
+                                             float* s_F, float* s_F2, int FW, float* s_h, int HR, int x0,
+                                             int y0, float* __restrict__ c32, size_t cpitch, size_t cplane,
                                              __nv_bfloat16* __restrict__ rm, __nv_bfloat16* __restrict__ cm,
                                              float (&a1)[kSRows], float (&a2)[kSRows]) {
     constexpr int KO = NO > 0 ? NO : kMaxOrient;
@@ -288,12 +319,24 @@ __device__ __forceinline__ void smooth_group(int g, const float* __restrict__ F,
     const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
     const int gx = x0 + col;
     float D[KO][kSRows];
+    if constexpr (KDG > 0) {
+        __syncthreads();  // the previous group is done with both tile buffers
+        tile_load_async<3 * KDG>(F + (size_t)(g * no) * fplane, fpitch, H, W, x0, y0, s_F, FW);
+    }
 #pragma unroll
     for (int k = 0; k < KO; ++k) {
         if (k >= no) break;
         const float* Fk = F + (size_t)(g * no + k) * fplane;
         if constexpr (KDG > 0) {
-            smooth_channel_123<KDG>(Fk, fpitch, H, W, x0, y0, t, s_F, FW, s_h, HR, D[k]);
+            // tile k is in buffer k & 1; prefetch tile k+1 into the other one
+            // (its last reader, channel k-1's horizontal pass, is behind the
+            // barrier that ended that pass)
+            if (k + 1 < no)
+                tile_load_async<3 * KDG>(Fk + fplane, fpitch, H, W, x0, y0, (k & 1) ? s_F : s_F2, FW);
+            if (k + 1 < no) asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();  // tile k visible; every thread is done with channel k-1
+            smooth_channel_123<KDG>(t, (k & 1) ? s_F2 : s_F, FW, s_h, HR, D[k]);
         } else {
             const int hal = tp.halo[g], Kd = tp.Kd[g];
             switch (Kd) {
@@ -371,15 +414,16 @@ __global__ void __launch_bounds__(kThreads, KD1 > 0 ? 2 : 1)
     for (int j = 0; j < kSRows; ++j) a1[j] = a2[j] = 0.f;
 
     if constexpr (KD1 > 0) {
-        smooth_group<NO, KD1>(0, F, fpitch, fplane, H, W, tp, s_dil, s_tap[0], s_F, FW, s_h, HR, x0, y0, c32, cpitch,
-                              cplane, rm, cm, a1, a2);
+        float* s_F2 = s_h + tp.n_dil * HR * kSTW;  // second input tile buffer
+        smooth_group<NO, KD1>(0, F, fpitch, fplane, H, W, tp, s_dil, s_tap[0], s_F, s_F2, FW, s_h, HR, x0, y0, c32,
+                              cpitch, cplane, rm, cm, a1, a2);
         if (ng > 1)
-            smooth_group<NO, KD2>(1, F, fpitch, fplane, H, W, tp, s_dil, s_tap[1], s_F, FW, s_h, HR, x0, y0, c32,
-                                  cpitch, cplane, rm, cm, a1, a2);
+            smooth_group<NO, KD2>(1, F, fpitch, fplane, H, W, tp, s_dil, s_tap[1], s_F, s_F2, FW, s_h, HR, x0, y0,
+                                  c32, cpitch, cplane, rm, cm, a1, a2);
     } else {
         for (int g = 0; g < ng; ++g)
-            smooth_group<NO, 0>(g, F, fpitch, fplane, H, W, tp, s_dil, s_tap[g], s_F, FW, s_h, HR, x0, y0, c32,
-                                cpitch, cplane, rm, cm, a1, a2);
+            smooth_group<NO, 0>(g, F, fpitch, fplane, H, W, tp, s_dil, s_tap[g], s_F, nullptr, FW, s_h, HR, x0, y0,
+                                c32, cpitch, cplane, rm, cm, a1, a2);
     }
 #pragma unroll
     for (int j = 0; j < kSRows; ++j) {
@@ -448,6 +492,7 @@ cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, cons
                        tp.dil[2] == 3 && tp.Kd[0] == 3 && tp.Kd[1] == 5;
     if (paper) {  // sigma_d 1.0 / 1.5 with rates 1, 2, 3 (Sec. 2.1)
         auto kern = k_sfoc_smooth<6, 3, 5>;
+        smem += sizeof(float) * (size_t)HR * FW;  // second input tile buffer
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
