@@ -85,6 +85,7 @@ cudaError_t launch_sfoc_steer(const uint16_t* img, int H, int W, size_t pitch, f
                               const SteerTaps& tp, int z_first, cudaStream_t st);
 cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,
                                cudaStream_t st);
+int smooth_launch_count(const SmoothTaps& tp);  // kernels launch_sfoc_smooth launches
 cudaError_t launch_cube_export(const Cube& c, float* out, cudaStream_t st);
 
 // Integral planes in fixed point: a value v counts as round(v * 2^28), sums

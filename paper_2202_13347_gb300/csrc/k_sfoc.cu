@@ -381,12 +381,52 @@ __device__ __forceinline__ void smooth_group(int g, const float* __restrict__ F,
     }
 }
 
-// KD1, KD2 > 0: the paper's dilation rates 1, 2, 3 with smoothing radii KD1
-// (first-order group) and KD2 (second-order group) at compile time, so the
-// kernel holds only the code it runs and fits two CTAs per SM; KD1 == 0:
-// any radii and rates at run time.
-template <int NO, int KD1, int KD2>
-__global__ void __launch_bounds__(kThreads, KD1 > 0 ? 2 : 1)
+// The paper's dilation rates 1, 2, 3 with smoothing radius KDG at compile
+// time, one group g per launch: the kernel holds only one group's code (its
+// instruction footprint is what limits the fully unrolled passes) and fits
+// two CTAs per SM.  The second group's launch continues the per-pixel sums
+// from the stored planes, adding in the same order as one launch would.
+template <int NO, int KDG>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_sfoc_smooth_grp(const float* __restrict__ F, size_t fpitch, size_t fplane, int H, int W, SmoothTaps tp, int g,
+                      float* __restrict__ c32, size_t cpitch, size_t cplane, __nv_bfloat16* __restrict__ rm,
+                      __nv_bfloat16* __restrict__ cm, float* __restrict__ s1, float* __restrict__ s2) {
+    extern __shared__ float sm[];
+    __shared__ float s_tap[kMaxSmoothRadius + 1];
+    if (threadIdx.x <= kMaxSmoothRadius) s_tap[threadIdx.x] = tp.g[g][threadIdx.x];
+    constexpr int hal = 3 * KDG;
+    const int FW = smooth_row_stride(hal);
+    constexpr int HR = kSTH + 2 * hal;
+    float* s_F = sm;                   // HR x FW
+    float* s_h = s_F + HR * FW;        // 3 x HR x kSTW
+    float* s_F2 = s_h + 3 * HR * kSTW;  // second input tile buffer
+    const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH;
+    const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
+    const int gx = x0 + col;
+
+    float a1[kSRows], a2[kSRows];
+#pragma unroll
+    for (int j = 0; j < kSRows; ++j) {
+        const int gy = y0 + rb + j;
+        const bool in = g > 0 && gy < H && gx < W;
+        a1[j] = in ? s1[(size_t)gy * cpitch + gx] : 0.f;
+        a2[j] = in ? s2[(size_t)gy * cpitch + gx] : 0.f;
+    }
+    smooth_group<NO, KDG>(g, F, fpitch, fplane, H, W, tp, nullptr, s_tap, s_F, s_F2, FW, s_h, HR, x0, y0, c32, cpitch,
+                          cplane, rm, cm, a1, a2);
+#pragma unroll
+    for (int j = 0; j < kSRows; ++j) {
+        const int gy = y0 + rb + j;
+        if (gy < H && gx < W) {
+            s1[(size_t)gy * cpitch + gx] = a1[j];
+            s2[(size_t)gy * cpitch + gx] = a2[j];
+        }
+    }
+}
+
+// Any radii and rates at run time.
+template <int NO>
+__global__ void __launch_bounds__(kThreads, 1)
     k_sfoc_smooth(const float* __restrict__ F, size_t fpitch, size_t fplane, int H, int W, SmoothTaps tp,
                   float* __restrict__ c32, size_t cpitch, size_t cplane, __nv_bfloat16* __restrict__ rm,
                   __nv_bfloat16* __restrict__ cm, float* __restrict__ s1, float* __restrict__ s2) {
@@ -412,19 +452,9 @@ __global__ void __launch_bounds__(kThreads, KD1 > 0 ? 2 : 1)
     float a1[kSRows], a2[kSRows];
 #pragma unroll
     for (int j = 0; j < kSRows; ++j) a1[j] = a2[j] = 0.f;
-
-    if constexpr (KD1 > 0) {
-        float* s_F2 = s_h + tp.n_dil * HR * kSTW;  // second input tile buffer
-        smooth_group<NO, KD1>(0, F, fpitch, fplane, H, W, tp, s_dil, s_tap[0], s_F, s_F2, FW, s_h, HR, x0, y0, c32,
-                              cpitch, cplane, rm, cm, a1, a2);
-        if (ng > 1)
-            smooth_group<NO, KD2>(1, F, fpitch, fplane, H, W, tp, s_dil, s_tap[1], s_F, s_F2, FW, s_h, HR, x0, y0,
-                                  c32, cpitch, cplane, rm, cm, a1, a2);
-    } else {
-        for (int g = 0; g < ng; ++g)
-            smooth_group<NO, 0>(g, F, fpitch, fplane, H, W, tp, s_dil, s_tap[g], s_F, nullptr, FW, s_h, HR, x0, y0,
-                                c32, cpitch, cplane, rm, cm, a1, a2);
-    }
+    for (int g = 0; g < ng; ++g)
+        smooth_group<NO, 0>(g, F, fpitch, fplane, H, W, tp, s_dil, s_tap[g], s_F, nullptr, FW, s_h, HR, x0, y0, c32,
+                            cpitch, cplane, rm, cm, a1, a2);
 #pragma unroll
     for (int j = 0; j < kSRows; ++j) {
         const int gy = y0 + rb + j;
@@ -433,6 +463,11 @@ __global__ void __launch_bounds__(kThreads, KD1 > 0 ? 2 : 1)
             s2[(size_t)gy * cpitch + gx] = a2[j];
         }
     }
+}
+
+bool smooth_is_paper(const SmoothTaps& tp) {
+    return tp.no == 6 && tp.z == 12 && tp.n_dil == 3 && tp.dil[0] == 1 && tp.dil[1] == 2 && tp.dil[2] == 3 &&
+           tp.Kd[0] == 3 && tp.Kd[1] == 5;
 }
 
 __global__ void k_cube_export_bf16(const __nv_bfloat16* __restrict__ rm, int H, int W, int z, float* __restrict__ out) {
@@ -481,36 +516,43 @@ cudaError_t launch_sfoc_steer(const uint16_t* img, int H, int W, size_t pitch, f
     return launch_steer_any(img, H, W, pitch, F, fpitch, tp, st);
 }
 
+int smooth_launch_count(const SmoothTaps& tp) { return smooth_is_paper(tp) ? 2 : 1; }
+
 cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,
                                cudaStream_t st) {
+    dim3 grid((W + kSTW - 1) / kSTW, (H + kSTH - 1) / kSTH);
+    cudaError_t e;
+    if (smooth_is_paper(tp)) {  // sigma_d 1.0 / 1.5 with rates 1, 2, 3 (Sec. 2.1): one launch per group
+        auto run = [&](auto kern, int g, int hal) -> cudaError_t {
+            const int HR = kSTH + 2 * hal, FW = smooth_row_stride(hal);
+            const size_t smem = sizeof(float) * (2 * (size_t)HR * FW + 3 * (size_t)HR * kSTW);
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e2 == cudaSuccess)
+                e2 = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared);
+            if (e2 != cudaSuccess) return e2;
+            kern<<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, g, c.f32, c.pitch,
+                                               c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+            return cudaGetLastError();
+        };
+        e = run(k_sfoc_smooth_grp<6, 3>, 0, 9);
+        if (e == cudaSuccess) e = run(k_sfoc_smooth_grp<6, 5>, 1, 15);
+        return e;
+    }
     const int maxhal = tp.halo[0] > tp.halo[1] ? tp.halo[0] : tp.halo[1];
     const int HR = kSTH + 2 * maxhal, FW = smooth_row_stride(maxhal);
     size_t smem = sizeof(float) * ((size_t)HR * FW + (size_t)tp.n_dil * HR * kSTW);
-    dim3 grid((W + kSTW - 1) / kSTW, (H + kSTH - 1) / kSTH);
-    cudaError_t e;
-    const bool paper = tp.no == 6 && tp.z == 12 && tp.n_dil == 3 && tp.dil[0] == 1 && tp.dil[1] == 2 &&
-                       tp.dil[2] == 3 && tp.Kd[0] == 3 && tp.Kd[1] == 5;
-    if (paper) {  // sigma_d 1.0 / 1.5 with rates 1, 2, 3 (Sec. 2.1)
-        auto kern = k_sfoc_smooth<6, 3, 5>;
-        smem += sizeof(float) * (size_t)HR * FW;  // second input tile buffer
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
+    if (tp.no == 6) {
+        e = cudaFuncSetAttribute(k_sfoc_smooth<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
-                                           c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
-    } else if (tp.no == 6) {
-        e = cudaFuncSetAttribute(k_sfoc_smooth<6, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_sfoc_smooth<6, 0, 0><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
-                                                             c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+        k_sfoc_smooth<6><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
+                                                       c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
     } else {
         if (c.rm) return cudaErrorNotSupported;  // bf16 layouts need 12 channels
-        e = cudaFuncSetAttribute(k_sfoc_smooth<0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sfoc_smooth<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_sfoc_smooth<0, 0, 0><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
-                                                             c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
+        k_sfoc_smooth<0><<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, c.f32, c.pitch,
+                                                       c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
     }
     return cudaGetLastError();
 }

@@ -347,7 +347,7 @@ sfoc_status build_cube(sfoc_ctx* ctx, const T* d_image, int H, int W, size_t pit
         e = launch_sfoc_steer(d_image, H, W, pitch_elems, F, fpitch, st, z, ctx->stream);
     }
     if (e == cudaSuccess) {
-        StageScope sc(ctx, ST_SMOOTH, 1);
+        StageScope sc(ctx, ST_SMOOTH, smooth_launch_count(sm));
         e = launch_sfoc_smooth(F, fpitch, H, W, sm, cube->c, ctx->stream);
     }
     if (e != cudaSuccess) {
@@ -794,7 +794,7 @@ sfoc_status sfoc_build_static(sfoc_ctx* ctx, const float* d_image, int H, int W,
     c.s2 = c.s1 + (size_t)H * W;
     const SteerTaps st = make_steer(p);
     const SmoothTaps sm = make_smooth(p);
-    ctx->launches += 2;
+    ctx->launches += 1 + smooth_launch_count(sm);
     e = launch_sfoc_steer(d_image, H, W, pitch_elems, F, fpitch, st, z, ctx->stream);
     if (e == cudaSuccess) e = launch_sfoc_smooth(F, fpitch, H, W, sm, c, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sfoc kernels");
