@@ -11,6 +11,8 @@
 // output pixel.  Borders clamp to the edge in every convolution.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace sfoc {
@@ -121,6 +123,138 @@ __global__ void __launch_bounds__(kThreads) k_sfoc_steer(const T* __restrict__ i
                 float v = fmaf(c2, Ixx, fmaf(s2, Iyy, -cs * Ixy));
                 out[(size_t)(tp.no + k) * fplane] = tp.rectify ? fabsf(v) : v;
             }
+        }
+    }
+}
+
+// Steering with the radii at compile time (three first-order scales of
+// radii KA, KB, KC and the second-order radius KS; the paper's scales give
+// 2, 3, 3 and 5).  Same arithmetic per output as k_sfoc_steer, register
+// blocked: a thread of the horizontal pass loads one row span once (float4)
+// and produces all nine basis planes for 8 columns; a thread of the
+// vertical pass loads each plane's column span once and produces 4 rows.
+template <int K>
+__device__ __forceinline__ float ceven(const float* x, const float* t) {
+    float acc = t[0] * x[0];
+#pragma unroll
+    for (int q = 1; q <= K; ++q) acc = fmaf(t[q], x[-q] + x[q], acc);
+    return acc;
+}
+template <int K>
+__device__ __forceinline__ float codd(const float* x, const float* t) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 1; q <= K; ++q) acc = fmaf(t[q], x[-q] - x[q], acc);
+    return acc;
+}
+
+template <typename T, int KA, int KB, int KC, int KS>
+__global__ void __launch_bounds__(kThreads) k_sfoc_steer_ct(const T* __restrict__ img, int H, int W, size_t pitch,
+                                                             float* __restrict__ F, size_t fpitch, size_t fplane,
+                                                             SteerTaps tp) {
+    constexpr int HAL = KS > KA ? (KS > KB ? (KS > KC ? KS : KC) : (KB > KC ? KB : KC))
+                                : (KA > KB ? (KA > KC ? KA : KC) : (KB > KC ? KB : KC));
+    constexpr int IH = kTH + 2 * HAL, IW = kTW + 2 * HAL;
+    constexpr int NV = (8 + 2 * HAL + 3) / 4;            // float4 per horizontal span
+    constexpr int IWP = ((24 + 4 * NV + 3) / 4 % 2) ? (24 + 4 * NV + 3) / 4 * 4 : (24 + 4 * NV + 3) / 4 * 4 + 4;
+    constexpr int NP = 9;                                 // basis planes
+    __shared__ __align__(16) float s_img[IH * IWP];
+    extern __shared__ float4 sm4[];
+    float* s_h = reinterpret_cast<float*>(sm4);          // NP x IH x kTW
+    __shared__ float s_t[NP][kMaxDerivRadius + 1];        // taps of the nine 1-D factors
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    if (threadIdx.x < NP * (kMaxDerivRadius + 1)) {
+        const int pl = threadIdx.x / (kMaxDerivRadius + 1), q = threadIdx.x % (kMaxDerivRadius + 1);
+        const float* src = pl < 6 ? ((pl & 1) ? tp.g1[pl >> 1] : tp.a1[pl >> 1])
+                                  : (pl == 6 ? tp.a2 : (pl == 7 ? tp.g2 : tp.c2x));
+        s_t[pl][q] = src[q];
+    }
+    for (int i = threadIdx.x; i < IH * IW; i += kThreads) {
+        const int r = i / IW, c = i - r * IW;
+        const int gy = clampi(y0 + r - HAL, 0, H - 1), gx = clampi(x0 + c - HAL, 0, W - 1);
+        s_img[r * IWP + c] = to_unit(__ldg(img + (size_t)gy * pitch + gx));
+    }
+    __syncthreads();
+    // horizontal: task = (row, 8-column block); planes 2s = a1_s (odd),
+    // 2s+1 = g1_s (even), 6 = a2 (even), 7 = g2 (even), 8 = c2x (odd)
+    for (int task = threadIdx.x; task < IH * 4; task += kThreads) {
+        const int rr = task >> 2, cb = (task & 3) * 8;
+        const float4* x4 = reinterpret_cast<const float4*>(s_img + rr * IWP + cb);
+        float in[NV * 4];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float4 f = x4[v];
+            in[4 * v] = f.x;
+            in[4 * v + 1] = f.y;
+            in[4 * v + 2] = f.z;
+            in[4 * v + 3] = f.w;
+        }
+        float o[NP][8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float* x = in + HAL + c;
+            o[0][c] = codd<KA>(x, s_t[0]);
+            o[1][c] = ceven<KA>(x, s_t[1]);
+            o[2][c] = codd<KB>(x, s_t[2]);
+            o[3][c] = ceven<KB>(x, s_t[3]);
+            o[4][c] = codd<KC>(x, s_t[4]);
+            o[5][c] = ceven<KC>(x, s_t[5]);
+            o[6][c] = ceven<KS>(x, s_t[6]);
+            o[7][c] = ceven<KS>(x, s_t[7]);
+            o[8][c] = codd<KS>(x, s_t[8]);
+        }
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl) {
+            float4* dst = reinterpret_cast<float4*>(s_h + (pl * IH + rr) * kTW + cb);
+            dst[0] = make_float4(o[pl][0], o[pl][1], o[pl][2], o[pl][3]);
+            dst[1] = make_float4(o[pl][4], o[pl][5], o[pl][6], o[pl][7]);
+        }
+    }
+    __syncthreads();
+    // vertical: thread = (column, 4-row block)
+    const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * 4;
+    float Ix[3][4], Iy[3][4], Ixx[4], Iyy[4], Ixy[4];
+    auto vpass = [&](int pl, auto kr, auto odd, const float* t, float (&out)[4]) {
+        constexpr int K = decltype(kr)::value;
+        float in[4 + 2 * K];
+        const float* x = s_h + (pl * IH + rb + HAL - K) * kTW + col;
+#pragma unroll
+        for (int i = 0; i < 4 + 2 * K; ++i) in[i] = x[i * kTW];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[j] = decltype(odd)::value ? codd<K>(in + K + j, t) : ceven<K>(in + K + j, t);
+    };
+    using F0 = std::integral_constant<bool, false>;
+    using T1 = std::integral_constant<bool, true>;
+    vpass(0, std::integral_constant<int, KA>(), F0(), tp.g1[0], Ix[0]);  // a1(x) g(y)
+    vpass(1, std::integral_constant<int, KA>(), T1(), tp.a1[0], Iy[0]);  // g(x) a1(y)
+    vpass(2, std::integral_constant<int, KB>(), F0(), tp.g1[1], Ix[1]);
+    vpass(3, std::integral_constant<int, KB>(), T1(), tp.a1[1], Iy[1]);
+    vpass(4, std::integral_constant<int, KC>(), F0(), tp.g1[2], Ix[2]);
+    vpass(5, std::integral_constant<int, KC>(), T1(), tp.a1[2], Iy[2]);
+    vpass(6, std::integral_constant<int, KS>(), F0(), tp.g2, Ixx);       // a2(x) g2(y)
+    vpass(7, std::integral_constant<int, KS>(), F0(), tp.a2, Iyy);       // g2(x) a2(y)
+    vpass(8, std::integral_constant<int, KS>(), T1(), tp.c2y, Ixy);      // c(x) c(y)
+    const int gx = x0 + col;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gy = y0 + rb + j;
+        if (gy >= H || gx >= W) continue;
+        float* out = F + (size_t)gy * fpitch + gx;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float f = 0.f;
+#pragma unroll
+            for (int sc = 0; sc < 3; ++sc) {
+                float v = fmaf(tp.ct[k], Ix[sc][j], tp.st[k] * Iy[sc][j]);
+                f += tp.rectify ? fabsf(v) : v;
+            }
+            out[(size_t)k * fplane] = f;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float c2 = tp.ct[k] * tp.ct[k], s2 = tp.st[k] * tp.st[k], cs = 2.f * tp.st[k] * tp.ct[k];
+            float v = fmaf(c2, Ixx[j], fmaf(s2, Iyy[j], -cs * Ixy[j]));
+            out[(size_t)(6 + k) * fplane] = tp.rectify ? fabsf(v) : v;
         }
     }
 }
@@ -493,13 +627,22 @@ __global__ void k_cube_export_f32(const float* __restrict__ c32, int H, int W, i
 template <typename T>
 cudaError_t launch_steer_any(const T* img, int H, int W, size_t pitch, float* F, size_t fpitch, const SteerTaps& tp,
                              cudaStream_t st) {
+    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
+    // the paper's scales (0.6, 0.8, 1.0 and 1.5 at 3 sigma: radii 2, 3, 3, 5), six orientations
+    if (tp.ns == 3 && tp.K1[0] == 2 && tp.K1[1] == 3 && tp.K1[2] == 3 && tp.second && tp.K2 == 5 && tp.no == 6) {
+        auto kern = k_sfoc_steer_ct<T, 2, 3, 3, 5>;
+        const size_t smem = sizeof(float) * 9 * (size_t)(kTH + 10) * kTW;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, kThreads, smem, st>>>(img, H, W, pitch, F, fpitch, fpitch * (size_t)H, tp);
+        return cudaGetLastError();
+    }
     const int hal = tp.halo;
     const int IH = kTH + 2 * hal, IW = kTW + 2 * hal;
     const int np = 2 * tp.ns + (tp.second ? 3 : 0);
     size_t smem = sizeof(float) * ((size_t)IH * IW + (size_t)np * IH * kTW);
     cudaError_t e = cudaFuncSetAttribute(k_sfoc_steer<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
     k_sfoc_steer<T><<<grid, kThreads, smem, st>>>(img, H, W, pitch, F, fpitch, fpitch * (size_t)H, tp);
     return cudaGetLastError();
 }
