@@ -509,8 +509,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ---------------------------------------------------------------------------
 constexpr int kColMaxG = 16;
 constexpr int kColQ = 8;   // template columns per stage and columns per slab
-constexpr int kColMaxWS = 5;
-constexpr int kColMaxTS = 3;
+constexpr int kColMaxWS = 4;
+constexpr int kColMaxTS = 2;
+constexpr int kColSmemMax = 225 * 1024;  // dynamic shared memory (static shared memory needs the rest)
 // Stage-done barriers.  The issuer can run at most TS stages ahead of the
 // relay (a template slab is reused only after the relay freed it), so with
 // more barriers than that no barrier completes twice before the relay has
@@ -527,8 +528,10 @@ struct ColGeom {
     int wrows, trows;          // rows loaded per window / template column (multiples of 8)
     int WS, TS;                // window / template slab ring sizes
     int ws_bytes, ts_bytes;    // slab sizes
+    int NB;                    // band buffers (accumulators drained before the sums)
+    int bk_bytes;              // one band buffer (with 32 dummy slots)
     int t_off, w_off, bk_off;  // shared-memory offsets
-    int part_off;              // partial diagonal sums: 2 x 256 floats
+    int part_off;              // partial diagonal sums: NB x kColDrain floats
     int bk_stride;             // band buffer row stride in floats (odd: no bank conflicts)
     int smem;
 };
@@ -543,7 +546,11 @@ __host__ __device__ inline ColGeom col_geom(int m, int R) {
     int G = 512 / c.Npad;
     G = G > c.P1 ? c.P1 : G;
     c.G = G > kColMaxG ? kColMaxG : G;
-    c.WS = (kColQ + c.G - 1 + kColQ - 1) / kColQ + 2;  // slabs one stage reads, plus two in flight
+    // a stage reads `span` window slabs; one more is in flight, and one
+    // template slab besides the stage's own (a copy lands in ~1.2K cycles,
+    // a stage takes ~3K)
+    const int span = (kColQ + c.G - 2) / kColQ + 1;
+    c.WS = span + 1;
     c.TS = kColMaxTS;
     c.wrows = (c.Lw + 7) / 8 * 8;
     c.trows = (m + 7) / 8 * 8;
@@ -553,17 +560,15 @@ __host__ __device__ inline ColGeom col_geom(int m, int R) {
     c.w_off = c.TS * c.ts_bytes;
     c.bk_stride = c.m | 1;
     c.bk_off = c.w_off + c.WS * c.ws_bytes;
-    c.part_off = c.bk_off + ((c.P1 * c.bk_stride + 32) * 4 + 127) / 128 * 128;  // + 32 dummy slots
+    c.bk_bytes = ((c.P1 * c.bk_stride + 32) * 4 + 127) / 128 * 128;
     // an MMA on the last window slab may read up to 2048 - 16 wrows bytes
     // past it (template slabs are followed by the window slabs)
-    c.smem = c.part_off + 2 * kColDrain * 4 + (2048 - 16 * c.wrows);
-    if (c.smem > 225 * 1024) {  // drop the third template slab (static shared memory needs the rest)
-        c.TS = 2;
-        c.w_off -= c.ts_bytes;
-        c.bk_off -= c.ts_bytes;
-        c.part_off -= c.ts_bytes;
-        c.smem -= c.ts_bytes;
-    }
+    const int guard = 2048 - 16 * c.wrows;
+    int nb = (kColSmemMax - c.bk_off - guard) / (c.bk_bytes + kColDrain * 4);
+    nb = nb > c.G ? c.G : nb;
+    c.NB = nb < 1 ? 1 : nb;
+    c.part_off = c.bk_off + c.NB * c.bk_bytes;
+    c.smem = c.part_off + c.NB * kColDrain * 4 + guard;
     // one CTA per SM: the CTA allocates all 512 TMEM columns
     c.smem = c.smem < 120 * 1024 ? 120 * 1024 : c.smem;
     return c;
@@ -788,8 +793,9 @@ __global__ void __launch_bounds__(kColThreads, 1)
             // ---------------- drain: diagonal sums ----------------
             // Thread t holds accumulator row y (its TMEM lane) and stores the
             // band entries D[y][c], 0 <= y - c < 2R+1, c < m, skewed into
-            // bk[y - c][c]; the two teams split each warp's 16-column chunks.
-            // Then nparts threads per dy sum row dy of bk.
+            // bk[y - c][c] (one buffer per accumulator of a round); the two
+            // teams split each warp's 16-column chunks.  Then nparts threads
+            // per dy sum row dy of each buffer.
             const int t = tid - 128;  // 0 .. kColDrain-1
             const int team = (warp - 4) >> 2;
             const int quarter = warp & 3;
@@ -811,7 +817,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 if (team == 0) chi = clo + h0 - 1;
                 else clo = clo + h0;
             }
-            float* bk = reinterpret_cast<float*>(smem + g.bk_off);
             const int dummy = g.P1 * Sb + lane;  // per-lane slot for entries outside the band
             float* pbuf = reinterpret_cast<float*>(smem + g.part_off);
             float* out = maps + (size_t)k * g.P1 * g.P1;
@@ -830,85 +835,93 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 if (!ok) break;
                 mbar_wait(bar(CB_AFULL), gg & 1, &s_abort);  // completed already: acquire for this thread
                 tc_fence_after();
-                for (int gi = 0; gi < Gg; ++gi) {
-                    // this warp's chunks, kColDB at a time: one batch of loads
-                    // and one wait per batch (the load latency is paid once)
-                    for (int cb = clo; cb <= chi; cb += kColDB) {
-                        uint32_t r[kColDB * 16];
+                // rounds of NB accumulators: every accumulator of a round is
+                // read from TMEM and stored to its band buffer back to back;
+                // after the last one TMEM is released, and the diagonal sums
+                // run while the next group's MMAs do
+                for (int r0 = 0; r0 < Gg; r0 += g.NB) {
+                    const int nb = Gg - r0 < g.NB ? Gg - r0 : g.NB;
+                    for (int gl = 0; gl < nb; ++gl) {
+                        const int gi = r0 + gl;
+                        float* bk = reinterpret_cast<float*>(smem + g.bk_off + gl * g.bk_bytes);
+                        // this warp's chunks, kColDB at a time: one batch of
+                        // loads and one wait per batch
+                        for (int cb = clo; cb <= chi; cb += kColDB) {
+                            uint32_t r[kColDB * 16];
 #pragma unroll
-                        for (int k2 = 0; k2 < kColDB; ++k2) {
-                            if (cb + k2 <= chi) {
-                                asm volatile(
-                                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
-                                    "%12,%13,%14,%15}, [%16];"
-                                    : "=r"(r[k2 * 16 + 0]), "=r"(r[k2 * 16 + 1]), "=r"(r[k2 * 16 + 2]),
-                                      "=r"(r[k2 * 16 + 3]), "=r"(r[k2 * 16 + 4]), "=r"(r[k2 * 16 + 5]),
-                                      "=r"(r[k2 * 16 + 6]), "=r"(r[k2 * 16 + 7]), "=r"(r[k2 * 16 + 8]),
-                                      "=r"(r[k2 * 16 + 9]), "=r"(r[k2 * 16 + 10]), "=r"(r[k2 * 16 + 11]),
-                                      "=r"(r[k2 * 16 + 12]), "=r"(r[k2 * 16 + 13]), "=r"(r[k2 * 16 + 14]),
-                                      "=r"(r[k2 * 16 + 15])
-                                    : "r"(lbase + (uint32_t)(gi * g.Npad + (cb + k2) * 16)));
+                            for (int k2 = 0; k2 < kColDB; ++k2) {
+                                if (cb + k2 <= chi) {
+                                    asm volatile(
+                                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,"
+                                        "%11,%12,%13,%14,%15}, [%16];"
+                                        : "=r"(r[k2 * 16 + 0]), "=r"(r[k2 * 16 + 1]), "=r"(r[k2 * 16 + 2]),
+                                          "=r"(r[k2 * 16 + 3]), "=r"(r[k2 * 16 + 4]), "=r"(r[k2 * 16 + 5]),
+                                          "=r"(r[k2 * 16 + 6]), "=r"(r[k2 * 16 + 7]), "=r"(r[k2 * 16 + 8]),
+                                          "=r"(r[k2 * 16 + 9]), "=r"(r[k2 * 16 + 10]), "=r"(r[k2 * 16 + 11]),
+                                          "=r"(r[k2 * 16 + 12]), "=r"(r[k2 * 16 + 13]), "=r"(r[k2 * 16 + 14]),
+                                          "=r"(r[k2 * 16 + 15])
+                                        : "r"(lbase + (uint32_t)(gi * g.Npad + (cb + k2) * 16)));
+                                }
+                            }
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            if (gi == Gg - 1 && cb + kColDB > chi) {  // every accumulator read: release TMEM
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(bar(CB_AEMPTY));
+                            }
+                            // band entries to bk[y - col][col]; the others to
+                            // this lane's dummy slot (branch-free stores)
+#pragma unroll
+                            for (int k2 = 0; k2 < kColDB; ++k2) {
+                                if (cb + k2 <= chi) {
+                                    const int col0 = (cb + k2) * 16;
+#pragma unroll
+                                    for (int j = 0; j < 16; ++j) {
+                                        const int col = col0 + j, d = y - col;
+                                        const bool in = (unsigned)d < (unsigned)g.P1 && col < m;
+                                        bk[in ? d * Sb + col : dummy] = __uint_as_float(r[k2 * 16 + j]);
+                                    }
+                                }
                             }
                         }
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (gi == Gg - 1 && cb + kColDB > chi) {  // every accumulator read: the next group may start
+                        if (clo > chi && gi == Gg - 1) {  // a warp without band entries still releases TMEM
                             tc_fence_before();
                             __syncwarp();
                             if (lane == 0) mbar_arrive(bar(CB_AEMPTY));
                         }
-                        // band entries to bk[y - col][col]; the others to this
-                        // lane's dummy slot (no branches: the store always runs)
+                    }
+                    if (t == 0) TC_TRACE(6, gg * 16 + r0);
+                    asm volatile("bar.sync 1, %0;" ::"r"(kColDrain) : "memory");
+                    if (part < nparts) {  // row dy of each band buffer, eight independent chains
+                        for (int gl = 0; gl < nb; ++gl) {
+                            const float* row =
+                                reinterpret_cast<const float*>(smem + g.bk_off + gl * g.bk_bytes) + dy * Sb;
+                            float sa[8];
 #pragma unroll
-                        for (int k2 = 0; k2 < kColDB; ++k2) {
-                            if (cb + k2 <= chi) {
-                                const int col0 = (cb + k2) * 16;
+                            for (int e = 0; e < 8; ++e) sa[e] = 0.f;
+                            int c = c0;
+                            for (; c + 8 <= c1; c += 8) {
+                                float v[8];
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    const int col = col0 + j, d = y - col;
-                                    const bool in = (unsigned)d < (unsigned)g.P1 && col < m;
-                                    bk[in ? d * Sb + col : dummy] = __uint_as_float(r[k2 * 16 + j]);
-                                }
+                                for (int e = 0; e < 8; ++e) v[e] = row[c + e];
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) sa[e] += v[e];
                             }
+#pragma unroll
+                            for (int e = 0; e < 7; ++e)
+                                if (c + e < c1) sa[e] += row[c + e];
+                            pbuf[gl * kColDrain + part * g.P1 + dy] =
+                                ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
                         }
                     }
-                    if (clo > chi && gi == Gg - 1) {  // a warp without band entries still releases TMEM
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(bar(CB_AEMPTY));
-                    }
                     asm volatile("bar.sync 1, %0;" ::"r"(kColDrain) : "memory");
-                    if (gi > 0 && t < g.P1) {  // finish offset d0 + gi - 1
-                        const float* pb = pbuf + ((gi - 1) & 1) * kColDrain;
+                    for (int idx = t; idx < nb * g.P1; idx += kColDrain) {  // offsets d0 + r0 .. d0 + r0 + nb - 1
+                        const int gl = idx / g.P1, dyy = idx - gl * g.P1;
+                        const float* pb = pbuf + gl * kColDrain;
                         float sum = 0.f;
-                        for (int p = 0; p < nparts; ++p) sum += pb[p * g.P1 + t];
-                        out[t * g.P1 + d0 + gi - 1] = sum;
+                        for (int p = 0; p < nparts; ++p) sum += pb[p * g.P1 + dyy];
+                        out[dyy * g.P1 + d0 + r0 + gl] = sum;
                     }
-                    if (part < nparts) {  // eight independent chains keep the loads in flight
-                        float sa[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) sa[e] = 0.f;
-                        const float* row = bk + dy * Sb;
-                        int c = c0;
-                        for (; c + 8 <= c1; c += 8) {
-                            float v[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) v[e] = row[c + e];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) sa[e] += v[e];
-                        }
-#pragma unroll
-                        for (int e = 0; e < 7; ++e)
-                            if (c + e < c1) sa[e] += row[c + e];
-                        pbuf[(gi & 1) * kColDrain + part * g.P1 + dy] =
-                            ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
-                    }
-                    asm volatile("bar.sync 1, %0;" ::"r"(kColDrain) : "memory");
-                }
-                if (t < g.P1) {  // finish offset d0 + Gg - 1
-                    const float* pb = pbuf + ((Gg - 1) & 1) * kColDrain;
-                    float sum = 0.f;
-                    for (int p = 0; p < nparts; ++p) sum += pb[p * g.P1 + t];
-                    out[t * g.P1 + d0 + Gg - 1] = sum;
                 }
                 if (t == 0) TC_TRACE(5, gg);
             }
@@ -1014,6 +1027,7 @@ cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (m + 2 * R <= kM && form != 1) {
         const ColGeom c = col_geom(m, R);
+        if (c.smem > kColSmemMax) return cudaErrorNotSupported;
         // slabs of 8 columns x 2 chunks, rows in 128-byte runs of 8 pixels
         alignas(64) CUtensorMap tmW, tmT;
         if (!make_map_rows8(&tmW, ref.cm, (uint64_t)ref.H, (uint64_t)ref.W, (uint32_t)c.wrows, kColQ) ||
