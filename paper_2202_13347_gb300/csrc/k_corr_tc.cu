@@ -575,9 +575,8 @@ __host__ __device__ inline ColGeom col_geom(int m, int R) {
 }
 
 enum {
-    CB_WFULL = 0,
-    CB_WEMPTY = kColMaxWS,
-    CB_TFULL = 2 * kColMaxWS,
+    CB_WEMPTY = 0,
+    CB_TFULL = kColMaxWS,  // per stage: the template slab and the window slabs loaded with it
     CB_TEMPTY = CB_TFULL + kColMaxTS,
     CB_STG = CB_TEMPTY + kColMaxTS,
     CB_AFULL = CB_STG + kColNS,
@@ -606,10 +605,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
     auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
 
     if (tid == 0) {
-        for (int i = 0; i < g.WS; ++i) {
-            mbar_init(bar(CB_WFULL + i), 1);
-            mbar_init(bar(CB_WEMPTY + i), 1);
-        }
+        for (int i = 0; i < g.WS; ++i) mbar_init(bar(CB_WEMPTY + i), 1);
         for (int i = 0; i < g.TS; ++i) {
             mbar_init(bar(CB_TFULL + i), 1);
             mbar_init(bar(CB_TEMPTY + i), 1);
@@ -635,7 +631,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
     // per-CTA running counts (window slabs, template slabs = stages, groups),
     // advanced identically by every role
     uint32_t wsc = 0, tsc = 0, grp = 0;
-    uint32_t w_issued = 0, t_issued = 0, mma_issued = 0;
+    uint32_t t_issued = 0, mma_issued = 0;
     const int nstage = (m + kColQ - 1) / kColQ;  // stages (template slabs) per group
 
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
@@ -654,33 +650,27 @@ __global__ void __launch_bounds__(kColThreads, 1)
                     const int nws = (m + Gg - 1 + kColQ - 1) / kColQ;
                     int wl = 0;  // window slabs of the group loaded
                     for (int s = 0; s < nstage && ok; ++s) {
-                        {  // template slab s
-                            const uint32_t slot = tv % g.TS;
-                            if (tv >= (uint32_t)g.TS)
-                                ok = mbar_wait(bar(CB_TEMPTY + slot), ((tv / g.TS) - 1) & 1, &s_abort);
-                            if (!ok) break;
-                            mbar_expect_tx(bar(CB_TFULL + slot), (uint32_t)g.ts_bytes);
-                            tma_load_4d(sbase + g.t_off + slot * g.ts_bytes, &tmT, 0, ty0, tx0 + s * kColQ, 0,
-                                        bar(CB_TFULL + slot));
-                            ++tv;
-                            ++t_issued;
-                        }
-                        // window slabs up to the last one stage s reads
+                        // stage s: template slab s and the window slabs up to
+                        // the last one it reads, all completing on the
+                        // template slot's barrier (one wait per stage)
                         int last = (s * kColQ + kColQ - 1 + Gg - 1) / kColQ;
                         last = last > nws - 1 ? nws - 1 : last;
                         if (s == nstage - 1) last = nws - 1;
-                        while (ok && wl <= last) {
-                            const uint32_t slot = wv % g.WS;
-                            if (wv >= (uint32_t)g.WS)
-                                ok = mbar_wait(bar(CB_WEMPTY + slot), ((wv / g.WS) - 1) & 1, &s_abort);
-                            if (!ok) break;
-                            mbar_expect_tx(bar(CB_WFULL + slot), (uint32_t)g.ws_bytes);
-                            tma_load_4d(sbase + g.w_off + slot * g.ws_bytes, &tmW, 0, wy0, wx0 + d0 + wl * kColQ, 0,
-                                        bar(CB_WFULL + slot));
-                            ++wv;
-                            ++w_issued;
-                            ++wl;
-                        }
+                        const uint32_t tslot = tv % g.TS;
+                        if (tv >= (uint32_t)g.TS)
+                            ok = mbar_wait(bar(CB_TEMPTY + tslot), ((tv / g.TS) - 1) & 1, &s_abort);
+                        for (uint32_t wi = wv; ok && wi < wv + (uint32_t)(last + 1 - wl); ++wi)
+                            if (wi >= (uint32_t)g.WS)
+                                ok = mbar_wait(bar(CB_WEMPTY + wi % g.WS), ((wi / g.WS) - 1) & 1, &s_abort);
+                        if (!ok) break;
+                        const uint32_t full = bar(CB_TFULL + tslot);
+                        mbar_expect_tx(full, (uint32_t)g.ts_bytes + (uint32_t)(last + 1 - wl) * (uint32_t)g.ws_bytes);
+                        tma_load_4d(sbase + g.t_off + tslot * g.ts_bytes, &tmT, 0, ty0, tx0 + s * kColQ, 0, full);
+                        ++tv;
+                        ++t_issued;
+                        for (; wl <= last; ++wl, ++wv)
+                            tma_load_4d(sbase + g.w_off + (wv % g.WS) * g.ws_bytes, &tmW, 0, wy0, wx0 + d0 + wl * kColQ,
+                                        0, full);
                     }
                 }
             }
@@ -709,21 +699,14 @@ __global__ void __launch_bounds__(kColThreads, 1)
                     if (gg >= 1) ok = mbar_wait(bar(CB_AEMPTY), (gg - 1) & 1, &s_abort);
                     if (!ok) break;
                     tc_fence_after();  // the drain's TMEM reads come before these MMAs
-                    uint32_t nws_slot = ws, nws_ph = wph;  // next window slab to wait for
-                    int ww = 0;                            // window slabs of the group waited for
-                    uint32_t wcur = ws;                    // slot of window slab s
+                    uint32_t wcur = ws;  // slot of window slab s
                     for (int s = 0; s < nstage && ok; ++s) {
                         const int u0 = s * kColQ;
                         const int nq = m - u0 < kColQ ? m - u0 : kColQ;
                         TC_TRACE(0, tvt);
+                        // the stage's template slab and every window slab it
+                        // reads complete on this barrier or an earlier stage's
                         ok = mbar_wait(bar(CB_TFULL + ts), tph, &s_abort);
-                        int last = (u0 + nq - 1 + Gg - 1) / kColQ;
-                        last = last > nws - 1 ? nws - 1 : last;
-                        while (ok && ww <= last) {
-                            ok = mbar_wait(bar(CB_WFULL + nws_slot), nws_ph, &s_abort);
-                            if (++nws_slot == (uint32_t)g.WS) { nws_slot = 0; nws_ph ^= 1u; }
-                            ++ww;
-                        }
                         if (!ok) break;
                         // descriptors: window slabs s .. s+kSpan-1, template slab ts
                         uint64_t dW[kSpan];
@@ -936,11 +919,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
     }
 
     if (*reinterpret_cast<volatile int*>(&s_abort)) {
-        if (warp == 0 && lane == 0) {  // let every copy in flight land
-            for (uint32_t i = 0; i < (uint32_t)g.WS && i < w_issued; ++i) {
-                const uint32_t wi = w_issued - 1 - i;
-                mbar_wait_short(bar(CB_WFULL + wi % g.WS), (wi / g.WS) & 1);
-            }
+        if (warp == 0 && lane == 0) {  // let every copy in flight land (all complete on template barriers)
             for (uint32_t i = 0; i < (uint32_t)g.TS && i < t_issued; ++i) {
                 const uint32_t ti = t_issued - 1 - i;
                 mbar_wait_short(bar(CB_TFULL + ti % g.TS), (ti / g.TS) & 1);
