@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_sfoc_steer_ct(const T* __restrict_
 // g = the six channels of group g and two zeros) in both pixel orders,
 // plus the per-pixel sum planes.  Tiles are 32 columns x 64 rows.
 constexpr int kSTW = 32, kSTH = 64, kSRows = 8;
+constexpr int kPRows = 4;  // rows per thread of the paired vertical pass (2 columns x 4 rows)
 
 template <int KD>
 __device__ __forceinline__ void smooth_channel(const float* __restrict__ Fk, size_t fpitch, int H, int W, int x0,
@@ -375,7 +376,7 @@ __device__ __forceinline__ void tile_load_async(const float* __restrict__ Fk, si
 // and synchronised the block).
 template <int KD>
 __device__ __forceinline__ void smooth_channel_123(const float* t, const float* s_F, int FW, float* s_h, int HR,
-                                                   float (&Dk)[kSRows]) {
+                                                   float2 (&Dk)[kPRows]) {
     constexpr int hal = 3 * KD;
     constexpr int IH = kSTH + 2 * hal;
     float tq[KD + 1];
@@ -413,65 +414,96 @@ __device__ __forceinline__ void smooth_channel_123(const float* t, const float* 
         }
     }
     __syncthreads();
-    // vertical: task = (column, 8-row block)
-    const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
+    // vertical: thread = (column pair, 4-row block); each value is a float2
+    // over two adjacent columns, so every filter step is one paired FP32
+    // instruction (per lane the same rounding as the scalar form)
+    const int cp = threadIdx.x & 15, rb = (threadIdx.x >> 4) * kPRows;
+    float2 tq2[KD + 1];
 #pragma unroll
-    for (int j = 0; j < kSRows; ++j) Dk[j] = 0.f;
+    for (int q = 0; q <= KD; ++q) tq2[q] = make_float2(tq[q], tq[q]);
+#pragma unroll
+    for (int j = 0; j < kPRows; ++j) Dk[j] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int r = 1; r <= 3; ++r) {
-        constexpr int kMaxSpan = kSRows + 2 * KD * 3;
-        const int span = kSRows + 2 * KD * r;
-        const float* x = s_h + ((r - 1) * HR + rb + hal - KD * r) * kSTW + col;
-        float in[kMaxSpan];
+        constexpr int kMaxSpan = kPRows + 2 * KD * 3;
+        const int span = kPRows + 2 * KD * r;
+        const float2* x = reinterpret_cast<const float2*>(s_h + ((r - 1) * HR + rb + hal - KD * r) * kSTW) + cp;
+        float2 in[kMaxSpan];
 #pragma unroll
         for (int i = 0; i < kMaxSpan; ++i)
-            if (i < span) in[i] = x[i * kSTW];
+            if (i < span) in[i] = x[i * (kSTW / 2)];
 #pragma unroll
-        for (int j = 0; j < kSRows; ++j) {
-            float a = tq[0] * in[KD * r + j];
+        for (int j = 0; j < kPRows; ++j) {
+            float2 a = __fmul2_rn(tq2[0], in[KD * r + j]);
 #pragma unroll
-            for (int q = 1; q <= KD; ++q) a = fmaf(tq[q], in[KD * r + j - q * r] + in[KD * r + j + q * r], a);
-            Dk[j] += a;
+            for (int q = 1; q <= KD; ++q)
+                a = __ffma2_rn(tq2[q], __fadd2_rn(in[KD * r + j - q * r], in[KD * r + j + q * r]), a);
+            Dk[j] = __fadd2_rn(Dk[j], a);
         }
     }
 }
 
-// One group of `no` channels: smooth each channel (KDG > 0: radius KDG and
-// the rates 1, 2, 3 at compile time; KDG == 0: radius and rates at run
-// time), normalise the group in registers and write it out, and add its
-// values to the per-pixel sums a1 (g) and a2 (g^2).
-template <int NO, int KDG>
+// Normalises one pixel's group of `no` smoothed values d[k] (Sec. 2.1) and
+// writes it out: F32 planes, or the bf16 chunk in both pixel orders; adds
+// the stored values to the per-pixel sums a1 (g) and a2 (g^2).
+template <int NO, int KO>
+__device__ __forceinline__ void write_pixel(int g, int no, const float* d, float eps, int gy, int gx, int H, int W,
+                                            float* __restrict__ c32, size_t cpitch, size_t cplane,
+                                            __nv_bfloat16* __restrict__ rm, __nv_bfloat16* __restrict__ cm,
+                                            float& a1, float& a2) {
+    const bool bf = rm != nullptr;
+    float n2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < KO; ++k)
+        if (k < no) n2 = fmaf(d[k], d[k], n2);
+    const float den = sqrtf(n2) + eps;
+    const float inv = den > 0.f ? 1.f / den : 0.f;  // NaN stays NaN through d * inv
+    const bool in = gy < H && gx < W;
+    float vs[KO];
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+        if (k >= no) break;
+        float v = (den > 0.f || den != den) ? d[k] * inv : 0.f;
+        if (bf) v = __bfloat162float(__float2bfloat16_rn(v));
+        vs[k] = v;
+        a1 += v;
+        a2 = fmaf(v, v, a2);
+        if (c32 && in) c32[(size_t)(g * no + k) * cplane + (size_t)gy * cpitch + gx] = v;
+    }
+    if constexpr (NO == 6) {
+        if (bf && in) {  // chunk g: the six channels, then two zeros
+            auto pack = [](float lo, float hi) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+                return *reinterpret_cast<const unsigned*>(&h);
+            };
+            const uint4 chunk = make_uint4(pack(vs[0], vs[1]), pack(vs[2], vs[3]), pack(vs[4], vs[5]), 0u);
+            const size_t npx = (size_t)H * W;
+            const size_t pix = (size_t)gy * W + gx, cpx = (size_t)gx * H + gy;
+            *reinterpret_cast<uint4*>(rm + ((size_t)g * npx + pix) * 8) = chunk;
+            *reinterpret_cast<uint4*>(cm + ((size_t)g * npx + cpx) * 8) = chunk;
+        }
+    }
+}
+
+// One group of `no` channels with radius and rates at run time: smooth each
+// channel, normalise the group in registers and write it out.
+template <int NO>
 __device__ __forceinline__ void smooth_group(int g, const float* __restrict__ F, size_t fpitch, size_t fplane, int H,
                                              int W, const SmoothTaps& tp, const int* s_dil, const float* t,
-                                             float* s_F, float* s_F2, int FW, float* s_h, int HR, int x0,
+                                             float* s_F, int FW, float* s_h, int HR, int x0,
                                              int y0, float* __restrict__ c32, size_t cpitch, size_t cplane,
                                              __nv_bfloat16* __restrict__ rm, __nv_bfloat16* __restrict__ cm,
                                              float (&a1)[kSRows], float (&a2)[kSRows]) {
     constexpr int KO = NO > 0 ? NO : kMaxOrient;
     const int no = NO > 0 ? NO : tp.no;
-    const bool bf = rm != nullptr;
     const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
     const int gx = x0 + col;
     float D[KO][kSRows];
-    if constexpr (KDG > 0) {
-        __syncthreads();  // the previous group is done with both tile buffers
-        tile_load_async<3 * KDG>(F + (size_t)(g * no) * fplane, fpitch, H, W, x0, y0, s_F, FW);
-    }
 #pragma unroll
     for (int k = 0; k < KO; ++k) {
         if (k >= no) break;
         const float* Fk = F + (size_t)(g * no + k) * fplane;
-        if constexpr (KDG > 0) {
-            // tile k is in buffer k & 1; prefetch tile k+1 into the other one
-            // (its last reader, channel k-1's horizontal pass, is behind the
-            // barrier that ended that pass)
-            if (k + 1 < no)
-                tile_load_async<3 * KDG>(Fk + fplane, fpitch, H, W, x0, y0, (k & 1) ? s_F : s_F2, FW);
-            if (k + 1 < no) asm volatile("cp.async.wait_group 1;" ::: "memory");
-            else asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncthreads();  // tile k visible; every thread is done with channel k-1
-            smooth_channel_123<KDG>(t, (k & 1) ? s_F2 : s_F, FW, s_h, HR, D[k]);
-        } else {
+        {
             const int hal = tp.halo[g], Kd = tp.Kd[g];
             switch (Kd) {
                 case 1: smooth_channel<1>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
@@ -486,32 +518,55 @@ __device__ __forceinline__ void smooth_group(int g, const float* __restrict__ F,
     // group normalisation in registers; write this group
 #pragma unroll
     for (int j = 0; j < kSRows; ++j) {
-        float n2 = 0.f;
+        float d[KO];
 #pragma unroll
-        for (int k = 0; k < KO; ++k)
-            if (k < no) n2 = fmaf(D[k][j], D[k][j], n2);
-        const float den = sqrtf(n2) + tp.eps;
-        const float inv = den > 0.f ? 1.f / den : 0.f;  // NaN stays NaN through D * inv
-        const int gy = y0 + rb + j;
-        const bool in = gy < H && gx < W;
-        __align__(16) __nv_bfloat16 ch[8];
+        for (int k = 0; k < KO; ++k) d[k] = D[k][j];
+        write_pixel<NO, KO>(g, no, d, tp.eps, y0 + rb + j, gx, H, W, c32, cpitch, cplane, rm, cm, a1[j], a2[j]);
+    }
+}
+
+// One group with radius KDG and the rates 1, 2, 3 at compile time: tiles
+// double-buffered with asynchronous copies, paired vertical pass; a thread
+// owns 2 columns x kPRows rows of every channel.
+template <int NO, int KDG>
+__device__ __forceinline__ void smooth_group_123(int g, const float* __restrict__ F, size_t fpitch, size_t fplane,
+                                                 int H, int W, float eps, const float* t, float* s_F,
+                                                 float* s_F2, int FW, float* s_h, int HR, int x0, int y0,
+                                                 float* __restrict__ c32, size_t cpitch, size_t cplane,
+                                                 __nv_bfloat16* __restrict__ rm, __nv_bfloat16* __restrict__ cm,
+                                                 float (&a1)[kPRows][2], float (&a2)[kPRows][2]) {
+    constexpr int KO = NO;
+    const int cp = threadIdx.x & 15, rb = (threadIdx.x >> 4) * kPRows;
+    const int gx = x0 + 2 * cp;
+    float2 D[KO][kPRows];
+    __syncthreads();  // the previous group is done with both tile buffers (and the taps are written)
+    tile_load_async<3 * KDG>(F + (size_t)(g * NO) * fplane, fpitch, H, W, x0, y0, s_F, FW);
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+        const float* Fk = F + (size_t)(g * NO + k) * fplane;
+        // tile k is in buffer k & 1; prefetch tile k+1 into the other one (its
+        // last reader, channel k-1's horizontal pass, is behind the barrier
+        // that ended that pass)
+        if (k + 1 < KO) {
+            tile_load_async<3 * KDG>(Fk + fplane, fpitch, H, W, x0, y0, (k & 1) ? s_F : s_F2, FW);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();  // tile k visible; every thread is done with channel k-1
+        smooth_channel_123<KDG>(t, (k & 1) ? s_F2 : s_F, FW, s_h, HR, D[k]);
+    }
+#pragma unroll
+    for (int j = 0; j < kPRows; ++j) {
+        float d0[KO], d1[KO];
 #pragma unroll
         for (int k = 0; k < KO; ++k) {
-            if (k >= no) break;
-            float v = (den > 0.f || den != den) ? D[k][j] * inv : 0.f;
-            if (bf) v = __bfloat162float(__float2bfloat16_rn(v));
-            a1[j] += v;
-            a2[j] = fmaf(v, v, a2[j]);
-            if (k < 8) ch[k] = __float2bfloat16_rn(v);
-            if (c32 && in) c32[(size_t)(g * no + k) * cplane + (size_t)gy * cpitch + gx] = v;
+            d0[k] = D[k][j].x;
+            d1[k] = D[k][j].y;
         }
-        if (NO == 6 && bf && in) {
-            ch[6] = ch[7] = __float2bfloat16_rn(0.f);
-            const size_t npx = (size_t)H * W;
-            const size_t pix = (size_t)gy * W + gx, cpx = (size_t)gx * H + gy;
-            *reinterpret_cast<uint4*>(rm + ((size_t)g * npx + pix) * 8) = *reinterpret_cast<uint4*>(ch);
-            *reinterpret_cast<uint4*>(cm + ((size_t)g * npx + cpx) * 8) = *reinterpret_cast<uint4*>(ch);
-        }
+        const int gy = y0 + rb + j;
+        write_pixel<NO, KO>(g, NO, d0, eps, gy, gx, H, W, c32, cpitch, cplane, rm, cm, a1[j][0], a2[j][0]);
+        write_pixel<NO, KO>(g, NO, d1, eps, gy, gx + 1, H, W, c32, cpitch, cplane, rm, cm, a1[j][1], a2[j][1]);
     }
 }
 
@@ -527,7 +582,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                       __nv_bfloat16* __restrict__ cm, float* __restrict__ s1, float* __restrict__ s2) {
     extern __shared__ float sm[];
     __shared__ float s_tap[kMaxSmoothRadius + 1];
-    if (threadIdx.x <= kMaxSmoothRadius) s_tap[threadIdx.x] = tp.g[g][threadIdx.x];
+    if (threadIdx.x == 0) {  // constant indices: the parameter block stays in the constant bank
+#pragma unroll
+        for (int q = 0; q <= kMaxSmoothRadius; ++q) s_tap[q] = g ? tp.g[1][q] : tp.g[0][q];
+    }
     constexpr int hal = 3 * KDG;
     const int FW = smooth_row_stride(hal);
     constexpr int HR = kSTH + 2 * hal;
@@ -535,27 +593,30 @@ __global__ void __launch_bounds__(kThreads, 2)
     float* s_h = s_F + HR * FW;        // 3 x HR x kSTW
     float* s_F2 = s_h + 3 * HR * kSTW;  // second input tile buffer
     const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH;
-    const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
-    const int gx = x0 + col;
+    const int cp = threadIdx.x & 15, rb = (threadIdx.x >> 4) * kPRows;
 
-    float a1[kSRows], a2[kSRows];
+    float a1[kPRows][2], a2[kPRows][2];
 #pragma unroll
-    for (int j = 0; j < kSRows; ++j) {
-        const int gy = y0 + rb + j;
-        const bool in = g > 0 && gy < H && gx < W;
-        a1[j] = in ? s1[(size_t)gy * cpitch + gx] : 0.f;
-        a2[j] = in ? s2[(size_t)gy * cpitch + gx] : 0.f;
-    }
-    smooth_group<NO, KDG>(g, F, fpitch, fplane, H, W, tp, nullptr, s_tap, s_F, s_F2, FW, s_h, HR, x0, y0, c32, cpitch,
-                          cplane, rm, cm, a1, a2);
+    for (int j = 0; j < kPRows; ++j)
 #pragma unroll
-    for (int j = 0; j < kSRows; ++j) {
-        const int gy = y0 + rb + j;
-        if (gy < H && gx < W) {
-            s1[(size_t)gy * cpitch + gx] = a1[j];
-            s2[(size_t)gy * cpitch + gx] = a2[j];
+        for (int e = 0; e < 2; ++e) {
+            const int gy = y0 + rb + j, gx = x0 + 2 * cp + e;
+            const bool in = g > 0 && gy < H && gx < W;
+            a1[j][e] = in ? s1[(size_t)gy * cpitch + gx] : 0.f;
+            a2[j][e] = in ? s2[(size_t)gy * cpitch + gx] : 0.f;
         }
-    }
+    smooth_group_123<NO, KDG>(g, F, fpitch, fplane, H, W, tp.eps, s_tap, s_F, s_F2, FW, s_h, HR, x0, y0, c32, cpitch,
+                              cplane, rm, cm, a1, a2);
+#pragma unroll
+    for (int j = 0; j < kPRows; ++j)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int gy = y0 + rb + j, gx = x0 + 2 * cp + e;
+            if (gy < H && gx < W) {
+                s1[(size_t)gy * cpitch + gx] = a1[j][e];
+                s2[(size_t)gy * cpitch + gx] = a2[j][e];
+            }
+        }
 }
 
 // Any radii and rates at run time.
@@ -587,8 +648,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int j = 0; j < kSRows; ++j) a1[j] = a2[j] = 0.f;
     for (int g = 0; g < ng; ++g)
-        smooth_group<NO, 0>(g, F, fpitch, fplane, H, W, tp, s_dil, s_tap[g], s_F, nullptr, FW, s_h, HR, x0, y0, c32,
-                            cpitch, cplane, rm, cm, a1, a2);
+        smooth_group<NO>(g, F, fpitch, fplane, H, W, tp, s_dil, s_tap[g], s_F, FW, s_h, HR, x0, y0, c32, cpitch,
+                         cplane, rm, cm, a1, a2);
 #pragma unroll
     for (int j = 0; j < kSRows; ++j) {
         const int gy = y0 + rb + j;
