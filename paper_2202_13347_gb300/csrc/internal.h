@@ -98,6 +98,12 @@ constexpr float kIntScale = 268435456.f;                  // 2^28
 constexpr long long kIntNonFinite = 1ll << 46;
 constexpr long long kIntNonFiniteMin = 1ll << 45;
 __host__ __device__ inline double int_units_to_double(long long v) { return (double)v * (1.0 / 268435456.0); }
+// one pixel value in those units (the integral images and the template sums
+// round every pixel with this one function)
+__device__ __forceinline__ unsigned long long int_quant(float v) {
+    if (!isfinite(v)) return (unsigned long long)kIntNonFinite;
+    return (unsigned long long)__float2ll_rn(v * kIntScale);
+}
 
 size_t integral_scratch_bytes(int H, int W);
 cudaError_t launch_integral(const Cube& c, void* scratch, cudaStream_t st, int* launches);
@@ -115,7 +121,8 @@ cudaError_t launch_template_stats(const Cube& ref, const Cube& sen, const int32_
 cudaError_t launch_corr_f32(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
                             const PointStat* stats, float* maps, cudaStream_t st);
 cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                           const PointStat* stats, float* maps, int* err_flag, int form, cudaStream_t st);
+                           const PointStat* stats, float* maps, int* err_flag, int form,
+                           cudaStream_t st);  // form: 0 auto, 1 Toeplitz, 2 column, 3 band
 size_t corr_tc_smem_bytes(int m, int R);
 cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m, int R, const PointStat* stats,
                               const float* num, int centered, float* out_maps, fastncc_result* out,

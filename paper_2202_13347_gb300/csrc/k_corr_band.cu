@@ -1,0 +1,487 @@
+// Correlation R_ST (Eq. 10 of arXiv 2202.13347), band form of the tcgen05
+// BF16 implicit GEMM with FP32 accumulation in tensor memory (sm_103a).
+// Every wait is bounded (about 2 s of %globaltimer); on expiry the CTA sets
+// the context's device error word, every role leaves its loop (the drain
+// warps run on to the end without waiting, so that their named barriers
+// stay matched), the producer waits (bounded) for its copies in flight,
+// TMEM is freed and the kernel returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "tc_ptx.h"
+
+namespace sfoc {
+
+namespace {
+
+using namespace tcx;
+// ---------------------------------------------------------------------------
+// Band form.  The window's rows are taken in bands of 16 and the offsets dx
+// in groups of 8; one accumulator per (band y0 = 16 b, offset group e):
+//   D[8g + r][n] = sum_{u, c} S[c][y0 + g][u + 8e + r] T[c][y0 - 2R + n][u]
+// M = 128 = 16 window rows x 8 offsets.  An A row is one 16-byte chunk of
+// the row-major window tile, so the 8 rows of a core matrix are 8
+// consecutive offsets (a 16-byte step, as in the Toeplitz form) and the
+// core-matrix groups step by one window row (SBO = the tile's row pitch).
+// N = roundup(16 + 2R, 16) template rows from y0 - 2R: every template row
+// that meets a row of the band at some dy in [0, 2R].
+// K = (template column u, 16 channels): one MMA per (band, offset group, u).
+// Per point this issues ceil((m + 2R)/16) ceil((2R+1)/8) m MMAs of N rows,
+// each reading a 4 KB A and a 32N-byte B from shared memory, against the
+// column form's (2R+1) m MMAs of 7 KB: about 3/4 of its operand traffic.
+// An accumulator is 128 lanes x N columns, so the two 256-column halves of
+// TMEM hold consecutive groups: the MMAs of one group run while the other
+// half is drained.  Each group reloads its template rows (one slab of
+// kBandQ columns per stage) and its window tile (16 rows, 8 GE + m - 1
+// columns), a third of the column form's copies per point.
+//
+// Diagonal sums.  Out[dy][dx] collects D[8g + r][n] with y0 + g - (y0 - 2R
+// + n) = dy, i.e. n = 2R + g - dy.  A drain thread owns one TMEM lane, i.e.
+// one (g, r): g = 4q + g' with q the warp's lane quarter and g' = lane / 8.
+// It shifts its row left by g' (two select steps), after which column j of
+// every lane of the warp with the same r holds dy = 2R + 4q - j; two
+// butterfly steps over the lanes 8 and 16 apart add the four rows g' and
+// leave each lane a quarter of the columns, kept as running sums over the
+// bands of one offset-group set.  Template rows outside [0, m) are zeroed
+// before the shift; window rows past m + 2R only reach dy > 2R.  After the
+// last band the eight drain warps' sums meet in shared memory and are added
+// in a fixed order, so the result does not depend on timing.
+// Teams: warps 4-7 drain the even groups (TMEM half 0), warps 8-11 the odd
+// ones (half 1).  Each accumulator spans m MMAs, like the column form's.
+// ---------------------------------------------------------------------------
+constexpr int kBandQ = 8;  // template columns per stage
+constexpr int kBandMaxTS = 4;
+constexpr int kBandThreads = 384;
+constexpr int kBandDrain = 256;
+constexpr int kBandMaxNQ = 6;  // N <= 96, i.e. R <= 40
+
+__host__ __device__ constexpr int band_ge_max(int nq) { return nq <= 3 ? 5 : 16 / nq; }
+
+struct BandGeom {
+    int m, R, P1, Lw;
+    int N, NQ;      // template rows per MMA (roundup(16 + 2R, 16)) and N / 16
+    int nE, GE;     // offset groups of 8; accumulators per group (<= band_ge_max)
+    int nEG, nYB;   // offset-group sets, bands of 16 window rows
+    int nS;         // stages (template slabs) per group
+    int Xw;         // window tile width in pixels: roundup(8 GE + m - 1, 8)
+    int trows;      // template rows per slab column: roundup(16 + 2R, 8)
+    int tile_bytes, slab_bytes, TS;
+    int tile_off, slab_off, part_off, smem;
+};
+
+__host__ __device__ inline BandGeom band_geom(int m, int R) {
+    BandGeom b;
+    b.m = m;
+    b.R = R;
+    b.P1 = 2 * R + 1;
+    b.Lw = m + 2 * R;
+    b.N = (16 + 2 * R + 15) / 16 * 16;
+    b.NQ = b.N / 16;
+    b.nE = (b.P1 + 7) / 8;
+    // as few offset-group sets as TMEM allows, of near-equal size
+    const int gm = band_ge_max(b.NQ);
+    b.nEG = (b.nE + gm - 1) / gm;
+    b.GE = (b.nE + b.nEG - 1) / b.nEG;
+    b.nYB = (b.Lw + 15) / 16;
+    b.nS = (m + kBandQ - 1) / kBandQ;
+    b.Xw = (8 * b.GE + m - 1 + 7) / 8 * 8;
+    b.trows = (16 + 2 * R + 7) / 8 * 8;
+    b.tile_bytes = 2 * 16 * b.Xw * 16;
+    b.slab_bytes = 2 * kBandQ * b.trows * 16;
+    b.tile_off = 0;
+    b.slab_off = 2 * b.tile_bytes;
+    const int part_bytes = 8 * b.GE * b.P1 * 8 * 4;
+    // an MMA on the last column of a slab reads N - trows rows past it; the
+    // partial-sum buffer follows the slabs, plus a guard for the last slot
+    const int guard = (b.N - b.trows) * 16 + 128;
+    int ts = (kTcSmemMax - b.slab_off - part_bytes - guard) / b.slab_bytes;
+    b.TS = ts > kBandMaxTS ? kBandMaxTS : ts;
+    b.part_off = b.slab_off + (b.TS > 0 ? b.TS : 0) * b.slab_bytes;
+    b.smem = b.part_off + part_bytes + guard;
+    return b;
+}
+
+__host__ inline bool band_supported(int m, int R) {
+    const BandGeom b = band_geom(m, R);
+    return b.NQ <= kBandMaxNQ && b.TS >= 2 && b.Xw <= 256 && b.trows <= 256 && b.smem <= kTcSmemMax;
+}
+
+enum {
+    BD_WFULL = 0,               // window tile slots (2)
+    BD_WEMPTY = 2,
+    BD_TFULL = 4,               // template slabs (kBandMaxTS)
+    BD_TEMPTY = BD_TFULL + kBandMaxTS,
+    BD_AFULL = BD_TEMPTY + kBandMaxTS,  // TMEM halves (2)
+    BD_AEMPTY = BD_AFULL + 2,
+    BD_FIN = BD_AEMPTY + 2,
+    BD_N
+};
+
+// One stage of the band form: template columns u0 + q (q < nq) of the slab
+// at dB against the window tile at dAu = tile + u0, for GG accumulators,
+// as straight-line code (an MMA that is predicated off still costs about
+// as much issue time as one that runs).  FIRST: the stage of u0 = 0, whose
+// first MMA per accumulator overwrites it.
+template <int N, int GG, bool FIRST>
+__device__ __forceinline__ void band_stage(uint32_t dacc, uint64_t dAu, uint64_t dB, uint32_t tcol, uint32_t idesc,
+                                           int nq) {
+    if (nq == kBandQ) {
+#pragma unroll
+        for (int q = 0; q < kBandQ; ++q)
+#pragma unroll
+            for (int e = 0; e < GG; ++e)
+                mma_bf16(dacc + (uint32_t)(e * N), dAu + (uint64_t)(q + 8 * e), dB + (uint64_t)(q * tcol), idesc,
+                         (FIRST && q == 0) ? 0u : 1u);
+    } else {
+#pragma unroll
+        for (int q = 0; q < kBandQ; ++q)
+            if (q < nq) {
+#pragma unroll
+                for (int e = 0; e < GG; ++e)
+                    mma_bf16(dacc + (uint32_t)(e * N), dAu + (uint64_t)(q + 8 * e), dB + (uint64_t)(q * tcol), idesc,
+                             (FIRST && q == 0) ? 0u : 1u);
+            }
+    }
+}
+
+template <int N, int GG>
+__device__ __forceinline__ void band_stage_any(bool first, uint32_t dacc, uint64_t dAu, uint64_t dB, uint32_t tcol,
+                                               uint32_t idesc, int nq) {
+    if (first)
+        band_stage<N, GG, true>(dacc, dAu, dB, tcol, idesc, nq);
+    else
+        band_stage<N, GG, false>(dacc, dAu, dB, tcol, idesc, nq);
+}
+
+// 16 TMEM columns of this warp's 32 lanes into v[0..15] (no wait)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(kBandThreads, 1)
+    k_corr_tc_band(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmT,
+                   const int32_t* __restrict__ pts, int n, int m, int R, const PointStat* __restrict__ stats,
+                   float* __restrict__ maps, int* __restrict__ err) {
+    constexpr int N = NQ * 16;
+    constexpr int N4 = N / 4;
+    constexpr int GEM = band_ge_max(NQ);
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_bar[BD_N];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const BandGeom g = band_geom(m, R);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int h = template_half(m);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bars = smem_u32(&s_bar[0]);
+    auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar(BD_WFULL + i), 1);
+            mbar_init(bar(BD_WEMPTY + i), 1);
+            mbar_init(bar(BD_AFULL + i), 1);
+            mbar_init(bar(BD_AEMPTY + i), 4);  // the four warps of the draining team
+        }
+        for (int i = 0; i < g.TS; ++i) {
+            mbar_init(bar(BD_TFULL + i), 1);
+            mbar_init(bar(BD_TEMPTY + i), 1);
+        }
+        mbar_init(bar(BD_FIN), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    // per-CTA running counts of groups and stages, advanced alike by every role
+    uint32_t gc = 0, tc = 0;
+    uint32_t t_issued = 0, w_issued = 0, mma_issued = 0;
+    bool ok = true;
+
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        if (warp < 4 && *reinterpret_cast<volatile int*>(&s_abort)) break;  // the drain warps never leave early
+        const PointStat st = stats[k];
+        if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
+        const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
+        const int wy0 = ty0 - R, wx0 = tx0 - R;
+        if (warp == 0) {
+            // ---------------- TMA producer ----------------
+            if (lane == 0) {
+                uint32_t gp = gc, tp = tc;
+                for (int eg = 0; eg < g.nEG && ok; ++eg) {
+                    const int e0 = eg * g.GE;
+                    for (int yb = 0; yb < g.nYB && ok; ++yb, ++gp) {
+                        const uint32_t slot = gp & 1u;
+                        if (gp >= 2) ok = mbar_wait(bar(BD_WEMPTY + slot), ((gp >> 1) - 1) & 1, &s_abort);
+                        if (!ok) break;
+                        mbar_expect_tx(bar(BD_WFULL + slot), (uint32_t)g.tile_bytes);
+                        tma_load_4d(sbase + g.tile_off + slot * g.tile_bytes, &tmW, 0, wx0 + 8 * e0, wy0 + 16 * yb, 0,
+                                    bar(BD_WFULL + slot));
+                        ++w_issued;
+                        for (int s = 0; s < g.nS && ok; ++s, ++tp) {
+                            const uint32_t ts = tp % (uint32_t)g.TS;
+                            if (tp >= (uint32_t)g.TS)
+                                ok = mbar_wait(bar(BD_TEMPTY + ts), ((tp / g.TS) - 1) & 1, &s_abort);
+                            if (!ok) break;
+                            // a run of 8 rows that starts above the image is zero filled whole, so
+                            // the slab starts at row 0 at the latest (the issuer compensates)
+                            const int r0 = ty0 + 16 * yb - 2 * R;
+                            mbar_expect_tx(bar(BD_TFULL + ts), (uint32_t)g.slab_bytes);
+                            tma_load_4d(sbase + g.slab_off + ts * g.slab_bytes, &tmT, 0, r0 < 0 ? 0 : r0,
+                                        tx0 + s * kBandQ, 0, bar(BD_TFULL + ts));
+                            ++t_issued;
+                        }
+                    }
+                }
+            }
+        } else if (warp == 1) {
+            // ---------------- MMA issuer ----------------
+            if (lane == 0) {
+                const uint32_t idesc = idesc_bf16(kM, N);
+                const uint64_t da0 = smem_desc(sbase + g.tile_off, 16u * g.Xw * 16u, (uint32_t)g.Xw * 16u);
+                const uint64_t db0 = smem_desc(sbase + g.slab_off, (uint32_t)(kBandQ * g.trows * 16), 128);
+                const uint32_t tile_step = (uint32_t)g.tile_bytes >> 4, slab_step = (uint32_t)g.slab_bytes >> 4;
+                const uint32_t tcol = (uint32_t)g.trows;  // slab column stride in 16-byte units
+                uint32_t gi = gc, tvt = tc;  // tvt: stage count (tracing)
+                uint32_t ts = tc % (uint32_t)g.TS, tph = (tc / (uint32_t)g.TS) & 1u;
+                for (int eg = 0; eg < g.nEG && ok; ++eg) {
+                    const int Gg = g.nE - eg * g.GE < g.GE ? g.nE - eg * g.GE : g.GE;
+                    for (int yb = 0; yb < g.nYB && ok; ++yb, ++gi) {
+                        const uint32_t half = gi & 1u;
+                        if (gi >= 2) ok = mbar_wait(bar(BD_AEMPTY + half), ((gi >> 1) - 1) & 1, &s_abort);
+                        if (ok) ok = mbar_wait(bar(BD_WFULL + half), (gi >> 1) & 1, &s_abort);
+                        if (!ok) break;
+                        tc_fence_after();  // the drain's TMEM reads come before these MMAs
+                        const uint64_t dA = da0 + (uint64_t)(half * tile_step);
+                        const uint32_t dacc = tmem + half * 256u;
+                        // B row n is template row 16 yb - 2R + n; a slab clamped to image row 0
+                        // holds it clamp rows further on (rows before the slab only meet
+                        // template rows i < 0, which the drain drops)
+                        const int r0 = ty0 + 16 * yb - 2 * R;
+                        const uint32_t clamp = r0 < 0 ? (uint32_t)(-r0) : 0u;
+                        for (int s = 0; s < g.nS; ++s) {
+                            TC_TRACE(0, tvt);
+                            ok = mbar_wait(bar(BD_TFULL + ts), tph, &s_abort);
+                            if (!ok) break;
+                            tc_fence_after();
+                            TC_TRACE(1, tvt);
+                            const uint64_t dB = db0 + (uint64_t)(ts * slab_step) - (uint64_t)clamp;
+                            const int u0 = s * kBandQ;
+                            const int nq = m - u0 < kBandQ ? m - u0 : kBandQ;
+                            const uint64_t dAu = dA + (uint64_t)u0;
+                            switch (Gg) {  // outside the run of MMAs
+                                case 1: band_stage_any<N, 1>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
+                                case 2: band_stage_any<N, 2>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
+                                case 3: band_stage_any<N, GEM < 3 ? GEM : 3>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
+                                case 4: band_stage_any<N, GEM < 4 ? GEM : 4>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
+                                default: band_stage_any<N, GEM < 5 ? GEM : 5>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
+                            }
+                            mma_issued += (uint32_t)(nq * Gg);
+                            mma_commit(bar(BD_TEMPTY + ts));
+                            TC_TRACE(2, tvt);
+                            ++tvt;
+                            if (++ts == (uint32_t)g.TS) { ts = 0; tph ^= 1u; }
+                        }
+                        if (!ok) break;
+                        mma_commit(bar(BD_WEMPTY + half));
+                        mma_commit(bar(BD_AFULL + half));
+                    }
+                }
+            }
+        } else if (warp >= 4) {
+            // ---------------- drain: diagonal sums ----------------
+            const int t = tid - 128;  // 0 .. kBandDrain-1
+            const int team = t >> 7;
+            const int q = warp & 3;
+            const int w8 = warp - 4;
+            const int gq = lane >> 3, r = lane & 7;
+            const bool b0 = (gq & 1) != 0, b1 = (gq & 2) != 0;
+            const int joff = (b0 ? N / 2 : 0) + (b1 ? N4 : 0);
+            float* part = reinterpret_cast<float*>(smem + g.part_off);
+            float* out = maps + (size_t)k * g.P1 * g.P1;
+            const uint32_t lbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)team * 256u;
+            uint32_t gd = gc;
+            for (int eg = 0; eg < g.nEG; ++eg) {
+                const int e0 = eg * g.GE;
+                const int Gg = g.nE - e0 < g.GE ? g.nE - e0 : g.GE;
+                float sums[GEM][N4];
+#pragma unroll
+                for (int e = 0; e < GEM; ++e)
+#pragma unroll
+                    for (int p = 0; p < N4; ++p) sums[e][p] = 0.f;
+                for (int yb = 0; yb < g.nYB; ++yb, ++gd) {
+                    if ((int)(gd & 1u) != team) continue;
+                    if (lane == 0 && q == 0) TC_TRACE(4, gd);
+                    // lane 0 takes the bounded wait; the warp follows its verdict
+                    int okw = 0;
+                    if (lane == 0 && ok) okw = mbar_wait(bar(BD_AFULL + team), (gd >> 1) & 1, &s_abort) ? 1 : 0;
+                    okw = __shfl_sync(0xffffffffu, okw, 0);
+                    if (!okw) {
+                        ok = false;
+                        continue;
+                    }
+                    mbar_wait(bar(BD_AFULL + team), (gd >> 1) & 1, &s_abort);  // completed: acquire for this lane
+                    tc_fence_after();
+                    // template rows i = 16 yb - 2R + n outside [0, m) are zeroed
+                    const int ilo = 16 * yb - 2 * R;
+                    const int nlo = ilo < 0 ? -ilo : 0;
+                    const int nhi = m - ilo < N ? m - ilo : N;
+#pragma unroll
+                    for (int e = 0; e < GEM; ++e) {
+                        if (e < Gg) {
+                            float v[N];
+#pragma unroll
+                            for (int c = 0; c < NQ; ++c) tmem_ld16_nowait(lbase + (uint32_t)(e * N + 16 * c), v + 16 * c);
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            if (e == Gg - 1) {  // every accumulator of the group read: release the TMEM half
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(bar(BD_AEMPTY + team));
+                            }
+                            if (nlo > 0 || nhi < N) {
+#pragma unroll
+                                for (int j = 0; j < N; ++j) v[j] = (j >= nlo && j < nhi) ? v[j] : 0.f;
+                            }
+                            // shift left by g' = 2 b1 + b0
+#pragma unroll
+                            for (int j = 0; j < N; ++j) v[j] = b0 ? (j + 1 < N ? v[j + 1] : 0.f) : v[j];
+#pragma unroll
+                            for (int j = 0; j < N; ++j) v[j] = b1 ? (j + 2 < N ? v[j + 2] : 0.f) : v[j];
+                            // add the four rows g': lanes 8 apart, then 16 apart
+#pragma unroll
+                            for (int p = 0; p < N / 2; ++p) {
+                                const float lo = v[p], hi = v[p + N / 2];
+                                const float snd = b0 ? lo : hi;
+                                v[p] = (b0 ? hi : lo) + __shfl_xor_sync(0xffffffffu, snd, 8);
+                            }
+#pragma unroll
+                            for (int p = 0; p < N4; ++p) {
+                                const float lo = v[p], hi = v[p + N4];
+                                const float snd = b1 ? lo : hi;
+                                sums[e][p] += (b1 ? hi : lo) + __shfl_xor_sync(0xffffffffu, snd, 16);
+                            }
+                        }
+                    }
+                    if (lane == 0 && q == 0) TC_TRACE(5, gd);
+                }
+                // sums of this offset-group set: column j = joff + p is dy = 2R + 4q - j
+#pragma unroll
+                for (int e = 0; e < GEM; ++e) {
+                    if (e < Gg) {
+#pragma unroll
+                        for (int p = 0; p < N4; ++p) {
+                            const int dy = 2 * R + 4 * q - joff - p;
+                            if ((unsigned)dy < (unsigned)g.P1) part[((w8 * g.GE + e) * g.P1 + dy) * 8 + r] = sums[e][p];
+                        }
+                    }
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(kBandDrain) : "memory");
+                for (int idx = t; idx < Gg * g.P1 * 8; idx += kBandDrain) {
+                    const int e = idx / (g.P1 * 8);
+                    const int rem = idx - e * g.P1 * 8;
+                    const int dy = rem >> 3, rr = rem & 7;
+                    const int dx = 8 * (e0 + e) + rr;
+                    if (dx < g.P1) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) s += part[((w * g.GE + e) * g.P1 + dy) * 8 + rr];
+                        out[dy * g.P1 + dx] = s;
+                    }
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(kBandDrain) : "memory");
+            }
+        }
+        gc += (uint32_t)(g.nEG * g.nYB);
+        tc += (uint32_t)(g.nEG * g.nYB * g.nS);
+        if (!ok) atomicExch(&s_abort, 1);
+    }
+
+    if (*reinterpret_cast<volatile int*>(&s_abort)) {
+        if (warp == 0 && lane == 0) {  // let every copy in flight land
+            for (uint32_t i = 0; i < (uint32_t)g.TS && i < t_issued; ++i) {
+                const uint32_t ti = t_issued - 1 - i;
+                mbar_wait_short(bar(BD_TFULL + ti % g.TS), (ti / g.TS) & 1);
+            }
+            for (uint32_t i = 0; i < 2u && i < w_issued; ++i) {
+                const uint32_t wi = w_issued - 1 - i;
+                mbar_wait_short(bar(BD_WFULL + (wi & 1u)), (wi >> 1) & 1);
+            }
+        }
+        if (warp == 1 && lane == 0 && mma_issued > 0) {  // and every MMA issued
+            mma_commit(bar(BD_FIN));
+            mbar_wait_short(bar(BD_FIN), 0);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort && tid == 0) atomicExch(err, 1);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+}  // namespace
+
+bool corr_band_supported(int m, int R) { return band_supported(m, R); }
+
+long long corr_band_mmas(int m, int R) {
+    const BandGeom b = band_geom(m, R);
+    return (long long)b.nYB * b.nE * m;
+}
+
+cudaError_t launch_corr_band(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
+                             const PointStat* stats, float* maps, int* err_flag, int sms, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (!band_supported(m, R)) return cudaErrorNotSupported;
+    const BandGeom bg = band_geom(m, R);
+    // window tiles: 16 rows x Xw pixels of rm = [2][H][W][8]; template slabs:
+    // kBandQ columns x trows rows of cm = [2][W][H][8]; both in 128-byte runs
+    // of 8 pixels
+    alignas(64) CUtensorMap tmW, tmT;
+    if (!make_map_rows8(&tmW, ref.rm, (uint64_t)ref.W, (uint64_t)ref.H, (uint32_t)bg.Xw, 16) ||
+        !make_map_rows8(&tmT, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, (uint32_t)bg.trows, kBandQ))
+        return cudaErrorNotSupported;
+    const int grid = n < sms ? n : sms;
+    cudaError_t e = cudaErrorNotSupported;
+#define SFOC_BAND_CASE(NQV)                                                                                   \
+    case NQV:                                                                                                 \
+        e = cudaFuncSetAttribute(k_corr_tc_band<NQV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bg.smem); \
+        if (e != cudaSuccess) return e;                                                                       \
+        k_corr_tc_band<NQV><<<grid, kBandThreads, bg.smem, st>>>(tmW, tmT, pts, n, m, R, stats, maps, err_flag); \
+        return cudaGetLastError();
+    switch (bg.NQ) {
+        SFOC_BAND_CASE(1)
+        SFOC_BAND_CASE(2)
+        SFOC_BAND_CASE(3)
+        SFOC_BAND_CASE(4)
+        SFOC_BAND_CASE(5)
+        SFOC_BAND_CASE(6)
+        default: break;
+    }
+#undef SFOC_BAND_CASE
+    return e;
+}
+
+}  // namespace sfoc

@@ -45,16 +45,16 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "tc_ptx.h"
 
 namespace sfoc {
 
 namespace {
 
+using namespace tcx;
+
 constexpr int kThreads = 256;
 constexpr int kY = 8;    // window rows per stage
-constexpr int kM = 128;  // MMA M (dx rows)
-constexpr unsigned long long kWaitNs = 2000000000ull;
-constexpr unsigned long long kDrainNs = 200000000ull;
 constexpr int kMaxNA = 6;
 
 struct TcGeom {
@@ -89,130 +89,6 @@ __host__ __device__ inline TcGeom tc_geom(int m, int R, int U) {
     g.tmem_cols = c;
     return g;
 }
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait; on expiry (or once another role aborted) returns false.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* s_abort) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*reinterpret_cast<volatile int*>(s_abort)) return false;
-        if (globaltimer() - t0 > kWaitNs) {
-            atomicExch(s_abort, 1);
-            return false;
-        }
-    }
-}
-
-// Bounded wait that ignores the abort flag (used to let copies land).
-__device__ void mbar_wait_short(uint32_t bar, uint32_t parity) {
-    const uint64_t t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer() - t0 > kDrainNs) return;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// K-major, no-swizzle shared-memory matrix descriptor (tcgen05 format).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    return d;                // base offset 0, layout SWIZZLE_NONE
-}
-
-// Instruction descriptor, kind::f16: D f32, A/B bf16, both K-major.
-__host__ __device__ inline uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Optional per-stage timestamps of CTA 0 (compiled in only when
-// SFOC_TC_TRACE is defined; rows: 0 window-slab TMA issued, 1 MMA waits
-// begin, 2 MMA issue begins, 3 MMA issue ends, 4 drain waits begin,
-// 5 drain done, 6 zero rows begin, 7 zero rows done).
-#ifdef SFOC_TC_TRACE
-__device__ unsigned long long g_tc_trace[8][8192];
-#define TC_TRACE(row, idx)                                           \
-    do {                                                             \
-        if (blockIdx.x == 0 && (idx) < 8192u) g_tc_trace[row][idx] = clock64(); \
-    } while (0)
-#else
-#define TC_TRACE(row, idx) \
-    do {                   \
-    } while (0)
-#endif
 
 // barrier slots
 enum {
@@ -511,7 +387,7 @@ constexpr int kColMaxG = 16;
 constexpr int kColQ = 8;   // template columns per stage and columns per slab
 constexpr int kColMaxWS = 4;
 constexpr int kColMaxTS = 2;
-constexpr int kColSmemMax = 225 * 1024;  // dynamic shared memory (static shared memory needs the rest)
+constexpr int kColSmemMax = kTcSmemMax;
 // Stage-done barriers.  The issuer can run at most TS stages ahead of the
 // relay (a template slab is reused only after the relay freed it), so with
 // more barriers than that no barrier completes twice before the relay has
@@ -580,8 +456,8 @@ enum {
     CB_TEMPTY = CB_TFULL + kColMaxTS,
     CB_STG = CB_TEMPTY + kColMaxTS,
     CB_AFULL = CB_STG + kColNS,
-    CB_AEMPTY,
-    CB_FIN,
+    CB_AEMPTY,  // per accumulator: its contents read by every drain warp
+    CB_FIN = CB_AEMPTY + kColMaxG,
     CB_N
 };
 
@@ -612,7 +488,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
         }
         for (int i = 0; i < kColNS; ++i) mbar_init(bar(CB_STG + i), 1);
         mbar_init(bar(CB_AFULL), 1);
-        mbar_init(bar(CB_AEMPTY), kColDrain / 32);  // every drain warp
+        for (int i = 0; i < kColMaxG; ++i) mbar_init(bar(CB_AEMPTY + i), kColDrain / 32);  // every drain warp
         mbar_init(bar(CB_FIN), 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -696,9 +572,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 for (int d0 = 0; d0 < g.P1 && ok; d0 += G, ++gg) {
                     const int Gg = g.P1 - d0 < G ? g.P1 - d0 : G;
                     const int nws = (m + Gg - 1 + kColQ - 1) / kColQ;
-                    if (gg >= 1) ok = mbar_wait(bar(CB_AEMPTY), (gg - 1) & 1, &s_abort);
-                    if (!ok) break;
-                    tc_fence_after();  // the drain's TMEM reads come before these MMAs
                     uint32_t wcur = ws;  // slot of window slab s
                     for (int s = 0; s < nstage && ok; ++s) {
                         const int u0 = s * kColQ;
@@ -719,7 +592,28 @@ __global__ void __launch_bounds__(kColThreads, 1)
                         const uint64_t dT = db_base + (uint64_t)(ts * t_step);
                         const uint32_t acc0 = u0 > 0 ? 1u : 0u;
                         TC_TRACE(1, tvt);
-                        if (nq == kColQ && Gg == G) {
+                        if (s == 0) {
+                            // the group's first stage accumulator by accumulator: each
+                            // starts once the drain has read the previous group's
+                            // contents of it (the drain releases them one by one)
+#pragma unroll
+                            for (int gi = 0; gi < G; ++gi) {
+                                if (gi < Gg) {
+                                    if (gg >= 1) {
+                                        ok = mbar_wait(bar(CB_AEMPTY + gi), (gg - 1) & 1, &s_abort);
+                                        if (!ok) break;
+                                        tc_fence_after();  // the drain's TMEM reads come before these MMAs
+                                    }
+#pragma unroll
+                                    for (int q = 0; q < kColQ; ++q)
+                                        if (q < nq)
+                                            mma_bf16(dD[gi],
+                                                     dW[(q + gi) / kColQ] + (uint64_t)(((q + gi) % kColQ) * wcol),
+                                                     dT + (uint64_t)(q * tcol), idesc, q > 0 ? 1u : 0u);
+                                }
+                            }
+                            if (!ok) break;
+                        } else if (nq == kColQ && Gg == G) {
 #pragma unroll
                             for (int q = 0; q < kColQ; ++q)
 #pragma unroll
@@ -818,10 +712,13 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 if (!ok) break;
                 mbar_wait(bar(CB_AFULL), gg & 1, &s_abort);  // completed already: acquire for this thread
                 tc_fence_after();
+                // accumulators this group left unused are released at once
+                for (int gi = Gg; gi < G; ++gi)
+                    if (lane == 0) mbar_arrive(bar(CB_AEMPTY + gi));
                 // rounds of NB accumulators: every accumulator of a round is
-                // read from TMEM and stored to its band buffer back to back;
-                // after the last one TMEM is released, and the diagonal sums
-                // run while the next group's MMAs do
+                // read from TMEM and stored to its band buffer back to back,
+                // each released to the issuer as soon as every warp has read
+                // it; the diagonal sums run while the next group's MMAs do
                 for (int r0 = 0; r0 < Gg; r0 += g.NB) {
                     const int nb = Gg - r0 < g.NB ? Gg - r0 : g.NB;
                     for (int gl = 0; gl < nb; ++gl) {
@@ -847,10 +744,10 @@ __global__ void __launch_bounds__(kColThreads, 1)
                                 }
                             }
                             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                            if (gi == Gg - 1 && cb + kColDB > chi) {  // every accumulator read: release TMEM
+                            if (cb + kColDB > chi) {  // this warp's part of accumulator gi read: release it
                                 tc_fence_before();
                                 __syncwarp();
-                                if (lane == 0) mbar_arrive(bar(CB_AEMPTY));
+                                if (lane == 0) mbar_arrive(bar(CB_AEMPTY + gi));
                             }
                             // band entries to bk[y - col][col]; the others to
                             // this lane's dummy slot (branch-free stores)
@@ -867,10 +764,10 @@ __global__ void __launch_bounds__(kColThreads, 1)
                                 }
                             }
                         }
-                        if (clo > chi && gi == Gg - 1) {  // a warp without band entries still releases TMEM
+                        if (clo > chi) {  // a warp without band entries still releases it
                             tc_fence_before();
                             __syncwarp();
-                            if (lane == 0) mbar_arrive(bar(CB_AEMPTY));
+                            if (lane == 0) mbar_arrive(bar(CB_AEMPTY + gi));
                         }
                     }
                     if (t == 0) TC_TRACE(6, gg * 16 + r0);
@@ -939,7 +836,17 @@ __global__ void __launch_bounds__(kColThreads, 1)
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+int pick_U(int m, int R) {
+    TcGeom g = tc_geom(m, R, 8);
+    if (g.NA >= 3) return 8;
+    return 4;
+}
+
+}  // namespace
+
+namespace tcx {
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         void* p = nullptr;
@@ -966,19 +873,20 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t d1, uint64_t d2, uint
     return r == CUDA_SUCCESS;
 }
 
-// 4-D bf16 view of a column-major chunked cube [2][W][H][8] whose innermost
-// dimension is 8 pixels x 8 channels (128 contiguous bytes) and whose second
-// dimension is the pixel row (16-byte stride) traversed with stride 8: a
-// box {64, rows, cols, 2} loads, per column and chunk, `rows` consecutive
-// pixels from any start row as rows/8 runs of 128 bytes.  The last run of
-// a column may read up to 7 pixels past the column (the cube buffers are
-// padded for the last column).
-bool make_map_rows8(CUtensorMap* map, const void* base, uint64_t H, uint64_t W, uint32_t rows, uint32_t cols) {
+// 4-D bf16 view of a chunked cube [2][d2][d1][8] (d1 = H, d2 = W for the
+// column-major layout cm; d1 = W, d2 = H for the row-major layout rm) whose
+// innermost dimension is 8 pixels x 8 channels (128 contiguous bytes) and
+// whose second dimension is the pixel index along d1 (16-byte stride)
+// traversed with stride 8: a box {64, b1, b2, 2} loads, per line of d2 and
+// chunk, b1 consecutive pixels from any start as b1/8 runs of 128 bytes.
+// The last run of a line may read up to 7 pixels past it (the cube buffers
+// are padded for the last line).
+bool make_map_rows8(CUtensorMap* map, const void* base, uint64_t d1, uint64_t d2, uint32_t b1, uint32_t b2) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[4] = {64, H, W, 2};
-    cuuint64_t strides[3] = {16, 16 * H, 16 * H * W};
-    cuuint32_t box[4] = {64, rows, cols, 2};
+    cuuint64_t dims[4] = {64, d1, d2, 2};
+    cuuint64_t strides[3] = {16, 16 * d1, 16 * d1 * d2};
+    cuuint32_t box[4] = {64, b1, b2, 2};
     cuuint32_t es[4] = {1, 8, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -986,13 +894,7 @@ bool make_map_rows8(CUtensorMap* map, const void* base, uint64_t H, uint64_t W, 
     return r == CUDA_SUCCESS;
 }
 
-int pick_U(int m, int R) {
-    TcGeom g = tc_geom(m, R, 8);
-    if (g.NA >= 3) return 8;
-    return 4;
-}
-
-}  // namespace
+}  // namespace tcx
 
 size_t corr_tc_smem_bytes(int m, int R) { return (size_t)tc_geom(m, R, pick_U(m, R)).smem; }
 
@@ -1004,7 +906,18 @@ cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts,
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (m + 2 * R <= kM && form != 1) {
+    // Automatic choice: every form's MMAs cost about the same (M = 128, K = 16
+    // and N <= 96 are bound by shared-memory operand reads), so the form that
+    // issues fewer per point wins: the column form (2R+1) m, the band form
+    // ceil((m+2R)/16) ceil((2R+1)/8) m; the Toeplitz form ((m+2R) m narrow
+    // ones) only when neither of the others runs.
+    const bool col_ok = m + 2 * R <= kM && col_geom(m, R).smem <= kColSmemMax;
+    if (form == 0 && corr_band_supported(m, R) &&
+        (!col_ok || corr_band_mmas(m, R) < (long long)(2 * R + 1) * m))
+        form = 3;
+    if (form == 3) return launch_corr_band(ref, sen, pts, n, m, R, stats, maps, err_flag, sms, st);
+    if (form == 2 && !col_ok) return cudaErrorNotSupported;
+    if (col_ok && form != 1) {
         const ColGeom c = col_geom(m, R);
         if (c.smem > kColSmemMax) return cudaErrorNotSupported;
         // slabs of 8 columns x 2 chunks, rows in 128-byte runs of 8 pixels

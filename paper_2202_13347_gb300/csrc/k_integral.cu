@@ -29,10 +29,7 @@ namespace {
 constexpr int kT = 64;
 typedef unsigned long long u64;
 
-__device__ __forceinline__ u64 quant(float v) {
-    if (!isfinite(v)) return (u64)kIntNonFinite;
-    return (u64)__float2ll_rn(v * kIntScale);
-}
+__device__ __forceinline__ u64 quant(float v) { return int_quant(v); }
 
 struct IntLayout {
     int H, W, nty, ntx;

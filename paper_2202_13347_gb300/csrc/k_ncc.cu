@@ -1,8 +1,13 @@
 // NCC assembly, peak picking and sub-pixel refinement (Eq. 9, 12, 16 of
 // arXiv 2202.13347; Sec. 3.2.2 takes the most similar position as the CP).
 //
-// k_template_stats  per point: bounds check, R_T and R_TT from the sensed
-//                   cube's integral images (Eq. 12 via Eq. 16).
+// k_template_stats  per point (one CTA): bounds check, then R_T and R_TT
+//                   (Eq. 12) as sums of the sensed cube's channel-summed
+//                   planes over the template, each pixel rounded to 2^-28
+//                   units exactly as the integral images round it and added
+//                   in 64-bit integers: the same exact values a lookup in
+//                   integral images of the sensed cube would give, without
+//                   building them.
 // k_ncc_argmax      per point (one CTA): for every offset, R_S and R_SS from
 //                   the reference integral images (4 lookups each, exact
 //                   64-bit fixed point), the variance R_SS - R_S^2/mnz and
@@ -28,28 +33,54 @@ __device__ __forceinline__ long long rect(const u64* P, size_t ip, int y0, int x
                        P[(size_t)y0 * ip + x0]);
 }
 
-__global__ void k_template_stats(const u64* __restrict__ Pr, int Hr, int Wr, const u64* __restrict__ Ps,
-                                 int Hs, int Ws, size_t ips, const int32_t* __restrict__ pts, int n, int m, int R,
-                                 int z, PointStat* __restrict__ stats) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    (void)Pr;
+constexpr int kStatThreads = 128;
+
+__global__ void __launch_bounds__(kStatThreads)
+    k_template_stats(const float* __restrict__ s1, const float* __restrict__ s2, size_t pitch, int Hs, int Ws,
+                     int Hr, int Wr, const int32_t* __restrict__ pts, int m, int R, int z,
+                     PointStat* __restrict__ stats) {
+    __shared__ u64 s_acc[kStatThreads / 32][2];
+    const int k = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = template_half(m);
-    int px = pts[2 * k], py = pts[2 * k + 1];
+    const int px = pts[2 * k], py = pts[2 * k + 1];
+    const int ty0 = py - h, tx0 = px - h;
+    const bool ok = ty0 >= 0 && tx0 >= 0 && ty0 + m <= Hs && tx0 + m <= Ws && ty0 - R >= 0 && tx0 - R >= 0 &&
+                    ty0 + m + R <= Hr && tx0 + m + R <= Wr;
+    u64 a1 = 0, a2 = 0;  // modulo 2^64, like the integral images
+    if (ok) {
+        for (int r = warp; r < m; r += kStatThreads / 32) {
+            const size_t row = (size_t)(ty0 + r) * pitch + tx0;
+            for (int c = lane; c < m; c += 32) {
+                a1 += int_quant(s1[row + c]);
+                a2 += int_quant(s2[row + c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a1 += __shfl_down_sync(0xffffffffu, a1, o);
+        a2 += __shfl_down_sync(0xffffffffu, a2, o);
+    }
+    if (lane == 0) {
+        s_acc[warp][0] = a1;
+        s_acc[warp][1] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     PointStat s;
     s.RT = s.RTT = 0.0;
     s.tmean = 0.f;
-    int ty0 = py - h, tx0 = px - h;
-    bool ok = ty0 >= 0 && tx0 >= 0 && ty0 + m <= Hs && tx0 + m <= Ws && ty0 - R >= 0 && tx0 - R >= 0 &&
-              ty0 + m + R <= Hr && tx0 + m + R <= Wr;
     if (!ok) {
         s.status = SFOC_PT_OUT_OF_BOUNDS;
     } else {
+        u64 t1 = 0, t2 = 0;
+        for (int w = 0; w < kStatThreads / 32; ++w) {
+            t1 += s_acc[w][0];
+            t2 += s_acc[w][1];
+        }
+        const long long rt = (long long)t1, rtt = (long long)t2;
         const double N = (double)m * m * z;
-        const u64* P1 = Ps;
-        const u64* P2 = Ps + (size_t)(Hs + 1) * ips;
-        const long long rt = rect(P1, ips, ty0, tx0, ty0 + m, tx0 + m);
-        const long long rtt = rect(P2, ips, ty0, tx0, ty0 + m, tx0 + m);
         if (rt >= kIntNonFiniteMin || rtt >= kIntNonFiniteMin) {
             s.RT = s.RTT = NAN;
             s.status = SFOC_PT_NAN;
@@ -183,8 +214,8 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const u64* __restric
 cudaError_t launch_template_stats(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
                                   PointStat* stats, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_template_stats<<<(n + 127) / 128, 128, 0, st>>>(ref.integ, ref.H, ref.W, sen.integ, sen.H, sen.W, sen.ipitch,
-                                                     pts, n, m, R, sen.z, stats);
+    k_template_stats<<<n, kStatThreads, 0, st>>>(sen.s1, sen.s2, sen.pitch, sen.H, sen.W, ref.H, ref.W, pts, m, R,
+                                                 sen.z, stats);
     return cudaGetLastError();
 }
 

@@ -582,15 +582,17 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
     if (path == SFOC_CORR_AUTO) path = ref->c.dtype == SFOC_DTYPE_BF16 ? SFOC_CORR_IGEMM_TC : SFOC_CORR_DIRECT_F32;
     if (path == SFOC_CORR_DIRECT_F32 && ref->c.dtype != SFOC_DTYPE_F32)
         return fail(ctx, SFOC_ERR_UNSUPPORTED, "DIRECT_F32 needs F32 cubes");
-    if ((path == SFOC_CORR_IGEMM_TC || path == SFOC_CORR_TC_TOEPLITZ) && ref->c.dtype != SFOC_DTYPE_BF16)
-        return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
-    if (path != SFOC_CORR_DIRECT_F32 && path != SFOC_CORR_IGEMM_TC && path != SFOC_CORR_TC_TOEPLITZ)
+    if (path != SFOC_CORR_DIRECT_F32 && path != SFOC_CORR_IGEMM_TC && path != SFOC_CORR_TC_TOEPLITZ &&
+        path != SFOC_CORR_TC_COLUMN && path != SFOC_CORR_TC_BAND)
         return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown corr_path");
+    if (path != SFOC_CORR_DIRECT_F32 && ref->c.dtype != SFOC_DTYPE_BF16)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
     DeviceGuard g(ctx->device);
     if (n == 0) return SFOC_OK;
 
+    // integral images of the searched (reference) cube; the template sums
+    // come straight from the sensed cube's sum planes
     sfoc_status s = build_integral(ctx, ref->c);
-    if (s == SFOC_OK) s = build_integral(ctx, sen->c);
     if (s != SFOC_OK) return s;
     s = ensure_ws(ctx, sfoc_match_workspace_bytes(n, search_radius));
     if (s != SFOC_OK) return s;
@@ -610,7 +612,11 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
             e = launch_corr_f32(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->stream);
         else
             e = launch_corr_tc(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->d_err,
-                               path == SFOC_CORR_TC_TOEPLITZ ? 1 : 0, ctx->stream);
+                               path == SFOC_CORR_TC_TOEPLITZ  ? 1
+                               : path == SFOC_CORR_TC_COLUMN ? 2
+                               : path == SFOC_CORR_TC_BAND   ? 3
+                                                             : 0,
+                               ctx->stream);
     }
     if (e == cudaErrorInvalidValue || e == cudaErrorNotSupported)
         return fail(ctx, SFOC_ERR_UNSUPPORTED, "correlation kernel does not support this m / R");

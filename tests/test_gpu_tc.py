@@ -53,6 +53,14 @@ def gpu_bf16(ctx, b, pair, want_maps=False, path=None):
                              corr_path=b.CORR_IGEMM_TC if path is None else path, want_maps=want_maps)
 
 
+FORMS = ["auto", "toeplitz", "column", "band"]
+
+
+def form_path(b, form):
+    return {"auto": None, "toeplitz": b.CORR_TC_TOEPLITZ, "column": b.CORR_TC_COLUMN,
+            "band": b.CORR_TC_BAND}[form]
+
+
 SMALL = [
     (70, 83, 9, 4, 12, 11),
     (96, 61, 10, 3, 9, 12),     # even template
@@ -64,25 +72,27 @@ SMALL = [
 ]
 
 
-@pytest.mark.parametrize("form", ["auto", "toeplitz"])
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("H,W,m,R,npts,seed", SMALL)
 def test_tc_small_cases(b, ctx, orc, H, W, m, R, npts, seed, form):
-    """Both tensor-core forms on the same inputs: the column form (chosen
-    when m + 2R <= 128) and the Toeplitz form."""
+    """Every tensor-core form on the same inputs: the column form (m + 2R
+    <= 128), the Toeplitz form and the band form."""
     pair = tiny_pair(seed, H, W, m, R, npts, shift=(2, -1))
-    g = gpu_bf16(ctx, b, pair, want_maps=True, path=b.CORR_TC_TOEPLITZ if form == "toeplitz" else None)
+    g = gpu_bf16(ctx, b, pair, want_maps=True, path=form_path(b, form))
     ctx.sync()
     o_r, o_u, regions = oracle_side(orc, pair)
     check(g, o_r, o_u, regions, R, {})
 
 
+@pytest.mark.parametrize("form", ["auto", "band"])
 @pytest.mark.parametrize("H,W,m,R,npts,seed", [
-    (230, 240, 61, 35, 8, 18),   # m + 2R = 131: Toeplitz form under the default path
+    (230, 240, 61, 35, 8, 18),   # m + 2R = 131: no column form
     (200, 190, 101, 14, 6, 19),  # m + 2R = 129
+    (260, 250, 101, 40, 4, 20),  # the largest radius of the band form
 ])
-def test_tc_wide_windows(b, ctx, orc, H, W, m, R, npts, seed):
+def test_tc_wide_windows(b, ctx, orc, H, W, m, R, npts, seed, form):
     pair = tiny_pair(seed, H, W, m, R, npts, shift=(-3, 2))
-    g = gpu_bf16(ctx, b, pair, want_maps=True)
+    g = gpu_bf16(ctx, b, pair, want_maps=True, path=form_path(b, form))
     ctx.sync()
     o_r, o_u, regions = oracle_side(orc, pair)
     check(g, o_r, o_u, regions, R, {})
@@ -99,10 +109,10 @@ def test_bf16_cube_is_rounded_oracle_cube(b, ctx, orc):
     assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 2e-5)
 
 
-@pytest.mark.parametrize("form", ["auto", "toeplitz"])
+@pytest.mark.parametrize("form", FORMS)
 def test_tc_config1(b, ctx, orc, form):
     pair = config1()
-    g = gpu_bf16(ctx, b, pair, want_maps=True, path=b.CORR_TC_TOEPLITZ if form == "toeplitz" else None)
+    g = gpu_bf16(ctx, b, pair, want_maps=True, path=form_path(b, form))
     ctx.sync()
     o_r, o_u, regions = oracle_side(orc, pair)
     rep = {}
@@ -111,11 +121,12 @@ def test_tc_config1(b, ctx, orc, form):
     assert rep["bf16_vs_fp64_offsets_equal"] >= 95
 
 
-def test_tc_config2_full_size_sampled(b, ctx, orc):
+@pytest.mark.parametrize("form", ["auto", "band"])
+def test_tc_config2_full_size_sampled(b, ctx, orc, form):
     """2048^2, 1000 points, m=81, R=20 in the benchmark's launch
     configuration; a seeded sample of 6 points against the oracle."""
     pair = config2()
-    g = gpu_bf16(ctx, b, pair)
+    g = gpu_bf16(ctx, b, pair, path=form_path(b, form))
     ctx.sync()
     rng = np.random.default_rng(77)
     idx = np.sort(rng.choice(len(pair.points), 6, replace=False))
