@@ -58,15 +58,19 @@ typedef enum { SFOC_DTYPE_F32 = 0, SFOC_DTYPE_BF16 = 1 } sfoc_dtype;
 
 /* Correlation kernel for R_ST (Eq. 10). */
 typedef enum {
-    SFOC_CORR_AUTO = 0,       /* pick by dtype and autotuned shape class */
+    SFOC_CORR_AUTO = 0,       /* BF16 cubes: IGEMM_TC; F32 cubes: FFT when m + 2R <= 128, else
+                               * DIRECT_F32 */
     SFOC_CORR_DIRECT_F32 = 1, /* FP32 CUDA-core direct correlation (F32 cubes) */
     SFOC_CORR_IGEMM_TC = 2,   /* tcgen05 BF16 implicit GEMM, FP32 accumulate (BF16 cubes):
                                * the column or band form, whichever issues fewer MMAs for
                                * (m, R); the Toeplitz form when neither runs */
     SFOC_CORR_TC_TOEPLITZ = 3, /* the Toeplitz form of the tcgen05 kernel for any m, R */
     SFOC_CORR_TC_COLUMN = 4,  /* the column form: m + 2R <= 128, else SFOC_ERR_UNSUPPORTED */
-    SFOC_CORR_TC_BAND = 5     /* the band form (bands of 16 window rows x 8 offsets):
+    SFOC_CORR_TC_BAND = 5,    /* the band form (bands of 16 window rows x 8 offsets):
                                * R <= 40 and its shared memory fits, else SFOC_ERR_UNSUPPORTED */
+    SFOC_CORR_FFT = 6         /* Eq. 13: FP32 Fourier transforms of the zero-padded window and
+                               * zero-mean template, summed over channels (F32 cubes,
+                               * m + 2R <= 128, else SFOC_ERR_UNSUPPORTED) */
 } sfoc_corr_path;
 
 /*

@@ -20,7 +20,8 @@ ERR_NAMES = {0: "SFOC_OK", -1: "SFOC_ERR_INVALID_ARG", -2: "SFOC_ERR_SHAPE", -3:
              -4: "SFOC_ERR_CUDA", -5: "SFOC_ERR_TIMEOUT", -6: "SFOC_ERR_UNSUPPORTED"}
 PT_OK, PT_OUT_OF_BOUNDS, PT_FLAT_TEMPLATE, PT_PEAK_ON_EDGE, PT_NAN = 0, 1, 2, 3, 4
 DTYPE_F32, DTYPE_BF16 = 0, 1
-CORR_AUTO, CORR_DIRECT_F32, CORR_IGEMM_TC, CORR_TC_TOEPLITZ, CORR_TC_COLUMN, CORR_TC_BAND = 0, 1, 2, 3, 4, 5
+(CORR_AUTO, CORR_DIRECT_F32, CORR_IGEMM_TC, CORR_TC_TOEPLITZ, CORR_TC_COLUMN, CORR_TC_BAND,
+ CORR_FFT) = 0, 1, 2, 3, 4, 5, 6
 STATIC_SCRATCH_FLOATS = 1 << 24  # SFOC_STATIC_SCRATCH_FLOATS
 
 

@@ -120,6 +120,9 @@ cudaError_t launch_template_stats(const Cube& ref, const Cube& sen, const int32_
                                   PointStat* stats, cudaStream_t st);
 cudaError_t launch_corr_f32(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
                             const PointStat* stats, float* maps, cudaStream_t st);
+bool corr_fft_supported(int m, int R);
+cudaError_t launch_corr_fft(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
+                            const PointStat* stats, float* maps, cudaStream_t st);
 cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
                            const PointStat* stats, float* maps, int* err_flag, int form,
                            cudaStream_t st);  // form: 0 auto, 1 Toeplitz, 2 column, 3 band

@@ -1,0 +1,332 @@
+// Correlation R_ST (Eq. 10 of arXiv 2202.13347) by the discrete Fourier
+// transform, Eq. 13: per point and channel the window S_c and the zero-mean
+// template T_c - mean(T) are zero-padded to L x L (L >= m + 2R, so the
+// circular correlation equals the linear one at every offset in [0, 2R]),
+// their spectra multiplied (one conjugated) and summed over the channels,
+// and one inverse transform gives the numerator of Eq. 9 at every offset.
+// FP32 throughout, from the F32 cube; one CTA per point.
+//
+// Transforms.  A length-L transform (L = 8E) is done by a group of 8
+// threads: thread t holds x[t + 8j] (j < E), takes the E-point DFT over j in
+// registers, multiplies by W_L^{t k1}, and after an 8 x 8 transpose through
+// a padded shared-memory scratch takes the 8-point DFT over t.  The output
+// X[t + 8m] lands in the same stride-8 layout, so rows and columns of the
+// L x L array chain without reordering.
+// Channel c: z = S_c + i (T_c - mean) is transformed once (rows, then
+// columns); the spectra of the two real inputs follow from Z[k] and
+// conj(Z[-k]):  X = (Z[k] + conj Z[-k]) / 2,  Y = (Z[k] - conj Z[-k]) / 2i.
+// Columns are taken in conjugate pairs (c, L - c) (and the two
+// self-conjugate columns 0 and L/2 together), so a group holds both Z[k]
+// and Z[-k]; the products X conj(Y) for the half spectrum kx in [0, L/2]
+// are summed over the channels in registers (the Nyquist column kx = L/2 in
+// shared memory).  Inverse: columns kx in [0, L/2], then for each of the
+// 2R + 1 wanted rows the Hermitian-extended row.
+#include <math.h>
+
+#include "internal.h"
+
+namespace sfoc {
+
+namespace {
+
+constexpr int kScP = 9;  // transpose scratch row pitch (float2): conflict-free columns
+
+// One group of 8 threads per conjugate column pair: L/2 groups.
+template <int L>
+struct FftShape {
+    static constexpr int E = L / 8;
+    static constexpr int G = L / 2;                     // groups of 8 threads
+    static constexpr int T = 8 * G;                     // threads
+    static constexpr int ZP = L + 2;                    // row pitch of the L x L array (float2)
+    static constexpr int SG = E * kScP + 8;             // scratch per group (float2); consecutive groups 64 B apart mod 128
+    static constexpr size_t smem = sizeof(float2) * ((size_t)L * ZP + (size_t)G * SG + 8 * E + L);
+};
+
+// cos(2 pi q / 16) for q in [0, 16)
+__device__ __forceinline__ constexpr float cos16(int q) {
+    constexpr float c1 = 0.92387953251128674f, c2 = 0.70710678118654752f, c3 = 0.38268343236508977f;
+    switch (q & 15) {
+        case 0: return 1.f;
+        case 1: return c1;
+        case 2: return c2;
+        case 3: return c3;
+        case 4: return 0.f;
+        case 5: return -c3;
+        case 6: return -c2;
+        case 7: return -c1;
+        case 8: return -1.f;
+        case 9: return -c1;
+        case 10: return -c2;
+        case 11: return -c3;
+        case 12: return 0.f;
+        case 13: return c3;
+        case 14: return c2;
+        default: return c1;
+    }
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// x * exp(SIGN 2 pi i k / N), k and N compile-time after unrolling (N divides 16)
+template <int SIGN>
+__device__ __forceinline__ float2 twiddle(float2 x, int k, int N) {
+    const int q = (k * (16 / N)) & 15;
+    if (q == 0) return x;
+    if (q == 8) return make_float2(-x.x, -x.y);
+    if (q == 4) return SIGN < 0 ? make_float2(x.y, -x.x) : make_float2(-x.y, x.x);
+    if (q == 12) return SIGN < 0 ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+    const float c = cos16(q), s = SIGN * cos16(q - 4);
+    return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+}
+
+// in-place N-point DFT, sum_j v[j] exp(SIGN 2 pi i j k / N), natural order
+template <int N, int SIGN>
+__device__ __forceinline__ void dft(float2 (&v)[N]) {
+#pragma unroll
+    for (int s = N / 2; s >= 1; s >>= 1) {
+#pragma unroll
+        for (int b = 0; b < N; b += 2 * s) {
+#pragma unroll
+            for (int j = 0; j < s; ++j) {
+                const float2 a = v[b + j], c = v[b + j + s];
+                v[b + j] = cadd(a, c);
+                v[b + j + s] = twiddle<SIGN>(csub(a, c), j * (N / (2 * s)), N);
+            }
+        }
+    }
+    // decimation in frequency leaves X[k] at the bit-reversed position of k
+    float2 o[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int bit = 1, rb = N / 2; bit < N; bit <<= 1, rb >>= 1)
+            if (i & bit) r |= rb;
+        o[r] = v[i];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = o[i];
+}
+
+// Length-L transform by the 8 threads of a group (t = thread in group):
+// v[j] = x[t + 8j] on entry, v[m] = X[t + 8m] on return.  tw[8 k1 + t] =
+// exp(-2 pi i t k1 / L).  Every thread of the warp must call it together.
+template <int E, int SIGN>
+__device__ __forceinline__ void group_fft(float2 (&v)[E], int t, float2* sc, const float2* tw) {
+    dft<E, SIGN>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < E; ++k1) {
+        float2 w = tw[8 * k1 + t];
+        if (SIGN > 0) w.y = -w.y;
+        v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) sc[k1 * kScP + t] = v[k1];
+    __syncwarp();
+    float2 w8[E / 8][8];
+#pragma unroll
+    for (int a = 0; a < E / 8; ++a)
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt) w8[a][tt] = sc[(t + 8 * a) * kScP + tt];
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < E / 8; ++a) {
+        dft<8, SIGN>(w8[a]);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) v[a + (E / 8) * k2] = w8[a][k2];
+    }
+}
+
+// X conj(Y) from a = Z[k] and b = conj(Z[-k]) of z = x + i y
+__device__ __forceinline__ float2 cross_spectrum(float2 a, float2 b) {
+    const float2 s = cadd(a, b), d = csub(a, b);
+    return make_float2(0.25f * fmaf(s.x, d.y, -s.y * d.x), 0.25f * fmaf(s.x, d.x, s.y * d.y));
+}
+
+template <int L>
+__global__ void __launch_bounds__(FftShape<L>::T, 1)
+    k_corr_fft(const float* __restrict__ Sf, size_t spitch, size_t splane, const float* __restrict__ Tf,
+               size_t tpitch, size_t tplane, const int32_t* __restrict__ pts, int n, int m, int R, int z,
+               const PointStat* __restrict__ stats, float* __restrict__ maps) {
+    using Sh = FftShape<L>;
+    constexpr int E = Sh::E, ZP = Sh::ZP, kFftGroups = Sh::G, kFftThreads = Sh::T;
+    extern __shared__ __align__(16) float2 fsm[];
+    float2* Z = fsm;                                       // L x ZP
+    float2* scr = Z + (size_t)L * ZP;                      // kFftGroups x SG
+    float2* tw = scr + (size_t)kFftGroups * Sh::SG;        // 8E twiddles W_L^{t k1} at 8 k1 + t
+    float2* P64 = tw + 8 * E;                              // Nyquist column of the channel sum
+
+    const int tid = threadIdx.x;
+    const int grp = tid >> 3, t = tid & 7;
+    const int lane = tid & 31, gbase = lane & ~7;
+    float2* sc = scr + grp * Sh::SG;
+    const int P1 = 2 * R + 1, Lw = m + 2 * R;
+    const int h = template_half(m);
+    const float inv_area = 1.f / ((float)L * (float)L);
+    // partner of row t + 8m is row -(t + 8m): thread (8 - t) mod 8, index
+    // (E - m) mod E for t = 0, E - 1 - m otherwise
+    const int tpart = gbase + ((8 - t) & 7);
+
+    for (int p = tid; p < 8 * E; p += kFftThreads) {
+        double s, c;
+        sincospi(-2.0 * ((p & 7) * (p >> 3)) / L, &s, &c);
+        tw[p] = make_float2((float)c, (float)s);
+    }
+    for (int i = tid; i < L * ZP; i += kFftThreads) Z[i] = make_float2(0.f, 0.f);  // rows >= m + 2R stay zero
+    __syncthreads();
+
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const PointStat st = stats[k];
+        if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
+        const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
+        const int wy0 = ty0 - R, wx0 = tx0 - R;
+        const float tmean = st.tmean;
+        float2 acc[E];  // channel sum of X conj(Y) on column pr of this group's pair
+#pragma unroll
+        for (int j = 0; j < E; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int i = tid; i < L; i += kFftThreads) P64[i] = make_float2(0.f, 0.f);
+
+        for (int c = 0; c < z; ++c) {
+            const float* Sp = Sf + (size_t)c * splane;
+            const float* Tp = Tf + (size_t)c * tplane;
+            // ---- rows: z = S + i (T - mean), zero outside the window / template
+            for (int y0 = 0; y0 < Lw; y0 += kFftGroups) {
+                const int y = y0 + grp;
+                const bool rs = y < Lw, rt = y < m;
+                const float* srow = Sp + (size_t)(wy0 + (rs ? y : 0)) * spitch + wx0;
+                const float* trow = Tp + (size_t)(ty0 + (rt ? y : 0)) * tpitch + tx0;
+                float2 v[E];
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int x = t + 8 * j;
+                    v[j].x = (rs && x < Lw) ? srow[x] : 0.f;
+                    v[j].y = (rt && x < m) ? trow[x] - tmean : 0.f;
+                }
+                group_fft<E, -1>(v, t, sc, tw);
+                if (rs) {
+#pragma unroll
+                    for (int j = 0; j < E; ++j) Z[(size_t)y * ZP + t + 8 * j] = v[j];
+                }
+            }
+            __syncthreads();
+            // ---- columns in conjugate pairs, cross spectrum into the sums
+            {
+                const int pr = grp;  // pair pr: columns (pr, L - pr); pair 0: (0, L/2)
+                const int c1 = pr, c2 = pr == 0 ? L / 2 : L - pr;
+                float2 a[E], b[E];
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    a[j] = Z[(size_t)(t + 8 * j) * ZP + c1];
+                    b[j] = Z[(size_t)(t + 8 * j) * ZP + c2];
+                }
+                group_fft<E, -1>(a, t, sc, tw);
+                group_fft<E, -1>(b, t, sc, tw);
+                // Z[-k] of column c1 lives in column c2 (in column c1 itself for
+                // pair 0).  Row -(t + 8j) is held by thread (8 - t) mod 8 at index
+                // E - 1 - j; for t = 0 by the thread itself at index (E - j) mod E.
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const float2 sb = make_float2(__shfl_sync(0xffffffffu, b[E - 1 - j].x, tpart),
+                                                  __shfl_sync(0xffffffffu, b[E - 1 - j].y, tpart));
+                    const float2 pb = t == 0 ? b[(E - j) & (E - 1)] : sb;
+                    if (pr != 0) acc[j] = cadd(acc[j], cross_spectrum(a[j], make_float2(pb.x, -pb.y)));
+                }
+                if (pr == 0) {  // lanes 0-7 of warp 0: columns 0 and L/2 each pair with themselves
+#pragma unroll
+                    for (int j = 0; j < E; ++j) {
+                        const float2 sa = make_float2(__shfl_sync(0xffu, a[E - 1 - j].x, tpart),
+                                                      __shfl_sync(0xffu, a[E - 1 - j].y, tpart));
+                        const float2 sb = make_float2(__shfl_sync(0xffu, b[E - 1 - j].x, tpart),
+                                                      __shfl_sync(0xffu, b[E - 1 - j].y, tpart));
+                        const float2 pa = t == 0 ? a[(E - j) & (E - 1)] : sa;
+                        const float2 pb = t == 0 ? b[(E - j) & (E - 1)] : sb;
+                        acc[j] = cadd(acc[j], cross_spectrum(a[j], make_float2(pa.x, -pa.y)));
+                        P64[t + 8 * j] = cadd(P64[t + 8 * j], cross_spectrum(b[j], make_float2(pb.x, -pb.y)));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- inverse along the columns kx in [0, L/2]: rows y < 2R + 1 of Q in Z
+        {
+            const int pr = grp;
+            group_fft<E, 1>(acc, t, sc, tw);
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                if (t + 8 * j < P1) Z[(size_t)(t + 8 * j) * ZP + pr] = acc[j];
+        }
+        {
+            float2 v[E];
+#pragma unroll
+            for (int j = 0; j < E; ++j) v[j] = P64[t + 8 * j];
+            group_fft<E, 1>(v, t, sc, tw);  // every group computes it (uniform); group 0 stores it
+            if (grp == 0) {
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+                    if (t + 8 * j < P1) Z[(size_t)(t + 8 * j) * ZP + L / 2] = v[j];
+            }
+        }
+        __syncthreads();
+        // ---- inverse along the rows (Hermitian extension), real part
+        float* out = maps + (size_t)k * P1 * P1;
+        for (int y0 = 0; y0 < P1; y0 += kFftGroups) {
+            const int y = y0 + grp;
+            const int yy = y < P1 ? y : 0;
+            float2 v[E];
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int kx = t + 8 * j;
+                const float2 q = Z[(size_t)yy * ZP + (kx <= L / 2 ? kx : L - kx)];
+                v[j] = kx <= L / 2 ? q : make_float2(q.x, -q.y);
+            }
+            group_fft<E, 1>(v, t, sc, tw);
+            if (y < P1) {
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const int x = t + 8 * j;
+                    if (x < P1) out[(size_t)y * P1 + x] = v[j].x * inv_area;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+bool corr_fft_supported(int m, int R) { return m + 2 * R <= 128; }
+
+cudaError_t launch_corr_fft(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
+                            const PointStat* stats, float* maps, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (ref.dtype != SFOC_DTYPE_F32 || sen.dtype != SFOC_DTYPE_F32 || !corr_fft_supported(m, R))
+        return cudaErrorNotSupported;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t rplane = ref.pitch * ref.H, splane = sen.pitch * sen.H;
+    cudaError_t e;
+#define SFOC_FFT_LAUNCH(LV)                                                                                       \
+    {                                                                                                             \
+        const int smem = (int)FftShape<LV>::smem;                                                                 \
+        e = cudaFuncSetAttribute(k_corr_fft<LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);             \
+        if (e != cudaSuccess) return e;                                                                           \
+        const int grid = n < sms ? n : sms;                                                                       \
+        k_corr_fft<LV><<<grid, FftShape<LV>::T, smem, st>>>(ref.f32, ref.pitch, rplane, sen.f32, sen.pitch, splane, \
+                                                        pts, n, m, R, ref.z, stats, maps);                      \
+    }
+    if (m + 2 * R <= 64) {
+        SFOC_FFT_LAUNCH(64)
+    } else {
+        SFOC_FFT_LAUNCH(128)
+    }
+#undef SFOC_FFT_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace sfoc

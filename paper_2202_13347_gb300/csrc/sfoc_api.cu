@@ -579,13 +579,17 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
     if (ref->c.z != sen->c.z) return fail(ctx, SFOC_ERR_SHAPE, "cubes have different channel counts");
     if (ref->c.dtype != sen->c.dtype) return fail(ctx, SFOC_ERR_SHAPE, "cubes have different dtypes");
     int path = opts ? opts->corr_path : SFOC_CORR_AUTO;
-    if (path == SFOC_CORR_AUTO) path = ref->c.dtype == SFOC_DTYPE_BF16 ? SFOC_CORR_IGEMM_TC : SFOC_CORR_DIRECT_F32;
-    if (path == SFOC_CORR_DIRECT_F32 && ref->c.dtype != SFOC_DTYPE_F32)
-        return fail(ctx, SFOC_ERR_UNSUPPORTED, "DIRECT_F32 needs F32 cubes");
+    if (path == SFOC_CORR_AUTO)
+        path = ref->c.dtype == SFOC_DTYPE_BF16                       ? SFOC_CORR_IGEMM_TC
+               : corr_fft_supported(template_size, search_radius) ? SFOC_CORR_FFT
+                                                                    : SFOC_CORR_DIRECT_F32;
     if (path != SFOC_CORR_DIRECT_F32 && path != SFOC_CORR_IGEMM_TC && path != SFOC_CORR_TC_TOEPLITZ &&
-        path != SFOC_CORR_TC_COLUMN && path != SFOC_CORR_TC_BAND)
+        path != SFOC_CORR_TC_COLUMN && path != SFOC_CORR_TC_BAND && path != SFOC_CORR_FFT)
         return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown corr_path");
-    if (path != SFOC_CORR_DIRECT_F32 && ref->c.dtype != SFOC_DTYPE_BF16)
+    const bool f32_path = path == SFOC_CORR_DIRECT_F32 || path == SFOC_CORR_FFT;
+    if (f32_path && ref->c.dtype != SFOC_DTYPE_F32)
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "DIRECT_F32 and FFT need F32 cubes");
+    if (!f32_path && ref->c.dtype != SFOC_DTYPE_BF16)
         return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
     DeviceGuard g(ctx->device);
     if (n == 0) return SFOC_OK;
@@ -610,6 +614,8 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
         StageScope sc(ctx, ST_CORR, 1);
         if (path == SFOC_CORR_DIRECT_F32)
             e = launch_corr_f32(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->stream);
+        else if (path == SFOC_CORR_FFT)
+            e = launch_corr_fft(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->stream);
         else
             e = launch_corr_tc(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->d_err,
                                path == SFOC_CORR_TC_TOEPLITZ  ? 1
@@ -623,7 +629,7 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
     if (e != cudaSuccess) return cuda_fail(ctx, e, "correlation launch");
     {
         StageScope sc(ctx, ST_NCC, 1);
-        e = launch_ncc_argmax(ref->c, d_points, n, m, R, stats, maps, path == SFOC_CORR_DIRECT_F32 ? 1 : 0,
+        e = launch_ncc_argmax(ref->c, d_points, n, m, R, stats, maps, f32_path ? 1 : 0,
                               opts ? opts->d_maps : nullptr, d_out, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ncc launch");

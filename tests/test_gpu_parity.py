@@ -98,16 +98,24 @@ def test_integral_planes(b, ctx, orc):
 # matching (Sec. 2.2, Eq. 8-16)
 # ---------------------------------------------------------------------------
 
+F32_PATHS = ["direct", "fft"]
+
+
+def f32_path(b, name):
+    return {"direct": b.CORR_DIRECT_F32, "fft": b.CORR_FFT}[name]
+
+
 def gpu_match(ctx, b, pair, p=None, corr=0, want_maps=False):
     rc = ctx.sfoc_build(dev(pair.ref), p=p)
     sc = ctx.sfoc_build(dev(pair.sen), p=p)
     return ctx.fastncc_match(rc, sc, dev(pair.points), pair.m, pair.R, corr_path=corr, want_maps=want_maps)
 
 
-def test_match_config1_f32(b, ctx, orc):
+@pytest.mark.parametrize("path", F32_PATHS)
+def test_match_config1_f32(b, ctx, orc, path):
     pair = config1()
     o = orc.match_pair(pair.ref, pair.sen, pair.points, pair.m, pair.R, want_maps=True, roi=False)
-    g = gpu_match(ctx, b, pair, want_maps=True)
+    g = gpu_match(ctx, b, pair, corr=f32_path(b, path), want_maps=True)
     st = compare(g, o, pair.R, oracle_maps=o["maps"])
     # the NCC maps themselves agree everywhere
     gm = g["maps"].cpu().numpy()
@@ -121,15 +129,19 @@ def test_match_config1_f32(b, ctx, orc):
     (64, 64, 1, 2, 16, 13),     # m = 1
     (60, 75, 15, 0, 9, 14),     # R = 0
     (150, 140, 31, 12, 20, 15),
+    (120, 130, 24, 20, 10, 16),  # m + 2R = 64: the smallest transform's edge
+    (200, 210, 65, 31, 6, 17),   # m + 2R = 127
 ])
-def test_match_small_cases(b, ctx, orc, H, W, m, R, npts, seed):
+@pytest.mark.parametrize("path", F32_PATHS)
+def test_match_small_cases(b, ctx, orc, H, W, m, R, npts, seed, path):
     pair = tiny_pair(seed, H, W, m, R, npts, shift=(2, -1))
     o = orc.match_pair(pair.ref, pair.sen, pair.points, m, R, want_maps=True, roi=False)
-    g = gpu_match(ctx, b, pair, want_maps=True)
+    g = gpu_match(ctx, b, pair, corr=f32_path(b, path), want_maps=True)
     compare(g, o, R, oracle_maps=o["maps"])
 
 
-def test_status_cases(b, ctx, orc):
+@pytest.mark.parametrize("path", F32_PATHS)
+def test_status_cases(b, ctx, orc, path):
     """Out-of-bounds points, a flat template and a NaN pixel."""
     pair = tiny_pair(21, 90, 90, 11, 5, 4)
     sen = pair.sen.copy()
@@ -141,15 +153,16 @@ def test_status_cases(b, ctx, orc):
     pair.points = pts
     o = orc.match_pair(pair.ref, sen, pts, 11, 5, want_maps=True, roi=False)
     assert set(o["status"].tolist()) >= {1, 2, 4}
-    g = gpu_match(ctx, b, pair, want_maps=True)
+    g = gpu_match(ctx, b, pair, corr=f32_path(b, path), want_maps=True)
     compare(g, o, 5, oracle_maps=o["maps"])
 
 
-def test_config2_full_size_sampled(b, ctx, orc):
+@pytest.mark.parametrize("path", F32_PATHS)
+def test_config2_full_size_sampled(b, ctx, orc, path):
     """2048^2, 1000 points, m=81, R=20: the benchmark's configuration; the
     oracle checks a seeded sample of 8 points."""
     pair = config2()
-    g = gpu_match(ctx, b, pair)
+    g = gpu_match(ctx, b, pair, corr=f32_path(b, path))
     rng = np.random.default_rng(2024)
     idx = np.sort(rng.choice(len(pair.points), 8, replace=False))
     o = orc.match_pair(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R, want_maps=True)
