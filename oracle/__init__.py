@@ -15,6 +15,8 @@ Function map (paper citation in each C function's comment):
   ncc_eq9_dft  Eq. 9 with Eq. 13 (naive DFT) and Eq. 14-16 (tiny inputs)
   integral     Eq. 14-15 (exclusive prefix), rect_sum Eq. 16
   kernel_*     Eq. 2, 3, 5 and the dilated Gaussian
+  ransac       RANSAC with a projective / affine model (Sec. 3.2.3)
+  match_quality  NCM, CMR and the RMSE of Eq. 22 (Sec. 4.1)
 """
 from __future__ import annotations
 
@@ -27,6 +29,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sfoc_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "ransac_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # status codes (values fixed by the paper-derived conventions, independent of
@@ -36,9 +39,9 @@ OK, OUT_OF_BOUNDS, FLAT_TEMPLATE, PEAK_ON_EDGE, NAN_INPUT = 0, 1, 2, 3, 4
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc -O2 -fopenmp (plain C, portable)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp] + _SRCS + ["-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -134,6 +137,15 @@ def lib():
         L.oracle_complexity_ratio.argtypes = [C.c_int] * 5
         L.oracle_ncc_eq9_dft.restype = C.c_int
         L.oracle_ncc_eq9_dft.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, dp]
+        up = C.POINTER(C.c_uint8)
+        ip = C.POINTER(C.c_int)
+        L.oracle_ransac.restype = C.c_int
+        L.oracle_ransac.argtypes = [dp, dp, up, C.c_int, C.c_int, ip, C.c_int, C.c_double, C.c_int, dp, up, ip, ip,
+                                    ip]
+        L.oracle_ransac_fit.restype = C.c_int
+        L.oracle_ransac_fit.argtypes = [dp, dp, up, C.c_int, C.c_int, ip, dp]
+        L.oracle_match_quality.restype = C.c_int
+        L.oracle_match_quality.argtypes = [dp, dp, dp, up, C.c_int, C.c_double, dp, dp]
         _lib = L
     return _lib
 
@@ -332,3 +344,65 @@ def match_pair(ref_img, sen_img, points, m, R, p: Params = None, want_maps=False
     if not outs:
         return {k: np.zeros((0,)) for k in keys}
     return {k: np.concatenate([o[k] for o in outs]) for k in keys}
+
+
+# ---------------------------------------------------------------------------
+# outlier rejection (Sec. 3.2.3) and matching criteria (Sec. 4.1)
+# ---------------------------------------------------------------------------
+PROJECTIVE, AFFINE = 1, 0
+
+
+def _pts(a):
+    return np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1, 2))
+
+
+def _mask(valid, n):
+    if valid is None:
+        return None, None
+    v = np.ascontiguousarray(np.asarray(valid, np.uint8).reshape(n))
+    return v, v.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def ransac(src, dst, samples, valid=None, model=PROJECTIVE, tau=1.5, refits=1):
+    """RANSAC over correspondences src -> dst (n x 2, pixels) with the given
+    minimal samples (n_hyp x 4, or x 3 for the affine model).  Returns
+    H (3 x 3), inlier mask, per-hypothesis scores, winning hypothesis and
+    inlier count."""
+    src, dst = _pts(src), _pts(dst)
+    n = len(src)
+    k = 4 if model == PROJECTIVE else 3
+    samp = np.ascontiguousarray(np.asarray(samples, np.int32).reshape(-1, k))
+    v, vp = _mask(valid, n)
+    H = np.zeros(9)
+    inl = np.zeros(n, np.uint8)
+    scores = np.zeros(len(samp), np.int32)
+    best, cnt = C.c_int(0), C.c_int(0)
+    ip = C.POINTER(C.c_int)
+    rc = lib().oracle_ransac(_dp(src), _dp(dst), vp, n, int(model), samp.ctypes.data_as(ip), len(samp), float(tau),
+                             int(refits), _dp(H), inl.ctypes.data_as(C.POINTER(C.c_uint8)),
+                             scores.ctypes.data_as(ip), C.byref(best), C.byref(cnt))
+    if rc != 0:
+        raise ValueError("oracle_ransac: bad arguments")
+    return dict(H=H.reshape(3, 3), inlier=inl.astype(bool), scores=scores, best=best.value, count=cnt.value)
+
+
+def ransac_fit(src, dst, idx, valid=None, model=PROJECTIVE):
+    """The exact model on one minimal sample (None when singular)."""
+    src, dst = _pts(src), _pts(dst)
+    v, vp = _mask(valid, len(src))
+    ix = np.ascontiguousarray(np.asarray(idx, np.int32))
+    H = np.zeros(9)
+    ok = lib().oracle_ransac_fit(_dp(src), _dp(dst), vp, len(src), int(model),
+                                 ix.ctypes.data_as(C.POINTER(C.c_int)), _dp(H))
+    return H.reshape(3, 3) if ok else None
+
+
+def match_quality(P, src, dst, valid=None, tau=1.5):
+    """NCM, CMR and RMSE (Eq. 22) of the matches src -> dst against model P."""
+    src, dst = _pts(src), _pts(dst)
+    v, vp = _mask(valid, len(src))
+    Pm = np.ascontiguousarray(np.asarray(P, np.float64).reshape(9))
+    cmr, rmse = C.c_double(0), C.c_double(0)
+    ncm = lib().oracle_match_quality(_dp(Pm), _dp(src), _dp(dst), vp, len(src), float(tau), C.byref(cmr),
+                                     C.byref(rmse))
+    return dict(ncm=ncm, cmr=cmr.value, rmse=rmse.value)

@@ -427,3 +427,56 @@ def tiny_pair(seed, H, W, m, R, n_points, shift=(0, 0), kind="piecewise"):
     pts = _points_for(sen, ref.shape, m, R, (g, g), "grad", n_points)
     truth = np.tile(np.array([[-sx, -sy]], np.float64), (len(pts), 1))
     return Pair(np.ascontiguousarray(ref), np.ascontiguousarray(sen), pts, m, R, truth, dict(seed=seed))
+
+
+# ---------------------------------------------------------------------------
+# control-point sets for outlier rejection: correspondences under a planted
+# model with outliers, and the minimal samples (random draws) of RANSAC
+# ---------------------------------------------------------------------------
+def planted_model(rng, projective=True):
+    """A near-identity planted model (3 x 3, last entry 1): small rotation /
+    shear / scale, a translation of up to 40 px and, if projective, a small
+    perspective row."""
+    H = np.eye(3)
+    H[0, 0] += rng.uniform(-0.02, 0.02)
+    H[1, 1] += rng.uniform(-0.02, 0.02)
+    H[0, 1] = rng.uniform(-0.02, 0.02)
+    H[1, 0] = rng.uniform(-0.02, 0.02)
+    H[0, 2] = rng.uniform(-40, 40)
+    H[1, 2] = rng.uniform(-40, 40)
+    if projective:
+        H[2, 0] = rng.uniform(-2e-5, 2e-5)
+        H[2, 1] = rng.uniform(-2e-5, 2e-5)
+    return H
+
+
+def apply_model(H, pts):
+    q = np.c_[pts, np.ones(len(pts))] @ np.asarray(H).T
+    return q[:, :2] / q[:, 2:]
+
+
+def planted_correspondences(seed, n, projective=True, outlier_frac=0.3, noise=0.0, extent=2000.0):
+    """n source points uniform in [0, extent)^2; destinations = the planted
+    model applied to them (plus Gaussian noise of std `noise` px); a fraction
+    replaced by outliers 20-200 px off their planted position.  Returns
+    (src, dst, H0, is_outlier)."""
+    rng = np.random.default_rng(seed)
+    H0 = planted_model(rng, projective)
+    src = rng.uniform(0, extent, (n, 2))
+    dst = apply_model(H0, src)
+    if noise > 0:
+        dst = dst + rng.normal(0, noise, dst.shape)
+    out = rng.random(n) < outlier_frac
+    k = int(out.sum())
+    dst[out] += rng.uniform(20, 200, (k, 2)) * rng.choice([-1.0, 1.0], (k, 2))
+    return src, dst, H0, out
+
+
+def ransac_samples(seed, n, n_hyp, k):
+    """n_hyp minimal samples of k distinct indices in [0, n): the random
+    draws of RANSAC, passed to both the oracle and the kernels."""
+    rng = np.random.default_rng(seed)
+    s = np.empty((n_hyp, k), np.int32)
+    for h in range(n_hyp):
+        s[h] = rng.choice(n, k, replace=False)
+    return s
