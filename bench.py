@@ -174,7 +174,44 @@ def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
     ms = [a.elapsed_time(c) for a, c in evs]
     status = raw[:, 5].cpu()
     return dict(ms=sum(ms), ms_steps=ms, matched=int((status == 0).sum()), valid=int(((status == 0) | (status == 3)).sum()),
-                stages=st, launches=launches, p=p, corr=corr, d=(d_ref, d_sen, d_pts))
+                stages=st, launches=launches, p=p, corr=corr, d=(d_ref, d_sen, d_pts), raw=raw)
+
+
+def run_ransac(b, torch, ctx, pair, r, n_hyp=4096, reps=10, seed=7):
+    """The outlier rejection that follows matching (Sec. 3.2.3): projective
+    RANSAC over the step's control points with n_hyp seeded minimal samples,
+    timed apart from the step (CUDA events, median of reps); plus the
+    matches' NCM / CMR / RMSE (Sec. 4.1) against the planted ground truth."""
+    import numpy as np
+    from workloads import ransac_samples
+    d_pts, raw = r["d"][2], r["raw"]
+    src, dst, valid = ctx.points_from_results(d_pts, raw)
+    samp = torch.from_numpy(ransac_samples(seed, src.shape[0], n_hyp, 4)).cuda()
+    for _ in range(2):
+        g = ctx.fastncc_ransac(src, dst, samp, valid=valid)
+    stream = torch.cuda.current_stream()
+    t = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = ctx.fastncc_ransac(src, dst, samp, valid=valid)
+        e1.record(stream)
+        e1.synchronize()
+        t.append(e0.elapsed_time(e1))
+    info = g["info"].cpu().numpy()
+    res = raw.cpu().numpy()
+    ok = res[:, 5] == 0
+    off = np.stack([res[:, 3].view(np.float32), res[:, 4].view(np.float32)], 1).astype(np.float64)  # refined offsets
+    err = np.linalg.norm(off - pair.truth, axis=1)
+    correct = ok & (err <= 1.5)
+    ncm = int(correct.sum())
+    quality = dict(ncm=ncm, cmr=ncm / max(1, int(ok.sum())),
+                   rmse=float(np.sqrt(np.mean(err[correct] ** 2))) if ncm else None, tolerance_px=1.5,
+                   truth="planted offset of each point")
+    return dict(ms=statistics.median(t), hypotheses=n_hyp, points=int(src.shape[0]), valid=int(valid.sum()),
+                inliers=int(info[1]), best_hypothesis=int(info[0]), model="projective", threshold_px=1.5,
+                launches=3), quality
 
 
 def run_e2e(b, torch, ctx, pair, p, corr, steps):
@@ -386,6 +423,7 @@ def main():
         ms_max, matched_all = reduce_over_ranks(dist, torch, r["ms"], r["matched"] * r["steps"], "cuda")
         e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=r["h2d_bytes_per_step"],
                    d2h_bytes_per_step=r["d2h_bytes_per_step"], ms_per_step=ms_max / r["steps"])
+    ransac, quality = run_ransac(b, torch, ctx, pair, r0) if rank == 0 else (None, None)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pair)
@@ -398,6 +436,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
             "sfoc_mpix_s": main["sfoc_mpix_s"], "stage_ms_per_step": main["stage_ms_per_step"],
             "forms": {f: {k: v for k, v in s.items() if k not in ("clocks",)} for f, s in summ.items()},
+            "ransac": ransac, "match_quality": quality,
             "errors": {f: results[f]["error"] for f in forms if "error" in results[f]} or None}
     print(json.dumps(line))
 

@@ -284,6 +284,49 @@ SFOC_API sfoc_status fastncc_match_batch(sfoc_ctx* ctx, int n_pairs, sfoc_cube* 
                                 const int32_t* const* d_points, const int* n_points, const int* template_size,
                                 const int* search_radius, const fastncc_opts* opts, fastncc_result* const* d_outs);
 
+/* ---- outlier rejection over the control points (Sec. 3.2.3) ------------- */
+
+typedef enum { SFOC_MODEL_AFFINE = 0, SFOC_MODEL_PROJECTIVE = 1 } sfoc_model;
+
+/*
+ * Control-point pairs from one match.  For point k (sensed-image coordinates
+ * p_k = (d_points[2k], d_points[2k+1])): d_src[2k..] = p_k, d_dst[2k..] =
+ * p_k + (sub_dx, sub_dy) (its match in the reference image at the refined offset),
+ * d_valid[k] = 1 when its status is SFOC_PT_OK, else 0.  d_src, d_dst: n x 2
+ * doubles; d_valid: n bytes; all device memory owned by the caller.
+ * Asynchronous on the context stream.  INVALID_ARG for a null pointer with
+ * n > 0 or n < 0.
+ */
+SFOC_API sfoc_status fastncc_points_from_results(sfoc_ctx* ctx, const int32_t* d_points,
+                                                 const fastncc_result* d_results, int n, double* d_src,
+                                                 double* d_dst, uint8_t* d_valid);
+
+/*
+ * RANSAC (Sec. 3.2.3) with the projective transformation of the paper or an
+ * affine model, in FP64 on the device:
+ *   x' = (h0 x + h1 y + h2) / (h6 x + h7 y + 1),
+ *   y' = (h3 x + h4 y + h5) / (h6 x + h7 y + 1)      (affine: h6 = h7 = 0).
+ * d_src, d_dst: n x 2 doubles (pixels; src -> dst); d_valid: n bytes or NULL
+ * (all valid).  d_samples: n_hyp x k int32 point indices, k = 4 (projective)
+ * or 3 (affine): the random draws, supplied by the caller.  Coordinates are
+ * normalised (the valid points' centroid to the origin, mean distance
+ * sqrt(2)); each hypothesis is the exact solution on its sample and scores
+ * the number of valid points within `threshold` pixels of the model's image
+ * (-1 for a singular sample or an index outside [0, n)).  The highest score
+ * wins (ties: the lower index); its inliers are refitted by least squares
+ * and recounted, `refits` times.
+ * Outputs (device memory owned by the caller): d_model 9 doubles (row-major
+ * 3 x 3, d_model[8] = 1; identity when no hypothesis scored), d_inlier n
+ * bytes, d_info 2 int32 (winning hypothesis or -1, inlier count), d_scores
+ * n_hyp int32 per-hypothesis scores or NULL.  Uses the context workspace.
+ * Asynchronous on the context stream.  INVALID_ARG for null pointers, n < 0,
+ * n_hyp < 0, threshold < 0 or not finite, refits < 0 or an unknown model.
+ */
+SFOC_API sfoc_status fastncc_ransac(sfoc_ctx* ctx, const double* d_src, const double* d_dst, const uint8_t* d_valid,
+                                    int n, int model, const int32_t* d_samples, int n_hyp, double threshold,
+                                    int refits, double* d_model, uint8_t* d_inlier, int32_t* d_info,
+                                    int32_t* d_scores);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,7 @@ PT_OK, PT_OUT_OF_BOUNDS, PT_FLAT_TEMPLATE, PT_PEAK_ON_EDGE, PT_NAN = 0, 1, 2, 3,
 DTYPE_F32, DTYPE_BF16 = 0, 1
 (CORR_AUTO, CORR_DIRECT_F32, CORR_IGEMM_TC, CORR_TC_TOEPLITZ, CORR_TC_COLUMN, CORR_TC_BAND,
  CORR_FFT) = 0, 1, 2, 3, 4, 5, 6
+MODEL_AFFINE, MODEL_PROJECTIVE = 0, 1
 STATIC_SCRATCH_FLOATS = 1 << 24  # SFOC_STATIC_SCRATCH_FLOATS
 
 
@@ -96,6 +97,9 @@ _SIGS = {
     "fastncc_match_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(Opts), C.POINTER(_P)]),
+    "fastncc_points_from_results": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
+    "fastncc_ransac": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P, _P,
+                                 _P]),
 }
 
 
@@ -303,6 +307,7 @@ class Context:
         self._chk(lib().fastncc_match(self.h, ref.handle, sen.handle, _ptr(points), n, int(template_size),
                                       int(search_radius), C.byref(o), _ptr(raw)))
         res = _results(raw)
+        res["raw"] = raw  # the (n, 6) int32 result rows themselves
         if want_maps:
             res["maps"] = maps
         return res
@@ -366,6 +371,43 @@ class Context:
         o = Opts(int(corr_path), None)
         self._chk(lib().fastncc_match_batch(self.h, n, R, S, Pp, Np, Mp, Rp, C.byref(o), Op))
         return outs
+
+    def points_from_results(self, points: torch.Tensor, raw: torch.Tensor):
+        """Control-point pairs of a match: (src, dst) float64 (n, 2) and the
+        uint8 valid flags (status OK)."""
+        _check_cuda(points, "points", torch.int32)
+        _check_cuda(raw, "results", torch.int32)
+        n = points.shape[0]
+        src = torch.empty((n, 2), dtype=torch.float64, device=self.device)
+        dst = torch.empty((n, 2), dtype=torch.float64, device=self.device)
+        valid = torch.empty((n,), dtype=torch.uint8, device=self.device)
+        self._chk(lib().fastncc_points_from_results(self.h, _ptr(points), _ptr(raw), n, _ptr(src), _ptr(dst),
+                                                    _ptr(valid)))
+        return src, dst, valid
+
+    def fastncc_ransac(self, src: torch.Tensor, dst: torch.Tensor, samples: torch.Tensor, valid=None,
+                       model=MODEL_PROJECTIVE, threshold=1.5, refits=1, want_scores=False):
+        """RANSAC over src -> dst (float64 (n, 2) device tensors) with the
+        given minimal samples (int32 (n_hyp, 4), or (n_hyp, 3) for the affine
+        model).  Returns {H (3, 3) float64, inlier bool (n,), best, count,
+        scores (n_hyp,) when asked} on the device (best/count as a tensor)."""
+        _check_cuda(src, "src", torch.float64)
+        _check_cuda(dst, "dst", torch.float64)
+        _check_cuda(samples, "samples", torch.int32)
+        if valid is not None:
+            _check_cuda(valid, "valid", torch.uint8)
+        n, n_hyp = src.shape[0], samples.shape[0]
+        H = torch.empty((3, 3), dtype=torch.float64, device=self.device)
+        inl = torch.empty((n,), dtype=torch.uint8, device=self.device)
+        info = torch.empty((2,), dtype=torch.int32, device=self.device)
+        sc = torch.empty((n_hyp,), dtype=torch.int32, device=self.device) if want_scores else None
+        self._chk(lib().fastncc_ransac(self.h, _ptr(src), _ptr(dst), _ptr(valid) if valid is not None else None, n,
+                                       int(model), _ptr(samples), n_hyp, float(threshold), int(refits), _ptr(H),
+                                       _ptr(inl), _ptr(info), _ptr(sc) if sc is not None else None))
+        out = dict(H=H, inlier=inl.bool(), info=info)
+        if sc is not None:
+            out["scores"] = sc
+        return out
 
 
 def results(raw: torch.Tensor):

@@ -131,6 +131,14 @@ cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m,
                               const float* num, int centered, float* out_maps, fastncc_result* out,
                               cudaStream_t st);
 
+// outlier rejection (k_ransac.cu)
+size_t ransac_workspace_bytes(int n_hyp);
+cudaError_t launch_ransac(const double* src, const double* dst, const uint8_t* valid, int n, int proj,
+                          const int32_t* samples, int n_hyp, double threshold, int refits, double* H_out,
+                          uint8_t* mask, int32_t* info, int32_t* scores_out, void* ws, cudaStream_t st, int* launches);
+cudaError_t launch_results_to_points(const int32_t* pts, const fastncc_result* res, int n, double* src, double* dst,
+                                     uint8_t* valid, cudaStream_t st);
+
 // template half-width: rows before the centre
 __host__ __device__ inline int template_half(int m) { return (m % 2) ? (m - 1) / 2 : m / 2; }
 

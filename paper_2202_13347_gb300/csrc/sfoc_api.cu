@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <string>
@@ -538,6 +539,48 @@ sfoc_status sfoc_cube_export(sfoc_ctx* ctx, const sfoc_cube* cube, float* d_out)
         e = launch_cube_export(cube->c, d_out, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "export launch");
+    return SFOC_OK;
+}
+
+sfoc_status fastncc_points_from_results(sfoc_ctx* ctx, const int32_t* d_points, const fastncc_result* d_results,
+                                        int n, double* d_src, double* d_dst, uint8_t* d_valid) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (n < 0) return fail(ctx, SFOC_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!d_points || !d_results || !d_src || !d_dst || !d_valid))
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "null pointer");
+    if (n == 0) return SFOC_OK;
+    DeviceGuard g(ctx->device);
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_OTHER, 1);
+        e = launch_results_to_points(d_points, d_results, n, d_src, d_dst, d_valid, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "points launch");
+    return SFOC_OK;
+}
+
+sfoc_status fastncc_ransac(sfoc_ctx* ctx, const double* d_src, const double* d_dst, const uint8_t* d_valid, int n,
+                           int model, const int32_t* d_samples, int n_hyp, double threshold, int refits,
+                           double* d_model, uint8_t* d_inlier, int32_t* d_info, int32_t* d_scores) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (n < 0 || n_hyp < 0 || refits < 0) return fail(ctx, SFOC_ERR_INVALID_ARG, "n, n_hyp and refits must be >= 0");
+    if (!(threshold >= 0.0) || !std::isfinite(threshold))
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "threshold must be finite and >= 0");
+    if (model != SFOC_MODEL_AFFINE && model != SFOC_MODEL_PROJECTIVE)
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown model");
+    if (!d_model || !d_info || (n > 0 && (!d_src || !d_dst || !d_inlier)) || (n_hyp > 0 && !d_samples))
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "null pointer");
+    DeviceGuard g(ctx->device);
+    sfoc_status s = ensure_ws(ctx, ransac_workspace_bytes(n_hyp));
+    if (s != SFOC_OK) return s;
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_OTHER, n_hyp > 0 ? 3 : 2);
+        int nl = 0;
+        e = launch_ransac(d_src, d_dst, d_valid, n, model == SFOC_MODEL_PROJECTIVE ? 1 : 0, d_samples, n_hyp,
+                          threshold, refits, d_model, d_inlier, d_info, d_scores, ctx->ws, ctx->stream, &nl);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ransac launch");
     return SFOC_OK;
 }
 
