@@ -17,6 +17,7 @@ Function map (paper citation in each C function's comment):
   kernel_*     Eq. 2, 3, 5 and the dilated Gaussian
   ransac       RANSAC with a projective / affine model (Sec. 3.2.3)
   match_quality  NCM, CMR and the RMSE of Eq. 22 (Sec. 4.1)
+  fast_score / fast_blocks  block-based FAST interest points (Sec. 3.1.1)
 """
 from __future__ import annotations
 
@@ -29,7 +30,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sfoc_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "ransac_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "ransac_oracle.c"), os.path.join(_HERE, "fast_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # status codes (values fixed by the paper-derived conventions, independent of
@@ -146,6 +147,11 @@ def lib():
         L.oracle_ransac_fit.argtypes = [dp, dp, up, C.c_int, C.c_int, ip, dp]
         L.oracle_match_quality.restype = C.c_int
         L.oracle_match_quality.argtypes = [dp, dp, dp, up, C.c_int, C.c_double, dp, dp]
+        fp = C.POINTER(C.c_float)
+        L.oracle_fast_score.argtypes = [fp, C.c_int, C.c_int, C.c_float, fp]
+        L.oracle_fast_blocks.restype = C.c_int
+        L.oracle_fast_blocks.argtypes = [fp, C.c_int, C.c_int, C.c_float, C.c_int, C.c_int, C.c_int,
+                                         C.POINTER(C.c_int32), fp]
         _lib = L
     return _lib
 
@@ -406,3 +412,36 @@ def match_quality(P, src, dst, valid=None, tau=1.5):
     ncm = lib().oracle_match_quality(_dp(Pm), _dp(src), _dp(dst), vp, len(src), float(tau), C.byref(cmr),
                                      C.byref(rmse))
     return dict(ncm=ncm, cmr=cmr.value, rmse=rmse.value)
+
+
+# ---------------------------------------------------------------------------
+# block-based FAST interest points (Sec. 3.1.1)
+# ---------------------------------------------------------------------------
+def _img32(img):
+    return np.ascontiguousarray(np.asarray(img, np.float32))
+
+
+def fast_score(img, t=0.05):
+    """FAST-9 score of every pixel (0 where it is no corner)."""
+    a = _img32(img)
+    H, W = a.shape
+    out = np.zeros((H, W), np.float32)
+    fp = C.POINTER(C.c_float)
+    lib().oracle_fast_score(a.ctypes.data_as(fp), H, W, C.c_float(t), out.ctypes.data_as(fp))
+    return out
+
+
+def fast_blocks(img, t=0.05, grid_y=8, grid_x=8, margin=3):
+    """One FAST point per block: points (grid_y * grid_x, 2) int32 (x, y;
+    -1 where a block has none), scores (grid_y * grid_x,) float32."""
+    a = _img32(img)
+    H, W = a.shape
+    nb = grid_y * grid_x
+    pts = np.zeros((nb, 2), np.int32)
+    sc = np.zeros(nb, np.float32)
+    fp = C.POINTER(C.c_float)
+    rc = lib().oracle_fast_blocks(a.ctypes.data_as(fp), H, W, C.c_float(t), int(grid_y), int(grid_x), int(margin),
+                                  pts.ctypes.data_as(C.POINTER(C.c_int32)), sc.ctypes.data_as(fp))
+    if rc < 0:
+        raise ValueError("oracle_fast_blocks: bad arguments")
+    return pts, sc
