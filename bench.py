@@ -177,6 +177,32 @@ def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
                 stages=st, launches=launches, p=p, corr=corr, d=(d_ref, d_sen, d_pts), raw=raw)
 
 
+def run_fast(torch, ctx, pair, hbm_gbs, reps=10, grid=32, t=0.05):
+    """Block-based FAST (Sec. 3.1.1) on the sensed image of the workload,
+    timed apart from the step (CUDA events, median of reps).  HBM-bound:
+    algorithmic bytes = the image read once (4 B/px)."""
+    img = torch.from_numpy(pair.sen).cuda()
+    margin = pair.m // 2 + pair.R
+    for _ in range(2):
+        pts, sc = ctx.fast_blocks(img, t, grid, grid, margin)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.fast_blocks(img, t, grid, grid, margin)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    gbs = pair.sen.size * 4 / (ms * 1e-3) / 1e9
+    return dict(ms=ms, mpix_s=pair.sen.size / (ms * 1e-3) / 1e6, blocks=grid * grid,
+                points=int((pts[:, 0] >= 0).sum()), threshold=t, margin=margin,
+                roofline={"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
+                          "work": "4 B read per pixel"}, launches=1)
+
+
 def run_ransac(b, torch, ctx, pair, r, n_hyp=4096, reps=10, seed=7):
     """The outlier rejection that follows matching (Sec. 3.2.3): projective
     RANSAC over the step's control points with n_hyp seeded minimal samples,
@@ -424,6 +450,7 @@ def main():
         e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=r["h2d_bytes_per_step"],
                    d2h_bytes_per_step=r["d2h_bytes_per_step"], ms_per_step=ms_max / r["steps"])
     ransac, quality = run_ransac(b, torch, ctx, pair, r0) if rank == 0 else (None, None)
+    fast = run_fast(torch, ctx, pair, pk["hbm"]) if rank == 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pair)
@@ -436,7 +463,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
             "sfoc_mpix_s": main["sfoc_mpix_s"], "stage_ms_per_step": main["stage_ms_per_step"],
             "forms": {f: {k: v for k, v in s.items() if k not in ("clocks",)} for f, s in summ.items()},
-            "ransac": ransac, "match_quality": quality,
+            "ransac": ransac, "match_quality": quality, "fast": fast,
             "errors": {f: results[f]["error"] for f in forms if "error" in results[f]} or None}
     print(json.dumps(line))
 

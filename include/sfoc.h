@@ -284,6 +284,31 @@ SFOC_API sfoc_status fastncc_match_batch(sfoc_ctx* ctx, int n_pairs, sfoc_cube* 
                                 const int32_t* const* d_points, const int* n_points, const int* template_size,
                                 const int* search_radius, const fastncc_opts* opts, fastncc_result* const* d_outs);
 
+/* ---- interest points (Sec. 3.1.1) --------------------------------------- */
+
+/*
+ * Block-based FAST interest points (Sec. 3.1.1): FAST-9 on the 16 pixels of
+ * the radius-3 circle, one point per block of a grid_y x grid_x partition of
+ * the image (rows [by H / grid_y, (by + 1) H / grid_y), columns likewise).
+ * A pixel's score is the largest threshold for which 9 contiguous circle
+ * pixels are all brighter (or all darker) than it by more (FP32 differences
+ * of the stored values); it is a corner when the score exceeds `threshold`.
+ * Pixels closer than 3 to the border score 0.  Corners survive 3 x 3
+ * non-maximum suppression when they are at least every neighbour and above
+ * the neighbours before them in raster order.  Each block keeps its
+ * strongest surviving corner at least `margin` pixels from the border
+ * (ties: smaller y, then x).
+ *   d_image   float32 image (finite values), row-major, pitch >= W elements.
+ *   d_points  grid_y * grid_x x 2 int32 (x, y) per block, (-1, -1) when a
+ *             block has no corner; d_scores grid_y * grid_x float32 (0 then).
+ * Device memory owned by the caller; asynchronous on the context stream.
+ * INVALID_ARG for null pointers, H or W < 1, pitch < W, grid sizes outside
+ * [1, H] / [1, W], margin < 0 or a threshold that is negative or not finite.
+ */
+SFOC_API sfoc_status sfoc_fast_blocks(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems,
+                                      float threshold, int grid_y, int grid_x, int margin, int32_t* d_points,
+                                      float* d_scores);
+
 /* ---- outlier rejection over the control points (Sec. 3.2.3) ------------- */
 
 typedef enum { SFOC_MODEL_AFFINE = 0, SFOC_MODEL_PROJECTIVE = 1 } sfoc_model;

@@ -98,6 +98,8 @@ _SIGS = {
                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(Opts), C.POINTER(_P)]),
     "fastncc_points_from_results": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
+    "sfoc_fast_blocks": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, C.c_float, C.c_int, C.c_int, C.c_int, _P,
+                                   _P]),
     "fastncc_ransac": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P, _P,
                                  _P]),
 }
@@ -371,6 +373,18 @@ class Context:
         o = Opts(int(corr_path), None)
         self._chk(lib().fastncc_match_batch(self.h, n, R, S, Pp, Np, Mp, Rp, C.byref(o), Op))
         return outs
+
+    def fast_blocks(self, image: torch.Tensor, threshold=0.05, grid_y=32, grid_x=32, margin=3):
+        """Block-based FAST: (points (grid_y * grid_x, 2) int32 (x, y; -1 for
+        an empty block), scores float32) on the device."""
+        _check_cuda(image, "image", torch.float32)
+        H, W = image.shape
+        nb = int(grid_y) * int(grid_x)
+        pts = torch.empty((nb, 2), dtype=torch.int32, device=self.device)
+        sc = torch.empty((nb,), dtype=torch.float32, device=self.device)
+        self._chk(lib().sfoc_fast_blocks(self.h, _ptr(image), H, W, W, C.c_float(threshold), int(grid_y),
+                                         int(grid_x), int(margin), _ptr(pts), _ptr(sc)))
+        return pts, sc
 
     def points_from_results(self, points: torch.Tensor, raw: torch.Tensor):
         """Control-point pairs of a match: (src, dst) float64 (n, 2) and the

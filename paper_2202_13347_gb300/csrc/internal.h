@@ -131,6 +131,10 @@ cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m,
                               const float* num, int centered, float* out_maps, fastncc_result* out,
                               cudaStream_t st);
 
+// block-based FAST (k_fast.cu)
+cudaError_t launch_fast_blocks(const float* img, int H, int W, size_t pitch, float t, int grid_y, int grid_x,
+                               int margin, int32_t* points, float* scores, cudaStream_t st);
+
 // outlier rejection (k_ransac.cu)
 size_t ransac_workspace_bytes(int n_hyp);
 cudaError_t launch_ransac(const double* src, const double* dst, const uint8_t* valid, int n, int proj,

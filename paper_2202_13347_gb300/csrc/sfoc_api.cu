@@ -542,6 +542,26 @@ sfoc_status sfoc_cube_export(sfoc_ctx* ctx, const sfoc_cube* cube, float* d_out)
     return SFOC_OK;
 }
 
+sfoc_status sfoc_fast_blocks(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems, float threshold,
+                             int grid_y, int grid_x, int margin, int32_t* d_points, float* d_scores) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!d_image || !d_points || !d_scores) return fail(ctx, SFOC_ERR_INVALID_ARG, "null pointer");
+    if (H < 1 || W < 1 || pitch_elems < (size_t)W) return fail(ctx, SFOC_ERR_INVALID_ARG, "bad image shape");
+    if (grid_y < 1 || grid_y > H || grid_x < 1 || grid_x > W || grid_y > 65535)
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "grid sizes must be in [1, H] and [1, W]");
+    if (margin < 0 || !(threshold >= 0.f) || !std::isfinite(threshold))
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "margin >= 0 and a finite threshold >= 0 required");
+    DeviceGuard g(ctx->device);
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_OTHER, 1);
+        e = launch_fast_blocks(d_image, H, W, pitch_elems, threshold, grid_y, grid_x, margin, d_points, d_scores,
+                               ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fast launch");
+    return SFOC_OK;
+}
+
 sfoc_status fastncc_points_from_results(sfoc_ctx* ctx, const int32_t* d_points, const fastncc_result* d_results,
                                         int n, double* d_src, double* d_dst, uint8_t* d_valid) {
     if (!ctx) return SFOC_ERR_INVALID_ARG;
