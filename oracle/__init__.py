@@ -18,6 +18,7 @@ Function map (paper citation in each C function's comment):
   ransac       RANSAC with a projective / affine model (Sec. 3.2.3)
   match_quality  NCM, CMR and the RMSE of Eq. 22 (Sec. 4.1)
   fast_score / fast_blocks  block-based FAST interest points (Sec. 3.1.1)
+  rectify      bilinear resampling of the sensed image with the model (Sec. 3.2.3)
 """
 from __future__ import annotations
 
@@ -148,6 +149,8 @@ def lib():
         L.oracle_match_quality.restype = C.c_int
         L.oracle_match_quality.argtypes = [dp, dp, dp, up, C.c_int, C.c_double, dp, dp]
         fp = C.POINTER(C.c_float)
+        L.oracle_rectify.restype = C.c_int
+        L.oracle_rectify.argtypes = [fp, C.c_int, C.c_int, dp, C.c_float, C.c_int, C.c_int, fp]
         L.oracle_fast_score.argtypes = [fp, C.c_int, C.c_int, C.c_float, fp]
         L.oracle_fast_blocks.restype = C.c_int
         L.oracle_fast_blocks.argtypes = [fp, C.c_int, C.c_int, C.c_float, C.c_int, C.c_int, C.c_int,
@@ -445,3 +448,18 @@ def fast_blocks(img, t=0.05, grid_y=8, grid_x=8, margin=3):
     if rc < 0:
         raise ValueError("oracle_fast_blocks: bad arguments")
     return pts, sc
+
+
+def rectify(img, H, out_shape=None, fill=0.0):
+    """The sensed image resampled into the reference frame with the model H
+    (sensed -> reference), bilinear; out_shape defaults to img.shape."""
+    a = np.ascontiguousarray(np.asarray(img, np.float32))
+    h, w = a.shape
+    oh, ow = out_shape or (h, w)
+    Hm = np.ascontiguousarray(np.asarray(H, np.float64).reshape(9))
+    out = np.zeros((oh, ow), np.float32)
+    fp = C.POINTER(C.c_float)
+    rc = lib().oracle_rectify(a.ctypes.data_as(fp), h, w, _dp(Hm), C.c_float(fill), oh, ow, out.ctypes.data_as(fp))
+    if rc != 0:
+        raise ValueError("singular model")
+    return out

@@ -274,3 +274,43 @@ int oracle_match_quality(const double* P, const double* src, const double* dst, 
     *rmse = ncm ? sqrt(se / ncm) : 0.0;
     return ncm;
 }
+
+/*
+ * Rectification (Sec. 3.2.3, last paragraph): the sensed image resampled
+ * into the reference frame with the fitted model H (sensed -> reference):
+ * output pixel (x, y) of an out_h x out_w image takes the sensed image at
+ * (u, v) = H^-1 (x, y) by bilinear interpolation (Sec. 3.2.3 names it);
+ * positions outside [0, W-1] x [0, H-1] take `fill`.  H^-1 is the adjugate
+ * of H scaled by its last entry; the interpolation weights and the blend
+ * are computed in double and the result rounded to float once.
+ * Returns 0, or -1 when H is singular.
+ */
+int oracle_rectify(const float* img, int H, int W, const double* Hm, float fill, int out_h, int out_w, float* out) {
+    const double a = Hm[0], b = Hm[1], c = Hm[2], d = Hm[3], e = Hm[4], f = Hm[5], g = Hm[6], h = Hm[7], i = Hm[8];
+    double inv[9] = {e * i - f * h, c * h - b * i, b * f - c * e, f * g - d * i, a * i - c * g,
+                     c * d - a * f, d * h - e * g, b * g - a * h, a * e - b * d};
+    const double det = a * inv[0] + b * inv[3] + c * inv[6];
+    if (det == 0.0 || inv[8] == 0.0) return -1;
+    for (int k = 0; k < 9; ++k) inv[k] /= inv[8];
+    for (int y = 0; y < out_h; ++y)
+        for (int x = 0; x < out_w; ++x) {
+            const double w = inv[6] * x + inv[7] * y + inv[8];
+            float v = fill;
+            if (w != 0.0) {
+                const double u = (inv[0] * x + inv[1] * y + inv[2]) / w;
+                const double t = (inv[3] * x + inv[4] * y + inv[5]) / w;
+                if (u >= 0.0 && t >= 0.0 && u <= W - 1 && t <= H - 1) {
+                    int u0 = (int)floor(u), t0 = (int)floor(t);
+                    if (u0 > W - 2) u0 = W - 2 < 0 ? 0 : W - 2;
+                    if (t0 > H - 2) t0 = H - 2 < 0 ? 0 : H - 2;
+                    const int u1 = u0 + 1 < W ? u0 + 1 : u0, t1 = t0 + 1 < H ? t0 + 1 : t0;
+                    const double fu = u - u0, ft = t - t0;
+                    const double p00 = img[(size_t)t0 * W + u0], p01 = img[(size_t)t0 * W + u1];
+                    const double p10 = img[(size_t)t1 * W + u0], p11 = img[(size_t)t1 * W + u1];
+                    v = (float)((1.0 - ft) * ((1.0 - fu) * p00 + fu * p01) + ft * ((1.0 - fu) * p10 + fu * p11));
+                }
+            }
+            out[(size_t)y * out_w + x] = v;
+        }
+    return 0;
+}
