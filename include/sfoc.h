@@ -352,6 +352,19 @@ SFOC_API sfoc_status fastncc_ransac(sfoc_ctx* ctx, const double* d_src, const do
                                     int refits, double* d_model, uint8_t* d_inlier, int32_t* d_info,
                                     int32_t* d_scores);
 
+/*
+ * Rectification (Sec. 3.2.3, last paragraph): the sensed image resampled
+ * into the reference frame with a model H (sensed -> reference, 9 doubles
+ * row-major in device memory, e.g. fastncc_ransac's d_model): output pixel
+ * (x, y) of the out_h x out_w image d_out takes the bilinear sample of
+ * d_image at H^-1 (x, y), or `fill` outside [0, W-1] x [0, H-1].  Mapping in
+ * FP64, blend in FP32.  A singular model gives an all-fill image.  Device
+ * memory owned by the caller; asynchronous on the context stream.
+ * INVALID_ARG for null pointers, H, W, out_h or out_w < 1, pitch < W.
+ */
+SFOC_API sfoc_status sfoc_rectify(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems,
+                                  const double* d_model, float fill, int out_h, int out_w, float* d_out);
+
 #ifdef __cplusplus
 }
 #endif

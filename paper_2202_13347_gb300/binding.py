@@ -98,6 +98,7 @@ _SIGS = {
                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(Opts), C.POINTER(_P)]),
     "fastncc_points_from_results": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
+    "sfoc_rectify": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, _P, C.c_float, C.c_int, C.c_int, _P]),
     "sfoc_fast_blocks": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, C.c_float, C.c_int, C.c_int, C.c_int, _P,
                                    _P]),
     "fastncc_ransac": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P, _P,
@@ -385,6 +386,18 @@ class Context:
         self._chk(lib().sfoc_fast_blocks(self.h, _ptr(image), H, W, W, C.c_float(threshold), int(grid_y),
                                          int(grid_x), int(margin), _ptr(pts), _ptr(sc)))
         return pts, sc
+
+    def rectify(self, image: torch.Tensor, model: torch.Tensor, out_shape=None, fill=0.0, out=None):
+        """The sensed image resampled into the reference frame with the
+        (3, 3) float64 device model (sensed -> reference), bilinear."""
+        _check_cuda(image, "image", torch.float32)
+        _check_cuda(model, "model", torch.float64)
+        H, W = image.shape
+        oh, ow = out_shape or (H, W)
+        if out is None:
+            out = torch.empty((oh, ow), dtype=torch.float32, device=self.device)
+        self._chk(lib().sfoc_rectify(self.h, _ptr(image), H, W, W, _ptr(model), C.c_float(fill), oh, ow, _ptr(out)))
+        return out
 
     def points_from_results(self, points: torch.Tensor, raw: torch.Tensor):
         """Control-point pairs of a match: (src, dst) float64 (n, 2) and the

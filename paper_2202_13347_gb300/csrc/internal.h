@@ -140,6 +140,8 @@ size_t ransac_workspace_bytes(int n_hyp);
 cudaError_t launch_ransac(const double* src, const double* dst, const uint8_t* valid, int n, int proj,
                           const int32_t* samples, int n_hyp, double threshold, int refits, double* H_out,
                           uint8_t* mask, int32_t* info, int32_t* scores_out, void* ws, cudaStream_t st, int* launches);
+cudaError_t launch_rectify(const float* img, int H, int W, size_t pitch, const double* Hm, float fill, int out_h,
+                           int out_w, float* out, cudaStream_t st);
 cudaError_t launch_results_to_points(const int32_t* pts, const fastncc_result* res, int n, double* src, double* dst,
                                      uint8_t* valid, cudaStream_t st);
 

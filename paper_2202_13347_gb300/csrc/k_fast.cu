@@ -74,18 +74,28 @@ __global__ void __launch_bounds__(kFastThreads)
                     float d[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) d[k] = s_img[iy + c_cdy[k]][ix + c_cdx[k]] - c;
-                    float best = -INFINITY;
+                    // smallest and largest difference over every arc of 9 (cyclic),
+                    // by doubling: windows of 2, 4, 8, then one more pixel
+                    float lo[16], hi[16], l2[16], h2[16];
 #pragma unroll
-                    for (int s = 0; s < 16; ++s) {
-                        float mb = d[s], md = -d[s];
-#pragma unroll
-                        for (int j = 1; j < 9; ++j) {
-                            const float v = d[(s + j) & 15];
-                            mb = fminf(mb, v);
-                            md = fminf(md, -v);
-                        }
-                        best = fmaxf(best, fmaxf(mb, md));
+                    for (int k = 0; k < 16; ++k) {
+                        lo[k] = fminf(d[k], d[(k + 1) & 15]);
+                        hi[k] = fmaxf(d[k], d[(k + 1) & 15]);
                     }
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        l2[k] = fminf(lo[k], lo[(k + 2) & 15]);
+                        h2[k] = fmaxf(hi[k], hi[(k + 2) & 15]);
+                    }
+                    float bright = -INFINITY, dark = INFINITY;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float mn = fminf(fminf(l2[k], l2[(k + 4) & 15]), d[(k + 8) & 15]);
+                        const float mx = fmaxf(fmaxf(h2[k], h2[(k + 4) & 15]), d[(k + 8) & 15]);
+                        bright = fmaxf(bright, mn);   // brighter arc: its smallest rise
+                        dark = fminf(dark, mx);       // darker arc: minus its smallest drop
+                    }
+                    const float best = fmaxf(bright, -dark);
                     sc = best > t ? best : 0.f;
                 }
                 s_sc[ly][lx] = sc;

@@ -14,7 +14,8 @@
 // and recounted, `refits` times.
 //
 //   k_ransac_frames  one block: the two normalising frames (fixed-order sums)
-//   k_ransac_hyp     one warp per hypothesis: lane 0 solves, the warp counts
+//   k_ransac_hyp     one warp per 8 hypotheses: each of 8 lanes solves one,
+//                    then the warp counts inliers for each model in turn
 //   k_ransac_final   one block: argmax, refits (normal equations reduced in a
 //                    fixed order: warp shuffles, then the warps in order)
 #include <math.h>
@@ -26,7 +27,7 @@ namespace sfoc {
 namespace {
 
 constexpr int kRsThreads = 256;
-constexpr int kHypWarps = 4;
+constexpr int kHpw = 8;  // hypotheses per warp (one warp per CTA)
 
 struct Frames {
     double s[3];  // source: scale, cx, cy  (p -> s (p - c))
@@ -161,51 +162,58 @@ __device__ __forceinline__ bool inlier(const double* H, const double* src, const
     return ex * ex + ey * ey <= t2;
 }
 
-__global__ void __launch_bounds__(32 * kHypWarps)
+// One warp (CTA) per kHpw hypotheses: lane l < kHpw solves hypothesis
+// h0 + l, then the warp counts inliers for each of the models in turn.
+__global__ void __launch_bounds__(32)
     k_ransac_hyp(const double* __restrict__ src, const double* __restrict__ dst, const uint8_t* __restrict__ valid,
                  int n, int proj, const int32_t* __restrict__ samples, int n_hyp, double t2,
                  const Frames* __restrict__ frames, int32_t* __restrict__ scores, double* __restrict__ models) {
-    __shared__ double sH[kHypWarps][9];
-    __shared__ int sok[kHypWarps];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int h = blockIdx.x * kHypWarps + w;
-    if (h >= n_hyp) return;  // whole warps leave together
+    __shared__ double sH[kHpw][9];
+    __shared__ int sok[kHpw];
+    const int lane = threadIdx.x & 31;
+    const int h0 = blockIdx.x * kHpw;
     const bool pj = proj != 0;
     const int k = pj ? 4 : 3, nu = pj ? 8 : 6;
-    if (lane == 0) {
-        const Frames F = *frames;
-        double A[64], b[8], x[8], r1[8], r2[8];
-        bool in_range = true;
-        for (int j = 0; j < k; ++j) {
-            const int i0 = samples[(size_t)h * k + j];
-            in_range = in_range && i0 >= 0 && i0 < n;
-            const int i = (i0 >= 0 && i0 < n) ? i0 : 0;  // an index outside [0, n) voids the hypothesis
-            const double sx = F.s[0] * (src[2 * i] - F.s[1]), sy = F.s[0] * (src[2 * i + 1] - F.s[2]);
-            const double dx = F.d[0] * (dst[2 * i] - F.d[1]), dy = F.d[0] * (dst[2 * i + 1] - F.d[2]);
-            eq_rows(pj, sx, sy, dx, dy, r1, r2);
-            for (int c = 0; c < nu; ++c) {
-                A[(2 * j) * 8 + c] = r1[c];
-                A[(2 * j + 1) * 8 + c] = r2[c];
+    if (lane < kHpw) {
+        const int h = h0 + lane;
+        bool ok = false;
+        if (h < n_hyp) {
+            const Frames F = *frames;
+            double A[64], b[8], x[8], r1[8], r2[8];
+            bool in_range = true;
+            for (int j = 0; j < k; ++j) {
+                const int i0 = samples[(size_t)h * k + j];
+                in_range = in_range && i0 >= 0 && i0 < n;
+                const int i = (i0 >= 0 && i0 < n) ? i0 : 0;  // an index outside [0, n) voids the hypothesis
+                const double sx = F.s[0] * (src[2 * i] - F.s[1]), sy = F.s[0] * (src[2 * i + 1] - F.s[2]);
+                const double dx = F.d[0] * (dst[2 * i] - F.d[1]), dy = F.d[0] * (dst[2 * i + 1] - F.d[2]);
+                eq_rows(pj, sx, sy, dx, dy, r1, r2);
+                for (int c = 0; c < nu; ++c) {
+                    A[(2 * j) * 8 + c] = r1[c];
+                    A[(2 * j + 1) * 8 + c] = r2[c];
+                }
+                b[2 * j] = dx;
+                b[2 * j + 1] = dy;
             }
-            b[2 * j] = dx;
-            b[2 * j + 1] = dy;
+            ok = in_range && solve_small(A, b, nu, x) && to_pixels(x, pj, F, sH[lane]);
         }
-        const bool ok = in_range && solve_small(A, b, nu, x) && to_pixels(x, pj, F, sH[w]);
-        sok[w] = ok ? 1 : 0;
+        sok[lane] = ok ? 1 : 0;
     }
     __syncwarp();
-    int c = 0;
-    if (sok[w]) {
-        double H[9];
+    const int nh = n_hyp - h0 < kHpw ? n_hyp - h0 : kHpw;
+    for (int q = 0; q < nh; ++q) {
+        int c = 0;
+        if (sok[q]) {
+            double H[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) H[q] = sH[w][q];
-        for (int i = lane; i < n; i += 32) c += (is_valid(valid, i) && inlier(H, src, dst, i, t2)) ? 1 : 0;
+            for (int r = 0; r < 9; ++r) H[r] = sH[q][r];
+            for (int i = lane; i < n; i += 32) c += (is_valid(valid, i) && inlier(H, src, dst, i, t2)) ? 1 : 0;
+        }
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if (lane == 0) scores[h0 + q] = sok[q] ? c : -1;
     }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if (lane == 0) {
-        scores[h] = sok[w] ? c : -1;
-        for (int q = 0; q < 9; ++q) models[(size_t)h * 9 + q] = sok[w] ? sH[w][q] : 0.0;
-    }
+    if (lane < nh)
+        for (int r = 0; r < 9; ++r) models[(size_t)(h0 + lane) * 9 + r] = sok[lane] ? sH[lane][r] : 0.0;
 }
 
 constexpr int kNE = 44;  // unique entries of the 8 x 8 normal matrix (36) and the right side (8)
@@ -322,6 +330,48 @@ __global__ void __launch_bounds__(kRsThreads)
     }
 }
 
+// Rectification (Sec. 3.2.3): out(x, y) = bilinear sample of the sensed
+// image at H^-1 (x, y); outside [0, W-1] x [0, H-1] the fill value.  The
+// mapping is FP64 (coordinates of 10^4 px keep their sub-pixel part), the
+// blend FP32.  Each CTA inverts H (the adjugate scaled by its last entry);
+// a singular model gives an all-fill image.
+__global__ void k_rectify(const float* __restrict__ img, int H, int W, size_t pitch, const double* __restrict__ Hm,
+                          float fill, int out_h, int out_w, float* __restrict__ out) {
+    __shared__ double s_inv[9];
+    __shared__ int s_ok;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const double a = Hm[0], b = Hm[1], c = Hm[2], d = Hm[3], e = Hm[4], f = Hm[5], g = Hm[6], h = Hm[7],
+                     i = Hm[8];
+        double inv[9] = {e * i - f * h, c * h - b * i, b * f - c * e, f * g - d * i, a * i - c * g,
+                         c * d - a * f, d * h - e * g, b * g - a * h, a * e - b * d};
+        const double det = a * inv[0] + b * inv[3] + c * inv[6];
+        s_ok = det != 0.0 && inv[8] != 0.0;
+        for (int k = 0; k < 9; ++k) s_inv[k] = s_ok ? inv[k] / inv[8] : 0.0;
+    }
+    __syncthreads();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= out_w || y >= out_h) return;
+    float v = fill;
+    const double w = s_inv[6] * x + s_inv[7] * y + s_inv[8];
+    if (s_ok && w != 0.0) {
+        const double rw = 1.0 / w;  // one division per pixel (FP64 is slow on this part)
+        const double u = (s_inv[0] * x + s_inv[1] * y + s_inv[2]) * rw;
+        const double t = (s_inv[3] * x + s_inv[4] * y + s_inv[5]) * rw;
+        if (u >= 0.0 && t >= 0.0 && u <= W - 1 && t <= H - 1) {
+            int u0 = (int)floor(u), t0 = (int)floor(t);
+            u0 = min(u0, max(W - 2, 0));
+            t0 = min(t0, max(H - 2, 0));
+            const int u1 = min(u0 + 1, W - 1), t1 = min(t0 + 1, H - 1);
+            const float fu = (float)(u - u0), ft = (float)(t - t0);
+            const float p00 = img[(size_t)t0 * pitch + u0], p01 = img[(size_t)t0 * pitch + u1];
+            const float p10 = img[(size_t)t1 * pitch + u0], p11 = img[(size_t)t1 * pitch + u1];
+            const float r0 = fmaf(fu, p01 - p00, p00), r1 = fmaf(fu, p11 - p10, p10);
+            v = fmaf(ft, r1 - r0, r0);
+        }
+    }
+    out[(size_t)y * out_w + x] = v;
+}
+
 __global__ void k_results_to_points(const int32_t* __restrict__ pts, const fastncc_result* __restrict__ res, int n,
                                     double* __restrict__ src, double* __restrict__ dst, uint8_t* __restrict__ valid) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -355,14 +405,21 @@ cudaError_t launch_ransac(const double* src, const double* dst, const uint8_t* v
     k_ransac_frames<<<1, kRsThreads, 0, st>>>(src, dst, valid, n, frames);
     int nl = 1;
     if (n_hyp > 0) {
-        k_ransac_hyp<<<(n_hyp + kHypWarps - 1) / kHypWarps, 32 * kHypWarps, 0, st>>>(src, dst, valid, n, proj, samples,
-                                                                                    n_hyp, t2, frames, scores, models);
+        k_ransac_hyp<<<(n_hyp + kHpw - 1) / kHpw, 32, 0, st>>>(src, dst, valid, n, proj, samples, n_hyp, t2, frames,
+                                                                scores, models);
         ++nl;
     }
     k_ransac_final<<<1, kRsThreads, 0, st>>>(src, dst, valid, n, proj, n_hyp, t2, refits, frames, scores, models,
                                              H_out, mask, info);
     ++nl;
     if (launches) *launches = nl;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rectify(const float* img, int H, int W, size_t pitch, const double* Hm, float fill, int out_h,
+                           int out_w, float* out, cudaStream_t st) {
+    dim3 blk(32, 8), grid((unsigned)((out_w + 31) / 32), (unsigned)((out_h + 7) / 8));
+    k_rectify<<<grid, blk, 0, st>>>(img, H, W, pitch, Hm, fill, out_h, out_w, out);
     return cudaGetLastError();
 }
 

@@ -562,6 +562,22 @@ sfoc_status sfoc_fast_blocks(sfoc_ctx* ctx, const float* d_image, int H, int W, 
     return SFOC_OK;
 }
 
+sfoc_status sfoc_rectify(sfoc_ctx* ctx, const float* d_image, int H, int W, size_t pitch_elems, const double* d_model,
+                         float fill, int out_h, int out_w, float* d_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!d_image || !d_model || !d_out) return fail(ctx, SFOC_ERR_INVALID_ARG, "null pointer");
+    if (H < 1 || W < 1 || out_h < 1 || out_w < 1 || pitch_elems < (size_t)W || out_h > 65535 * 8)
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "bad image shape");
+    DeviceGuard g(ctx->device);
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_OTHER, 1);
+        e = launch_rectify(d_image, H, W, pitch_elems, d_model, fill, out_h, out_w, d_out, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rectify launch");
+    return SFOC_OK;
+}
+
 sfoc_status fastncc_points_from_results(sfoc_ctx* ctx, const int32_t* d_points, const fastncc_result* d_results,
                                         int n, double* d_src, double* d_dst, uint8_t* d_valid) {
     if (!ctx) return SFOC_ERR_INVALID_ARG;
