@@ -30,6 +30,9 @@ struct sfoc_ctx {
     sfoc_cube* pair_sen = nullptr;
     void* stage = nullptr;
     size_t stage_bytes = 0;
+    // second stream for the sensed image's host copy (overlaps the reference cube)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_copied = nullptr;
     // per-stage timing
     bool timing = false;
     struct Ev {
@@ -397,6 +400,12 @@ sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx) {
         cudaEventDestroy(e.b);
     }
     for (auto e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
     delete ctx;
     return SFOC_OK;
 }
@@ -753,14 +762,34 @@ sfoc_status fastncc_register_pair_host(sfoc_ctx* ctx, const float* h_ref, int Hr
     float* d_sen = reinterpret_cast<float*>(b + b_ref);
     int32_t* d_pts = reinterpret_cast<int32_t*>(b + b_ref + b_sen);
     fastncc_result* d_out = reinterpret_cast<fastncc_result*>(b + b_ref + b_sen + b_pts);
-    cudaError_t e = cudaMemcpyAsync(d_ref, h_ref, sizeof(float) * (size_t)Hr * Wr, cudaMemcpyHostToDevice, ctx->stream);
+    cudaError_t e = cudaSuccess;
+    if (!ctx->copy_stream) {
+        e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+    }
+    // the reference image on the context stream, the sensed image and the
+    // points on the copy stream (after everything queued before this call):
+    // the sensed copy lands while the reference cube is built
+    e = cudaEventRecord(ctx->ev_start, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_start, 0);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_sen, h_sen, sizeof(float) * (size_t)Hs * Ws, cudaMemcpyHostToDevice, ctx->stream);
+        e = cudaMemcpyAsync(d_ref, h_ref, sizeof(float) * (size_t)Hr * Wr, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_sen, h_sen, sizeof(float) * (size_t)Hs * Ws, cudaMemcpyHostToDevice, ctx->copy_stream);
     if (e == cudaSuccess && n > 0)
-        e = cudaMemcpyAsync(d_pts, h_points, sizeof(int32_t) * 2 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
+        e = cudaMemcpyAsync(d_pts, h_points, sizeof(int32_t) * 2 * (size_t)n, cudaMemcpyHostToDevice,
+                            ctx->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied, ctx->copy_stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
-    sfoc_status s = fastncc_register_pair(ctx, d_ref, Hr, Wr, d_sen, Hs, Ws, d_pts, n, template_size, search_radius, p,
-                                          opts, d_out);
+    sfoc_status s = sfoc_build(ctx, d_ref, Hr, Wr, (size_t)Wr, nullptr, 0, 0, p, &ctx->pair_ref);
+    if (s != SFOC_OK) return s;
+    e = cudaStreamWaitEvent(ctx->stream, ctx->ev_copied, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamWaitEvent");
+    s = sfoc_build(ctx, d_sen, Hs, Ws, (size_t)Ws, nullptr, 0, 0, p, &ctx->pair_sen);
+    if (s == SFOC_OK)
+        s = fastncc_match(ctx, ctx->pair_ref, ctx->pair_sen, d_pts, n, template_size, search_radius, opts, d_out);
     if (s != SFOC_OK) return s;
     if (n > 0) {
         e = cudaMemcpyAsync(h_out, d_out, sizeof(fastncc_result) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
