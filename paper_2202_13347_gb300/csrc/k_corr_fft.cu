@@ -38,7 +38,9 @@ struct FftShape {
     static constexpr int G = L / 2;                     // groups of 8 threads
     static constexpr int T = 8 * G;                     // threads
     static constexpr int ZP = L + 2;                    // row pitch of the L x L array (float2)
-    static constexpr int SG = E * kScP + 8;             // scratch per group (float2); consecutive groups 64 B apart mod 128
+    // scratch per group (float2): 8 rows per array, both arrays of the dual
+    // transform (16 rows), or E rows of one; consecutive groups 64 B apart mod 128
+    static constexpr int SG = (E < 16 ? 16 : E) * kScP + 8;
     static constexpr size_t smem = sizeof(float2) * ((size_t)L * ZP + (size_t)G * SG + 8 * E + L);
 };
 
@@ -141,6 +143,46 @@ __device__ __forceinline__ void group_fft(float2 (&v)[E], int t, float2* sc, con
     }
 }
 
+// The second half of group_fft: after the twiddles, the 8 x 8 transposes
+// through the group's scratch and the 8-point DFTs over t.
+template <int E, int SIGN>
+__device__ __forceinline__ void group_fft_tail(float2 (&v)[E], int t, float2* sc) {
+#pragma unroll
+    for (int k1 = 0; k1 < E; ++k1) sc[k1 * kScP + t] = v[k1];
+    __syncwarp();
+    float2 w8[E / 8][8];
+#pragma unroll
+    for (int a = 0; a < E / 8; ++a)
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt) w8[a][tt] = sc[(t + 8 * a) * kScP + tt];
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < E / 8; ++a) {
+        dft<8, SIGN>(w8[a]);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) v[a + (E / 8) * k2] = w8[a][k2];
+    }
+}
+
+// Two independent length-L transforms by one group (the column pair): the
+// E-point DFTs interleave and each twiddle feeds both; the transposes run
+// one array after the other (every input of an array is in the scratch
+// before any of its outputs is written back).
+template <int E, int SIGN>
+__device__ __forceinline__ void group_fft2(float2 (&va)[E], float2 (&vb)[E], int t, float2* sc, const float2* tw) {
+    dft<E, SIGN>(va);
+    dft<E, SIGN>(vb);
+#pragma unroll
+    for (int k1 = 1; k1 < E; ++k1) {
+        float2 w = tw[8 * k1 + t];
+        if (SIGN > 0) w.y = -w.y;
+        va[k1] = cmul(va[k1], w);
+        vb[k1] = cmul(vb[k1], w);
+    }
+    group_fft_tail<E, SIGN>(va, t, sc);
+    group_fft_tail<E, SIGN>(vb, t, sc);
+}
+
 // X conj(Y) from a = Z[k] and b = conj(Z[-k]) of z = x + i y
 __device__ __forceinline__ float2 cross_spectrum(float2 a, float2 b) {
     const float2 s = cadd(a, b), d = csub(a, b);
@@ -223,8 +265,7 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
                     a[j] = Z[(size_t)(t + 8 * j) * ZP + c1];
                     b[j] = Z[(size_t)(t + 8 * j) * ZP + c2];
                 }
-                group_fft<E, -1>(a, t, sc, tw);
-                group_fft<E, -1>(b, t, sc, tw);
+                group_fft2<E, -1>(a, b, t, sc, tw);
                 // Z[-k] of column c1 lives in column c2 (in column c1 itself for
                 // pair 0).  Row -(t + 8j) is held by thread (8 - t) mod 8 at index
                 // E - 1 - j; for t = 0 by the thread itself at index (E - j) mod E.
