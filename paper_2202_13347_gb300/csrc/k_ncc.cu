@@ -49,28 +49,12 @@ __global__ void __launch_bounds__(kStatThreads)
                     ty0 + m + R <= Hr && tx0 + m + R <= Wr;
     u64 a1 = 0, a2 = 0;  // modulo 2^64, like the integral images
     if (ok) {
-        // four rows per warp per step: independent loads in flight
-        for (int r0 = warp; r0 < m; r0 += 4 * (kStatThreads / 32)) {
-            float v1[4][4], v2[4][4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = r0 + q * (kStatThreads / 32);
-                const size_t row = (size_t)(ty0 + (r < m ? r : 0)) * pitch + tx0;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const int c = lane + 32 * cc;
-                    const bool in = r < m && c < m;
-                    v1[q][cc] = in ? s1[row + c] : 0.f;
-                    v2[q][cc] = in ? s2[row + c] : 0.f;
-                }
+        for (int r = warp; r < m; r += kStatThreads / 32) {
+            const size_t row = (size_t)(ty0 + r) * pitch + tx0;
+            for (int c = lane; c < m; c += 32) {
+                a1 += int_quant(s1[row + c]);
+                a2 += int_quant(s2[row + c]);
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    a1 += int_quant(v1[q][cc]);
-                    a2 += int_quant(v2[q][cc]);
-                }
         }
     }
 #pragma unroll
