@@ -149,7 +149,7 @@ __device__ __forceinline__ float codd(const float* x, const float* t) {
 }
 
 template <typename T, int KA, int KB, int KC, int KS>
-__global__ void __launch_bounds__(kThreads) k_sfoc_steer_ct(const T* __restrict__ img, int H, int W, size_t pitch,
+__global__ void __launch_bounds__(kThreads, 3) k_sfoc_steer_ct(const T* __restrict__ img, int H, int W, size_t pitch,
                                                              float* __restrict__ F, size_t fpitch, size_t fplane,
                                                              SteerTaps tp) {
     constexpr int HAL = KS > KA ? (KS > KB ? (KS > KC ? KS : KC) : (KB > KC ? KB : KC))
