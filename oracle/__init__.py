@@ -84,7 +84,10 @@ class Cube(C.Structure):
 
 def params(scales=(0.6, 0.8, 1.0), sigma2=1.5, n_orient=6, dil=(1, 2, 3), sigma_d1=1.0,
            sigma_d2=1.5, eps=1e-3, rectify=True, radius_mult=3.0, first_order_only=False) -> Params:
-    """Paper defaults: Table 2 STDs, 6 orientations and rates {1,2,3} (Sec. 2.1)."""
+    """Paper defaults: Table 2 STDs, 6 orientations and rates {1,2,3} (Sec. 2.1).
+    Variants: first_order_only (F-SFOC, Sec. 4.2); dil=(1,) (a plain
+    Gaussian, Fig. 3 (e)); sigma_d1 / sigma_d2 = 0 (that group unsmoothed,
+    Fig. 3 (d))."""
     p = Params()
     p.n_scales = len(scales)
     for i, s in enumerate(scales):

@@ -23,6 +23,8 @@
  *   |.| of every steered response, summed over scales per orientation;
  *   dilated Gaussian smoothing with sigma_d = 1.0 (first group) and 1.5
  *   (second group), radius ceil(3 sigma_d), rates {1,2,3}, results summed;
+ *   sigma_d = 0 switches a group's smoothing off (D = F, the descriptor
+ *   "without Gaussian convolution" that Sec. 2.1 compares in Fig. 3);
  *   per-pixel L2 normalisation of each group, v / (||v|| + eps);
  *   clamp-to-edge borders for every convolution;
  *   a window (template) is flat when its variance is <= 1e-6 * mnz: NCC := 0
@@ -213,6 +215,7 @@ int oracle_sfoc_roi(const float* image, int H, int W, const oracle_params* p,
     if (y0 < 0 || x0 < 0 || y0 + h > H || x0 + w > W) return OR_ERR_ROI;
     if (p->n_scales < 1 || p->n_scales > 8 || p->n_orient < 1 || p->n_orient > 8) return OR_ERR_ARG;
     if (p->n_dil < 1 || p->n_dil > 4) return OR_ERR_ARG;
+    if (!(p->sigma_d1 >= 0.0) || !(p->sigma_d2 >= 0.0)) return OR_ERR_ARG;
     const int no = p->n_orient;
     const int z = oracle_channels(p);
     const int ns = p->n_scales;
@@ -242,6 +245,11 @@ int oracle_sfoc_roi(const float* image, int H, int W, const oracle_params* p,
     int reach = 0;
     for (int g = 0; g < 2; ++g)
         for (int r = 0; r < p->n_dil; ++r) {
+            if (sd[g] == 0.0) { /* no smoothing: no kernel */
+                wK[g][r] = 0;
+                wd[g][r] = NULL;
+                continue;
+            }
             int rate = p->dil[r];
             wK[g][r] = rate * Kd[g];
             int n = 2 * wK[g][r] + 1;
@@ -305,6 +313,10 @@ int oracle_sfoc_roi(const float* image, int H, int W, const oracle_params* p,
             for (int c = 0; c < z; ++c) {
                 int g = c < no ? 0 : 1;
                 const double* Fc = F + (size_t)c * eh * ew;
+                if (sd[g] == 0.0) { /* smoothing off: the steered channel itself */
+                    D[c] = Fc[(size_t)(y - ey0) * ew + (x - ex0)];
+                    continue;
+                }
                 double acc = 0.0;
                 for (int r = 0; r < p->n_dil; ++r) {
                     int K = wK[g][r], n = 2 * K + 1;

@@ -302,6 +302,72 @@ def test_first_order_only_variant(orc):
     np.testing.assert_allclose(c, full[:6], atol=0)
 
 
+
+def _pre_norm(orc, img, **kw):
+    """The input D of the group normalisation: with eps = 1e30 the division
+    by ||D|| + eps is an exact division by 1e30 (||D|| is far below the
+    spacing of doubles near 1e30), so the cube times 1e30 returns D to
+    within two roundings."""
+    return orc.sfoc_roi(img, orc.params(eps=1e30, **kw)).data * 1e30
+
+
+def _dilated_smooth(F, sd, rates):
+    """Parallel dilated Gaussian of Sec. 2.1 through scipy: taps
+    exp(-t^2 / 2 sd^2) / sum over |t| <= ceil(3 sd), spread to spacing r,
+    applied separably with edge replication, summed over r."""
+    from scipy.ndimage import correlate1d
+    K = math.ceil(3 * sd - 1e-9)
+    t = np.arange(-K, K + 1)
+    g = np.exp(-t * t / (2 * sd * sd))
+    g /= g.sum()
+    out = np.zeros_like(F)
+    for r in rates:
+        w = np.zeros(2 * r * K + 1)
+        w[::r] = g
+        out += correlate1d(correlate1d(F, w, axis=0, mode="nearest"), w, axis=1, mode="nearest")
+    return out
+
+
+def test_no_smoothing_variant_feeds_the_smoothing(orc):
+    """sigma_d = 0 switches the smoothing off (the descriptor without
+    Gaussian convolution of Fig. 3 (d), Sec. 2.1): its pre-normalisation
+    planes are the steered channels F, and scipy's Gaussian filters of those
+    planes reproduce the paper's parallel dilated smoothing (Fig. 3 (f)) and
+    the plain Gaussian of Fig. 3 (e) (one rate, r = 1).  A wrong offset or
+    channel in the unsmoothed branch, or a wrong rate, STD or border in the
+    smoothed one, breaks the agreement."""
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.default_rng(21)
+    from workloads import optical_like
+    img = optical_like(rng, 48, 61)
+    F = _pre_norm(orc, img, sigma_d1=0.0, sigma_d2=0.0)
+    assert F.shape == (12, 48, 61) and np.abs(F).max() > 1e-2
+    D = _pre_norm(orc, img)
+    Dg = _pre_norm(orc, img, dil=(1,))
+    for c in range(12):
+        sd = 1.0 if c < 6 else 1.5      # group STDs of the defaults
+        scale = np.abs(D[c]).max()
+        np.testing.assert_allclose(D[c], _dilated_smooth(F[c], sd, (1, 2, 3)), atol=1e-13 * scale + 1e-300)
+        np.testing.assert_allclose(Dg[c], gaussian_filter(F[c], sd, mode="nearest", truncate=3.0),
+                                   atol=1e-13 * scale + 1e-300)
+    # one group smoothed, the other not
+    Dm = _pre_norm(orc, img, sigma_d1=0.0)
+    np.testing.assert_allclose(Dm[:6], F[:6], atol=0)
+    np.testing.assert_allclose(Dm[6:], D[6:], atol=0)
+
+
+def test_no_smoothing_is_the_narrow_gaussian_limit(orc):
+    """As sigma_d shrinks the taps off the centre vanish (exp(-200) at
+    sigma_d = 0.05); with eps = 0 the sum over three rates only scales the
+    group, which the normalisation removes, so sigma_d = 0 is the limit."""
+    rng = np.random.default_rng(22)
+    img = rng.random((30, 37)).astype(np.float32)
+    c0 = orc.sfoc_roi(img, orc.params(eps=0.0, sigma_d1=0.0, sigma_d2=0.0)).data
+    c1 = orc.sfoc_roi(img, orc.params(eps=0.0, sigma_d1=0.05, sigma_d2=0.05)).data
+    np.testing.assert_allclose(c0, c1, atol=1e-13)
+    with pytest.raises(RuntimeError):
+        orc.sfoc_roi(img, orc.params(sigma_d1=-1.0))
+
 # --------------------------------------------------------------------------
 # NCC (Eq. 8), its rewrite (Eq. 9, 13-16), argmax and sub-pixel
 # --------------------------------------------------------------------------
