@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--forms", default="bf16,f32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--noise-sweep", action="store_true",
+                    help="instead of the benchmark: CMR of the descriptor variants under the noise series of Sec. 4.3")
     return ap.parse_args()
 
 
@@ -340,8 +342,73 @@ def fft_flops(pair, z=12):
     return z * ((pair.m + 2 * pair.R + L) * t + 12.0 * L * (L // 2 + 1)) + (L // 2 + 1 + P1) * t
 
 
+# Descriptor variants compared under noise: the paper's SFOC, F-SFOC (first
+# order only, Sec. 4.2) and the two weaker smoothings of Fig. 3 (Sec. 2.1).
+NOISE_VARIANTS = {
+    "SFOC": {},
+    "F-SFOC": {"first_order_only": True},
+    "SFOC plain Gaussian": {"dil": (1,)},
+    "SFOC unsmoothed": {"sigma_d1": 0.0, "sigma_d2": 0.0},
+}
+# Sec. 4.3: variances 0..0.01 step 0.001 (Gaussian) and 0..0.1 step 0.01 (speckle)
+NOISE_LEVELS = {"gaussian": [round(0.001 * i, 3) for i in range(11)],
+                "speckle": [round(0.01 * i, 2) for i in range(11)]}
+
+
+def noise_sweep(args):
+    """Noise sensitivity (Sec. 4.3) on the GPU path: the average CMR of each
+    descriptor variant over four seeded pairs as noise of growing variance is
+    added to the sensed image.  Pairs stand in for the paper's
+    optical-to-infrared cases: 1024^2 optical-like reference, sensed image an
+    inverting piecewise-linear map of the reference shifted by an integer s in
+    [-8, 8]^2; 196 block-gradient points picked on the clean sensed image;
+    template 80 x 80 (the paper's), search radius 10.  A match is correct
+    within 1.5 px of -s (Sec. 4.1); CMR = correct / matched.  The noise of a
+    (pair, kind, level) is drawn once and shared by all variants."""
+    import numpy as np
+    import torch
+    from workloads import add_noise, config1
+    import paper_2202_13347_gb300 as pkg
+    pkg.build()
+    b = pkg.load()
+    torch.cuda.set_device(0)
+    ctx = b.Context(torch.cuda.current_device())
+    seeds = (4301, 4302, 4303, 4304)
+    cmr = {v: {k: np.zeros(len(L)) for k, L in NOISE_LEVELS.items()} for v in NOISE_VARIANTS}
+    n_points = 0
+    t0 = time.perf_counter()
+    for seed in seeds:
+        pair = config1(seed=seed, H=1024, W=1024, n_side=14, m=80, R=10)
+        n_points += len(pair.points)
+        d_ref = torch.from_numpy(pair.ref).cuda()
+        d_pts = torch.from_numpy(pair.points).cuda()
+        prm = {v: b.params(**kw) for v, kw in NOISE_VARIANTS.items()}
+        ref_cubes = {v: ctx.sfoc_build(d_ref, p=prm[v]) for v in NOISE_VARIANTS}
+        for kind, levels in NOISE_LEVELS.items():
+            for li, var in enumerate(levels):
+                rng = np.random.default_rng([seed, 0 if kind == "gaussian" else 1, li])
+                d_sen = torch.from_numpy(add_noise(rng, pair.sen, kind, var)).cuda()
+                for v in NOISE_VARIANTS:
+                    sen_cube = ctx.sfoc_build(d_sen, p=prm[v])
+                    raw = ctx.fastncc_match(ref_cubes[v], sen_cube, d_pts, pair.m, pair.R)["raw"].cpu().numpy()
+                    ok = raw[:, 5] == 0
+                    off = np.stack([raw[:, 3].view(np.float32), raw[:, 4].view(np.float32)], 1).astype(np.float64)
+                    correct = ok & (np.linalg.norm(off - pair.truth, axis=1) <= 1.5)
+                    cmr[v][kind][li] += correct.sum() / max(1, int(ok.sum())) / len(seeds)
+                    del sen_cube
+        del ref_cubes
+    line = {"experiment": "noise sensitivity (Sec. 4.3)", "metric": "average CMR", "pairs": len(seeds),
+            "points": n_points, "template": 80, "search_radius": 10, "tolerance_px": 1.5,
+            "noise_on": "sensed image", "levels": NOISE_LEVELS,
+            "cmr": {v: {k: [round(float(x), 4) for x in a] for k, a in d.items()} for v, d in cmr.items()},
+            "data": "synthetic", "seconds": round(time.perf_counter() - t0, 1)}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
+    if args.noise_sweep:
+        return noise_sweep(args)
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

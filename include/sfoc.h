@@ -83,6 +83,10 @@ typedef enum {
  *   response); radius_mult = 3 (kernel radius ceil(3 sigma));
  *   first_order_only = 0 (1 gives the F-SFOC variant of Sec. 4.2);
  *   cube_dtype = SFOC_DTYPE_F32.
+ * The smoothing variants that Sec. 2.1 compares in Fig. 3: n_dil = 1 with
+ * dil = {1} smooths with a plain Gaussian; sigma_d1 or sigma_d2 = 0 leaves
+ * that group unsmoothed (the steered channels go straight to the group
+ * normalisation).  Negative STDs are SFOC_ERR_INVALID_ARG.
  * Limits: n_scales 1..4, each radius <= 9; sigma2 radius <= 9; n_orient 1..8;
  * n_dil 1..3 with rates 1..3; smoothing radii <= 6; cube_dtype BF16 needs
  * n_orient == 6 and first_order_only == 0 (12 channels).

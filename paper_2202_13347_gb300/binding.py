@@ -122,6 +122,10 @@ def lib():
 
 def params(scales=(0.6, 0.8, 1.0), sigma2=1.5, n_orient=6, dil=(1, 2, 3), sigma_d1=1.0, sigma_d2=1.5,
            eps=1e-3, rectify=True, radius_mult=3.0, first_order_only=False, dtype=DTYPE_F32) -> Params:
+    """Descriptor parameters; the defaults are the paper's (Sec. 2.1, Table 2).
+    Variants: first_order_only (F-SFOC, Sec. 4.2); dil=(1,) (a plain
+    Gaussian, Fig. 3 (e)); sigma_d1 / sigma_d2 = 0 (that group unsmoothed,
+    Fig. 3 (d))."""
     p = Params()
     lib().sfoc_params_default(C.byref(p))
     p.n_scales = len(scales)

@@ -276,6 +276,7 @@ __device__ __forceinline__ void smooth_channel(const float* __restrict__ Fk, siz
                                                int y0, int hal, int n_dil, const int* s_dil, const float* t,
                                                float* s_F, int FW, float* s_h, int HR, float (&Dk)[kSRows]) {
     const int IW = kSTW + 2 * hal, IH = kSTH + 2 * hal;
+    const int nd = KD > 0 ? n_dil : 1;  // radius 0: the group is unsmoothed, D = F (no sum over rates)
     __syncthreads();  // previous channel done with s_F / s_h
     // load: 8 threads per row, 8 consecutive columns each
     for (int rr = threadIdx.x >> 3; rr < IH; rr += kThreads >> 3) {
@@ -293,7 +294,7 @@ __device__ __forceinline__ void smooth_channel(const float* __restrict__ Fk, siz
     for (int task = threadIdx.x; task < IH * 4; task += kThreads) {
         const int rr = task >> 2, cb = (task & 3) * 8;
         const float* x = s_F + rr * FW + cb;  // x[c + hal] is column cb + c
-        for (int ri = 0; ri < n_dil; ++ri) {
+        for (int ri = 0; ri < nd; ++ri) {
             const int rate = s_dil[ri];
             float o[8];
 #pragma unroll
@@ -314,7 +315,7 @@ __device__ __forceinline__ void smooth_channel(const float* __restrict__ Fk, siz
     const int col = threadIdx.x & 31, rb = (threadIdx.x >> 5) * kSRows;
 #pragma unroll
     for (int j = 0; j < kSRows; ++j) Dk[j] = 0.f;
-    for (int ri = 0; ri < n_dil; ++ri) {
+    for (int ri = 0; ri < nd; ++ri) {
         const int rate = s_dil[ri];
         const float* x = s_h + (ri * HR + rb + hal) * kSTW + col;  // x[j * kSTW] is output row rb + j
 #pragma unroll
@@ -506,6 +507,7 @@ __device__ __forceinline__ void smooth_group(int g, const float* __restrict__ F,
         {
             const int hal = tp.halo[g], Kd = tp.Kd[g];
             switch (Kd) {
+                case 0: smooth_channel<0>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
                 case 1: smooth_channel<1>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
                 case 2: smooth_channel<2>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;
                 case 3: smooth_channel<3>(Fk, fpitch, H, W, x0, y0, hal, tp.n_dil, s_dil, t, s_F, FW, s_h, HR, D[k]); break;

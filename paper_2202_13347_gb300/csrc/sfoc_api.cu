@@ -155,7 +155,7 @@ sfoc_status check_params(sfoc_ctx* ctx, const sfoc_params& p) {
         if (p.dil[r] < 1 || p.dil[r] > 3) return fail(ctx, SFOC_ERR_UNSUPPORTED, "dilation rates must be 1..3");
     double sd[2] = {p.sigma_d1, p.sigma_d2};
     for (int g = 0; g < 2; ++g) {
-        if (!(sd[g] > 0.0)) return fail(ctx, SFOC_ERR_INVALID_ARG, "smoothing STDs must be > 0");
+        if (!(sd[g] >= 0.0)) return fail(ctx, SFOC_ERR_INVALID_ARG, "smoothing STDs must be >= 0 (0: unsmoothed)");
         if (radius_of(sd[g], p.radius_mult) > kMaxSmoothRadius)
             return fail(ctx, SFOC_ERR_UNSUPPORTED, "smoothing radius > 6");
     }
@@ -223,6 +223,12 @@ SmoothTaps make_smooth(const sfoc_params& p) {
     }
     double sd[2] = {p.sigma_d1, p.sigma_d2};
     for (int g = 0; g < 2; ++g) {
+        if (sd[g] == 0.0) {  // smoothing off for this group (Fig. 3 (d)): one unit tap, no rate sum
+            t.Kd[g] = 0;
+            t.g[g][0] = 1.f;
+            t.halo[g] = 0;
+            continue;
+        }
         int K = radius_of(sd[g], p.radius_mult);
         t.Kd[g] = K;
         double w[kMaxSmoothRadius + 1], sum = 0.0;

@@ -69,6 +69,44 @@ def test_cube_variants_match_oracle(b, ctx, orc):
         assert np.abs(got - want).max() <= CUBE_ATOL, kw
 
 
+def _group_norm_tol(orc, img, kw):
+    """Per-value bound for a cube whose groups may be unsmoothed: the FP32
+    error of a pre-normalisation value (at most 1e-6 here) is divided by
+    ||D|| + eps in the group normalisation, so a group with a small norm
+    gets 1e-6 / (||D|| + eps) on top of CUBE_ATOL.  D is the oracle's
+    pre-normalisation input (eps = 1e30 makes the normalisation an exact
+    division by 1e30)."""
+    p = orc.params(eps=1e30, **kw)
+    D = orc.sfoc_roi(img, p).data * 1e30
+    no = 6
+    nrm = np.concatenate([np.repeat(np.linalg.norm(D[g * no:(g + 1) * no], axis=0)[None], no, 0)
+                          for g in range(D.shape[0] // no)])
+    return CUBE_ATOL + 1e-6 / (nrm + 1e-3)
+
+
+SMOOTHING_VARIANTS = [dict(sigma_d1=0.0, sigma_d2=0.0), dict(sigma_d1=0.0), dict(dil=(1,)),
+                      dict(dil=(2,), sigma_d2=0.0)]
+
+
+@pytest.mark.parametrize("kw", SMOOTHING_VARIANTS, ids=["unsmoothed", "first_unsmoothed", "plain_gauss",
+                                                        "rate2_second_unsmoothed"])
+def test_cube_smoothing_variants_match_oracle(b, ctx, orc, kw):
+    """The smoothing variants of Fig. 3 (Sec. 2.1): unsmoothed groups
+    (sigma_d = 0), a plain Gaussian (one rate, r = 1), a single other rate."""
+    rng = np.random.default_rng(4)
+    img = rng.random((45, 70)).astype(np.float32)
+    got = ctx.sfoc_build(dev(img), p=b.params(**kw)).export().cpu().numpy().astype(np.float64)
+    want = orc.sfoc_roi(img, orc.params(**kw)).data
+    tol = _group_norm_tol(orc, img, kw)
+    err = np.abs(got - want)
+    assert np.all(err <= tol), "max err %g (tol there %g)" % (err.max(), tol.flat[err.argmax()])
+
+
+def test_negative_smoothing_std_is_rejected(b, ctx):
+    img = np.zeros((40, 40), np.float32)
+    with pytest.raises(b.SfocError):
+        ctx.sfoc_build(dev(img), p=b.params(sigma_d2=-1.0))
+
 def test_integral_planes(b, ctx, orc):
     """Eq. 14: exclusive prefix of the channel sums.  The library keeps exact
     64-bit sums of each pixel's value rounded to a multiple of 2^-28, so an
@@ -139,6 +177,21 @@ def test_match_small_cases(b, ctx, orc, H, W, m, R, npts, seed, path):
     g = gpu_match(ctx, b, pair, corr=f32_path(b, path), want_maps=True)
     compare(g, o, R, oracle_maps=o["maps"])
 
+
+@pytest.mark.parametrize("kw", [dict(first_order_only=True), dict(sigma_d1=0.0, sigma_d2=0.0), dict(dil=(1,))],
+                         ids=["f_sfoc", "unsmoothed", "plain_gauss"])
+@pytest.mark.parametrize("path", F32_PATHS)
+def test_match_descriptor_variants(b, ctx, orc, kw, path):
+    """Matching on the variant cubes (F-SFOC's 6 channels, Sec. 4.2; the
+    smoothings of Fig. 3).  An unsmoothed cube's larger error at small-norm
+    pixels (up to about 1e-4) moves NCC by |dS| / |S - mean S| ~ 1e-5 over
+    a 21 x 21 x z window, inside the 1e-4 target."""
+    pair = tiny_pair(31, 120, 130, 21, 8, 12, shift=(3, -2))
+    o = orc.match_pair(pair.ref, pair.sen, pair.points, pair.m, pair.R, p=orc.params(**kw), want_maps=True,
+                       roi=False)
+    g = gpu_match(ctx, b, pair, p=b.params(**kw), corr=f32_path(b, path), want_maps=True)
+    st = compare(g, o, pair.R, oracle_maps=o["maps"])
+    assert st["valid"] >= 8
 
 @pytest.mark.parametrize("path", F32_PATHS)
 def test_status_cases(b, ctx, orc, path):

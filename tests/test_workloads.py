@@ -25,3 +25,19 @@ def test_tiny_pair_and_half():
     assert p.ref.shape == (70, 83)
     assert len(p.points) <= 12
     assert template_half(9) == 4 and template_half(10) == 5
+
+
+def test_noise_series_statistics():
+    """Sec. 4.3 noise: Gaussian of variance v, speckle n * I with n of
+    variance v; v = 0 is the identity.  Checked on a mid-grey image so that
+    clipping to [0, 1] stays negligible."""
+    from workloads import add_noise
+    img = np.full((400, 500), 0.5, np.float32)
+    rng = np.random.default_rng(0)
+    assert np.array_equal(add_noise(rng, img, "gaussian", 0.0), img)
+    g = add_noise(rng, img, "gaussian", 0.004) - img
+    assert abs(g.mean()) < 1e-3 and abs(g.var() - 0.004) < 2e-4
+    sp = add_noise(rng, img, "speckle", 0.04) / img - 1.0
+    assert abs(sp.mean()) < 2e-3 and abs(sp.var() - 0.04) < 2e-3
+    assert np.abs(sp).max() <= np.sqrt(3 * 0.04) + 1e-6
+    assert add_noise(rng, np.ones((50, 50), np.float32), "gaussian", 0.01).max() <= 1.0

@@ -202,6 +202,25 @@ def radiometric(rng, img, kind):
     raise ValueError(kind)
 
 
+def add_noise(rng, img, kind, v):
+    """The noise series of Sec. 4.3 on a [0, 1] image: 'gaussian' adds white
+    noise of mean 0 and variance v; 'speckle' adds n * I with n uniform of
+    mean 0 and variance v (half-width sqrt(3 v)).  The result is clipped to
+    [0, 1]; v = 0 returns the image unchanged."""
+    img = np.asarray(img, np.float32)
+    if v == 0:
+        return img.copy()
+    if kind == "gaussian":
+        n = rng.normal(0.0, math.sqrt(v), img.shape).astype(np.float32)
+        out = img + n
+    elif kind == "speckle":
+        a = math.sqrt(3.0 * v)
+        n = rng.uniform(-a, a, img.shape).astype(np.float32)
+        out = img + n * img
+    else:
+        raise ValueError(kind)
+    return np.clip(out, 0.0, 1.0).astype(np.float32)
+
 # --------------------------------------------------------------------------
 # interest points (harness, not the method)
 # --------------------------------------------------------------------------
