@@ -8,8 +8,8 @@
  * (the CUDA library under paper_2202_13347_gb300/) never calls it, and the
  * two share no code, headers or constants.
  *
- * The paper names the operator and the partitioning only.  Readings (each
- * listed in the design doc):
+ * The paper names the operator and the partitioning only.  The readings
+ * taken where it is silent:
  *   segment test (FAST-9): the 16 pixels of the radius-3 Bresenham circle
  *   around p; p is a corner when 9 contiguous circle pixels are all brighter
  *   than I(p) + t or all darker than I(p) - t;

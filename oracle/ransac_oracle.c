@@ -9,8 +9,8 @@
  * (the CUDA library under paper_2202_13347_gb300/) never calls it, and the
  * two share no code, headers or constants.
  *
- * The paper names the method and the model only.  Readings (each listed in
- * the design doc):
+ * The paper names the method and the model only.  The readings taken where
+ * it is silent:
  *   model: x' = (h0 x + h1 y + h2) / (h6 x + h7 y + 1),
  *          y' = (h3 x + h4 y + h5) / (h6 x + h7 y + 1)   (projective, 8 dof);
  *          affine: h6 = h7 = 0 (6 dof);

@@ -15,7 +15,7 @@
  * means, all in double precision.  OpenMP only splits independent pixels or
  * points across threads; it never changes an operation's order.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   sigma is a standard deviation (Sec. 2.1 text after Eq. 1 vs Eq. 6 text);
  *   kernel radius K = ceil(3 sigma), taps sampled at integer offsets;
  *   the second-order x (y) kernel is made zero-sum along its derivative axis;
