@@ -41,9 +41,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop 
 FFT_SIZES = (64, 128)  # transform sides of the Fourier correlation (the smallest with m + 2R <= L)
 # DRAM bytes (read + write) per launch of each form's correlation kernel on
 # the 2048x2048 workload, from one ncu capture of the kernel as it stands
-# (profiles/k_corr_tc_col_c2_2048.md, profiles/k_corr_fft_c2_2048.md); to be
+# (profiles/k_corr_tc_col_sar2048.md, profiles/k_corr_fft_sar2048.md); to be
 # retaken whenever the kernel changes.
-CORR_TRAFFIC_C2 = {"bf16": 270.0e6, "f32": 407.75e6}
+CORR_TRAFFIC_SAR2048 = {"bf16": 270.0e6, "f32": 407.75e6}
 
 
 def parse():
@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2"])
+    ap.add_argument("--workload", default="sar2048", choices=["inverting512", "sar2048"])
     ap.add_argument("--forms", default="bf16,f32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -73,13 +73,13 @@ def peaks():
 
 
 def workload(name, rank):
-    from workloads import config1, config2
-    if name == "c1":
-        p = config1(seed=1000 + 7919 * rank)
-        desc = "c1: 512x512 pair, piecewise inverting map, 100 block-max points, m=41, R=10, z=12"
+    from workloads import inverting_pair_512, sar_pair_2048
+    if name == "inverting512":
+        p = inverting_pair_512(seed=1000 + 7919 * rank)
+        desc = "512x512 pair, piecewise inverting map, 100 block-max points, m=41, R=10, z=12"
     else:
-        p = config2(seed=2000 + 7919 * rank)
-        desc = ("c2: 2048x2048 optical-like ref vs SAR-like sensed (Gamma L=4 speckle, 256-px shift field), "
+        p = sar_pair_2048(seed=2000 + 7919 * rank)
+        desc = ("2048x2048 optical-like ref vs SAR-like sensed (Gamma L=4 speckle, 256-px shift field), "
                 "1000 block-Harris points, m=81, R=20, z=12")
     return p, desc
 
@@ -367,7 +367,7 @@ def noise_sweep(args):
     (pair, kind, level) is drawn once and shared by all variants."""
     import numpy as np
     import torch
-    from workloads import add_noise, config1
+    from workloads import add_noise, inverting_pair_512
     import paper_2202_13347_gb300 as pkg
     pkg.build()
     b = pkg.load()
@@ -378,7 +378,7 @@ def noise_sweep(args):
     n_points = 0
     t0 = time.perf_counter()
     for seed in seeds:
-        pair = config1(seed=seed, H=1024, W=1024, n_side=14, m=80, R=10)
+        pair = inverting_pair_512(seed=seed, H=1024, W=1024, n_side=14, m=80, R=10)
         n_points += len(pair.points)
         d_ref = torch.from_numpy(pair.ref).cuda()
         d_pts = torch.from_numpy(pair.points).cuda()
@@ -422,7 +422,7 @@ def main():
         if torch.cuda.is_available():
             torch.cuda.set_device(0)
 
-    pair, desc = workload(args.config, rank)
+    pair, desc = workload(args.workload, rank)
     config = {"workload": desc, "H": int(pair.ref.shape[0]), "W": int(pair.ref.shape[1]),
               "points_per_pair": int(len(pair.points)), "m": pair.m, "R": pair.R, "z": 12,
               "pairs_per_rank": 1, "l2": "flushed between timed steps (256 MB write)"}
@@ -496,7 +496,7 @@ def main():
         flops = corr_flops(pair) * r["valid"]          # processed points only
         per_launch = corr_ms / max(1, corr_n)
         ach = flops / (per_launch * 1e-3) / 1e12
-        traffic = CORR_TRAFFIC_C2.get(form) if args.config == "c2" else None
+        traffic = CORR_TRAFFIC_SAR2048.get(form) if args.workload == "sar2048" else None
         if form == "bf16":
             roof = {"bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
                     "frac": ach / pk["bf16"], "traffic": traffic,

@@ -1,10 +1,10 @@
-"""The batched workload (c4) and the 10000^2 workload (c5) against the oracle.
+"""The mixed batch of pairs and the 10000^2 pair against the oracle.
 
-c4: pairs of different sizes, radiometric maps, m in {41, 61, 81, 101} and
+Mixed batch: pairs of different sizes, radiometric maps, m in {41, 61, 81, 101} and
 R in [10, 40], built and matched through the batched entry points
 (sfoc_build_batch, fastncc_match_batch), F32 and BF16 forms; the oracle
 checks a seeded sample of points per pair.
-c5: the 10000^2 pair at full size, the 16-bit reference read through
+10000^2 pair: at full size, the 16-bit reference read through
 sfoc_build_u16; 10000 points, m = 101, R = 40 (the BF16 form takes the
 Toeplitz tensor-core kernel since m + 2R > 128); the oracle checks a seeded
 sample of points.  Tolerances as in the other parity tests.
@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from workloads import config4, config5  # noqa: E402
+from workloads import mixed_batch, speckle_pair_10000  # noqa: E402
 
 from parity import bf16_check, bf16_oracle_side, compare  # noqa: E402
 
@@ -46,18 +46,18 @@ def sample(pair, k, seed):
 
 
 @pytest.fixture(scope="module")
-def c4():
+def batch():
     # 16 of the 64 pairs at a quarter of the side lengths and point counts
-    return config4(n_pairs=16, scale=0.25)
+    return mixed_batch(n_pairs=16, scale=0.25)
 
 
-def test_config4_batched_f32(b, ctx, orc, c4):
-    refs = ctx.sfoc_build_batch([dev(p.ref) for p in c4])
-    sens = ctx.sfoc_build_batch([dev(p.sen) for p in c4])
-    outs = ctx.fastncc_match_batch(refs, sens, [dev(p.points) for p in c4], [p.m for p in c4], [p.R for p in c4],
+def test_mixed_batch_f32(b, ctx, orc, batch):
+    refs = ctx.sfoc_build_batch([dev(p.ref) for p in batch])
+    sens = ctx.sfoc_build_batch([dev(p.sen) for p in batch])
+    outs = ctx.fastncc_match_batch(refs, sens, [dev(p.points) for p in batch], [p.m for p in batch], [p.R for p in batch],
                                    corr_path=b.CORR_DIRECT_F32)
     ctx.sync()
-    for k, pair in enumerate(c4):
+    for k, pair in enumerate(batch):
         g = b.results(outs[k])
         idx, sub = sample(pair, 3, 400 + k)
         o = orc.match_pair(sub.ref, sub.sen, sub.points, sub.m, sub.R, want_maps=True)
@@ -65,14 +65,14 @@ def test_config4_batched_f32(b, ctx, orc, c4):
         compare(gi, o, pair.R, oracle_maps=o["maps"])
 
 
-def test_config4_batched_bf16(b, ctx, orc, c4):
+def test_mixed_batch_bf16(b, ctx, orc, batch):
     p = b.params(dtype=b.DTYPE_BF16)
-    refs = ctx.sfoc_build_batch([dev(pp.ref) for pp in c4], p=p)
-    sens = ctx.sfoc_build_batch([dev(pp.sen) for pp in c4], p=p)
-    outs = ctx.fastncc_match_batch(refs, sens, [dev(pp.points) for pp in c4], [pp.m for pp in c4],
-                                   [pp.R for pp in c4], corr_path=b.CORR_IGEMM_TC)
+    refs = ctx.sfoc_build_batch([dev(pp.ref) for pp in batch], p=p)
+    sens = ctx.sfoc_build_batch([dev(pp.sen) for pp in batch], p=p)
+    outs = ctx.fastncc_match_batch(refs, sens, [dev(pp.points) for pp in batch], [pp.m for pp in batch],
+                                   [pp.R for pp in batch], corr_path=b.CORR_IGEMM_TC)
     ctx.sync()
-    for k, pair in enumerate(c4):
+    for k, pair in enumerate(batch):
         g = b.results(outs[k])
         idx, sub = sample(pair, 2, 500 + k)
         o_r, o_u, regions = bf16_oracle_side(orc, sub, roi=True)
@@ -81,12 +81,12 @@ def test_config4_batched_bf16(b, ctx, orc, c4):
 
 
 @pytest.fixture(scope="module")
-def c5():
-    return config5()
+def big():
+    return speckle_pair_10000()
 
 
-def test_config5_full_size_sampled(b, ctx, orc, c5):
-    pair = c5
+def test_speckle_pair_10000_full_size_sampled(b, ctx, orc, big):
+    pair = big
     ref16 = pair.meta["ref_u16"]
     bits = torch.from_numpy(ref16.view(np.int16)).cuda()
     pts = dev(pair.points)

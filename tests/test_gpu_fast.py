@@ -8,7 +8,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from workloads import config2, optical_like  # noqa: E402
+from workloads import sar_pair_2048, optical_like  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +49,7 @@ def test_matches_oracle(b, ctx, orc, H, W, gy, gx, t, margin, seed):
 
 def test_full_size_reference(b, ctx, orc):
     """The 2048^2 reference of the benchmark workload, 32 x 32 blocks."""
-    img = config2().ref
+    img = sar_pair_2048().ref
     g = gpu_fast(ctx, img, 0.05, 32, 32, 61)
     o = orc.fast_blocks(img, 0.05, 32, 32, 61)
     np.testing.assert_array_equal(g[0], o[0])

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from workloads import config1, config2, tiny_pair  # noqa: E402
+from workloads import inverting_pair_512, sar_pair_2048, tiny_pair  # noqa: E402
 
 from parity import compare  # noqa: E402
 
@@ -150,8 +150,8 @@ def gpu_match(ctx, b, pair, p=None, corr=0, want_maps=False):
 
 
 @pytest.mark.parametrize("path", F32_PATHS)
-def test_match_config1_f32(b, ctx, orc, path):
-    pair = config1()
+def test_match_inverting_pair_512_f32(b, ctx, orc, path):
+    pair = inverting_pair_512()
     o = orc.match_pair(pair.ref, pair.sen, pair.points, pair.m, pair.R, want_maps=True, roi=False)
     g = gpu_match(ctx, b, pair, corr=f32_path(b, path), want_maps=True)
     st = compare(g, o, pair.R, oracle_maps=o["maps"])
@@ -211,10 +211,10 @@ def test_status_cases(b, ctx, orc, path):
 
 
 @pytest.mark.parametrize("path", F32_PATHS)
-def test_config2_full_size_sampled(b, ctx, orc, path):
+def test_sar_pair_2048_full_size_sampled(b, ctx, orc, path):
     """2048^2, 1000 points, m=81, R=20: the benchmark's configuration; the
     oracle checks a seeded sample of 8 points."""
-    pair = config2()
+    pair = sar_pair_2048()
     g = gpu_match(ctx, b, pair, corr=f32_path(b, path))
     rng = np.random.default_rng(2024)
     idx = np.sort(rng.choice(len(pair.points), 8, replace=False))
@@ -225,7 +225,7 @@ def test_config2_full_size_sampled(b, ctx, orc, path):
 
 
 def test_host_entry_matches_device(b, ctx):
-    pair = config1()
+    pair = inverting_pair_512()
     p = b.params()
     raw_d = ctx.register_pair(dev(pair.ref), dev(pair.sen), dev(pair.points), pair.m, pair.R, p=p)
     raw_h = ctx.register_pair_host(torch.from_numpy(pair.ref).pin_memory(), torch.from_numpy(pair.sen).pin_memory(),

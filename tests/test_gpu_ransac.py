@@ -9,7 +9,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from workloads import apply_model, config1, planted_correspondences, ransac_samples  # noqa: E402
+from workloads import apply_model, inverting_pair_512, planted_correspondences, ransac_samples  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -98,8 +98,8 @@ def test_out_of_range_index_voids_the_hypothesis(b, ctx, orc):
     np.testing.assert_array_equal(sc[keep], o["scores"])
 
 
-def test_config1_matches_give_the_planted_shift(b, ctx):
-    pair = config1()
+def test_inverting_pair_512_matches_give_the_planted_shift(b, ctx):
+    pair = inverting_pair_512()
     p = b.params(dtype=b.DTYPE_F32)
     rc = ctx.sfoc_build(dev(pair.ref), p=p)
     sc = ctx.sfoc_build(dev(pair.sen), p=p)

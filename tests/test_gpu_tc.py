@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from workloads import config1, config2, tiny_pair  # noqa: E402
+from workloads import inverting_pair_512, sar_pair_2048, tiny_pair  # noqa: E402
 
 from parity import bf16_check as check, bf16_oracle_side as oracle_side  # noqa: E402
 
@@ -116,8 +116,8 @@ def test_bf16_cube_is_rounded_oracle_cube(b, ctx, orc, kw):
 
 
 @pytest.mark.parametrize("form", FORMS)
-def test_tc_config1(b, ctx, orc, form):
-    pair = config1()
+def test_tc_inverting_pair_512(b, ctx, orc, form):
+    pair = inverting_pair_512()
     g = gpu_bf16(ctx, b, pair, want_maps=True, path=form_path(b, form))
     ctx.sync()
     o_r, o_u, regions = oracle_side(orc, pair)
@@ -128,10 +128,10 @@ def test_tc_config1(b, ctx, orc, form):
 
 
 @pytest.mark.parametrize("form", ["auto", "band"])
-def test_tc_config2_full_size_sampled(b, ctx, orc, form):
+def test_tc_sar_pair_2048_full_size_sampled(b, ctx, orc, form):
     """2048^2, 1000 points, m=81, R=20 in the benchmark's launch
     configuration; a seeded sample of 6 points against the oracle."""
-    pair = config2()
+    pair = sar_pair_2048()
     g = gpu_bf16(ctx, b, pair, path=form_path(b, form))
     ctx.sync()
     rng = np.random.default_rng(77)

@@ -31,7 +31,7 @@ def _rank_main(rank, world, port, ms, matched, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         got = bench.reduce_over_ranks(dist, torch, ms[rank], matched[rank], "cpu")
-        p, _ = bench.workload("c1", rank)
+        p, _ = bench.workload("inverting512", rank)
         q.put((rank, got, float(p.ref[0, :8].sum())))
     finally:
         dist.destroy_process_group()

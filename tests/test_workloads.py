@@ -1,12 +1,12 @@
 """The seeded generators are deterministic and produce the workload shapes."""
 import numpy as np
 
-from workloads import config1, tiny_pair, template_half, margin_for
+from workloads import inverting_pair_512, tiny_pair, template_half, margin_for
 
 
-def test_config1_deterministic_and_shaped():
-    a = config1()
-    b = config1()
+def test_inverting_pair_512_deterministic_and_shaped():
+    a = inverting_pair_512()
+    b = inverting_pair_512()
     np.testing.assert_array_equal(a.ref, b.ref)
     np.testing.assert_array_equal(a.sen, b.sen)
     np.testing.assert_array_equal(a.points, b.points)

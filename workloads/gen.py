@@ -187,7 +187,7 @@ def gamma_speckle(rng, shape, looks):
 
 
 def radiometric(rng, img, kind):
-    """One of the c4 maps: linear, gamma, inverted, speckled."""
+    """One of the mixed batch's maps: linear, gamma, inverted, speckled."""
     if kind == "linear":
         a = rng.uniform(0.5, 1.5)
         b = rng.uniform(-0.2, 0.2)
@@ -317,7 +317,7 @@ def _points_for(sen, ref_shape, m, R, grid, score, n_max=None):
     return pts
 
 
-def config1(seed=1000, H=512, W=512, n_side=10, m=41, R=10, max_shift=8):
+def inverting_pair_512(seed=1000, H=512, W=512, n_side=10, m=41, R=10, max_shift=8):
     """512^2 reference from value noise + 30 rectangles + 20 lines; sensed is
     a monotone-then-inverting piecewise map of the reference shifted by an
     integer (sx, sy) in [-8, 8]^2; 100 block-max points; m=41, R=10."""
@@ -331,7 +331,7 @@ def config1(seed=1000, H=512, W=512, n_side=10, m=41, R=10, max_shift=8):
     return Pair(ref, sen, pts, m, R, truth, dict(shift=(sx, sy), knot=knot, seed=seed))
 
 
-def config2(seed=2000, H=2048, W=2048, grid=32, n_points=1000, m=81, R=20,
+def sar_pair_2048(seed=2000, H=2048, W=2048, grid=32, n_points=1000, m=81, R=20,
             max_shift=15, block=256, looks=4):
     """2048^2 optical-like reference; SAR-like sensed image: nonlinear remap,
     Gamma speckle with L=4 looks, and a piecewise-constant shift field with
@@ -353,7 +353,7 @@ def config2(seed=2000, H=2048, W=2048, grid=32, n_points=1000, m=81, R=20,
     return Pair(ref, sen, pts, m, R, truth, dict(gamma=g, block=block, seed=seed))
 
 
-def config4(seed=4000, n_pairs=64, side_lo=512, side_hi=4096, templates=(41, 61, 81, 101),
+def mixed_batch(seed=4000, n_pairs=64, side_lo=512, side_hi=4096, templates=(41, 61, 81, 101),
             r_lo=10, r_hi=40, pts_lo=200, pts_hi=4000, max_shift=8, scale=1.0):
     """64 pairs, sides uniform in [512, 4096] (non-square allowed), each with
     one radiometric map of {linear, gamma, inverted, speckled}, 200-4000
@@ -383,7 +383,7 @@ def config4(seed=4000, n_pairs=64, side_lo=512, side_hi=4096, templates=(41, 61,
     return pairs
 
 
-def config5(seed=5000, H=10000, W=10000, n_points=10000, m=101, R=40, block=512,
+def speckle_pair_10000(seed=5000, H=10000, W=10000, n_points=10000, m=101, R=40, block=512,
             max_rot_deg=1.0, scale_lo=0.99, scale_hi=1.01, max_translation=28, looks=1):
     """10000^2 uint16 reference (converted to float32 / 65535); the sensed
     image is an L=1 Gamma-speckled, bilinearly resampled copy under a
