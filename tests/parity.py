@@ -103,10 +103,12 @@ def ncc_rounding_bound(S, T, cube_err=2e-5, base=NCC_TOL):
     """Per-offset bound on |dNCC| between the GPU's bf16 cube and the
     oracle's cube rounded to bf16.  The two FP32/FP64 cubes differ by at most
     `cube_err` per value, so only values within `cube_err` of a rounding
-    midpoint can round differently, by one ulp each.  A perturbation delta of
-    a centred vector s changes the cosine by at most ||delta|| / ||s||, so
+    midpoint can round differently: by one ulp where the ulp exceeds
+    cube_err, by at most floor(cube_err / ulp) + 1 ulps where it does not (the
+    values near zero).  A perturbation delta of a centred vector s changes
+    the cosine by at most ||delta|| / ||s||, so
       bound = base + ||delta_S|| / sigma_S + ||delta_T|| / sigma_T
-    with ||delta||^2 the sum of the squared ulps of the ambiguous values and
+    with ||delta||^2 the sum of the squared moves of the ambiguous values and
     sigma the centred norms.
     S: (z, M, M) window region (FP64, unrounded), T: (z, m, m).  Returns a
     (M-m+1, M-m+1) map."""
@@ -117,7 +119,8 @@ def ncc_rounding_bound(S, T, cube_err=2e-5, base=NCC_TOL):
         lo = bf16_round(v)
         u = bf16_ulp(v)
         d = np.minimum(np.abs(v - (lo + u / 2)), np.abs(v - (lo - u / 2)))
-        return np.where(d <= cube_err, u * u, 0.0)   # squared one-ulp moves
+        mv = (np.floor(cube_err / u) + 1.0) * u       # the largest move of a value within cube_err
+        return np.where(d <= cube_err, mv * mv, 0.0)
 
     wS = amb(S)
     wT = amb(T)
@@ -133,11 +136,13 @@ def ncc_rounding_bound(S, T, cube_err=2e-5, base=NCC_TOL):
 def flip_tolerance(Sw, T, cube_err=2e-5, base=NCC_TOL, k_sigma=6.0):
     """Tolerance at one offset for the GPU bf16 cube vs the oracle cube
     rounded to bf16.  Ambiguous values (within cube_err of a rounding
-    midpoint) move by +-1 ulp independently; to first order the NCC moves by
+    midpoint) move independently by +-1 ulp (+-(floor(cube_err / ulp) + 1)
+    ulps at most where the ulp is below cube_err); to first order the NCC
+    moves by
     sum_i g_i delta_i with g the exact NCC gradient
       dNCC/ds_i = b_i/(|a||b|) - NCC a_i/|a|^2,  a = s - mean(s), b = t - mean(t)
     (and symmetrically for t), whose spread is
-      sigma^2 = sum over ambiguous i of (ulp_i g_i)^2.
+      sigma^2 = sum over ambiguous i of (move_i g_i)^2.
     Returns base + k_sigma * sigma.  Sw: (z, m, m) window, T: (z, m, m)."""
     a = (Sw - Sw.mean()).ravel()
     bb = (T - T.mean()).ravel()
@@ -152,7 +157,7 @@ def flip_tolerance(Sw, T, cube_err=2e-5, base=NCC_TOL, k_sigma=6.0):
         lo = bf16_round(v)
         u = bf16_ulp(v)
         d = np.minimum(np.abs(v - (lo + u / 2)), np.abs(v - (lo - u / 2)))
-        return np.where(d <= cube_err, u, 0.0).ravel()
+        return np.where(d <= cube_err, (np.floor(cube_err / u) + 1.0) * u, 0.0).ravel()
 
     sig = np.sqrt(((w(Sw) * gS) ** 2).sum() + ((w(T) * gT) ** 2).sum())
     return base + k_sigma * sig
