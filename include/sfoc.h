@@ -127,7 +127,13 @@ typedef struct {
 
 /* Creates a context on CUDA device `device` issuing work on `stream` (a
  * cudaStream_t; NULL = the legacy default stream).  The context owns its
- * workspace (grown on demand, freed by sfoc_ctx_destroy). */
+ * workspace (grown on demand, freed by sfoc_ctx_destroy).  *out is NULL on
+ * failure: SFOC_ERR_INVALID_ARG for a NULL `out` or a device index out of
+ * range, SFOC_ERR_CUDA when no CUDA device can be reached, SFOC_ERR_OOM when
+ * the context's error word cannot be allocated.
+ * Every call below that takes a context returns SFOC_ERR_INVALID_ARG for a
+ * NULL one (sfoc_last_error_string returns "null context",
+ * sfoc_ctx_launch_count 0). */
 SFOC_API sfoc_status sfoc_ctx_create(sfoc_ctx** out, int device, void* stream);
 SFOC_API sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx);
 SFOC_API sfoc_status sfoc_ctx_set_stream(sfoc_ctx* ctx, void* stream);

@@ -377,7 +377,8 @@ sfoc_status sfoc_ctx_create(sfoc_ctx** out, int device, void* stream) {
     if (!out) return SFOC_ERR_INVALID_ARG;
     *out = nullptr;
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SFOC_ERR_INVALID_ARG;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) return SFOC_ERR_CUDA;  // no driver or no device reachable
+    if (device < 0 || device >= ndev) return SFOC_ERR_INVALID_ARG;
     sfoc_ctx* c = new (std::nothrow) sfoc_ctx();
     if (!c) return SFOC_ERR_OOM;
     c->device = device;

@@ -73,6 +73,41 @@ def test_host_only_calls(b):
     assert L.fastncc_match(None, None, None, None, 0, 1, 1, None, None) == -1
 
 
+def test_null_context_is_rejected_everywhere(b):
+    """Every entry point that takes a context (or a cube) refuses a NULL
+    one with SFOC_ERR_INVALID_ARG before touching the device, whatever the
+    other arguments are (here all zero / NULL)."""
+    L = b.lib()
+    host_only = {"sfoc_ctx_create", "sfoc_match_workspace_bytes", "sfoc_params_default", "sfoc_last_error_string",
+                 "sfoc_ctx_launch_count"}
+    checked = 0
+    for name, (res, args) in b._SIGS.items():
+        if name in host_only:
+            continue
+        vals = [0.0 if a in (C.c_float, C.c_double) else (0 if a in (C.c_int, C.c_size_t, C.c_int64) else None)
+                for a in args]
+        assert getattr(L, name)(*vals) == -1, name
+        checked += 1
+    assert checked >= 24
+    assert L.sfoc_ctx_launch_count(None) == 0
+    assert L.sfoc_ctx_create(None, 0, None) == -1
+
+
+def test_context_without_a_device():
+    """Without a reachable CUDA device sfoc_ctx_create reports SFOC_ERR_CUDA
+    and leaves *out NULL (an out-of-range index is SFOC_ERR_INVALID_ARG)."""
+    torch = pytest.importorskip("torch")
+    import paper_2202_13347_gb300 as pkg
+    pkg.build()
+    b = pkg.load()
+    L = b.lib()
+    h = C.c_void_p(1)
+    if torch.cuda.is_available():
+        assert L.sfoc_ctx_create(C.byref(h), 1 << 20, None) == -1 and h.value is None
+        pytest.skip("a CUDA device is present")
+    assert L.sfoc_ctx_create(C.byref(h), 0, None) == -4
+    assert h.value is None
+
 def test_no_oracle_in_product_path():
     """The product package never imports the oracle and the library holds no
     CPU fallback: the sources do not mention it."""
