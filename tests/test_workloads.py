@@ -41,3 +41,34 @@ def test_noise_series_statistics():
     assert abs(sp.mean()) < 2e-3 and abs(sp.var() - 0.04) < 2e-3
     assert np.abs(sp).max() <= np.sqrt(3 * 0.04) + 1e-6
     assert add_noise(rng, np.ones((50, 50), np.float32), "gaussian", 0.01).max() <= 1.0
+
+
+def _recovered(pair, k, seed=0):
+    """How many of k seeded points the FP64 oracle matches within 1.5 px of
+    the generator's truth (Sec. 4.1's correct-match radius), and how many
+    within 1.5 px of its negation (a sign error in the truth)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(pair.points), k, replace=False))
+    o = oracle.match_pair(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R)
+    ok = o["status"] == 0
+    off = np.stack([o["sub_dx"], o["sub_dy"]], 1)
+    t = pair.truth[idx]
+    return (int((ok & (np.linalg.norm(off - t, axis=1) <= 1.5)).sum()),
+            int((ok & (np.linalg.norm(off + t, axis=1) <= 1.5) & (np.linalg.norm(t, axis=1) > 3)).sum()))
+
+
+def test_planted_truth_is_what_the_oracle_finds():
+    """The generators' ground truth (the offset d with sensed(p) showing the
+    reference at p + d) agrees with what the oracle's matching finds on
+    reduced versions of the workloads: the inverting 512^2 pair, the SAR-like
+    pair's block shift field, and the per-block affine field of the 10000^2
+    pair with its speckle turned off (L = 1 speckle defeats most matches at
+    any template size, which is the workload's purpose, not the truth's)."""
+    from workloads import inverting_pair_512, sar_pair_2048, speckle_pair_10000
+    good, flipped = _recovered(inverting_pair_512(), 8)
+    assert good >= 7 and flipped == 0
+    good, flipped = _recovered(sar_pair_2048(seed=2100, H=1024, W=1024, grid=8, n_points=64, block=256), 10)
+    assert good >= 4 and flipped == 0
+    good, flipped = _recovered(speckle_pair_10000(seed=5100, H=1024, W=1024, n_points=36, looks=10 ** 6), 6)
+    assert good >= 4 and flipped == 0
