@@ -1,0 +1,47 @@
+"""The work figures behind the benchmark's roofline numerators, against the
+per-point numbers the design notes and profiles state, and the whole-job
+throughput arithmetic.  No GPU needed."""
+from types import SimpleNamespace
+
+import pytest
+
+import bench
+
+
+def _pair(m, R):
+    return SimpleNamespace(m=m, R=R)
+
+
+@pytest.mark.parametrize("m,R,want", [(41, 10, 1.78e7), (81, 20, 2.647e8), (101, 40, 1.606e9)])
+def test_direct_flop_per_point(m, R, want):
+    """2 m^2 z (2R+1)^2 with z = 12 (Eq. 10 at every offset): the 512^2,
+    2048^2 and 10000^2 workloads' template and search sizes."""
+    assert bench.corr_flops(_pair(m, R)) == pytest.approx(want, rel=2e-3)
+
+
+def test_fourier_flop_per_point():
+    """The Fourier form's count for m = 81, R = 20 on 128-point transforms:
+    15.06 Mflop per point, the figure its profile summary quotes."""
+    p = _pair(81, 20)
+    assert bench.fft_side(p) == 128
+    assert bench.fft_flops(p) == pytest.approx(15.0592e6, rel=1e-5)
+    assert bench.fft_side(_pair(41, 10)) == 64
+    assert bench.fft_side(_pair(101, 40)) is None      # m + 2R = 181 > 128: no Fourier form
+
+
+@pytest.mark.parametrize("m,R,kernel", [
+    (81, 20, "k_corr_tc_col"),                 # column 41 * 81 = 3321 MMAs, band 8 * 6 * 81 = 3888
+    (41, 10, "k_corr_tc_band"),                # band 4 * 3 * 41 = 492, column 21 * 41 = 861
+    (101, 40, "k_corr_tc_band"),               # m + 2R = 181 > 128: no column form
+    (101, 45, "k_corr_tc (Toeplitz form)"),    # neither: R > 40 and m + 2R > 128
+])
+def test_tensor_form_choice(m, R, kernel):
+    """The bench names the tensor-core kernel the library picks: the column
+    or band form with fewer MMAs per point, else the Toeplitz form."""
+    assert bench.tc_kernel(_pair(m, R)) == kernel
+
+
+def test_job_value():
+    """934 matched points per step, 20 steps in 35.95 ms: 519.6 K CP/s."""
+    assert bench.job_value(934, 20, 35.95) == pytest.approx(519610.6, rel=1e-6)
+    assert bench.reduce_over_ranks(None, None, 12.5, 7, "cpu") == (12.5, 7)

@@ -6,7 +6,8 @@ R in [10, 40], built and matched through the batched entry points
 checks a seeded sample of points per pair.
 10000^2 pair: at full size, the 16-bit reference read through
 sfoc_build_u16; 10000 points, m = 101, R = 40 (the BF16 form takes the
-Toeplitz tensor-core kernel since m + 2R > 128); the oracle checks a seeded
+band tensor-core kernel: m + 2R = 181 rules the column form out, and the
+band form issues fewer MMAs than the Toeplitz one); the oracle checks a seeded
 sample of points.  Tolerances as in the other parity tests.
 """
 import numpy as np
@@ -102,7 +103,7 @@ def test_speckle_pair_10000_full_size_sampled(b, ctx, orc, big):
     assert int((g["status"] == 0).sum()) >= 0.5 * len(pair.points)
     rc.free()
     sc.free()
-    # BF16 form (Toeplitz tensor-core kernel: m + 2R = 181)
+    # BF16 form (band tensor-core kernel: R <= 40, m + 2R = 181 > 128)
     p = b.params(dtype=b.DTYPE_BF16)
     rc = ctx.sfoc_build_u16(bits, p=p)
     sc = ctx.sfoc_build(dev(pair.sen), p=p)
