@@ -252,9 +252,19 @@ SFOC_API sfoc_status sfoc_cube_free(sfoc_cube* cube);
  *   opts            NULL = defaults (AUTO path, no maps).
  *   d_out           caller-owned array of n fastncc_result.
  * NCC is the Eq. 8 value computed through Eq. 9: R_ST by a correlation
- * kernel, R_S and R_SS from FP64 integral images (Eq. 14-16), the variances
- * in FP64.  Ties go to the smallest dy, then the smallest dx.
- * Limits: m <= 128, R <= 63.
+ * kernel (opts->corr_path), R_S and R_SS from the reference cube's integral
+ * images (Eq. 14-16: exact 64-bit sums of the per-pixel channel sums rounded
+ * to multiples of 2^-28, built on first use and kept with the cube), R_T and
+ * R_TT from the same sums over the template, the variances in FP64.  Ties go
+ * to the smallest dy, then the smallest dx.  The workspace grows to
+ * sfoc_match_workspace_bytes(n, R) if it is smaller.
+ * Errors: SFOC_ERR_INVALID_ARG for a NULL cube, NULL points or output with
+ * n > 0, n < 0, m < 1, R < 0 or an unknown corr_path; SFOC_ERR_SHAPE when
+ * the cubes' channel counts or dtypes differ; SFOC_ERR_UNSUPPORTED beyond
+ * m <= 128, R <= 63, for a path the cube dtype does not serve (DIRECT_F32
+ * and FFT need F32 cubes, the tensor-core paths BF16 cubes) or a forced
+ * form outside its limits; SFOC_ERR_OOM when the workspace cannot grow.
+ * Points whose template or windows leave an image get status OUT_OF_BOUNDS.
  */
 SFOC_API sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const int32_t* d_points, int n,
                           int template_size, int search_radius, const fastncc_opts* opts,
