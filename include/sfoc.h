@@ -175,9 +175,12 @@ SFOC_API sfoc_status sfoc_params_default(sfoc_params* p);
  *   n_orient     orientations per group (overrides p->n_orient; <= 0 = p's).
  *   p            NULL = sfoc_params_default().
  *   out          receives a cube owned by the library (free with
- *                sfoc_cube_free).  If *out already holds a cube of the same
- *                H, W, channel count and dtype, it is rebuilt in place and no
- *                memory is allocated.
+ *                sfoc_cube_free).  On entry *out is NULL or a cube from an
+ *                earlier build: a cube of the same H, W, channel count,
+ *                dtype and device is rebuilt in place and no memory is
+ *                allocated; any other cube is left as it is (the caller
+ *                still frees it) and *out receives a new one.  On failure
+ *                *out is unchanged.
  * The cube holds z = 2*n_orient channels (first-order then second-order
  * orientations), each normalised per group, plus per-pixel sums over
  * channels of g and g^2 used for the integral images of Eq. 14.
