@@ -413,7 +413,8 @@ static inline double cube_at(const oracle_cube* c, int ch, int y, int x) {
 int oracle_template_half(int m) { return (m % 2) ? (m - 1) / 2 : m / 2; }
 
 /* Parabola through (-1, cm), (0, c0), (1, cp): vertex offset, or 0 when the
- * curvature is not negative; clamped to [-0.5, 0.5]. */
+ * curvature is not negative; clamped to [-0.5, 0.5].  The paper has no
+ * sub-pixel step; this is the separable 3-point reading applied per axis. */
 double oracle_parabola(double cm, double c0, double cp) {
     double den = cm - 2.0 * c0 + cp;
     if (!(den < 0.0)) return 0.0;
@@ -424,7 +425,9 @@ double oracle_parabola(double cm, double c0, double cp) {
 }
 
 /* Picks the best offset of an NCC map (rows dy = -R..R, cols dx = -R..R) with
- * the order (NCC desc, dy asc, dx asc); NaN entries are skipped and flagged. */
+ * the order (NCC desc, dy asc, dx asc); NaN entries are skipped and flagged.
+ * The most similar position is the control point (Sec. 3.2.2); the paper
+ * gives no tie rule, so ties go to the smallest dy, then dx. */
 void oracle_pick(const double* map, int R, oracle_result* out) {
     int P1 = 2 * R + 1;
     int best = -1, has_nan = 0;
