@@ -93,7 +93,8 @@ cudaError_t launch_cube_export(const Cube& c, float* out, cudaStream_t st);
 // sums stay below 2^45: at most 128^2 pixels of |s1| <= 2 sqrt(8) < 5.7 (two
 // unit-norm groups of at most 8 channels) or s2 <= 2, i.e. < 2^44.6 units.
 // A non-finite value enters as kIntNonFinite, so a window sum >= 2^45 holds
-// one (windows of up to 2^17 such values still fit below 2^63).
+// one (a window has at most 128^2 = 2^14 pixels, so even one made only of
+// such values sums to 2^60 at most, well below 2^63).
 constexpr float kIntScale = 268435456.f;                  // 2^28
 constexpr long long kIntNonFinite = 1ll << 46;
 constexpr long long kIntNonFiniteMin = 1ll << 45;

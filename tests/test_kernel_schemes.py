@@ -1,0 +1,301 @@
+"""The arithmetic schemes of the GPU kernels, emulated on the CPU.
+
+Each CUDA kernel computes R_ST (Eq. 10), or the integral images of
+Eq. 14-16, by a decomposition chosen for the hardware: diagonal sums of
+tensor-core accumulators, lane shuffles in a drain, two real transforms
+packed in one complex transform, 64-bit fixed-point prefix sums.  These
+tests replay each decomposition with numpy, index for index as the kernel
+arranges it, and check that it reproduces the plain definition exactly (up
+to rounding).  They pin the design of the kernels; the GPU parity tests pin
+the kernels themselves.
+"""
+import numpy as np
+import pytest
+
+
+def direct_corr(S, T, m, R):
+    """Eq. 10: R[dy][dx] = sum_{c,i,u} S[c][i+dy][u+dx] T[c][i][u]."""
+    P1 = 2 * R + 1
+    return np.array([[np.sum(S[:, dy:dy + m, dx:dx + m] * T) for dx in range(P1)] for dy in range(P1)])
+
+
+def _case(z, m, R, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((z, m + 2 * R, m + 2 * R)), rng.standard_normal((z, m, m))
+
+
+# --------------------------------------------------------------------------
+# tensor-core forms (BF16 cubes): which products each accumulator holds and
+# how the correlation is read back out of them
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("z,m,R", [(3, 5, 2), (2, 9, 4), (2, 1, 3), (4, 7, 0)])
+def test_column_form_diagonal_sums(z, m, R):
+    """Column form: for one offset dx the accumulator holds
+    D[y][i] = sum_{u,c} S[c][y][u+dx] T[c][i][u] (M = window row y, N =
+    template row i, K = template column and channel); R_ST[dy][dx] is the
+    diagonal sum over i < m of D[i+dy][i]."""
+    S, T = _case(z, m, R, 1)
+    Lw, P1 = m + 2 * R, 2 * R + 1
+    out = np.zeros((P1, P1))
+    for dx in range(P1):
+        D = np.einsum("cyu,ciu->yi", S[:, :, dx:dx + m], T)       # (Lw, m)
+        assert D.shape == (Lw, m)
+        for dy in range(P1):
+            out[dy, dx] = sum(D[i + dy, i] for i in range(m))
+    np.testing.assert_allclose(out, direct_corr(S, T, m, R), atol=1e-11)
+
+
+@pytest.mark.parametrize("z,m,R", [(3, 6, 2), (2, 4, 5), (2, 1, 1)])
+def test_toeplitz_form_sums(z, m, R):
+    """Toeplitz form: D[dx][2R - dy] = sum_{y,u,c} S[c][y][u+dx] T[c][y-dy][u]
+    over window rows y (M = offset dx, N = 2R - dy), template rows outside
+    [0, m) being zero."""
+    S, T = _case(z, m, R, 2)
+    Lw, P1 = m + 2 * R, 2 * R + 1
+    D = np.zeros((P1, P1))
+    for dx in range(P1):
+        for n in range(P1):
+            dy = 2 * R - n
+            acc = 0.0
+            for y in range(Lw):
+                i = y - dy
+                if 0 <= i < m:
+                    acc += np.sum(S[:, y, dx:dx + m] * T[:, i, :])
+            D[dx, n] = acc
+    out = np.array([[D[dx, 2 * R - dy] for dx in range(P1)] for dy in range(P1)])
+    np.testing.assert_allclose(out, direct_corr(S, T, m, R), atol=1e-11)
+
+
+def _band_form(S, T, m, R):
+    """Band form as the kernel runs it.  Window rows in bands of 16, offsets in
+    groups of 8; the accumulator of (band y0, group e) is
+      D[8g + r][n] = sum_{u,c} S[c][y0+g][u+8e+r] T[c][y0-2R+n][u]
+    (M = 128 = 16 rows x 8 offsets, N = roundup(16 + 2R, 16) template rows).
+    The drain: lane l of warp quarter q holds accumulator row 32q + l, i.e.
+    g = 4q + l/8, r = l % 8.  Template rows outside [0, m) are zeroed, the
+    row is shifted left by g' = l/8 in two select steps (1, then 2), then two
+    butterflies over the lanes 8 and 16 apart add the four rows g' and leave
+    each lane a quarter of the columns; those sums run over the bands and the
+    drain warps' partial sums are added in a fixed order at the end."""
+    z = S.shape[0]
+    Lw, P1 = m + 2 * R, 2 * R + 1
+    N = (16 + 2 * R + 15) // 16 * 16
+    nE = (P1 + 7) // 8
+    nYB = (Lw + 15) // 16
+    # what the kernel's copies bring in around the region is other image
+    # data: window rows and columns past it, template rows above and below
+    # it.  Fill them with garbage; the scheme must not let it through.
+    junk = np.random.default_rng(99)
+    pad = 16 + 2 * R + N
+    Sp = junk.standard_normal((z, Lw + pad, Lw + pad))
+    Sp[:, :Lw, :Lw] = S
+    toff = 2 * R + N                                    # template row i lives at Tp[toff + i]
+    Tp = junk.standard_normal((z, m + 2 * toff, m))
+    Tp[:, toff:toff + m] = T
+    out = np.zeros((P1, P1))
+    for e in range(nE):
+        sums = np.zeros((2, 4, 32, N // 4))           # [team][quarter][lane][column]
+        for yb in range(nYB):
+            team = yb & 1                              # the two TMEM halves alternate
+            y0, ilo = 16 * yb, 16 * yb - 2 * R
+            D = np.zeros((128, N))
+            for g in range(16):
+                for r in range(8):
+                    for n in range(N):
+                        D[8 * g + r, n] = np.sum(Sp[:, y0 + g, 8 * e + r:8 * e + r + m] * Tp[:, toff + ilo + n, :])
+            valid = np.array([0 <= ilo + n < m for n in range(N)])
+            for q in range(4):
+                V = D[32 * q:32 * q + 32].copy()
+                V[:, ~valid] = 0.0                     # template rows outside [0, m) zeroed first
+                for l in range(32):                    # shift left by g' = l / 8
+                    gq = l >> 3
+                    if gq & 1:
+                        V[l] = np.concatenate([V[l, 1:], [0.0]])
+                    if gq & 2:
+                        V[l] = np.concatenate([V[l, 2:], [0.0, 0.0]])
+                W = np.zeros((32, N // 2))
+                for l in range(32):                    # butterfly over lanes 8 apart
+                    keep_hi = (l >> 3) & 1
+                    mine = V[l, N // 2:] if keep_hi else V[l, :N // 2]
+                    theirs = V[l ^ 8, N // 2:] if keep_hi else V[l ^ 8, :N // 2]
+                    W[l] = mine + theirs
+                for l in range(32):                    # butterfly over lanes 16 apart
+                    keep_hi = (l >> 4) & 1
+                    mine = W[l, N // 4:] if keep_hi else W[l, :N // 4]
+                    theirs = W[l ^ 16, N // 4:] if keep_hi else W[l ^ 16, :N // 4]
+                    sums[team, q, l] += mine + theirs
+        # each (team, quarter) is one drain warp; its lanes map back to (dy, dx)
+        part = np.zeros((8, P1, 8))
+        for team in range(2):
+            for q in range(4):
+                for l in range(32):
+                    r = l & 7
+                    joff = (N // 2 if (l >> 3) & 1 else 0) + (N // 4 if (l >> 4) & 1 else 0)
+                    for p in range(N // 4):
+                        dy = 2 * R + 4 * q - joff - p
+                        if 0 <= dy < P1:
+                            part[4 * team + q, dy, r] = sums[team, q, l, p]
+        for r in range(8):
+            if 8 * e + r < P1:
+                out[:, 8 * e + r] = sum(part[w, :, r] for w in range(8))   # fixed order over the warps
+    return out
+
+
+@pytest.mark.parametrize("z,m,R", [(2, 5, 2), (2, 9, 4), (3, 3, 0), (2, 12, 3), (2, 17, 9)])
+def test_band_form_accumulators_and_drain(z, m, R):
+    S, T = _case(z, m, R, 3)
+    np.testing.assert_allclose(_band_form(S, T, m, R), direct_corr(S, T, m, R), atol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# Fourier form (F32 cubes, Eq. 13)
+# --------------------------------------------------------------------------
+
+def _group_transform(x, sign):
+    """The kernel's length-L transform by a group of 8 threads (L = 8E).
+    Thread t holds x[t + 8j], j < E.  Each thread takes an E-point DFT over
+    j, multiplies output k1 by W_L^(t k1), the group transposes, and each
+    thread takes 8-point DFTs over t.  The result comes back in the same
+    stride-8 layout: thread t' holds X[t' + 8m].  Returns X in natural
+    order (sign -1 forward, +1 inverse without the 1/L)."""
+    L = len(x)
+    E = L // 8
+    W = np.exp(sign * 2j * np.pi * np.arange(L) / L)
+    y = np.zeros((8, E), complex)
+    for t in range(8):
+        v = x[t::8]
+        for k1 in range(E):
+            y[t, k1] = sum(v[j] * W[(8 * j * k1) % L] for j in range(E)) * W[(t * k1) % L]
+    X = np.zeros(L, complex)
+    for k1 in range(E):
+        for k2 in range(8):
+            X[k1 + E * k2] = sum(y[t, k1] * W[(E * t * k2) % L] for t in range(8))
+    # where the group leaves it: thread k1 % 8, slot k1 // 8 + (E / 8) k2
+    return X
+
+
+@pytest.mark.parametrize("L", [64, 128])
+def test_group_transform_is_the_dft(L):
+    rng = np.random.default_rng(L)
+    x = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    np.testing.assert_allclose(_group_transform(x, -1), np.fft.fft(x), atol=1e-9)
+    np.testing.assert_allclose(_group_transform(x, +1), np.fft.ifft(x) * L, atol=1e-9)
+    # the output slots: X[k1 + E k2] sits in thread k1 % 8, slot k1 // 8 + (E / 8) k2,
+    # which is the index t' + 8 m of the input layout
+    E = L // 8
+    for k1 in range(E):
+        for k2 in range(8):
+            t, mslot = k1 % 8, k1 // 8 + (E // 8) * k2
+            assert t + 8 * mslot == k1 + E * k2
+
+
+def _fourier_form(S, T, m, R, L):
+    """The kernel's dataflow for one point: per channel, rows of
+    z = S + i (T - mean T) (window zero-padded to L x L, template likewise),
+    row transforms, then the columns in conjugate pairs (pr, L - pr), pair 0
+    being the two self-conjugate columns (0, L/2).  From column spectra A, B
+    the window and template spectra of bin (ky, pr) are
+      S^ = (a + b) / 2,  T^ = (a - b) / (2 i),  a = A[ky], b = conj(B[-ky]),
+    and S^ conj(T^) = (a + b) i conj(a - b) / 4 is summed over channels in the
+    half spectrum kx in [0, L/2].  The inverse transforms those L/2 + 1
+    columns, then only rows 0..2R, each extended by Hermitian symmetry."""
+    z = S.shape[0]
+    Lw, P1 = m + 2 * R, 2 * R + 1
+    tmean = T.mean()
+    P = np.zeros((L, L // 2 + 1), complex)
+    for c in range(z):
+        Z = np.zeros((L, L), complex)
+        for y in range(Lw):
+            row = np.zeros(L, complex)
+            row[:Lw] = S[c, y]
+            if y < m:
+                row[:m] += 1j * (T[c, y] - tmean)
+            Z[y] = _group_transform(row, -1)
+        for pr in range(L // 2):
+            c1, c2 = (0, L // 2) if pr == 0 else (pr, L - pr)
+            A = _group_transform(Z[:, c1].copy(), -1)
+            B = _group_transform(Z[:, c2].copy(), -1)
+            for ky in range(L):
+                nky = (-ky) % L
+                if pr == 0:                            # each column is its own partner
+                    for col, arr in ((0, A), (L // 2, B)):
+                        a, b = arr[ky], np.conj(arr[nky])
+                        P[ky, col] += (a + b) * 1j * np.conj(a - b) / 4
+                else:
+                    a, b = A[ky], np.conj(B[nky])
+                    P[ky, c1] += (a + b) * 1j * np.conj(a - b) / 4
+    Q = np.zeros((L, L // 2 + 1), complex)
+    for kx in range(L // 2 + 1):
+        Q[:, kx] = _group_transform(P[:, kx].copy(), +1)
+    out = np.zeros((P1, P1))
+    for y in range(P1):
+        full = np.zeros(L, complex)
+        full[:L // 2 + 1] = Q[y]
+        full[L // 2 + 1:] = np.conj(Q[y, 1:L // 2][::-1])
+        out[y] = _group_transform(full, +1).real[:P1] / (L * L)
+    return out
+
+
+@pytest.mark.parametrize("z,m,R,L", [(2, 5, 2, 64), (2, 20, 6, 64), (1, 40, 12, 64), (2, 1, 0, 64)])
+def test_fourier_form_dataflow(z, m, R, L):
+    """Against Eq. 10 with the zero-mean template, i.e. the numerator of
+    Eq. 9: sum S (T - mean T) = R_ST - R_S R_T / mnz."""
+    S, T = _case(z, m, R, 4)
+    want = direct_corr(S, T - T.mean(), m, R)
+    np.testing.assert_allclose(_fourier_form(S, T, m, R, L), want, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# integral images (Eq. 14-16) in 64-bit fixed point
+# --------------------------------------------------------------------------
+
+SCALE = np.float32(2.0 ** 28)
+NON_FINITE = 1 << 46
+
+
+def _quant(v):
+    """One pixel value in units of 2^-28: the FP32 product v * 2^28 (exact),
+    rounded to nearest even; a non-finite value becomes 2^46."""
+    v = np.asarray(v, np.float32)
+    q = np.rint(np.where(np.isfinite(v), v, 0).astype(np.float32) * SCALE).astype(np.int64)
+    return np.where(np.isfinite(v), q, NON_FINITE)
+
+
+def test_fixed_point_integral_images():
+    """Exclusive prefix sums of the quantised values modulo 2^64; a window
+    sum from four lookups (Eq. 16) is the exact integer sum of its values,
+    a window holding a non-finite value sums to 2^45 or more, and a finite
+    window is within n 2^-29 of the FP64 sum of its FP32 values."""
+    rng = np.random.default_rng(5)
+    H, W = 37, 53
+    v = (rng.standard_normal((H, W)) * 2.5).astype(np.float32)
+    v[rng.random((H, W)) < 0.01] = np.nan
+    v[3, 40] = np.inf
+    q = _quant(v).astype(np.uint64)
+    P = np.zeros((H + 1, W + 1), np.uint64)
+    with np.errstate(over="ignore"):
+        P[1:, 1:] = np.cumsum(np.cumsum(q, axis=0, dtype=np.uint64), axis=1, dtype=np.uint64)
+    qi = _quant(v)
+    for (y0, x0, y1, x1) in [(0, 0, H, W), (2, 5, 30, 41), (10, 10, 11, 11), (0, 39, 6, 44), (20, 0, 37, 9)]:
+        with np.errstate(over="ignore"):
+            s = (P[y1, x1] - P[y0, x1] - P[y1, x0] + P[y0, x0]).astype(np.int64)
+        exact = sum(int(t) for t in qi[y0:y1, x0:x1].ravel())
+        bad = not np.isfinite(v[y0:y1, x0:x1]).all()
+        if bad:
+            assert s >= 1 << 45
+        else:
+            assert int(s) == exact
+            n = (y1 - y0) * (x1 - x0)
+            assert abs(int(s) * 2.0 ** -28 - v[y0:y1, x0:x1].astype(np.float64).sum()) <= n * 2.0 ** -29
+
+
+def test_fixed_point_headroom():
+    """Valid window sums stay below 2^45 units: at most 128^2 pixels of
+    |s1| < 5.7 (two unit-norm groups of at most 8 channels: 2 sqrt(8)) or
+    s2 <= 2.  A window of 128^2 non-finite values sums to 2^60, so no window
+    sum leaves the signed 64-bit range."""
+    assert 2 * np.sqrt(8) < 5.7
+    assert 128 * 128 * 5.7 * 2 ** 28 < 2 ** 45
+    assert 128 * 128 * 2.0 * 2 ** 28 < 2 ** 45
+    assert 128 * 128 * NON_FINITE + (1 << 45) < 1 << 63
