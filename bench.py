@@ -85,16 +85,26 @@ def workload(name, rank):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    Samples are time-stamped as they arrive.  After `mark(t0, t1)` (the
+    timed region, time.monotonic()), the summary keeps the samples taken in
+    it and in the sampling period after it (up to 1.5 periods, for jitter:
+    a region of a few tens of ms holds no 200 ms sample of its own), and
+    __exit__ waits (bounded) for that sample.  Without a mark, or with no sample there, every sample
+    of the run counts."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
+    PERIOD = 0.2  # seconds between samples (-lms 200)
+
     def __init__(self, gpu_index):
         self.idx = gpu_index
-        self.lines = []
+        self.lines = []       # (arrival time, csv line)
         self.proc = None
+        self.window = None
 
     def __enter__(self):
         try:
@@ -103,16 +113,29 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi can take longer to print its first sample than a short
+            # timed region lasts: wait (bounded) until it is running
+            t0 = time.monotonic()
+            while not self.lines and self.proc.poll() is None and time.monotonic() - t0 < 3.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc is not None:
+            if self.window is not None:
+                t_end = self.window[1]
+                while (not any(ts > t_end for ts, _ in self.lines) and self.proc.poll() is None
+                       and time.monotonic() - t_end < 3 * self.PERIOD):
+                    time.sleep(0.01)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -120,9 +143,16 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        lines = list(self.lines)
+        scope = "run"
+        if self.window is not None:
+            t0, t1 = self.window
+            near = [(ts, ln) for ts, ln in lines if t0 <= ts <= t1 + 1.5 * self.PERIOD]
+            if near:
+                lines, scope = near, "timed region + one period"
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -137,7 +167,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "scope": scope}
 
 
 def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
@@ -160,6 +190,7 @@ def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
     l0 = ctx.launch_count
     evs = []
     torch.cuda.synchronize()
+    t_start = time.monotonic()
     for _ in range(steps):
         flush.zero_()                       # L2 flush (256 MB write), outside the timed events
         e0 = torch.cuda.Event(enable_timing=True)
@@ -169,6 +200,7 @@ def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
+    t_end = time.monotonic()
     launches = ctx.launch_count - l0
     ctx.sync()
     st = ctx.stage_times()
@@ -176,7 +208,8 @@ def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
     ms = [a.elapsed_time(c) for a, c in evs]
     status = raw[:, 5].cpu()
     return dict(ms=sum(ms), ms_steps=ms, matched=int((status == 0).sum()), valid=int(((status == 0) | (status == 3)).sum()),
-                stages=st, launches=launches, p=p, corr=corr, d=(d_ref, d_sen, d_pts), raw=raw)
+                stages=st, launches=launches, p=p, corr=corr, d=(d_ref, d_sen, d_pts), raw=raw,
+                t_timed=(t_start, t_end))
 
 
 def run_fast(torch, ctx, pair, hbm_gbs, reps=10, grid=32, t=0.05):
@@ -492,6 +525,7 @@ def main():
             torch.cuda.synchronize()
             with ClockSampler(gpu_index) as cs:
                 r = run_form(b, torch, ctx, pair, form, args.steps, args.warmup, flush)
+                cs.mark(*r["t_timed"])
             r["ms_max"], r["matched_all"] = reduce_over_ranks(dist, torch, r["ms"], r["matched"], "cuda")
             r["clocks"] = cs.summary()
             results[form] = r

@@ -45,3 +45,33 @@ def test_job_value():
     """934 matched points per step, 20 steps in 35.95 ms: 519.6 K CP/s."""
     assert bench.job_value(934, 20, 35.95) == pytest.approx(519610.6, rel=1e-6)
     assert bench.reduce_over_ranks(None, None, 12.5, 7, "cpu") == (12.5, 7)
+
+
+def test_clock_sampler_keeps_the_timed_region(tmp_path, monkeypatch):
+    """The clocks object describes the timed region: samples before it (an
+    idle GPU during host-side set-up) are left out, the first sample after a
+    short region is waited for and kept, throttle reasons are reported."""
+    import os
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/bash\nsleep 0.2\ni=0\nwhile true; do\n"
+                    "  if [ $i -lt 3 ]; then c=990; r='Not Active'; else c=2070; r='Active'; fi\n"
+                    "  echo \"0, $c, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, $r\"\n"
+                    "  i=$((i+1)); sleep 0.2\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    with bench.ClockSampler(0) as cs:
+        assert cs.lines                          # running before the region starts
+        time.sleep(0.45)
+        t0 = time.monotonic()
+        time.sleep(0.03)
+        t1 = time.monotonic()
+        cs.mark(t0, t1)
+    s = cs.summary()
+    assert s["sm_mhz"] == 2070.0 and s["scope"] == "timed region + one period"
+    assert s["reasons"] == ["sw_power_cap"]
+    # without nvidia-smi the line still gets a clocks object, with no samples
+    monkeypatch.setenv("PATH", str(tmp_path / "nowhere"))
+    with bench.ClockSampler(0) as cs2:
+        cs2.mark(0.0, 0.0)
+    assert cs2.summary()["samples"] == 0
