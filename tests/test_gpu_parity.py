@@ -247,6 +247,41 @@ def test_invalid_arguments_return_errors(b, ctx):
         ctx.sfoc_build(dev(pair.ref), p=b.params(n_orient=9))
 
 
+def test_empty_point_sets(b, ctx):
+    """n = 0 through every matching entry point and path: nothing to match,
+    status OK, no result rows (empty inputs)."""
+    pair = tiny_pair(41, 60, 70, 9, 3, 4)
+    empty = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    rc, sc = ctx.sfoc_build(dev(pair.ref)), ctx.sfoc_build(dev(pair.sen))
+    for corr in (b.CORR_AUTO, b.CORR_FFT, b.CORR_DIRECT_F32):
+        assert ctx.fastncc_match(rc, sc, empty, 9, 3, corr_path=corr)["raw"].shape == (0, 6)
+    p16 = b.params(dtype=b.DTYPE_BF16)
+    rb, sb = ctx.sfoc_build(dev(pair.ref), p=p16), ctx.sfoc_build(dev(pair.sen), p=p16)
+    assert ctx.fastncc_match(rb, sb, empty, 9, 3, corr_path=b.CORR_IGEMM_TC)["raw"].shape == (0, 6)
+    assert ctx.register_pair(dev(pair.ref), dev(pair.sen), empty, 9, 3).shape == (0, 6)
+    outs = ctx.fastncc_match_batch([rc, rc], [sc, sc], [empty, dev(pair.points)], [9, 9], [3, 3])
+    ctx.sync()
+    assert outs[0].shape == (0, 6) and outs[1].shape == (len(pair.points), 6)
+
+
+@pytest.mark.parametrize("m,R,path", [
+    (129, 2, "auto"),       # m beyond the API's 128
+    (9, 64, "auto"),        # R beyond the API's 63
+    (128, 63, "direct"),    # the direct kernel's staged window (254 x 256 floats) exceeds shared memory
+    (9, 60, "fft"),         # m + 2R = 129 > 128: no transform size
+])
+def test_sizes_past_the_limits_are_refused(b, ctx, m, R, path):
+    """Sizes past the API's or a form's limits return SFOC_ERR_UNSUPPORTED
+    before any correlation kernel runs, and the context stays usable."""
+    pair = tiny_pair(43, 80, 80, 9, 3, 4)
+    rc, sc = ctx.sfoc_build(dev(pair.ref)), ctx.sfoc_build(dev(pair.sen))
+    corr = {"auto": b.CORR_AUTO, "direct": b.CORR_DIRECT_F32, "fft": b.CORR_FFT}[path]
+    with pytest.raises(b.SfocError) as e:
+        ctx.fastncc_match(rc, sc, dev(pair.points), m, R, corr_path=corr)
+    assert e.value.code == -6
+    ctx.sync()
+    assert ctx.fastncc_match(rc, sc, dev(pair.points), 9, 3)["raw"].shape == (len(pair.points), 6)
+
 def test_u16_input_matches_scaled_float(b, ctx, orc):
     """sfoc_build_u16: a 16-bit image is read as v / 65535 (the input step
     of the 10000^2 workload); the cube equals the oracle's on the FP64

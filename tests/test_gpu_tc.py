@@ -141,3 +141,20 @@ def test_tc_sar_pair_2048_full_size_sampled(b, ctx, orc, form):
     gs = {k: v[torch.from_numpy(idx).cuda()] for k, v in g.items()}
     check(gs, o_r, o_u, regions, pair.R, {})
     assert int((g["status"] == 0).sum()) >= 900
+
+
+@pytest.mark.parametrize("m,R,path", [
+    (20, 60, "column"),     # m + 2R = 140 > 128: no column form
+    (61, 41, "band"),       # R = 41: N = 112 rows, past the band form's 96
+])
+def test_forced_forms_past_their_limits_are_refused(b, ctx, m, R, path):
+    """Forcing a tensor-core form outside its limits returns
+    SFOC_ERR_UNSUPPORTED before the kernel runs; the context stays usable."""
+    pair = tiny_pair(44, 90, 90, 9, 3, 4)
+    p = b.params(dtype=b.DTYPE_BF16)
+    rc, sc = ctx.sfoc_build(dev(pair.ref), p=p), ctx.sfoc_build(dev(pair.sen), p=p)
+    with pytest.raises(b.SfocError) as e:
+        ctx.fastncc_match(rc, sc, dev(pair.points), m, R, corr_path=form_path(b, path))
+    assert e.value.code == -6
+    ctx.sync()
+    assert ctx.fastncc_match(rc, sc, dev(pair.points), 9, 3)["raw"].shape == (len(pair.points), 6)
