@@ -400,6 +400,7 @@ NOISE_VARIANTS = {
 # Sec. 4.3: variances 0..0.01 step 0.001 (Gaussian) and 0..0.1 step 0.01 (speckle)
 NOISE_LEVELS = {"gaussian": [round(0.001 * i, 3) for i in range(11)],
                 "speckle": [round(0.01 * i, 2) for i in range(11)]}
+NOISE_TEMPLATE = 80  # the template side of the experiment (Sec. 4.3)
 
 
 def noise_sweep(args):
@@ -425,7 +426,7 @@ def noise_sweep(args):
     n_points = 0
     t0 = time.perf_counter()
     for seed in seeds:
-        pair = inverting_pair_512(seed=seed, H=1024, W=1024, n_side=14, m=80, R=10)
+        pair = inverting_pair_512(seed=seed, H=1024, W=1024, n_side=14, m=NOISE_TEMPLATE, R=10)
         n_points += len(pair.points)
         d_ref = torch.from_numpy(pair.ref).cuda()
         d_pts = torch.from_numpy(pair.points).cuda()
@@ -445,7 +446,7 @@ def noise_sweep(args):
                     del sen_cube
         del ref_cubes
     line = {"experiment": "noise sensitivity (Sec. 4.3)", "metric": "average CMR", "pairs": len(seeds),
-            "points": n_points, "template": 80, "search_radius": 10, "tolerance_px": 1.5,
+            "points": n_points, "template": NOISE_TEMPLATE, "search_radius": 10, "tolerance_px": 1.5,
             "noise_on": "sensed image", "levels": NOISE_LEVELS,
             "cmr": {v: {k: [round(float(x), 4) for x in a] for k, a in d.items()} for v, d in cmr.items()},
             "data": "synthetic", "seconds": round(time.perf_counter() - t0, 1)}

@@ -75,3 +75,21 @@ def test_clock_sampler_keeps_the_timed_region(tmp_path, monkeypatch):
     with bench.ClockSampler(0) as cs2:
         cs2.mark(0.0, 0.0)
     assert cs2.summary()["samples"] == 0
+
+
+def test_noise_series_are_the_papers():
+    """The sweep's variances and template size are the ones Sec. 4.3 prints
+    (tests/golden/paper_values.txt)."""
+    import os
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = (t.strip() for t in line.split("=", 1))
+            vals[k] = v
+    for kind, vmax, step in (("gaussian", "gauss_var_max", "gauss_var_step"),
+                             ("speckle", "speckle_var_max", "speckle_var_step")):
+        lv = bench.NOISE_LEVELS[kind]
+        assert lv[0] == 0 and lv[-1] == pytest.approx(float(vals[vmax]))
+        assert all(b - a == pytest.approx(float(vals[step])) for a, b in zip(lv, lv[1:]))
+    assert bench.NOISE_TEMPLATE == int(vals["noise_template"])
