@@ -311,7 +311,10 @@ def run_e2e(b, torch, ctx, pair, p, corr, steps):
                 d2h_bytes_per_step=d2h)
 
 
-def cpu_baseline(pair, n_sample=16, seed=99):
+def cpu_baseline(pair, n_sample=64, seed=99):
+    """The oracle as it stands on a seeded sample of the workload's points
+    (64: about 12 s on 16 host cores at m = 81, R = 20), plus its SFOC build
+    rate on an image region."""
     import numpy as np
     import oracle
     oracle.build()
