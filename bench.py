@@ -587,11 +587,22 @@ def main():
         ms_max, matched_all = reduce_over_ranks(dist, torch, r["ms"], r["matched"] * r["steps"], "cuda")
         e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=r["h2d_bytes_per_step"],
                    d2h_bytes_per_step=r["d2h_bytes_per_step"], ms_per_step=ms_max / r["steps"])
-    ransac, quality = run_ransac(b, torch, ctx, pair, r0) if rank == 0 else (None, None)
-    fast = run_fast(torch, ctx, pair, pk["hbm"]) if rank == 0 else None
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(pair)
+    # the rows around matching and the CPU baseline run on rank 0 only; a
+    # failure in one of them is reported in its own entry, not in place of
+    # the line
+    def aux(fn, *a):
+        try:
+            return fn(*a)
+        except Exception as e:  # noqa: BLE001
+            return {"error": "%s: %s" % (type(e).__name__, e)}
+
+    ransac, quality, fast, cpu = None, None, None, None
+    if rank == 0:
+        rq = aux(run_ransac, b, torch, ctx, pair, r0)
+        ransac, quality = (rq, None) if isinstance(rq, dict) else rq
+        fast = aux(run_fast, torch, ctx, pair, pk["hbm"])
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = aux(cpu_baseline, pair)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
