@@ -72,6 +72,11 @@ sfoc_status fail(sfoc_ctx* ctx, sfoc_status s, const std::string& msg) {
 
 sfoc_status cuda_fail(sfoc_ctx* ctx, cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    // the error is reported now; a recoverable one (a failed allocation, a
+    // refused launch) is also the runtime's "last error", which the launch
+    // check of a later call (cudaGetLastError) would otherwise report again
+    // although that launch succeeded.  A sticky error stays sticky.
+    (void)cudaGetLastError();
     if (e == cudaErrorMemoryAllocation) return fail(ctx, SFOC_ERR_OOM, m);
     return fail(ctx, SFOC_ERR_CUDA, m);
 }

@@ -282,6 +282,19 @@ def test_sizes_past_the_limits_are_refused(b, ctx, m, R, path):
     ctx.sync()
     assert ctx.fastncc_match(rc, sc, dev(pair.points), 9, 3)["raw"].shape == (len(pair.points), 6)
 
+def test_allocation_failure_is_reported_and_the_context_recovers(b, ctx):
+    """A workspace no device can hold: sfoc_ctx_reserve returns SFOC_ERR_OOM,
+    the failed allocation leaves no error behind, and the next match on the
+    same context regrows its workspace and succeeds."""
+    pair = tiny_pair(45, 70, 70, 9, 3, 6)
+    rc, sc = ctx.sfoc_build(dev(pair.ref)), ctx.sfoc_build(dev(pair.sen))
+    with pytest.raises(b.SfocError) as e:
+        ctx.reserve(1 << 50)
+    assert e.value.code == -3
+    g = ctx.fastncc_match(rc, sc, dev(pair.points), pair.m, pair.R)
+    ctx.sync()
+    assert int((g["status"] == 0).sum()) > 0
+
 def test_u16_input_matches_scaled_float(b, ctx, orc):
     """sfoc_build_u16: a 16-bit image is read as v / 65535 (the input step
     of the 10000^2 workload); the cube equals the oracle's on the FP64
