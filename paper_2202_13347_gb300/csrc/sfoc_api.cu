@@ -724,8 +724,10 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
                                                              : 0,
                                ctx->stream);
     }
-    if (e == cudaErrorInvalidValue || e == cudaErrorNotSupported)
+    if (e == cudaErrorInvalidValue || e == cudaErrorNotSupported) {
+        (void)cudaGetLastError();  // a refused attribute or launch leaves no error for later calls
         return fail(ctx, SFOC_ERR_UNSUPPORTED, "correlation kernel does not support this m / R");
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "correlation launch");
     {
         StageScope sc(ctx, ST_NCC, 1);
