@@ -796,18 +796,26 @@ sfoc_status fastncc_register_pair_host(sfoc_ctx* ctx, const float* h_ref, int Hr
         e = cudaMemcpyAsync(d_pts, h_points, sizeof(int32_t) * 2 * (size_t)n, cudaMemcpyHostToDevice,
                             ctx->copy_stream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied, ctx->copy_stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
+    // the call is synchronous on every path: once copies from the caller's
+    // buffers are queued, a failure still waits for them before returning
+    auto drained = [&](sfoc_status st) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamSynchronize(ctx->stream);
+        (void)cudaGetLastError();
+        return st;
+    };
+    if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "host to device copy"));
     sfoc_status s = sfoc_build(ctx, d_ref, Hr, Wr, (size_t)Wr, nullptr, 0, 0, p, &ctx->pair_ref);
-    if (s != SFOC_OK) return s;
+    if (s != SFOC_OK) return drained(s);
     e = cudaStreamWaitEvent(ctx->stream, ctx->ev_copied, 0);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamWaitEvent");
+    if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "cudaStreamWaitEvent"));
     s = sfoc_build(ctx, d_sen, Hs, Ws, (size_t)Ws, nullptr, 0, 0, p, &ctx->pair_sen);
     if (s == SFOC_OK)
         s = fastncc_match(ctx, ctx->pair_ref, ctx->pair_sen, d_pts, n, template_size, search_radius, opts, d_out);
-    if (s != SFOC_OK) return s;
+    if (s != SFOC_OK) return drained(s);
     if (n > 0) {
         e = cudaMemcpyAsync(h_out, d_out, sizeof(fastncc_result) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
+        if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "device to host copy"));
     }
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
