@@ -136,6 +136,8 @@ typedef struct {
  * sfoc_ctx_launch_count 0). */
 SFOC_API sfoc_status sfoc_ctx_create(sfoc_ctx** out, int device, void* stream);
 SFOC_API sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx);
+/* Issues later calls on `stream`; first waits for the work already queued
+ * on the previous stream (it shares the context's workspace). */
 SFOC_API sfoc_status sfoc_ctx_set_stream(sfoc_ctx* ctx, void* stream);
 /* Blocks until the context's stream is idle; reports deferred device errors
  * (SFOC_ERR_CUDA, or SFOC_ERR_TIMEOUT when a bounded device wait expired). */

@@ -424,6 +424,12 @@ sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx) {
 
 sfoc_status sfoc_ctx_set_stream(sfoc_ctx* ctx, void* stream) {
     if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (static_cast<cudaStream_t>(stream) == ctx->stream) return SFOC_OK;
+    // the workspace is reused (and regrown) by calls on the new stream: the
+    // work still queued on the old one must be done with it first
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize(previous stream)");
     ctx->stream = static_cast<cudaStream_t>(stream);
     return SFOC_OK;
 }
