@@ -148,6 +148,26 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
 
 
+def _check_shape(t, name, shape):
+    """The library reads and writes exactly the elements the sizes it is
+    given imply; a tensor of another shape would be read or written past its
+    end, so the shape is checked here, before the call."""
+    if tuple(t.shape) != tuple(int(v) for v in shape):
+        raise ValueError("%s must have shape %s, not %s" % (name, tuple(int(v) for v in shape), tuple(t.shape)))
+
+
+def _channels(p) -> int:
+    """Channels of the cube `p` builds (NULL params = the defaults: 12)."""
+    if p is None:
+        return 12
+    return p.n_orient if p.first_order_only else 2 * p.n_orient
+
+
+def _check_host(t, name, dtype):
+    if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+        raise ValueError("%s must be a contiguous host %s tensor" % (name, dtype))
+
+
 def _check_cuda(t, name, dtype=None):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
@@ -297,6 +317,7 @@ class Context:
         _check_cuda(image, "image", torch.float32)
         _check_cuda(out, "out", torch.float32)
         H, W = image.shape
+        _check_shape(out, "out", (_channels(p), H, W))
         self._chk(lib().sfoc_build_static(self.h, _ptr(image), H, W, W, C.byref(p) if p is not None else None,
                                           _ptr(out)))
         return out
@@ -305,6 +326,7 @@ class Context:
                       corr_path=CORR_AUTO, want_maps=False):
         _check_cuda(points, "points", torch.int32)
         n = points.shape[0]
+        _check_shape(points, "points", (n, 2))
         raw = torch.empty((n, 6), dtype=torch.int32, device=self.device)
         maps = None
         if want_maps:
@@ -325,6 +347,10 @@ class Context:
         _check_cuda(sen, "sen", torch.float32)
         _check_cuda(points, "points", torch.int32)
         n = points.shape[0]
+        _check_shape(points, "points", (n, 2))
+        if out is not None:
+            _check_cuda(out, "out", torch.int32)
+            _check_shape(out, "out", (n, 6))
         raw = out if out is not None else torch.empty((n, 6), dtype=torch.int32, device=self.device)
         o = Opts(int(corr_path), None)
         self._chk(lib().fastncc_register_pair(self.h, _ptr(ref), ref.shape[0], ref.shape[1], _ptr(sen), sen.shape[0],
@@ -335,10 +361,16 @@ class Context:
     def register_pair_host(self, ref, sen, points, template_size: int, search_radius: int, p: Params = None,
                            corr_path=CORR_AUTO, out=None):
         """Host (CPU, ideally pinned) tensors in, host results out."""
-        for t, nm in ((ref, "ref"), (sen, "sen"), (points, "points")):
-            if t.is_cuda or not t.is_contiguous():
-                raise ValueError("%s must be a contiguous host tensor" % nm)
+        _check_host(ref, "ref", torch.float32)
+        _check_host(sen, "sen", torch.float32)
+        _check_host(points, "points", torch.int32)
+        if ref.dim() != 2 or sen.dim() != 2:
+            raise ValueError("ref and sen must be 2-D images")
         n = points.shape[0]
+        _check_shape(points, "points", (n, 2))
+        if out is not None:
+            _check_host(out, "out", torch.int32)
+            _check_shape(out, "out", (n, 6))
         raw = out if out is not None else torch.empty((n, 6), dtype=torch.int32)
         o = Opts(int(corr_path), None)
         self._chk(lib().fastncc_register_pair_host(
@@ -367,6 +399,11 @@ class Context:
 
     def fastncc_match_batch(self, refs, sens, points, template_sizes, search_radii, corr_path=CORR_AUTO):
         n = len(refs)
+        if not (len(sens) == len(points) == len(template_sizes) == len(search_radii) == n):
+            raise ValueError("refs, sens, points, template_sizes and search_radii must have the same length")
+        for i, pt in enumerate(points):
+            _check_cuda(pt, "points[%d]" % i, torch.int32)
+            _check_shape(pt, "points[%d]" % i, (pt.shape[0], 2))
         outs = [torch.empty((p.shape[0], 6), dtype=torch.int32, device=self.device) for p in points]
         R = (C.c_void_p * n)(*[c.handle for c in refs])
         S = (C.c_void_p * n)(*[c.handle for c in sens])
@@ -396,10 +433,14 @@ class Context:
         (3, 3) float64 device model (sensed -> reference), bilinear."""
         _check_cuda(image, "image", torch.float32)
         _check_cuda(model, "model", torch.float64)
+        _check_shape(model, "model", (3, 3))
         H, W = image.shape
         oh, ow = out_shape or (H, W)
         if out is None:
             out = torch.empty((oh, ow), dtype=torch.float32, device=self.device)
+        else:
+            _check_cuda(out, "out", torch.float32)
+            _check_shape(out, "out", (oh, ow))
         self._chk(lib().sfoc_rectify(self.h, _ptr(image), H, W, W, _ptr(model), C.c_float(fill), oh, ow, _ptr(out)))
         return out
 
@@ -409,6 +450,8 @@ class Context:
         _check_cuda(points, "points", torch.int32)
         _check_cuda(raw, "results", torch.int32)
         n = points.shape[0]
+        _check_shape(points, "points", (n, 2))
+        _check_shape(raw, "results", (n, 6))
         src = torch.empty((n, 2), dtype=torch.float64, device=self.device)
         dst = torch.empty((n, 2), dtype=torch.float64, device=self.device)
         valid = torch.empty((n,), dtype=torch.uint8, device=self.device)
@@ -428,6 +471,13 @@ class Context:
         if valid is not None:
             _check_cuda(valid, "valid", torch.uint8)
         n, n_hyp = src.shape[0], samples.shape[0]
+        _check_shape(src, "src", (n, 2))
+        _check_shape(dst, "dst", (n, 2))
+        k = {MODEL_PROJECTIVE: 4, MODEL_AFFINE: 3}.get(int(model))
+        if k is not None:  # an unknown model is refused by the library itself
+            _check_shape(samples, "samples", (n_hyp, k))
+        if valid is not None:
+            _check_shape(valid, "valid", (n,))
         H = torch.empty((3, 3), dtype=torch.float64, device=self.device)
         inl = torch.empty((n,), dtype=torch.uint8, device=self.device)
         info = torch.empty((2,), dtype=torch.int32, device=self.device)

@@ -118,3 +118,22 @@ def test_no_oracle_in_product_path():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt, f
+
+
+def test_binding_shape_checks(b):
+    """The binding checks every tensor's shape and dtype against the sizes
+    it passes, since the library reads and writes exactly those sizes."""
+    torch = pytest.importorskip("torch")
+    b._check_shape(torch.zeros((3, 2)), "x", (3, 2))
+    with pytest.raises(ValueError):
+        b._check_shape(torch.zeros((6,)), "x", (3, 2))
+    with pytest.raises(ValueError):
+        b._check_shape(torch.zeros((3, 3)), "x", (3, 2))
+    assert b._channels(None) == 12
+    assert b._channels(b.params(n_orient=8, first_order_only=True)) == 8
+    assert b._channels(b.params(n_orient=4)) == 8
+    b._check_host(torch.zeros(3, dtype=torch.float32), "h", torch.float32)
+    with pytest.raises(ValueError):
+        b._check_host(torch.zeros(3, dtype=torch.float64), "h", torch.float32)
+    with pytest.raises(ValueError):
+        b._check_host(torch.zeros((4, 4), dtype=torch.float32).t(), "h", torch.float32)

@@ -295,6 +295,24 @@ def test_allocation_failure_is_reported_and_the_context_recovers(b, ctx):
     ctx.sync()
     assert int((g["status"] == 0).sum()) > 0
 
+def test_binding_checks_shapes_before_the_library(b, ctx):
+    """Tensors whose shape does not match the sizes the binding passes are
+    refused in Python, before the library could read past their end."""
+    pair = tiny_pair(46, 60, 60, 9, 3, 4)
+    rc, sc = ctx.sfoc_build(dev(pair.ref)), ctx.sfoc_build(dev(pair.sen))
+    flat = dev(pair.points).reshape(-1).contiguous()
+    with pytest.raises(ValueError):
+        ctx.fastncc_match(rc, sc, flat, 9, 3)
+    with pytest.raises(ValueError):
+        ctx.register_pair(dev(pair.ref), dev(pair.sen), dev(pair.points), 9, 3,
+                          out=torch.empty((1, 6), dtype=torch.int32, device="cuda"))
+    src = torch.zeros((10, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        ctx.fastncc_ransac(src, src, torch.zeros((4, 3), dtype=torch.int32, device="cuda"))   # projective: 4 wide
+    with pytest.raises(ValueError):
+        ctx.rectify(dev(pair.ref), torch.eye(3, dtype=torch.float64, device="cuda").reshape(-1))
+    ctx.sync()
+
 def test_u16_input_matches_scaled_float(b, ctx, orc):
     """sfoc_build_u16: a 16-bit image is read as v / 65535 (the input step
     of the 10000^2 workload); the cube equals the oracle's on the FP64

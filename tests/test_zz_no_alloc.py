@@ -67,6 +67,11 @@ def test_static_build_rejects_oversize_and_bf16(b, ctx):
     out = torch.empty((12, H, W), dtype=torch.float32, device="cuda")
     with pytest.raises(b.SfocError, match="static scratch"):
         ctx.sfoc_build_static(x, out)
+    small = x[:64, :64].contiguous()
+    out64 = torch.empty((12, 64, 64), dtype=torch.float32, device="cuda")
     with pytest.raises(b.SfocError):
-        ctx.sfoc_build_static(x[:64, :64].contiguous(), out, p=b.params(dtype=b.DTYPE_BF16))
+        ctx.sfoc_build_static(small, out64, p=b.params(dtype=b.DTYPE_BF16))
+    # an output of the wrong shape never reaches the library
+    with pytest.raises(ValueError):
+        ctx.sfoc_build_static(small, out)
     ctx.sync()
