@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sar2048", choices=["inverting512", "sar2048"])
-    ap.add_argument("--forms", default="bf16,f32")
+    ap.add_argument("--forms", default="bf16,f32,f32direct",
+                    help="bf16: BF16 cubes, tensor-core correlation; f32: F32 cubes, automatic correlation (the "
+                         "Fourier form where m + 2R <= 128); f32direct: F32 cubes, the plain direct correlation")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--noise-sweep", action="store_true",
@@ -172,7 +174,7 @@ class ClockSampler:
 
 def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
     p = b.params(dtype=b.DTYPE_BF16 if form == "bf16" else b.DTYPE_F32)
-    corr = b.CORR_AUTO
+    corr = b.CORR_DIRECT_F32 if form == "f32direct" else b.CORR_AUTO
     d_ref = torch.from_numpy(pair.ref).cuda()
     d_sen = torch.from_numpy(pair.sen).cuda()
     d_pts = torch.from_numpy(pair.points).cuda()
@@ -392,6 +394,34 @@ def fft_flops(pair, z=12):
     return z * ((pair.m + 2 * pair.R + L) * t + 12.0 * L * (L // 2 + 1)) + (L // 2 + 1 + P1) * t
 
 
+def form_roofline(form, pair, per_launch_ms, processed, pk, workload):
+    """Roofline of a form's correlation kernel: the algorithmic work of the
+    points it processed over its mean launch time (CUDA events), against the
+    peak of the unit that bounds it."""
+    traffic = CORR_TRAFFIC_SAR2048.get(form) if workload == "sar2048" else None
+    secs = per_launch_ms * 1e-3
+    if form == "bf16":
+        ach = corr_flops(pair) * processed / secs / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
+                "frac": ach / pk["bf16"], "traffic": traffic,
+                "kernel": tc_kernel(pair) + " (tcgen05 bf16, fp32 accumulate)",
+                "peak_src": "bf16_tflops burst, %s" % pk["src"],
+                "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
+    fp32_src = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal, no FP32 peak measured)"
+    if form == "f32" and fft_side(pair):
+        ach = fft_flops(pair) * processed / secs / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "k_corr_fft<%d> (FP32 Fourier correlation, Eq. 13)" % fft_side(pair),
+                "peak_src": fp32_src,
+                "work": "5 L log2 L flop per length-L transform (z (m+2R+L) forward, L/2+1+2R+1 inverse) "
+                        "+ 12 flop per cross-spectrum bin, per processed point"}
+    ach = corr_flops(pair) * processed / secs / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
+            "kernel": "k_corr_f32 (direct FP32 FMA)", "peak_src": fp32_src,
+            "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
+
 # Descriptor variants compared under noise: the paper's SFOC, F-SFOC (first
 # order only, Sec. 4.2) and the two weaker smoothings of Fig. 3 (Sec. 2.1).
 NOISE_VARIANTS = {
@@ -546,30 +576,8 @@ def main():
         per_step = {k: v[0] / args.steps for k, v in st.items()}
         sfoc_ms = per_step["steer"] + per_step["smooth"]
         corr_ms, corr_n = st["correlation"]
-        flops = corr_flops(pair) * r["valid"]          # processed points only
         per_launch = corr_ms / max(1, corr_n)
-        ach = flops / (per_launch * 1e-3) / 1e12
-        traffic = CORR_TRAFFIC_SAR2048.get(form) if args.workload == "sar2048" else None
-        if form == "bf16":
-            roof = {"bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
-                    "frac": ach / pk["bf16"], "traffic": traffic,
-                    "kernel": tc_kernel(pair) + " (tcgen05 bf16, fp32 accumulate)",
-                    "peak_src": "bf16_tflops burst, %s" % pk["src"],
-                    "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
-        elif fft_side(pair):
-            ach = fft_flops(pair) * r["valid"] / (per_launch * 1e-3) / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
-                    "kernel": "k_corr_fft<%d> (FP32 Fourier correlation, Eq. 13)" % fft_side(pair),
-                    "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal, no FP32 peak measured)",
-                    "work": "5 L log2 L flop per length-L transform (z (m+2R+L) forward, L/2+1+2R+1 inverse) "
-                            "+ 12 flop per cross-spectrum bin, per processed point"}
-        else:
-            roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
-                    "kernel": "k_corr_f32 (FP32 FMA)",
-                    "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal, no FP32 peak measured)",
-                    "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
+        roof = form_roofline(form, pair, per_launch, r["valid"], pk, args.workload)
         return dict(value=job_value(r["matched_all"], args.steps, r["ms_max"]), ms_per_step=r["ms_max"] / args.steps,
                     sfoc_mpix_s=2 * pair.ref.size / (sfoc_ms * 1e-3) / 1e6 if sfoc_ms > 0 else None,
                     stage_ms_per_step={k: round(v, 4) for k, v in per_step.items()}, roofline=roof,

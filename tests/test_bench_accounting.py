@@ -93,3 +93,23 @@ def test_noise_series_are_the_papers():
         assert lv[0] == 0 and lv[-1] == pytest.approx(float(vals[vmax]))
         assert all(b - a == pytest.approx(float(vals[step])) for a, b in zip(lv, lv[1:]))
     assert bench.NOISE_TEMPLATE == int(vals["noise_template"])
+
+
+def test_form_rooflines_reproduce_the_last_line():
+    """form_roofline against the figures of a GB300 run of the 2048^2
+    workload: 999 processed points, 0.79 ms per Fourier launch, 1.1598 ms per
+    column-form launch, the measured bf16 peak 1921.3 TFLOP/s."""
+    p = _pair(81, 20)
+    pk = {"bf16": 1921.3, "src": "measured"}
+    f = bench.form_roofline("f32", p, 0.79, 999, pk, "sar2048")
+    assert f["bound"] == "alu" and f["kernel"].startswith("k_corr_fft<128>")
+    assert f["achieved"] == pytest.approx(19.04, rel=2e-3) and f["frac"] == pytest.approx(0.2364, rel=2e-3)
+    assert f["traffic"] == 407.75e6
+    t = bench.form_roofline("bf16", p, 1.1598, 999, pk, "sar2048")
+    assert t["bound"] == "tensor" and t["kernel"].startswith("k_corr_tc_col")
+    assert t["achieved"] == pytest.approx(228.0, rel=2e-3) and t["traffic"] is None
+    d = bench.form_roofline("f32direct", p, 7.51, 999, pk, "sar2048")
+    assert d["kernel"].startswith("k_corr_f32") and d["achieved"] == pytest.approx(35.2, rel=5e-3)
+    assert d["traffic"] is None
+    # the f32 form without a transform size falls back to the direct kernel's roofline
+    assert bench.form_roofline("f32", _pair(101, 40), 7.0, 10, pk, "inverting512")["kernel"].startswith("k_corr_f32")
