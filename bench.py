@@ -11,11 +11,13 @@ Default workload: 2048x2048 optical-like reference vs SAR-like sensed image
 template 81x81, search radius 20, 12 SFOC channels.
 
 Metric: matched control points per second (points whose status is OK),
-whole job over all ranks; SFOC Mpix/s is reported beside it.  Both forms
-are measured with the library's automatic correlation choice: the BF16
-cube + tcgen05 correlation form and the FP32 form (the Fourier correlation
-of Eq. 13 when m + 2R <= 128, else the direct FP32 kernel); the line's
-`value` is the faster form, the other is reported under `forms`.
+whole job over all ranks; SFOC Mpix/s is reported beside it.  Three forms
+are measured: the BF16 cube + tcgen05 correlation form and the FP32 form,
+both with the library's automatic correlation choice (for F32 cubes the
+Fourier correlation of Eq. 13 when m + 2R <= 128, else the direct FP32
+kernel), and the plain FP32 form (F32 cubes, direct correlation); the
+line's `value` is the fastest form, the others are reported under
+`forms`.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs its own replica (weak scaling).
