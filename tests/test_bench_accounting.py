@@ -113,3 +113,13 @@ def test_form_rooflines_reproduce_the_last_line():
     assert d["traffic"] is None
     # the f32 form without a transform size falls back to the direct kernel's roofline
     assert bench.form_roofline("f32", _pair(101, 40), 7.0, 10, pk, "inverting512")["kernel"].startswith("k_corr_f32")
+
+
+def test_fast_roofline():
+    """Block FAST on a 2048^2 image in 0.0843 ms (a GB300 run): 179 FP32 ops
+    per pixel give 8.9 Top/s, 22 % of 40.3 Top/s; the image read is 199 GB/s."""
+    assert bench.FAST_OPS_PER_PX == 179
+    r = bench.fast_roofline(0.0843, 2048, 2048, 6780.0)
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(40.28, rel=1e-3)
+    assert r["achieved"] == pytest.approx(8.906, rel=2e-3) and r["frac"] == pytest.approx(0.2211, rel=3e-3)
+    assert r["hbm_gbs"] == pytest.approx(199.0, rel=2e-3)
