@@ -101,6 +101,14 @@ def _fake_library(fail_ransac=False):
         def fast_blocks(self, img, t, gy, gx, margin):
             return torch.zeros((gy * gx, 2), dtype=torch.int32), torch.zeros(gy * gx)
 
+        def sfoc_build(self, img, p=None):
+            return object()
+
+        def fastncc_match(self, ref, sen, pts, m, R):
+            raw = torch.zeros((pts.shape[0], 6), dtype=torch.int32)
+            self._fill(pts, raw)
+            return {"raw": raw}
+
     b.Context = Context
     pkg = types.ModuleType("paper_2202_13347_gb300")
     pkg.build = lambda *a, **k: None
@@ -176,3 +184,14 @@ def test_reference_arm_line(monkeypatch, capsys):
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert np.isfinite(line["cpu_baseline"]["sfoc_mpix_s"])
+
+
+def test_noise_sweep_line(monkeypatch, capsys):
+    """--noise-sweep: one line with the CMR of every variant at every level
+    of both noise series (Sec. 4.3)."""
+    line = _run(monkeypatch, capsys, ["--noise-sweep"])
+    assert line["template"] == 80 and line["pairs"] == 4
+    assert set(line["cmr"]) == set(bench.NOISE_VARIANTS)
+    for v in line["cmr"].values():
+        for kind, levels in bench.NOISE_LEVELS.items():
+            assert len(v[kind]) == len(levels) and all(0.0 <= c <= 1.0 for c in v[kind])
