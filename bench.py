@@ -604,7 +604,7 @@ def main():
                     matched_per_step=r["matched"], gpu_launches=r["launches"], clocks=r["clocks"])
 
     summ = {f: summarize(results[f], f) for f in forms if "error" not in results[f]}
-    main_form = max(summ, key=lambda f: summ[f]["value"])  # the faster form heads the line
+    main_form = max(summ, key=lambda f: summ[f]["value"])  # the fastest form heads the line
     main = summ[main_form]
     r0 = results[main_form]
     e2e = None
