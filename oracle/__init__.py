@@ -33,6 +33,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sfoc_oracle.c")
 _SRCS = [_SRC, os.path.join(_HERE, "ransac_oracle.c"), os.path.join(_HERE, "fast_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
+# A prebuilt oracle library to load instead of the in-tree build: the
+# mutation tests point this at builds with one planted mistake each.
+_LIB_OVERRIDE = os.environ.get("SFOC_ORACLE_LIB")
 
 # status codes (values fixed by the paper-derived conventions, independent of
 # the CUDA library's header)
@@ -41,6 +44,8 @@ OK, OUT_OF_BOUNDS, FLAT_TEMPLATE, PEAK_ON_EDGE, NAN_INPUT = 0, 1, 2, 3, 4
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc -O2 -fopenmp (plain C, portable)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp] + _SRCS + ["-lm"]

@@ -100,6 +100,12 @@ def test_suppression_tie_keeps_the_first(orc):
     assert np.count_nonzero(s) == 2
     pts, sc = orc.fast_blocks(s_img, 0.05, 1, 1, 3)
     assert tuple(pts[0]) == (12, 14)
+    # the same tie across a block boundary (columns [0, 15) | [15, 30)): the
+    # second pixel is suppressed, so the right block has no corner at all
+    b_img = blank(0.5, 30)
+    b_img[14, 14] = b_img[14, 15] = 0.3
+    pts, sc = orc.fast_blocks(b_img, 0.05, 1, 2, 3)
+    assert tuple(pts[0]) == (14, 14) and tuple(pts[1]) == (-1, -1) and sc[1] == 0
 
 
 def test_flat_image_and_margin(orc):

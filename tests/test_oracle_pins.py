@@ -303,6 +303,27 @@ def test_first_order_only_variant(orc):
 
 
 
+@pytest.mark.parametrize("a,b,c", [(1, 3, -2), (-2, 1, 1), (0, 2, 0)])
+def test_second_order_channel_is_the_directional_second_derivative(orc, a, b, c):
+    """Eq. 7 read with x right and y down: second-order channel theta is the
+    second derivative along (cos theta, -sin theta).  On a quadratic image
+    I = a x^2 + b x y + c y^2 that derivative is exact from the image itself,
+    2a cos^2 - 2b cos sin + 2c sin^2, with no kernel involved.  The sampled,
+    truncated kernels reproduce d^2/dx^2 and d^2/dx dy of a quadratic to
+    within 1.8 % and 0.7 % (their second moments), so each term may be off
+    by 2 %; a flipped or halved cross term is off by far more.  Read
+    unsmoothed (sigma_d = 0), signed (rectify off) and before the group
+    normalisation (eps = 1e30: an exact division by 1e30)."""
+    n = 31
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64) - 15          # x right, y down, origin at the centre
+    img = (a * xx * xx + b * xx * yy + c * yy * yy).astype(np.float32)   # integers: exact in FP32
+    D = orc.sfoc_roi(img, orc.params(sigma_d1=0.0, sigma_d2=0.0, eps=1e30, rectify=False), 15, 15, 1, 1).data
+    D = D[:, 0, 0] * 1e30
+    for k, th in enumerate(_theta(6)):
+        cs, sn = math.cos(th), math.sin(th)
+        terms = (2 * a * cs * cs, -2 * b * cs * sn, 2 * c * sn * sn)
+        assert D[6 + k] == pytest.approx(sum(terms), abs=0.02 * sum(abs(t) for t in terms) + 1e-9), k
+
 def _pre_norm(orc, img, **kw):
     """The input D of the group normalisation: with eps = 1e30 the division
     by ||D|| + eps is an exact division by 1e30 (||D|| is far below the
@@ -508,6 +529,10 @@ def test_parabola_vertex(orc):
     assert orc.parabola(0.0, 1.0, 2.0) == 0.0
     assert orc.parabola(0.0, 0.0, 0.0) == 0.0
     assert abs(orc.parabola(0.99, 1.0, 0.0)) <= 0.5
+    # vertices inside the clamp are returned as they are, outside it at +-0.5
+    for v, want in ((0.45, 0.45), (-0.45, -0.45), (0.7, 0.5), (-0.9, -0.5)):
+        f = [-(x - v) ** 2 for x in (-1.0, 0.0, 1.0)]
+        assert orc.parabola(*f) == pytest.approx(want, abs=1e-12)
 
 
 def test_argmax_tiebreak_and_edges(orc):
@@ -538,6 +563,14 @@ def test_status_out_of_bounds_and_flat(orc):
     assert out["status"][3] == 1
     out2 = orc.match(_cube(ref), _cube(sen), np.array([[13, 6]], np.int32), 7, 3)
     assert out2["status"][0] == 2                # template is constant
+    # the flatness threshold (a reading: variance <= 1e-6 per value): a
+    # checkerboard of 1e-5 per value is texture, one of 5e-7 is flat
+    cb = np.where(np.add.outer(np.arange(7), np.arange(7)) % 2 == 0, 1.0, -1.0)
+    for var, flat in ((1e-5, False), (5e-7, True)):
+        s2 = sen.copy()
+        s2[:, 3:10, 10:17] = 0.5 + np.sqrt(var) * cb
+        st = orc.match(_cube(ref), _cube(s2), np.array([[13, 6]], np.int32), 7, 3)["status"][0]
+        assert (st == 2) == flat, (var, st)
 
 
 def test_even_template_centering(orc):
