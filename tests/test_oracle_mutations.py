@@ -58,6 +58,25 @@ MUTATIONS = [
     ("fast_arcs_of_8", F, "for (int j = 1; j < 9; ++j) {", "for (int j = 1; j < 8; ++j) {"),
     ("fast_min_polarity", F, "const float m = mb > md ? mb : md;", "const float m = mb < md ? mb : md;"),
     ("nms_tie_rule", F, "if (before ? !(v > u) : !(v >= u)) return 0;", "if (!(v >= u)) return 0;"),
+    ("g2_zero_mean_dropped", S, "        for (int x = 0; x < n; ++x) gxx[y * n + x] -= m;",
+     "        for (int x = 0; x < n; ++x) gxx[y * n + x] -= 0.0 * m;"),
+    ("gxy_sign", S, "gxy[(y + K) * n + (x + K)] = ((double)x * y / (2.0 * OR_PI * s6)) * e;",
+     "gxy[(y + K) * n + (x + K)] = (-(double)x * y / (2.0 * OR_PI * s6)) * e;"),
+    ("dilation_rows_undilated", S, "w[(r * u + r * Kd) * n + (r * t + r * Kd)] = g[u + Kd] * g[t + Kd];",
+     "w[(u + r * Kd) * n + (r * t + r * Kd)] = g[u + Kd] * g[t + Kd];"),
+    ("group_boundary", S, "int g = c < no ? 0 : 1;", "int g = c <= no ? 0 : 1;"),
+    ("window_mean_n_minus_1", S, "double sbar = ssum / N;", "double sbar = ssum / (N - 1.0);"),
+    ("ncc_without_sqrt", S, "else v = num / sqrt(vS * vT);", "else v = num / (vS * vT);"),
+    ("even_template_half", S, "int oracle_template_half(int m) { return (m % 2) ? (m - 1) / 2 : m / 2; }",
+     "int oracle_template_half(int m) { return (m % 2) ? (m - 1) / 2 : m / 2 - 1; }"),
+    ("refit_second_row_dropped", R, "M[a * nu + c] += r1[a] * r1[c] + r2[a] * r2[c];",
+     "M[a * nu + c] += r1[a] * r1[c];"),
+    ("rmse_without_sqrt", R, "*rmse = ncm ? sqrt(se / ncm) : 0.0;", "*rmse = ncm ? se / ncm : 0.0;"),
+    ("rectify_right_edge_open", R, "if (u >= 0.0 && t >= 0.0 && u <= W - 1 && t <= H - 1) {",
+     "if (u >= 0.0 && t >= 0.0 && u < W - 1 && t < H - 1) {"),
+    ("rectify_forward_map", R, "for (int k = 0; k < 9; ++k) inv[k] /= inv[8];",
+     "for (int k = 0; k < 9; ++k) inv[k] = (k == 0 ? a : k == 1 ? b : k == 2 ? c : k == 3 ? d : k == 4 ? e : "
+     "k == 5 ? f : k == 6 ? g : k == 7 ? h : i) / i;"),
 ]
 
 

@@ -112,6 +112,13 @@ def test_match_quality_closed_form(orc):
     assert q["ncm"] == 6
     assert q["cmr"] == pytest.approx(0.6, abs=1e-15)
     assert q["rmse"] == pytest.approx(1.0, abs=1e-12)
+    # Eq. 22 is a root mean square: correct matches at 0.6 and 1.2 px give sqrt(0.9), not 0.9
+    d2 = apply_model(P, src)
+    d2[:3] += np.array([0.36, 0.48])
+    d2[3:6] += np.array([0.72, 0.96])
+    d2[6:] += np.array([6.0, 8.0])
+    q = orc.match_quality(P, src, d2)
+    assert q["ncm"] == 6 and q["rmse"] == pytest.approx(np.sqrt(0.9), abs=1e-12)
     valid = np.ones(10, bool)
     valid[6:] = False                       # only the correct ones count as matches
     q = orc.match_quality(P, src, dst, valid=valid)
