@@ -117,3 +117,14 @@ def test_flat_image_and_margin(orc):
     assert tuple(pts[0]) == (-1, -1)
     with pytest.raises(ValueError):
         orc.fast_blocks(img, 0.05, 0, 1, 3)
+
+
+def test_blocks_partition_a_non_square_image(orc):
+    """Block rows are [by H / grid_y, (by + 1) H / grid_y) and columns
+    [bx W / grid_x, ...) (Sec. 3.1.1's partition): on a 30 x 60 image in
+    3 x 2 blocks a single corner at (x, y) = (45, 25) is block 2 * 2 + 1."""
+    img = np.full((30, 60), 0.5, np.float32)
+    img[25, 45] = 0.25                          # a dark spot: every circle pixel is brighter
+    pts, sc = orc.fast_blocks(img, 0.05, 3, 2, 3)
+    assert tuple(pts[5]) == (45, 25) and sc[5] == np.float32(0.25)
+    assert all(tuple(p) == (-1, -1) for k, p in enumerate(pts) if k != 5)

@@ -77,6 +77,19 @@ MUTATIONS = [
     ("rectify_forward_map", R, "for (int k = 0; k < 9; ++k) inv[k] /= inv[8];",
      "for (int k = 0; k < 9; ++k) inv[k] = (k == 0 ? a : k == 1 ? b : k == 2 ? c : k == 3 ? d : k == 4 ? e : "
      "k == 5 ? f : k == 6 ? g : k == 7 ? h : i) / i;"),
+    ("angles_over_2pi", S, "        ct[k] = cos(k * OR_PI / no);\n        st[k] = sin(k * OR_PI / no);",
+     "        ct[k] = cos(2.0 * k * OR_PI / no);\n        st[k] = sin(2.0 * k * OR_PI / no);"),
+    ("radius_floor", S, "return (int)ceil(mult * sigma - 1e-9);", "return (int)floor(mult * sigma + 1e-9);"),
+    ("zero_padded_borders", S,
+     "for (int qx = -K; qx <= K; ++qx) acc += kr[qx + K] * (double)row[clampi(x - qx, 0, W - 1)];",
+     "for (int qx = -K; qx <= K; ++qx) acc += (x - qx < 0 || x - qx >= W) ? 0.0 : "
+     "kr[qx + K] * (double)row[clampi(x - qx, 0, W - 1)];"),
+    ("eq13_conjugate_on_s", S, "acci[q] += si[q] * tr[q] - sr[q] * ti[q];", "acci[q] += sr[q] * ti[q] - si[q] * tr[q];"),
+    ("fast_circle_offset", F, "{1, 3},\n", "{1, 2},\n"),
+    ("fast_blocks_rows_by_w", F, "const int y0 = (int)((long long)by * H / grid_y), y1 = (int)((long long)(by + 1) * H / grid_y);",
+     "const int y0 = (int)((long long)by * W / grid_y), y1 = (int)((long long)(by + 1) * W / grid_y);"),
+    ("rectify_u_from_y", R, "const double u = (inv[0] * x + inv[1] * y + inv[2]) / w;",
+     "const double u = (inv[1] * x + inv[0] * y + inv[2]) / w;"),
 ]
 
 
