@@ -31,6 +31,15 @@ def test_uniform_circle_scores_its_contrast(orc, sign):
     assert s[7, 7] == np.float32(0.25)
 
 
+def test_score_must_exceed_the_threshold(orc):
+    """A pixel is a corner when its score exceeds t (the segment test's
+    strict inequality): a uniform circle of contrast exactly t is not one."""
+    img = blank(0.75)
+    img[7, 7] = 0.5                             # contrast 0.25, exact in FP32
+    assert orc.fast_score(img, t=0.25)[7, 7] == 0.0
+    assert orc.fast_score(img, t=0.2499)[7, 7] == np.float32(0.25)
+
+
 @pytest.mark.parametrize("start", range(16))
 @pytest.mark.parametrize("length,corner", [(9, True), (8, False), (12, True)])
 def test_arcs(orc, start, length, corner):

@@ -90,6 +90,16 @@ MUTATIONS = [
      "const int y0 = (int)((long long)by * W / grid_y), y1 = (int)((long long)(by + 1) * W / grid_y);"),
     ("rectify_u_from_y", R, "const double u = (inv[0] * x + inv[1] * y + inv[2]) / w;",
      "const double u = (inv[1] * x + inv[0] * y + inv[2]) / w;"),
+    ("norm_over_all_channels", S, "for (int k = 0; k < no; ++k) n2s += D[g * no + k] * D[g * no + k];",
+     "for (int k = 0; k < z; ++k) n2s += D[k] * D[k];"),
+    ("eps_inside_sqrt", S, "double den = sqrt(n2s) + p->eps;", "double den = sqrt(n2s + p->eps);"),
+    ("rates_averaged", S, "                D[c] = acc;", "                D[c] = acc / p->n_dil;"),
+    ("ransac_projective_sign", R, "        r1[6] = -x * xp; r1[7] = -y * xp;", "        r1[6] = x * xp; r1[7] = -y * xp;"),
+    ("eq9_square_plane", S, "g2[i] += v * v;", "g2[i] += v;"),
+    ("fast_threshold_inclusive", F, "return best > t ? best : 0.0f;", "return best >= t ? best : 0.0f;"),
+    ("abs_after_scale_sum", S,
+     "f += p->rectify ? fabs(v) : v;\n                }\n                F[((size_t)k * eh + yy) * ew + xx] = f;",
+     "f += v;\n                }\n                F[((size_t)k * eh + yy) * ew + xx] = p->rectify ? fabs(f) : f;"),
 ]
 
 
