@@ -299,3 +299,56 @@ def test_fixed_point_headroom():
     assert 128 * 128 * 5.7 * 2 ** 28 < 2 ** 45
     assert 128 * 128 * 2.0 * 2 ** 28 < 2 ** 45
     assert 128 * 128 * NON_FINITE + (1 << 45) < 1 << 63
+
+
+# --------------------------------------------------------------------------
+# NCC argmax (k_ncc_argmax): the reduction order cannot change the winner
+# --------------------------------------------------------------------------
+
+def _better(v, i, bv, bi):
+    return v > bv or (v == bv and i < bi)
+
+
+def _kernel_argmax(vals, threads=256):
+    """Strided scan per thread, a shuffle-down tree per warp (offsets 16..1),
+    then the warps' winners in order, all with `_better`; NaN skipped."""
+    P = len(vals)
+    bv = [-np.inf] * threads
+    bi = [2 ** 31 - 1] * threads
+    for t in range(threads):
+        for i in range(t, P, threads):
+            if vals[i] == vals[i] and _better(vals[i], i, bv[t], bi[t]):
+                bv[t], bi[t] = vals[i], i
+    wv, wi = [], []
+    for w in range(threads // 32):
+        lv, li = bv[32 * w:32 * w + 32], bi[32 * w:32 * w + 32]
+        o = 16
+        while o:
+            nv, ni = list(lv), list(li)
+            for lane in range(32 - o):               # shfl_down: lane reads lane + o
+                if _better(lv[lane + o], li[lane + o], lv[lane], li[lane]):
+                    nv[lane], ni[lane] = lv[lane + o], li[lane + o]
+            lv, li = nv, ni
+            o >>= 1
+        wv.append(lv[0])
+        wi.append(li[0])
+    v, i = wv[0], wi[0]
+    for w in range(1, len(wv)):
+        if _better(wv[w], wi[w], v, i):
+            v, i = wv[w], wi[w]
+    return i
+
+
+@pytest.mark.parametrize("R,seed", [(2, 0), (10, 1), (20, 2), (40, 3)])
+def test_argmax_reduction_picks_the_first_maximum(R, seed):
+    """Whatever thread and lane a value lands in, the winner is the first
+    maximum in row-major (dy, dx) order: the oracle's tie rule (NCC desc,
+    dy asc, dx asc).  Maps quantised to a few levels make ties common."""
+    rng = np.random.default_rng(seed)
+    P = (2 * R + 1) ** 2
+    for trial in range(5):
+        vals = np.round(rng.random(P) * 4) / 4
+        vals[rng.random(P) < 0.05] = np.nan
+        i = _kernel_argmax(list(vals))
+        finite = np.where(np.isnan(vals), -np.inf, vals)
+        assert i == int(np.argmax(finite))           # numpy's argmax: the first maximum
