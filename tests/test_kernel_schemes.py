@@ -237,7 +237,8 @@ def _fourier_form(S, T, m, R, L):
     return out
 
 
-@pytest.mark.parametrize("z,m,R,L", [(2, 5, 2, 64), (2, 20, 6, 64), (1, 40, 12, 64), (2, 1, 0, 64)])
+@pytest.mark.parametrize("z,m,R,L", [(2, 5, 2, 64), (2, 20, 6, 64), (1, 40, 12, 64), (2, 1, 0, 64),
+                                     (1, 30, 40, 128)])
 def test_fourier_form_dataflow(z, m, R, L):
     """Against Eq. 10 with the zero-mean template, i.e. the numerator of
     Eq. 9: sum S (T - mean T) = R_ST - R_S R_T / mnz."""
