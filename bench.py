@@ -474,6 +474,27 @@ def noise_sweep(args):
     b = pkg.load()
     torch.cuda.set_device(0)
     ctx = b.Context(torch.cuda.current_device())
+    # build rate of each variant's cube (CUDA events, median of 10) on the
+    # first pair's sensed image: the variants run other smoothing kernels
+    # than the paper's configuration
+    build_mpix = {}
+    probe = inverting_pair_512(seed=4301, H=1024, W=1024, n_side=14, m=NOISE_TEMPLATE, R=10)
+    d_probe = torch.from_numpy(probe.sen).cuda()
+    for v, kw in NOISE_VARIANTS.items():
+        pv = b.params(**kw)
+        cube = ctx.sfoc_build(d_probe, p=pv)
+        for _ in range(2):
+            cube = ctx.sfoc_build(d_probe, p=pv, out=cube)       # rebuilt in place: no allocation timed
+        ts = []
+        stream = torch.cuda.current_stream()
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cube = ctx.sfoc_build(d_probe, p=pv, out=cube)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        build_mpix[v] = round(probe.sen.size / (statistics.median(ts) * 1e-3) / 1e6, 1)
     seeds = (4301, 4302, 4303, 4304)
     cmr = {v: {k: np.zeros(len(L)) for k, L in NOISE_LEVELS.items()} for v in NOISE_VARIANTS}
     n_points = 0
@@ -502,6 +523,7 @@ def noise_sweep(args):
             "points": n_points, "template": NOISE_TEMPLATE, "search_radius": 10, "tolerance_px": 1.5,
             "noise_on": "sensed image", "levels": NOISE_LEVELS,
             "cmr": {v: {k: [round(float(x), 4) for x in a] for k, a in d.items()} for v, d in cmr.items()},
+            "sfoc_build_mpix_s": build_mpix, "build_image": "1024x1024",
             "data": "synthetic", "seconds": round(time.perf_counter() - t0, 1)}
     print(json.dumps(line))
 

@@ -101,8 +101,8 @@ def _fake_library(fail_ransac=False):
         def fast_blocks(self, img, t, gy, gx, margin):
             return torch.zeros((gy * gx, 2), dtype=torch.int32), torch.zeros(gy * gx)
 
-        def sfoc_build(self, img, p=None):
-            return object()
+        def sfoc_build(self, img, p=None, out=None):
+            return out if out is not None else object()
 
         def fastncc_match(self, ref, sen, pts, m, R):
             raw = torch.zeros((pts.shape[0], 6), dtype=torch.int32)
@@ -192,6 +192,7 @@ def test_noise_sweep_line(monkeypatch, capsys):
     line = _run(monkeypatch, capsys, ["--noise-sweep"])
     assert line["template"] == 80 and line["pairs"] == 4
     assert set(line["cmr"]) == set(bench.NOISE_VARIANTS)
+    assert set(line["sfoc_build_mpix_s"]) == set(bench.NOISE_VARIANTS)
     for v in line["cmr"].values():
         for kind, levels in bench.NOISE_LEVELS.items():
             assert len(v[kind]) == len(levels) and all(0.0 <= c <= 1.0 for c in v[kind])
