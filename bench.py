@@ -42,9 +42,8 @@ UNIT = "CP/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 FFT_SIZES = (64, 128)  # transform sides of the Fourier correlation (the smallest with m + 2R <= L)
 # DRAM bytes (read + write) per launch of each form's correlation kernel on
-# the 2048x2048 workload, from one ncu capture of the kernel as it stands
-# (profiles/k_corr_fft_sar2048.md); None where the kernel has changed since
-# its capture (the column form: profiles/k_corr_tc_col_sar2048.md).
+# the 2048x2048 workload, from one ncu capture of the kernel as it stands;
+# None where the kernel has changed since its capture.
 CORR_TRAFFIC_SAR2048 = {"bf16": None, "f32": 407.75e6}
 
 
@@ -224,19 +223,23 @@ FAST_OPS_PER_PX = 16 + 32 + 32 + 16 * 6 + 3
 FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12   # Top/s: one FP32 add / min / max per lane per clock
 
 
-def fast_roofline(ms, H, W, hbm_gbs):
+def fast_roofline(ms, H, W, hbm_gbs, pk=None):
     """Block FAST is bound by its score arithmetic, not by HBM (the image is
     read once, 4 B/px): achieved = FAST_OPS_PER_PX per pixel of the image
-    over the launch time, against one FP32 op per lane per clock."""
+    over the launch time, against one FP32 op per lane per clock (half the
+    measured scalar FMA flop rate, which counts 2 flop per FMA)."""
     ach = FAST_OPS_PER_PX * H * W / (ms * 1e-3) / 1e12
     gbs = 4.0 * H * W / (ms * 1e-3) / 1e9
-    return {"bound": "alu", "achieved": ach, "peak": FP32_OPS_PEAK, "unit": "Top/s", "frac": ach / FP32_OPS_PEAK,
+    if pk and pk.get("fp32_scalar"):
+        peak, src = pk["fp32_scalar"] / 2.0, "scalar FFMA chains of sfoc_measure_peaks, one op per lane per clock"
+    else:
+        peak, src = FP32_OPS_PEAK, "152 SMs x 128 FP32 lanes x 2070 MHz (nominal)"
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Top/s", "frac": ach / peak,
             "work": "%d FP32 ops per pixel (FAST-9 score by windowed min / max)" % FAST_OPS_PER_PX,
-            "peak_src": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal)",
-            "hbm_gbs": gbs, "hbm_frac": gbs / hbm_gbs}
+            "peak_src": src, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_gbs}
 
 
-def run_fast(torch, ctx, pair, hbm_gbs, reps=10, grid=32, t=0.05):
+def run_fast(torch, ctx, pair, hbm_gbs, reps=10, grid=32, t=0.05, pk=None):
     """Block-based FAST (Sec. 3.1.1) on the sensed image of the workload,
     timed apart from the step (CUDA events, median of reps)."""
     img = torch.from_numpy(pair.sen).cuda()
@@ -257,7 +260,7 @@ def run_fast(torch, ctx, pair, hbm_gbs, reps=10, grid=32, t=0.05):
     H, W = pair.sen.shape
     return dict(ms=ms, mpix_s=pair.sen.size / (ms * 1e-3) / 1e6, blocks=grid * grid,
                 points=int((pts[:, 0] >= 0).sum()), threshold=t, margin=margin,
-                roofline=fast_roofline(ms, H, W, hbm_gbs), launches=1)
+                roofline=fast_roofline(ms, H, W, hbm_gbs, pk), launches=1)
 
 
 def run_ransac(b, torch, ctx, pair, r, n_hyp=4096, reps=10, seed=7):
@@ -414,6 +417,15 @@ def fft_flops(pair, z=12):
     return z * ((pair.m + 2 * pair.R + L) * t + 12.0 * L * (L // 2 + 1)) + (L // 2 + 1 + P1) * t
 
 
+def fp32_peak(pk):
+    """FP32 TFLOP/s denominator and its source: the library's own FMA
+    microbenchmark (the faster of scalar FFMA and paired FFMA2 chains) when
+    it ran, else the nominal figure."""
+    if pk.get("fp32"):
+        return pk["fp32"], pk["fp32_src"]
+    return FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal: the microbenchmark did not run)"
+
+
 def form_roofline(form, pair, per_launch_ms, processed, pk, workload):
     """Roofline of a form's correlation kernel: the algorithmic work of the
     points it processed over its mean launch time (CUDA events), against the
@@ -427,18 +439,18 @@ def form_roofline(form, pair, per_launch_ms, processed, pk, workload):
                 "kernel": tc_kernel(pair) + " (tcgen05 bf16, fp32 accumulate)",
                 "peak_src": "bf16_tflops burst, %s" % pk["src"],
                 "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
-    fp32_src = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal, no FP32 peak measured)"
+    peak32, fp32_src = fp32_peak(pk)
     if form == "f32" and fft_side(pair):
         ach = fft_flops(pair) * processed / secs / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
+        return {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
+                "frac": ach / peak32, "traffic": traffic,
                 "kernel": "k_corr_fft<%d> (FP32 Fourier correlation, Eq. 13)" % fft_side(pair),
                 "peak_src": fp32_src,
                 "work": "5 L log2 L flop per length-L transform (z (m+2R+L) forward, L/2+1+2R+1 inverse) "
                         "+ 12 flop per cross-spectrum bin, per processed point"}
     ach = corr_flops(pair) * processed / secs / 1e12
-    return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
+    return {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
+            "frac": ach / peak32, "traffic": traffic,
             "kernel": "k_corr_f32 (direct FP32 FMA)", "peak_src": fp32_src,
             "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
 
@@ -590,6 +602,14 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     forms = [f for f in args.forms.split(",") if f]
     pk = peaks()
+    try:  # the FP32 peak of this device, by the library's own microbenchmark
+        mp = ctx.measure_peaks()
+        pk.update(fp32=max(mp["fp32_tflops"], mp["fp32x2_tflops"]), fp32_scalar=mp["fp32_tflops"],
+                  fp32_src="measured by sfoc_measure_peaks: %s FMA chains (scalar %.1f, paired %.1f TFLOP/s)" % (
+                      "paired FFMA2" if mp["fp32x2_tflops"] > mp["fp32_tflops"] else "scalar FFMA",
+                      mp["fp32_tflops"], mp["fp32x2_tflops"]), microbench=mp)
+    except Exception as e:  # noqa: BLE001
+        pk.update(microbench={"error": str(e)})
     results = {}
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if os.environ.get(
         "CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
@@ -650,7 +670,7 @@ def main():
     if rank == 0:
         rq = aux(run_ransac, b, torch, ctx, pair, r0)
         ransac, quality = (rq, None) if isinstance(rq, dict) else rq
-        fast = aux(run_fast, torch, ctx, pair, pk["hbm"])
+        fast = aux(run_fast, torch, ctx, pair, pk["hbm"], 10, 32, 0.05, pk)
         if world == 1 and not args.no_cpu_baseline:
             cpu = aux(cpu_baseline, pair)
     if rank != 0:
@@ -662,7 +682,9 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
             "sfoc_mpix_s": main["sfoc_mpix_s"], "stage_ms_per_step": main["stage_ms_per_step"],
             "forms": {f: {k: v for k, v in s.items() if k not in ("clocks",)} for f, s in summ.items()},
-            "ransac": ransac, "match_quality": quality, "fast": fast,
+            "ransac": ransac, "match_quality": quality, "fast": fast, "peaks": {
+                "hbm_gbs": pk["hbm"], "bf16_tflops": pk["bf16"], "src": pk["src"] + " (MEASURED_PEAKS.json)",
+                "microbench": pk.get("microbench")},
             "errors": {f: results[f]["error"] for f in forms if "error" in results[f]} or None}
     print(json.dumps(line))
 

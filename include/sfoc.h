@@ -136,8 +136,11 @@ typedef struct {
  * sfoc_ctx_launch_count 0). */
 SFOC_API sfoc_status sfoc_ctx_create(sfoc_ctx** out, int device, void* stream);
 SFOC_API sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx);
-/* Issues later calls on `stream`; first waits for the work already queued
- * on the previous stream (it shares the context's workspace). */
+/* Issues later calls on `stream`.  The work already queued on the previous
+ * stream shares the context's workspace, so the new stream is made to wait
+ * for it on the device (an event recorded on the previous stream; the host
+ * does not block).  SFOC_ERR_INVALID_ARG while either stream is being
+ * captured into a CUDA graph. */
 SFOC_API sfoc_status sfoc_ctx_set_stream(sfoc_ctx* ctx, void* stream);
 /* Blocks until the context's stream is idle; reports deferred device errors
  * (SFOC_ERR_CUDA, or SFOC_ERR_TIMEOUT when a bounded device wait expired). */
@@ -163,6 +166,23 @@ SFOC_API sfoc_status sfoc_ctx_enable_timing(sfoc_ctx* ctx, int enable);
  * and the number of launches since the last reset. */
 SFOC_API sfoc_status sfoc_ctx_stage_times(sfoc_ctx* ctx, double* ms_out, int64_t* launches_out);
 SFOC_API sfoc_status sfoc_ctx_reset_timing(sfoc_ctx* ctx);
+
+/* Peaks of this device measured by the library's own microbenchmarks (the
+ * denominators of roofline fractions): FP32 FMA chains as scalar FFMA and
+ * as paired FFMA2 (float2) instructions and FP64 FMA chains, in TFLOP/s
+ * (2 flop per FMA), and a float4 copy of 1 GiB to another 1 GiB, in GB/s
+ * of bytes read + written.  Each figure is the best of five timed launches
+ * (CUDA events) after a warm-up.  Synchronous; allocates 2 GiB (plus a
+ * small sink) for the copy and frees them before returning.  Not part of
+ * the paper's method.  SFOC_ERR_INVALID_ARG for a NULL output,
+ * SFOC_ERR_OOM / SFOC_ERR_CUDA when a buffer or a launch fails. */
+typedef struct {
+    double fp32_tflops;
+    double fp32x2_tflops;
+    double fp64_tflops;
+    double hbm_copy_gbs;
+} sfoc_peaks;
+SFOC_API sfoc_status sfoc_measure_peaks(sfoc_ctx* ctx, sfoc_peaks* out);
 
 /* ---- descriptor ----------------------------------------------------- */
 
@@ -204,8 +224,9 @@ SFOC_API sfoc_status sfoc_build(sfoc_ctx* ctx, const float* d_image, int H, int 
  *                n_orient with first_order_only); receives the cube.
  * Scratch: one library-owned device array of SFOC_STATIC_SCRATCH_FLOATS
  * floats (64 MiB) per device.  A call needs z*roundup(W,32)*H + 2*H*W
- * floats of it (12 channels: up to about 1024 x 1170 pixels); larger
- * images return SFOC_ERR_UNSUPPORTED with the sizes in the error string.
+ * floats of it (12 channels at H = 1024: W up to 1152, while W = 1153
+ * already needs 16,910,336); larger images return SFOC_ERR_UNSUPPORTED
+ * with the sizes in the error string.
  * The first call on a device looks up the array's address (this may load
  * the library's device code); make that first call before any stream
  * capture.  Calls that overlap in time on one device (several streams or

@@ -55,6 +55,11 @@ class Result(C.Structure):
                 ("sub_dy", C.c_float), ("status", C.c_int32)]
 
 
+class Peaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("fp32x2_tflops", C.c_double), ("fp64_tflops", C.c_double),
+                ("hbm_copy_gbs", C.c_double)]
+
+
 class Opts(C.Structure):
     _fields_ = [("corr_path", C.c_int), ("d_maps", C.c_void_p)]
 
@@ -76,6 +81,7 @@ _SIGS = {
     "sfoc_ctx_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "sfoc_ctx_reset_timing": (C.c_int, [_P]),
     "sfoc_params_default": (C.c_int, [C.POINTER(Params)]),
+    "sfoc_measure_peaks": (C.c_int, [_P, C.POINTER(Peaks)]),
     "sfoc_build": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, C.POINTER(C.c_double), C.c_int, C.c_int,
                              C.POINTER(Params), C.POINTER(_P)]),
     "sfoc_cube_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -168,9 +174,13 @@ def _check_host(t, name, dtype):
         raise ValueError("%s must be a contiguous host %s tensor" % (name, dtype))
 
 
-def _check_cuda(t, name, dtype=None):
+def _check_cuda(t, name, dtype=None, device=None):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
+    if device is not None and t.device != device:
+        # the library runs its kernels on the context's device; a pointer into
+        # another GPU's memory is not valid there
+        raise ValueError("%s is on %s, the context on %s" % (name, t.device, device))
     if dtype is not None and t.dtype != dtype:
         raise ValueError("%s must be %s" % (name, dtype))
     if not t.is_contiguous():
@@ -229,7 +239,8 @@ class Context:
 
     def __init__(self, device=0, stream=None):
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
-        idx = self.device.index if self.device.index is not None else 0
+        idx = self.device.index if self.device.index is not None else torch.cuda.current_device()
+        self.device = torch.device("cuda", idx)
         if stream is None:
             stream = torch.cuda.current_stream(idx)
         self.stream = stream
@@ -238,6 +249,9 @@ class Context:
         if rc != OK:
             raise SfocError(rc, "sfoc_ctx_create failed")
         self.h = h
+
+    def _cuda(self, t, name, dtype=None):
+        _check_cuda(t, name, dtype, self.device)
 
     def _chk(self, rc):
         if rc != OK:
@@ -264,6 +278,13 @@ class Context:
     def reserve(self, nbytes):
         self._chk(lib().sfoc_ctx_reserve(self.h, int(nbytes)))
 
+    def measure_peaks(self):
+        """This device's FP32 / FP32x2 / FP64 TFLOP/s and HBM copy GB/s,
+        measured by the library's microbenchmarks (synchronous)."""
+        pk = Peaks()
+        self._chk(lib().sfoc_measure_peaks(self.h, C.byref(pk)))
+        return {f: getattr(pk, f) for f, _ in Peaks._fields_}
+
     STAGES = ("steer", "smooth", "integral", "template_stats", "correlation", "ncc_argmax", "other")
 
     def enable_timing(self, on=True):
@@ -285,7 +306,7 @@ class Context:
 
     # -- paper-named calls -------------------------------------------------
     def sfoc_build(self, image: torch.Tensor, scales=None, n_orient=0, p: Params = None, out: Cube = None) -> Cube:
-        _check_cuda(image, "image", torch.float32)
+        self._cuda(image, "image", torch.float32)
         H, W = image.shape
         arr = None
         if scales is not None:
@@ -314,8 +335,8 @@ class Context:
     def sfoc_build_static(self, image: torch.Tensor, out: torch.Tensor, p: Params = None) -> torch.Tensor:
         """sfoc_build into the caller's dense float32 [z][H][W] tensor `out`,
         with the library's fixed scratch array instead of the workspace."""
-        _check_cuda(image, "image", torch.float32)
-        _check_cuda(out, "out", torch.float32)
+        self._cuda(image, "image", torch.float32)
+        self._cuda(out, "out", torch.float32)
         H, W = image.shape
         _check_shape(out, "out", (_channels(p), H, W))
         self._chk(lib().sfoc_build_static(self.h, _ptr(image), H, W, W, C.byref(p) if p is not None else None,
@@ -324,7 +345,7 @@ class Context:
 
     def fastncc_match(self, ref: Cube, sen: Cube, points: torch.Tensor, template_size: int, search_radius: int,
                       corr_path=CORR_AUTO, want_maps=False):
-        _check_cuda(points, "points", torch.int32)
+        self._cuda(points, "points", torch.int32)
         n = points.shape[0]
         _check_shape(points, "points", (n, 2))
         raw = torch.empty((n, 6), dtype=torch.int32, device=self.device)
@@ -343,13 +364,13 @@ class Context:
 
     def register_pair(self, ref: torch.Tensor, sen: torch.Tensor, points: torch.Tensor, template_size: int,
                       search_radius: int, p: Params = None, corr_path=CORR_AUTO, out: torch.Tensor = None):
-        _check_cuda(ref, "ref", torch.float32)
-        _check_cuda(sen, "sen", torch.float32)
-        _check_cuda(points, "points", torch.int32)
+        self._cuda(ref, "ref", torch.float32)
+        self._cuda(sen, "sen", torch.float32)
+        self._cuda(points, "points", torch.int32)
         n = points.shape[0]
         _check_shape(points, "points", (n, 2))
         if out is not None:
-            _check_cuda(out, "out", torch.int32)
+            self._cuda(out, "out", torch.int32)
             _check_shape(out, "out", (n, 6))
         raw = out if out is not None else torch.empty((n, 6), dtype=torch.int32, device=self.device)
         o = Opts(int(corr_path), None)
@@ -382,7 +403,7 @@ class Context:
     def sfoc_build_batch(self, images, p: Params = None, outs=None):
         n = len(images)
         for i, im in enumerate(images):
-            _check_cuda(im, "images[%d]" % i, torch.float32)
+            self._cuda(im, "images[%d]" % i, torch.float32)
         ptrs = (C.c_void_p * n)(*[im.data_ptr() for im in images])
         Hs = (C.c_int * n)(*[im.shape[0] for im in images])
         Ws = (C.c_int * n)(*[im.shape[1] for im in images])
@@ -402,7 +423,7 @@ class Context:
         if not (len(sens) == len(points) == len(template_sizes) == len(search_radii) == n):
             raise ValueError("refs, sens, points, template_sizes and search_radii must have the same length")
         for i, pt in enumerate(points):
-            _check_cuda(pt, "points[%d]" % i, torch.int32)
+            self._cuda(pt, "points[%d]" % i, torch.int32)
             _check_shape(pt, "points[%d]" % i, (pt.shape[0], 2))
         outs = [torch.empty((p.shape[0], 6), dtype=torch.int32, device=self.device) for p in points]
         R = (C.c_void_p * n)(*[c.handle for c in refs])
@@ -419,7 +440,7 @@ class Context:
     def fast_blocks(self, image: torch.Tensor, threshold=0.05, grid_y=32, grid_x=32, margin=3):
         """Block-based FAST: (points (grid_y * grid_x, 2) int32 (x, y; -1 for
         an empty block), scores float32) on the device."""
-        _check_cuda(image, "image", torch.float32)
+        self._cuda(image, "image", torch.float32)
         H, W = image.shape
         nb = int(grid_y) * int(grid_x)
         pts = torch.empty((nb, 2), dtype=torch.int32, device=self.device)
@@ -431,15 +452,15 @@ class Context:
     def rectify(self, image: torch.Tensor, model: torch.Tensor, out_shape=None, fill=0.0, out=None):
         """The sensed image resampled into the reference frame with the
         (3, 3) float64 device model (sensed -> reference), bilinear."""
-        _check_cuda(image, "image", torch.float32)
-        _check_cuda(model, "model", torch.float64)
+        self._cuda(image, "image", torch.float32)
+        self._cuda(model, "model", torch.float64)
         _check_shape(model, "model", (3, 3))
         H, W = image.shape
         oh, ow = out_shape or (H, W)
         if out is None:
             out = torch.empty((oh, ow), dtype=torch.float32, device=self.device)
         else:
-            _check_cuda(out, "out", torch.float32)
+            self._cuda(out, "out", torch.float32)
             _check_shape(out, "out", (oh, ow))
         self._chk(lib().sfoc_rectify(self.h, _ptr(image), H, W, W, _ptr(model), C.c_float(fill), oh, ow, _ptr(out)))
         return out
@@ -447,8 +468,8 @@ class Context:
     def points_from_results(self, points: torch.Tensor, raw: torch.Tensor):
         """Control-point pairs of a match: (src, dst) float64 (n, 2) and the
         uint8 valid flags (status OK)."""
-        _check_cuda(points, "points", torch.int32)
-        _check_cuda(raw, "results", torch.int32)
+        self._cuda(points, "points", torch.int32)
+        self._cuda(raw, "results", torch.int32)
         n = points.shape[0]
         _check_shape(points, "points", (n, 2))
         _check_shape(raw, "results", (n, 6))
@@ -465,11 +486,11 @@ class Context:
         given minimal samples (int32 (n_hyp, 4), or (n_hyp, 3) for the affine
         model).  Returns {H (3, 3) float64, inlier bool (n,), best, count,
         scores (n_hyp,) when asked} on the device (best/count as a tensor)."""
-        _check_cuda(src, "src", torch.float64)
-        _check_cuda(dst, "dst", torch.float64)
-        _check_cuda(samples, "samples", torch.int32)
+        self._cuda(src, "src", torch.float64)
+        self._cuda(dst, "dst", torch.float64)
+        self._cuda(samples, "samples", torch.int32)
         if valid is not None:
-            _check_cuda(valid, "valid", torch.uint8)
+            self._cuda(valid, "valid", torch.uint8)
         n, n_hyp = src.shape[0], samples.shape[0]
         _check_shape(src, "src", (n, 2))
         _check_shape(dst, "dst", (n, 2))

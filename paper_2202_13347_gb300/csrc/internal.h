@@ -146,6 +146,10 @@ cudaError_t launch_rectify(const float* img, int H, int W, size_t pitch, const d
 cudaError_t launch_results_to_points(const int32_t* pts, const fastncc_result* res, int n, double* src, double* dst,
                                      uint8_t* valid, cudaStream_t st);
 
+// peak microbenchmarks (k_peak.cu): FP32 FFMA, paired FFMA2 and FP64 TFLOP/s,
+// HBM copy GB/s; synchronous
+cudaError_t measure_peaks(cudaStream_t st, int sms, double* fp32, double* fp32x2, double* fp64, double* hbm);
+
 // template half-width: rows before the centre
 __host__ __device__ inline int template_half(int m) { return (m % 2) ? (m - 1) / 2 : m / 2; }
 

@@ -56,6 +56,7 @@ constexpr int kBandMaxTS = 4;
 constexpr int kBandThreads = 384;
 constexpr int kBandDrain = 256;
 constexpr int kBandMaxNQ = 6;  // N <= 96, i.e. R <= 40
+constexpr int kBandSmemFloor = 120 * 1024;  // dynamic shared memory of a launch: at least this
 
 __host__ __device__ constexpr int band_ge_max(int nq) { return nq <= 3 ? 5 : 16 / nq; }
 
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                 const uint64_t db0 = smem_desc(sbase + g.slab_off, (uint32_t)(kBandQ * g.trows * 16), 128);
                 const uint32_t tile_step = (uint32_t)g.tile_bytes >> 4, slab_step = (uint32_t)g.slab_bytes >> 4;
                 const uint32_t tcol = (uint32_t)g.trows;  // slab column stride in 16-byte units
-                uint32_t gi = gc, tvt = tc;  // tvt: stage count (tracing)
+                uint32_t gi = gc;
                 uint32_t ts = tc % (uint32_t)g.TS, tph = (tc / (uint32_t)g.TS) & 1u;
                 for (int eg = 0; eg < g.nEG && ok; ++eg) {
                     const int Gg = g.nE - eg * g.GE < g.GE ? g.nE - eg * g.GE : g.GE;
@@ -281,11 +282,9 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                         const int r0 = ty0 + 16 * yb - 2 * R;
                         const uint32_t clamp = r0 < 0 ? (uint32_t)(-r0) : 0u;
                         for (int s = 0; s < g.nS; ++s) {
-                            TC_TRACE(0, tvt);
                             ok = mbar_wait(bar(BD_TFULL + ts), tph, &s_abort);
                             if (!ok) break;
                             tc_fence_after();
-                            TC_TRACE(1, tvt);
                             const uint64_t dB = db0 + (uint64_t)(ts * slab_step) - (uint64_t)clamp;
                             const int u0 = s * kBandQ;
                             const int nq = m - u0 < kBandQ ? m - u0 : kBandQ;
@@ -299,8 +298,6 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                             }
                             mma_issued += (uint32_t)(nq * Gg);
                             mma_commit(bar(BD_TEMPTY + ts));
-                            TC_TRACE(2, tvt);
-                            ++tvt;
                             if (++ts == (uint32_t)g.TS) { ts = 0; tph ^= 1u; }
                         }
                         if (!ok) break;
@@ -332,7 +329,6 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                     for (int p = 0; p < N4; ++p) sums[e][p] = 0.f;
                 for (int yb = 0; yb < g.nYB; ++yb, ++gd) {
                     if ((int)(gd & 1u) != team) continue;
-                    if (lane == 0 && q == 0) TC_TRACE(4, gd);
                     // lane 0 takes the bounded wait; the warp follows its verdict
                     int okw = 0;
                     if (lane == 0 && ok) okw = mbar_wait(bar(BD_AFULL + team), (gd >> 1) & 1, &s_abort) ? 1 : 0;
@@ -383,7 +379,6 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                             }
                         }
                     }
-                    if (lane == 0 && q == 0) TC_TRACE(5, gd);
                 }
                 // sums of this offset-group set: column j = joff + p is dy = 2R + 4q - j
 #pragma unroll
@@ -464,12 +459,17 @@ cudaError_t launch_corr_band(const Cube& ref, const Cube& sen, const int32_t* pt
         !make_map_rows8(&tmT, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, (uint32_t)bg.trows, kBandQ))
         return cudaErrorNotSupported;
     const int grid = n < sms ? n : sms;
+    // one CTA per SM: the kernel allocates all 512 TMEM columns, so a second
+    // CTA on the SM would block in tcgen05.alloc until the first one's whole
+    // persistent loop ended; more than half of the SM's shared memory rules
+    // a second CTA out
+    const int smem = bg.smem > kBandSmemFloor ? bg.smem : kBandSmemFloor;
     cudaError_t e = cudaErrorNotSupported;
 #define SFOC_BAND_CASE(NQV)                                                                                   \
     case NQV:                                                                                                 \
-        e = cudaFuncSetAttribute(k_corr_tc_band<NQV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bg.smem); \
+        e = cudaFuncSetAttribute(k_corr_tc_band<NQV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);    \
         if (e != cudaSuccess) return e;                                                                       \
-        k_corr_tc_band<NQV><<<grid, kBandThreads, bg.smem, st>>>(tmW, tmT, pts, n, m, R, stats, maps, err_flag); \
+        k_corr_tc_band<NQV><<<grid, kBandThreads, smem, st>>>(tmW, tmT, pts, n, m, R, stats, maps, err_flag); \
         return cudaGetLastError();
     switch (bg.NQ) {
         SFOC_BAND_CASE(1)

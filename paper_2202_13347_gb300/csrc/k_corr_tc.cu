@@ -191,7 +191,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_expect_tx(bar(BA_FULL + slot), g.a_bytes);
                     tma_load_4d(sbase + g.a_off + slot * g.a_bytes, &tmA, 0, wx0 + ub * U, wy0 + yb * kY, 0,
                                 bar(BA_FULL + slot));
-                    TC_TRACE(0, ga);
                     ++a_issued;
                 }
             }
@@ -217,13 +216,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int ub = s / nyb, yb = s - ub * nyb;
                     const uint32_t ga = gs + s, slot = ga % g.NA, acc = ga & 1;
                     const uint32_t gk = gb + ub, bb = gk & 1;
-                    TC_TRACE(1, ga);
                     if (yb == 0) ok = mbar_wait(bar(BB_READY + bb), (gk >> 1) & 1, &s_abort);
                     if (ok) ok = mbar_wait(bar(BA_FULL + slot), (ga / g.NA) & 1, &s_abort);
                     if (ok && ga >= 2) ok = mbar_wait(bar(BACC_EMPTY + acc), ((ga >> 1) - 1) & 1, &s_abort);
                     if (!ok) break;
                     tc_fence_after();
-                    TC_TRACE(2, ga);
                     // descriptors advance in 16-byte units by plain integer adds
                     const uint64_t da0 = smem_desc(sbase + g.a_off + slot * g.a_bytes, a_lbo, 128);
                     const uint64_t db0 = smem_desc(sbase + g.b_off + bb * g.b_bytes, b_lbo, 128);
@@ -249,7 +246,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     }
-                    TC_TRACE(3, ga);
                     mma_commit(bar(BA_EMPTY + slot));
                     mma_commit(bar(BACC_FULL + acc));
                     if (yb == nyb - 1) mma_commit(bar(BB_EMPTY + bb));
@@ -262,7 +258,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t gk = gb + ub, bb = gk & 1;
                 ok = mbar_wait(bar(BB_FULL + bb), (gk >> 1) & 1, &s_abort);
                 if (!ok) break;
-                if (t == 0) TC_TRACE(6, gk);
                 uint8_t* b = smem + g.b_off + bb * g.b_bytes;
                 const int nz_lo = 2 * R;               // rows j < 0
                 const int nz_hi = g.JS - (m + 2 * R);  // rows j >= m, incl. the stride padding
@@ -276,7 +271,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(BB_READY + bb));
-                if (t == 0) TC_TRACE(7, gk);
             }
         } else {
             // ---------------- TMEM drain + output ----------------
@@ -288,7 +282,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int i = 0; i < 16; ++i) accr[q][i] = 0.f;
             for (int s = 0; s < T && ok; ++s) {
                 const uint32_t ga = gs + s, acc = ga & 1;
-                if (warp == 4 && lane == 0) TC_TRACE(4, ga);
                 ok = mbar_wait(bar(BACC_FULL + acc), (ga >> 1) & 1, &s_abort);
                 if (!ok) break;
                 tc_fence_after();
@@ -303,7 +296,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(BACC_EMPTY + acc));
-                if (warp == 4 && lane == 0) TC_TRACE(5, ga);
             }
             if (ok) {
                 const int r = quarter * 32 + lane;  // dx
@@ -566,7 +558,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 uint32_t stg = tsc % kColNS;                         // stage-done barrier of the next stage
                 // ring positions kept as running slot / parity pairs (no
                 // divisions on the issue path)
-                uint32_t gg = grp, tvt = tsc;                        // tvt: stage count (tracing)
+                uint32_t gg = grp;
                 uint32_t ts = tsc % g.TS, tph = (tsc / g.TS) & 1;  // template slab of the next stage
                 uint32_t ws = wsc % g.WS, wph = (wsc / g.WS) & 1;  // window slab 0 of the current group
                 for (int d0 = 0; d0 < g.P1 && ok; d0 += G, ++gg) {
@@ -576,7 +568,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                     for (int s = 0; s < nstage && ok; ++s) {
                         const int u0 = s * kColQ;
                         const int nq = m - u0 < kColQ ? m - u0 : kColQ;
-                        TC_TRACE(0, tvt);
                         // the stage's template slab and every window slab it
                         // reads complete on this barrier or an earlier stage's
                         ok = mbar_wait(bar(CB_TFULL + ts), tph, &s_abort);
@@ -591,7 +582,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                         }
                         const uint64_t dT = db_base + (uint64_t)(ts * t_step);
                         const uint32_t acc0 = u0 > 0 ? 1u : 0u;
-                        TC_TRACE(1, tvt);
                         if (s == 0) {
                             // the group's first stage accumulator by accumulator: each
                             // starts once the drain has read the previous group's
@@ -636,8 +626,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                         if (s == nstage - 1) mma_commit(bar(CB_AFULL));
                         mma_commit(bar(CB_STG + stg));
                         if (++stg == (uint32_t)kColNS) stg = 0;
-                        TC_TRACE(2, tvt);
-                        ++tvt;
                         if (++ts == (uint32_t)g.TS) { ts = 0; tph ^= 1u; }
                         if (++wcur == (uint32_t)g.WS) wcur = 0;
                     }
@@ -661,7 +649,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                         mbar_arrive(bar(CB_TEMPTY + tv % g.TS));
                         const int hi = s == nstage - 1 ? nws : s + 1;
                         for (int b = s; b < hi; ++b) mbar_arrive(bar(CB_WEMPTY + (wv + (uint32_t)b) % g.WS));
-                        TC_TRACE(3, tv);
                     }
                     wv += (uint32_t)nws;
                 }
@@ -704,7 +691,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 // one thread takes the bounded wait; the named barrier below
                 // is then reached by every drain warp in bounded time
                 if (t == 0) {
-                    TC_TRACE(4, gg);
                     s_go = mbar_wait(bar(CB_AFULL), gg & 1, &s_abort) ? 1 : 0;
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(kColDrain) : "memory");
@@ -770,7 +756,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                             if (lane == 0) mbar_arrive(bar(CB_AEMPTY + gi));
                         }
                     }
-                    if (t == 0) TC_TRACE(6, gg * 16 + r0);
                     asm volatile("bar.sync 1, %0;" ::"r"(kColDrain) : "memory");
                     if (part < nparts) {  // row dy of each band buffer, eight independent chains
                         for (int gl = 0; gl < nb; ++gl) {
@@ -803,7 +788,6 @@ __global__ void __launch_bounds__(kColThreads, 1)
                         out[dyy * g.P1 + d0 + r0 + gl] = sum;
                     }
                 }
-                if (t == 0) TC_TRACE(5, gg);
             }
         }
         for (int d0 = 0; d0 < g.P1; d0 += G) {

@@ -33,6 +33,7 @@ struct sfoc_ctx {
     // second stream for the sensed image's host copy (overlaps the reference cube)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_copied = nullptr;
+    cudaEvent_t ev_switch = nullptr;  // orders a new stream after the previous one
     // per-stage timing
     bool timing = false;
     struct Ev {
@@ -418,6 +419,7 @@ sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx) {
     }
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
     if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
+    if (ctx->ev_switch) cudaEventDestroy(ctx->ev_switch);
     delete ctx;
     return SFOC_OK;
 }
@@ -426,10 +428,21 @@ sfoc_status sfoc_ctx_set_stream(sfoc_ctx* ctx, void* stream) {
     if (!ctx) return SFOC_ERR_INVALID_ARG;
     if (static_cast<cudaStream_t>(stream) == ctx->stream) return SFOC_OK;
     // the workspace is reused (and regrown) by calls on the new stream: the
-    // work still queued on the old one must be done with it first
+    // work still queued on the old one must be done with it first.  An event
+    // recorded on the old stream orders it before the new one's work without
+    // blocking the host; a stream being captured into a graph is refused
+    // (the wait would pull the new stream into that capture)
     DeviceGuard g(ctx->device);
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize(previous stream)");
+    cudaStreamCaptureStatus c0 = cudaStreamCaptureStatusNone, c1 = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &c0);
+    cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &c1);
+    if (c0 != cudaStreamCaptureStatusNone || c1 != cudaStreamCaptureStatusNone)
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "sfoc_ctx_set_stream during a stream capture");
+    cudaError_t e = cudaSuccess;
+    if (!ctx->ev_switch) e = cudaEventCreateWithFlags(&ctx->ev_switch, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_switch, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), ctx->ev_switch, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ordering the new stream after the previous one");
     ctx->stream = static_cast<cudaStream_t>(stream);
     return SFOC_OK;
 }
@@ -500,6 +513,21 @@ sfoc_status sfoc_ctx_reset_timing(sfoc_ctx* ctx) {
         ctx->acc_n[i] = 0;
     }
     return s;
+}
+
+sfoc_status sfoc_measure_peaks(sfoc_ctx* ctx, sfoc_peaks* out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!out) return fail(ctx, SFOC_ERR_INVALID_ARG, "null output");
+    DeviceGuard g(ctx->device);
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaDeviceGetAttribute");
+    sfoc_peaks r = {0.0, 0.0, 0.0, 0.0};
+    ctx->launches += 4 * 6;
+    e = measure_peaks(ctx->stream, sms, &r.fp32_tflops, &r.fp32x2_tflops, &r.fp64_tflops, &r.hbm_copy_gbs);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "peak microbenchmarks");
+    *out = r;
+    return SFOC_OK;
 }
 
 sfoc_status sfoc_params_default(sfoc_params* p) {

@@ -126,22 +126,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Optional per-stage timestamps of CTA 0 (compiled in only when
-// SFOC_TC_TRACE is defined; rows: 0 window-slab TMA issued, 1 MMA waits
-// begin, 2 MMA issue begins, 3 MMA issue ends, 4 drain waits begin,
-// 5 drain done, 6 zero rows begin, 7 zero rows done).
-#ifdef SFOC_TC_TRACE
-static __device__ unsigned long long g_tc_trace[8][8192];
-#define TC_TRACE(row, idx)                                           \
-    do {                                                             \
-        if (blockIdx.x == 0 && (idx) < 8192u) g_tc_trace[row][idx] = clock64(); \
-    } while (0)
-#else
-#define TC_TRACE(row, idx) \
-    do {                   \
-    } while (0)
-#endif
-
 // 4-D bf16 view {8 channels, d1, d2, 2 chunks} of a chunked cube layout.
 bool make_map(CUtensorMap* map, const void* base, uint64_t d1, uint64_t d2, uint32_t b1, uint32_t b2, uint32_t b3);
 // The same view in 128-byte runs of 8 pixels along d1 (see k_corr_tc.cu).

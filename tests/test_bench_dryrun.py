@@ -72,6 +72,9 @@ def _fake_library(fail_ransac=False):
         def sync(self):
             pass
 
+        def measure_peaks(self):
+            return {"fp32_tflops": 70.0, "fp32x2_tflops": 75.0, "fp64_tflops": 1.2, "hbm_copy_gbs": 6500.0}
+
         def enable_timing(self, on=True):
             pass
 
@@ -137,6 +140,8 @@ def _patch_cuda(monkeypatch):
 
 
 def _run(monkeypatch, capsys, argv, fail_ransac=False):
+    import oracle
+    oracle.build()        # compiled before PATH is blanked below (gcc is found through PATH)
     _patch_cuda(monkeypatch)
     monkeypatch.setitem(sys.modules, "paper_2202_13347_gb300", _fake_library(fail_ransac))
     monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
@@ -167,6 +172,9 @@ def test_line_has_every_contract_key(monkeypatch, capsys):
     assert line["gpu_launches"] == 13 * 3
     assert line["ransac"]["ms"] >= 0 and "roofline" in line["fast"]
     assert set(line["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+    # FP32 fractions use the measured peak (the faster FMA form), FAST one op per lane per clock
+    assert line["forms"]["f32direct"]["roofline"]["peak"] == 75.0
+    assert line["fast"]["roofline"]["peak"] == 35.0
 
 
 def test_failing_side_measurement_keeps_the_line(monkeypatch, capsys):

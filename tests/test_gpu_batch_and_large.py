@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 
 from workloads import mixed_batch, speckle_pair_10000  # noqa: E402
 
-from parity import bf16_check, bf16_oracle_side, compare  # noqa: E402
+from parity import bf16_check, bf16_oracle_side, cached, compare  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -52,16 +52,30 @@ def batch():
     return mixed_batch(n_pairs=16, scale=0.25)
 
 
-def test_mixed_batch_f32(b, ctx, orc, batch):
+PER_PAIR = 8  # oracle points per pair of the mixed batch
+
+
+def oracle_f32(orc, batch, k):
+    pair = batch[k]
+    idx, sub = sample(pair, PER_PAIR, 400 + k)
+    o = cached(("mixed-f32", k), lambda: orc.match_pair(sub.ref, sub.sen, sub.points, sub.m, sub.R, want_maps=True))
+    return idx, o
+
+
+@pytest.mark.parametrize("path", ["direct", "auto"])
+def test_mixed_batch_f32(b, ctx, orc, batch, path):
+    """F32 cubes: the plain direct correlation, and the automatic choice
+    (the Fourier correlation of Eq. 13 wherever m + 2R <= 128, so it runs on
+    the batch's ragged m and R)."""
+    corr = {"direct": b.CORR_DIRECT_F32, "auto": b.CORR_AUTO}[path]
     refs = ctx.sfoc_build_batch([dev(p.ref) for p in batch])
     sens = ctx.sfoc_build_batch([dev(p.sen) for p in batch])
     outs = ctx.fastncc_match_batch(refs, sens, [dev(p.points) for p in batch], [p.m for p in batch], [p.R for p in batch],
-                                   corr_path=b.CORR_DIRECT_F32)
+                                   corr_path=corr)
     ctx.sync()
     for k, pair in enumerate(batch):
         g = b.results(outs[k])
-        idx, sub = sample(pair, 3, 400 + k)
-        o = orc.match_pair(sub.ref, sub.sen, sub.points, sub.m, sub.R, want_maps=True)
+        idx, o = oracle_f32(orc, batch, k)
         gi = {key: v[torch.from_numpy(idx).cuda()] for key, v in g.items()}
         compare(gi, o, pair.R, oracle_maps=o["maps"])
 
@@ -75,8 +89,8 @@ def test_mixed_batch_bf16(b, ctx, orc, batch):
     ctx.sync()
     for k, pair in enumerate(batch):
         g = b.results(outs[k])
-        idx, sub = sample(pair, 2, 500 + k)
-        o_r, o_u, regions = bf16_oracle_side(orc, sub, roi=True)
+        idx, sub = sample(pair, PER_PAIR, 500 + k)
+        o_r, o_u, regions = cached(("mixed-bf16", k), lambda: bf16_oracle_side(orc, sub, roi=True))
         gi = {key: v[torch.from_numpy(idx).cuda()] for key, v in g.items()}
         bf16_check(gi, o_r, o_u, regions, pair.R, {})
 
@@ -91,14 +105,15 @@ def test_speckle_pair_10000_full_size_sampled(b, ctx, orc, big):
     ref16 = pair.meta["ref_u16"]
     bits = torch.from_numpy(ref16.view(np.int16)).cuda()
     pts = dev(pair.points)
-    idx, sub = sample(pair, 6, 5005)
+    idx, sub = sample(pair, 32, 5005)
     sel = torch.from_numpy(idx).cuda()
     # F32 form
     rc = ctx.sfoc_build_u16(bits)
     sc = ctx.sfoc_build(dev(pair.sen))
     g = ctx.fastncc_match(rc, sc, pts, pair.m, pair.R, corr_path=b.CORR_DIRECT_F32)
     ctx.sync()
-    o = orc.match_pair(sub.ref, sub.sen, sub.points, sub.m, sub.R, want_maps=True)
+    o = cached(("speckle10000", 5005, 32),
+               lambda: orc.match_pair(sub.ref, sub.sen, sub.points, sub.m, sub.R, want_maps=True))
     compare({k: v[sel] for k, v in g.items()}, o, pair.R, oracle_maps=o["maps"])
     assert int((g["status"] == 0).sum()) >= 0.5 * len(pair.points)
     rc.free()

@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 
 from workloads import inverting_pair_512, sar_pair_2048, tiny_pair  # noqa: E402
 
-from parity import compare  # noqa: E402
+from parity import cached, compare  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -213,12 +213,14 @@ def test_status_cases(b, ctx, orc, path):
 @pytest.mark.parametrize("path", F32_PATHS)
 def test_sar_pair_2048_full_size_sampled(b, ctx, orc, path):
     """2048^2, 1000 points, m=81, R=20: the benchmark's configuration; the
-    oracle checks a seeded sample of 8 points."""
-    pair = sar_pair_2048()
+    oracle checks a seeded sample of 64 points (about 12 s of oracle work,
+    shared by both paths)."""
+    pair = cached("sar2048", sar_pair_2048)
     g = gpu_match(ctx, b, pair, corr=f32_path(b, path))
     rng = np.random.default_rng(2024)
-    idx = np.sort(rng.choice(len(pair.points), 8, replace=False))
-    o = orc.match_pair(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R, want_maps=True)
+    idx = np.sort(rng.choice(len(pair.points), 64, replace=False))
+    o = cached(("sar2048-oracle", 2024, 64),
+               lambda: orc.match_pair(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R, want_maps=True))
     gs = {k: v[torch.from_numpy(idx).cuda()] for k, v in g.items()}
     compare(gs, o, pair.R, oracle_maps=o["maps"])
     assert int((g["status"] == 0).sum()) >= 900

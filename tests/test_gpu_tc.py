@@ -24,7 +24,7 @@ torch = pytest.importorskip("torch")
 
 from workloads import inverting_pair_512, sar_pair_2048, tiny_pair  # noqa: E402
 
-from parity import bf16_check as check, bf16_oracle_side as oracle_side  # noqa: E402
+from parity import bf16_check as check, bf16_oracle_side as oracle_side, cached  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -130,14 +130,15 @@ def test_tc_inverting_pair_512(b, ctx, orc, form):
 @pytest.mark.parametrize("form", ["auto", "band"])
 def test_tc_sar_pair_2048_full_size_sampled(b, ctx, orc, form):
     """2048^2, 1000 points, m=81, R=20 in the benchmark's launch
-    configuration; a seeded sample of 6 points against the oracle."""
-    pair = sar_pair_2048()
+    configuration; a seeded sample of 64 points against the oracle (shared by
+    both forms)."""
+    pair = cached("sar2048", sar_pair_2048)
     g = gpu_bf16(ctx, b, pair, path=form_path(b, form))
     ctx.sync()
     rng = np.random.default_rng(77)
-    idx = np.sort(rng.choice(len(pair.points), 6, replace=False))
+    idx = np.sort(rng.choice(len(pair.points), 64, replace=False))
     sub = type(pair)(pair.ref, pair.sen, pair.points[idx], pair.m, pair.R, pair.truth[idx])
-    o_r, o_u, regions = oracle_side(orc, sub, roi=True)
+    o_r, o_u, regions = cached(("sar2048-bf16-oracle", 77, 64), lambda: oracle_side(orc, sub, roi=True))
     gs = {k: v[torch.from_numpy(idx).cuda()] for k, v in g.items()}
     check(gs, o_r, o_u, regions, pair.R, {})
     assert int((g["status"] == 0).sum()) >= 900

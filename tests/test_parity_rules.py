@@ -174,3 +174,22 @@ def test_compare_accepts_valid_ties_and_rejects_wrong_offsets():
         compare(_res([0], [0], [0.9 + 2e-4]), orc2, R, oracle_maps=omap[None])  # NCC beyond 1e-4
     with pytest.raises(AssertionError):
         compare(_res([0], [0], [0.9], status=[2]), orc2, R)                    # status differs
+
+
+def test_compare_bounds_and_reports_tie_flips(tmp_path, monkeypatch):
+    """Near-ties are counted and logged; valid tie flips beyond 1 % of the
+    valid points (at least one allowed) fail the comparison."""
+    import json
+    R, n = 1, 3
+    omap = np.full((n, 3, 3), 0.2)
+    omap[:, 1, 1], omap[:, 1, 2] = 0.9, 0.9 - 1e-4  # every point a near-tie
+    orc = _res([0] * n, [0] * n, [0.9] * n)
+    orc.update(margin=np.full(n, 1e-4), sub_dx=np.zeros(n), sub_dy=np.zeros(n))
+    log = tmp_path / "ties.jsonl"
+    monkeypatch.setenv("SFOC_PARITY_LOG", str(log))
+    st = compare(_res([1, 0, 0], [0] * n, [0.9 - 1e-4, 0.9, 0.9]), orc, R, oracle_maps=omap)  # one flip: allowed
+    assert st["near_ties"] == 3 and st["tie_flips"] == 1
+    rec = json.loads(log.read_text().splitlines()[-1])
+    assert rec["near_ties"] == 3 and rec["tie_flips"] == 1
+    with pytest.raises(AssertionError, match="tie flips"):
+        compare(_res([1, 1, 0], [0] * n, [0.9 - 1e-4, 0.9 - 1e-4, 0.9]), orc, R, oracle_maps=omap)
