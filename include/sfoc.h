@@ -58,8 +58,8 @@ typedef enum { SFOC_DTYPE_F32 = 0, SFOC_DTYPE_BF16 = 1 } sfoc_dtype;
 
 /* Correlation kernel for R_ST (Eq. 10). */
 typedef enum {
-    SFOC_CORR_AUTO = 0,       /* BF16 cubes: IGEMM_TC; F32 cubes: FFT when m + 2R <= 128, else
-                               * DIRECT_F32 */
+    SFOC_CORR_AUTO = 0,       /* the form the autotuner measured fastest for (cube dtype, m, R)
+                               * (see the autotuner section below) */
     SFOC_CORR_DIRECT_F32 = 1, /* FP32 CUDA-core direct correlation (F32 cubes) */
     SFOC_CORR_IGEMM_TC = 2,   /* tcgen05 BF16 implicit GEMM, FP32 accumulate (BF16 cubes):
                                * the column or band form, whichever issues fewer MMAs for
@@ -315,20 +315,103 @@ SFOC_API sfoc_status fastncc_register_pair_host(sfoc_ctx* ctx, const float* h_re
                                        fastncc_result* h_out);
 
 /* ---- batched forms -------------------------------------------------- */
+/*
+ * Many image pairs of uneven size, each with its own points, m and R, in one
+ * launch per stage instead of the per-point loop of Sec. 3.2.2 run pair after
+ * pair: the SFOC kernels run over the tiles of every image at once (in
+ * waves whose steering planes fit 4 GiB of workspace), the integral images
+ * over every reference cube, the template statistics and the NCC stage over
+ * every (pair, point) item, and the correlation as one persistent launch per
+ * kernel instance ("class": the Fourier side, the direct kernel's tile
+ * class, or a tensor-core form's instance; the Toeplitz form runs one launch
+ * per pair) over its items, largest template and radius first.  Every pair
+ * gets the correlation form opts->corr_path names, or with AUTO the one the
+ * autotuner measured fastest for its (cube dtype, m, R).
+ * A call's tables (a "plan") are built on its first use and kept in the
+ * context (the two most recent), keyed by every pointer, size and parameter
+ * of the call; that first call runs the stages one by one (measuring the
+ * forms of any (m, R) that have no autotuned entry yet, which waits for the
+ * device) and captures them into a CUDA graph; a later call with the same
+ * arguments launches that graph on the context's stream.  With per-stage
+ * timing on, plans run stage by stage instead (the stage events need their
+ * own launches).  Plans point into the workspace: a workspace that grows
+ * drops them.  Not thread-safe (like every call on a context).
+ * All pairs of a batch have the same cube dtype and channel count.  Errors
+ * as fastncc_match, checked for every pair before any work is queued.
+ */
 
-/* Builds n_img cubes; images[i] is H[i] x W[i] with pitch pitch_elems[i]. */
+/* Builds n_img cubes; images[i] is H[i] x W[i] with pitch pitch_elems[i]
+ * (NULL = dense).  outs[i] follows sfoc_build's in/out rule. */
 SFOC_API sfoc_status sfoc_build_batch(sfoc_ctx* ctx, int n_img, const float* const* d_images, const int* H, const int* W,
                              const size_t* pitch_elems, const sfoc_params* p, sfoc_cube** outs);
 
-/*
- * Matches n_pairs (ref, sen) pairs, each with its own points, m and R, in
- * order on the context stream (fastncc_match per pair, opts->corr_path for
- * every pair; per-pair maps are not returned).  Stops at the first pair
- * that fails and returns its status.
- */
+/* Matches n_pairs (refs[i], sens[i]) pairs; pair i has n_points[i] points
+ * d_points[i], template_size[i], search_radius[i] and writes d_outs[i]
+ * (per-pair NCC maps are not returned). */
 SFOC_API sfoc_status fastncc_match_batch(sfoc_ctx* ctx, int n_pairs, sfoc_cube* const* refs, sfoc_cube* const* sens,
                                 const int32_t* const* d_points, const int* n_points, const int* template_size,
                                 const int* search_radius, const fastncc_opts* opts, fastncc_result* const* d_outs);
+
+/* The whole path for n_pairs pairs of dense float images on the device
+ * (d_refs[i]: Hr[i] x Wr[i], d_sens[i]: Hs[i] x Ws[i]): SFOC of all
+ * 2 n_pairs images, then the batched match.  The cubes belong to the plan
+ * (freed with it).  Same plan and graph rules as above. */
+SFOC_API sfoc_status fastncc_register_batch(sfoc_ctx* ctx, int n_pairs, const float* const* d_refs, const int* Hr,
+                                            const int* Wr, const float* const* d_sens, const int* Hs, const int* Ws,
+                                            const int32_t* const* d_points, const int* n_points,
+                                            const int* template_size, const int* search_radius, const sfoc_params* p,
+                                            const fastncc_opts* opts, fastncc_result* const* d_outs);
+
+/* fastncc_register_batch from host buffers: copies every image and point
+ * set into a device staging buffer kept by the context, runs the batch and
+ * copies every pair's results to h_outs[i] before returning (synchronous).
+ * A staging buffer that has to grow drops the context's plans. */
+SFOC_API sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs,
+                                                 const int* Hr, const int* Wr, const float* const* h_sens,
+                                                 const int* Hs, const int* Ws, const int32_t* const* h_points,
+                                                 const int* n_points, const int* template_size,
+                                                 const int* search_radius, const sfoc_params* p,
+                                                 const fastncc_opts* opts, fastncc_result* const* h_outs);
+
+/* Number of batch plans the context holds; frees them all (waits for the
+ * context's stream first). */
+SFOC_API int sfoc_ctx_plan_count(const sfoc_ctx* ctx);
+SFOC_API sfoc_status sfoc_ctx_release_plans(sfoc_ctx* ctx);
+
+/* ---- autotuner -------------------------------------------------------- */
+/*
+ * With SFOC_CORR_AUTO the correlation form of a (cube dtype, m, R) is
+ * measured, not ruled: on the first match of that key (outside a stream
+ * capture) every form that runs for it is launched on the first
+ * min(n, 2 x SMs) points of that call (one warm-up launch, then the better
+ * of two timed with CUDA events): for F32 cubes the Fourier correlation
+ * (and, where m + 2R <= 64, also its 128-point transform) and the direct
+ * kernel; for BF16 cubes the band, column and Toeplitz tensor-core forms.
+ * The fastest is kept in the context and used from then on.  The paper
+ * weighs its FFT against spatial correlation by operation counts (Eq.
+ * 17-19); on this device the choice is made by measurement.  Without an
+ * entry (autotuning off, or inside a capture) AUTO takes the fixed rule: F32
+ * cubes the Fourier form when m + 2R <= 128, else the direct kernel; BF16
+ * cubes the tensor-core form with the fewest MMAs.
+ */
+SFOC_API sfoc_status sfoc_ctx_set_autotune(sfoc_ctx* ctx, int enable);
+/* The entry of (dtype, m, R): *corr_path = the chosen sfoc_corr_path (-1 when
+ * there is none), *option = its FFT side (else 0), and per candidate timed
+ * (*n_cand <= 6) its path, option and milliseconds (-1 = it failed to run);
+ * *sample = the points timed.  Output pointers other than corr_path may be
+ * NULL. */
+SFOC_API sfoc_status sfoc_ctx_autotune_entry(const sfoc_ctx* ctx, int dtype, int m, int R, int* corr_path,
+                                             int* option, int* n_cand, int* cand_path, int* cand_option,
+                                             float* cand_ms, int* sample);
+/* The context's entries as JSON text ({"sfoc_autotune": 1, "entries":
+ * [...]}).  *len receives the bytes needed including the terminating zero;
+ * with buf NULL nothing else is written; SFOC_ERR_INVALID_ARG when cap is
+ * smaller than that. */
+SFOC_API sfoc_status sfoc_ctx_autotune_export(const sfoc_ctx* ctx, char* buf, size_t cap, size_t* len);
+/* Adds (or replaces) the entries of text written by sfoc_ctx_autotune_export.
+ * SFOC_ERR_INVALID_ARG, with nothing added, for text that does not parse or
+ * an entry whose form does not run for its m / R. */
+SFOC_API sfoc_status sfoc_ctx_autotune_import(sfoc_ctx* ctx, const char* text);
 
 /* ---- interest points (Sec. 3.1.1) --------------------------------------- */
 

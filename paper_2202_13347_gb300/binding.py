@@ -103,6 +103,22 @@ _SIGS = {
     "fastncc_match_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(Opts), C.POINTER(_P)]),
+    "fastncc_register_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_P),
+                                         C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(Params), C.POINTER(Opts), C.POINTER(_P)]),
+    "fastncc_register_batch_host": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                              C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_P),
+                                              C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                              C.POINTER(Params), C.POINTER(Opts), C.POINTER(_P)]),
+    "sfoc_ctx_plan_count": (C.c_int, [_P]),
+    "sfoc_ctx_release_plans": (C.c_int, [_P]),
+    "sfoc_ctx_set_autotune": (C.c_int, [_P, C.c_int]),
+    "sfoc_ctx_autotune_entry": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_float), C.POINTER(C.c_int)]),
+    "sfoc_ctx_autotune_export": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "sfoc_ctx_autotune_import": (C.c_int, [_P, C.c_char_p]),
     "fastncc_points_from_results": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
     "sfoc_rectify": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, _P, C.c_float, C.c_int, C.c_int, _P]),
     "sfoc_fast_blocks": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_size_t, C.c_float, C.c_int, C.c_int, C.c_int, _P,
@@ -418,14 +434,22 @@ class Context:
                 res.append(Cube(self, hs[i]))
         return res
 
-    def fastncc_match_batch(self, refs, sens, points, template_sizes, search_radii, corr_path=CORR_AUTO):
+    def fastncc_match_batch(self, refs, sens, points, template_sizes, search_radii, corr_path=CORR_AUTO, outs=None):
+        """One (n, 6) int32 result tensor per pair (filled in place when
+        `outs` is given: a repeated call with the same tensors reuses the
+        context's plan)."""
         n = len(refs)
         if not (len(sens) == len(points) == len(template_sizes) == len(search_radii) == n):
             raise ValueError("refs, sens, points, template_sizes and search_radii must have the same length")
         for i, pt in enumerate(points):
             self._cuda(pt, "points[%d]" % i, torch.int32)
             _check_shape(pt, "points[%d]" % i, (pt.shape[0], 2))
-        outs = [torch.empty((p.shape[0], 6), dtype=torch.int32, device=self.device) for p in points]
+        if outs is None:
+            outs = [torch.empty((p.shape[0], 6), dtype=torch.int32, device=self.device) for p in points]
+        else:
+            for i, o in enumerate(outs):
+                self._cuda(o, "outs[%d]" % i, torch.int32)
+                _check_shape(o, "outs[%d]" % i, (points[i].shape[0], 6))
         R = (C.c_void_p * n)(*[c.handle for c in refs])
         S = (C.c_void_p * n)(*[c.handle for c in sens])
         Pp = (C.c_void_p * n)(*[p.data_ptr() for p in points])
@@ -436,6 +460,101 @@ class Context:
         o = Opts(int(corr_path), None)
         self._chk(lib().fastncc_match_batch(self.h, n, R, S, Pp, Np, Mp, Rp, C.byref(o), Op))
         return outs
+
+    def register_batch(self, refs, sens, points, template_sizes, search_radii, p: Params = None,
+                       corr_path=CORR_AUTO, outs=None):
+        """The whole path for a batch of pairs (fastncc_register_batch): lists
+        of dense float32 device images and int32 (n, 2) device points; returns
+        (or fills) one (n, 6) int32 result tensor per pair.  The first call
+        with given tensors builds and captures the batch's plan; later calls
+        with the same tensors replay it."""
+        n = len(refs)
+        if not (len(sens) == len(points) == len(template_sizes) == len(search_radii) == n):
+            raise ValueError("refs, sens, points, template_sizes and search_radii must have the same length")
+        for i in range(n):
+            self._cuda(refs[i], "refs[%d]" % i, torch.float32)
+            self._cuda(sens[i], "sens[%d]" % i, torch.float32)
+            self._cuda(points[i], "points[%d]" % i, torch.int32)
+            _check_shape(points[i], "points[%d]" % i, (points[i].shape[0], 2))
+            if refs[i].dim() != 2 or sens[i].dim() != 2:
+                raise ValueError("images must be 2-D")
+        if outs is None:
+            outs = [torch.empty((pt.shape[0], 6), dtype=torch.int32, device=self.device) for pt in points]
+        else:
+            for i, o in enumerate(outs):
+                self._cuda(o, "outs[%d]" % i, torch.int32)
+                _check_shape(o, "outs[%d]" % i, (points[i].shape[0], 6))
+        o = Opts(int(corr_path), None)
+        self._chk(lib().fastncc_register_batch(
+            self.h, n, (C.c_void_p * n)(*[t.data_ptr() for t in refs]), (C.c_int * n)(*[t.shape[0] for t in refs]),
+            (C.c_int * n)(*[t.shape[1] for t in refs]), (C.c_void_p * n)(*[t.data_ptr() for t in sens]),
+            (C.c_int * n)(*[t.shape[0] for t in sens]), (C.c_int * n)(*[t.shape[1] for t in sens]),
+            (C.c_void_p * n)(*[t.data_ptr() for t in points]), (C.c_int * n)(*[t.shape[0] for t in points]),
+            (C.c_int * n)(*[int(v) for v in template_sizes]), (C.c_int * n)(*[int(v) for v in search_radii]),
+            C.byref(p) if p is not None else None, C.byref(o), (C.c_void_p * n)(*[t.data_ptr() for t in outs])))
+        return outs
+
+    def register_batch_host(self, refs, sens, points, template_sizes, search_radii, p: Params = None,
+                            corr_path=CORR_AUTO, outs=None):
+        """fastncc_register_batch_host: host (ideally pinned) tensors in,
+        host result tensors out (synchronous)."""
+        n = len(refs)
+        if not (len(sens) == len(points) == len(template_sizes) == len(search_radii) == n):
+            raise ValueError("refs, sens, points, template_sizes and search_radii must have the same length")
+        for i in range(n):
+            _check_host(refs[i], "refs[%d]" % i, torch.float32)
+            _check_host(sens[i], "sens[%d]" % i, torch.float32)
+            _check_host(points[i], "points[%d]" % i, torch.int32)
+            _check_shape(points[i], "points[%d]" % i, (points[i].shape[0], 2))
+            if refs[i].dim() != 2 or sens[i].dim() != 2:
+                raise ValueError("images must be 2-D")
+        if outs is None:
+            outs = [torch.empty((pt.shape[0], 6), dtype=torch.int32) for pt in points]
+        else:
+            for i, o in enumerate(outs):
+                _check_host(o, "outs[%d]" % i, torch.int32)
+                _check_shape(o, "outs[%d]" % i, (points[i].shape[0], 6))
+        o = Opts(int(corr_path), None)
+        self._chk(lib().fastncc_register_batch_host(
+            self.h, n, (C.c_void_p * n)(*[t.data_ptr() for t in refs]), (C.c_int * n)(*[t.shape[0] for t in refs]),
+            (C.c_int * n)(*[t.shape[1] for t in refs]), (C.c_void_p * n)(*[t.data_ptr() for t in sens]),
+            (C.c_int * n)(*[t.shape[0] for t in sens]), (C.c_int * n)(*[t.shape[1] for t in sens]),
+            (C.c_void_p * n)(*[t.data_ptr() for t in points]), (C.c_int * n)(*[t.shape[0] for t in points]),
+            (C.c_int * n)(*[int(v) for v in template_sizes]), (C.c_int * n)(*[int(v) for v in search_radii]),
+            C.byref(p) if p is not None else None, C.byref(o), (C.c_void_p * n)(*[t.data_ptr() for t in outs])))
+        return outs
+
+    @property
+    def plan_count(self) -> int:
+        return int(lib().sfoc_ctx_plan_count(self.h))
+
+    def release_plans(self):
+        self._chk(lib().sfoc_ctx_release_plans(self.h))
+
+    def set_autotune(self, on=True):
+        self._chk(lib().sfoc_ctx_set_autotune(self.h, 1 if on else 0))
+
+    def autotune_entry(self, dtype, m, R):
+        """{path, option, sample, candidates: [(path, option, ms)]} of the
+        autotuner's entry for (dtype, m, R), or None."""
+        path, opt, nc, smp = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        cp, co, cm = (C.c_int * 6)(), (C.c_int * 6)(), (C.c_float * 6)()
+        self._chk(lib().sfoc_ctx_autotune_entry(self.h, int(dtype), int(m), int(R), C.byref(path), C.byref(opt),
+                                                 C.byref(nc), cp, co, cm, C.byref(smp)))
+        if path.value < 0:
+            return None
+        return dict(path=path.value, option=opt.value, sample=smp.value,
+                    candidates=[(cp[i], co[i], float(cm[i])) for i in range(nc.value)])
+
+    def autotune_export(self) -> str:
+        n = C.c_size_t()
+        self._chk(lib().sfoc_ctx_autotune_export(self.h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._chk(lib().sfoc_ctx_autotune_export(self.h, buf, n.value, C.byref(n)))
+        return buf.value.decode()
+
+    def autotune_import(self, text: str):
+        self._chk(lib().sfoc_ctx_autotune_import(self.h, text.encode()))
 
     def fast_blocks(self, image: torch.Tensor, threshold=0.05, grid_y=32, grid_x=32, margin=3):
         """Block-based FAST: (points (grid_y * grid_x, 2) int32 (x, y; -1 for

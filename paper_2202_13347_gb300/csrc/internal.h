@@ -2,6 +2,7 @@
 // Shared only between this library's own translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -78,6 +79,43 @@ struct Cube {
 
 struct TileSums;  // integral-image scratch layout (k_integral.cu)
 
+// One image of an SFOC launch: the input, its steering planes F and the
+// cube it builds.  A single-image launch passes one by value; a batched
+// launch passes a device table and the prefix `begin` of the launch's CTAs
+// per image (n_jobs + 1 entries), so one launch covers the tiles of every
+// image.
+struct ImgJob {
+    const void* img;   // float or uint16 samples
+    size_t pitch;
+    int H, W;
+    float* F;          // z steering planes [z][H][fpitch]
+    size_t fpitch;
+    float* c32;        // F32 cube [z][H][cpitch] or nullptr
+    size_t cpitch;
+    __nv_bfloat16* rm; // BF16 cube layouts or nullptr
+    __nv_bfloat16* cm;
+    float* s1;         // per-pixel sums [H][cpitch]
+    float* s2;
+};
+
+// The image of this CTA and its tile index within it.
+__device__ __forceinline__ const ImgJob& img_job(const ImgJob& one, const ImgJob* jobs, const int* begin, int n_jobs,
+                                                 int* tile) {
+    const int bid = blockIdx.x;
+    if (!jobs) {
+        *tile = bid;
+        return one;
+    }
+    int lo = 0, hi = n_jobs - 1;  // the last image whose first CTA is at or before this one
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= bid) lo = mid;
+        else hi = mid - 1;
+    }
+    *tile = bid - begin[lo];
+    return jobs[lo];
+}
+
 // ---- kernel launchers (return cudaError_t of the launch) ----------------
 cudaError_t launch_sfoc_steer(const float* img, int H, int W, size_t pitch, float* F, size_t fpitch,
                               const SteerTaps& tp, int z_first, cudaStream_t st);
@@ -85,6 +123,16 @@ cudaError_t launch_sfoc_steer(const uint16_t* img, int H, int W, size_t pitch, f
                               const SteerTaps& tp, int z_first, cudaStream_t st);
 cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,
                                cudaStream_t st);
+// Batched build of several float images with the paper's radii and rates
+// (sfoc_batch_supported): one steering launch and one smoothing launch per
+// group over the tiles of all images (device table `jobs`, n_jobs entries).
+// steer_begin / smooth_begin: device prefix sums of each kernel's CTAs per
+// image (sfoc_batch_tiles gives the counts).
+bool sfoc_batch_supported(const SteerTaps& st, const SmoothTaps& sm);
+void sfoc_batch_tiles(int H, int W, int* steer_ctas, int* smooth_ctas);
+cudaError_t launch_sfoc_batch(const ImgJob* jobs, int n_jobs, const int* steer_begin, int steer_ctas,
+                              const int* smooth_begin, int smooth_ctas, const SteerTaps& st, const SmoothTaps& sm,
+                              cudaStream_t s);
 int smooth_launch_count(const SmoothTaps& tp);  // kernels launch_sfoc_smooth launches
 cudaError_t launch_cube_export(const Cube& c, float* out, cudaStream_t st);
 
@@ -108,6 +156,14 @@ __device__ __forceinline__ unsigned long long int_quant(float v) {
 
 size_t integral_scratch_bytes(int H, int W);
 cudaError_t launch_integral(const Cube& c, void* scratch, cudaStream_t st, int* launches);
+// batched integral images of n cubes: a table blob (integral_batch_blob_bytes,
+// filled on the host by integral_batch_blob with each cube's scratch carved
+// from `scratch`, integral_batch_scratch_bytes in all) and one launch of each
+// of the four kernels over all cubes; ctas4 = the kernels' CTA counts
+size_t integral_batch_blob_bytes(int n);
+size_t integral_batch_scratch_bytes(const Cube* const* cubes, int n);
+void integral_batch_blob(const Cube* const* cubes, int n, char* scratch, void* blob, int* ctas4);
+cudaError_t launch_integral_batch(const void* d_blob, int n, const int* ctas4, cudaStream_t st);
 size_t integral_export_scratch_bytes(int H, int W);
 cudaError_t launch_integral_export(const Cube& c, void* scratch, double* out, cudaStream_t st);
 
@@ -117,20 +173,86 @@ struct PointStat {
     int status;           // SFOC_PT_*
 };
 
-cudaError_t launch_template_stats(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                                  PointStat* stats, cudaStream_t st);
-cudaError_t launch_corr_f32(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                            const PointStat* stats, float* maps, cudaStream_t st);
+// ---- work descriptions shared by single-pair and batched launches -------
+// One image pair of a match: both cubes, the pair's points, m and R, and
+// where its per-point scratch and results go.  A single-pair launch passes
+// one job by value (a __grid_constant__ kernel parameter, so its tensor maps
+// can be used by TMA in place); a batched launch passes a device table of
+// jobs and a list of items (job, point), so one launch covers the points of
+// every pair.  The tensor maps are those of the correlation form the job's
+// class runs (unused by the other kernels).
+struct MatchJob {  // aligned as its tensor maps (128 bytes)
+    CUtensorMap tm[3];
+    // reference (searched) cube
+    const float* rf32;
+    const __nv_bfloat16* rrm;
+    const __nv_bfloat16* rcm;
+    const unsigned long long* rint;
+    size_t rpitch, rplane, ripitch;
+    int Hr, Wr;
+    // sensed (template) cube
+    const float* sf32;
+    const float* ss1;
+    const float* ss2;
+    const __nv_bfloat16* srm;
+    const __nv_bfloat16* scm;
+    size_t spitch, splane;
+    int Hs, Ws;
+    int z, m, R, n;
+    const int32_t* pts;     // n x (x, y)
+    PointStat* stats;       // n
+    float* maps;            // n x (2R+1)^2 correlation maps (scratch)
+    float* out_maps;        // optional n x (2R+1)^2 NCC maps
+    fastncc_result* out;    // n
+};
+
+// The items of a launch: nullptr = the points 0 .. n-1 of `one`.
+struct ItemSet {
+    const MatchJob* jobs = nullptr;  // device table
+    const int2* items = nullptr;     // device list of (job, point)
+    int n = 0;                       // items
+    int* queue = nullptr;            // device counter for dynamic fetching (zeroed before the launch) or nullptr
+    int max_m = 0, max_R = 0;        // bounds over the items' jobs (shared-memory sizes)
+    int max_lw = 0;                  // largest m + 2R of the items' jobs
+};
+
+__device__ __forceinline__ const MatchJob& item_job(const MatchJob& one, const MatchJob* jobs, const int2* items,
+                                                     int k, int* point) {
+    if (!items) {
+        *point = k;
+        return one;
+    }
+    const int2 it = items[k];
+    *point = it.y;
+    return jobs[it.x];
+}
+
+MatchJob make_job(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R, PointStat* stats,
+                  float* maps, float* out_maps, fastncc_result* out);
+
+// Each launcher runs its kernel over the items of `is` (is.items == nullptr:
+// the points of `one`).
+cudaError_t launch_template_stats(const MatchJob& one, const ItemSet& is, cudaStream_t st);
+// direct FP32 correlation: threads-per-tile class of a radius (1, 2, 4 or 8;
+// 0 when R is too large), and whether the shared memory of (m, R) fits
+int corr_f32_class(int R);
+bool corr_f32_supported(int m, int R);
+cudaError_t launch_corr_f32(const MatchJob& one, const ItemSet& is, int tpt, cudaStream_t st);
 bool corr_fft_supported(int m, int R);
-cudaError_t launch_corr_fft(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                            const PointStat* stats, float* maps, cudaStream_t st);
-cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                           const PointStat* stats, float* maps, int* err_flag, int form,
-                           cudaStream_t st);  // form: 0 auto, 1 Toeplitz, 2 column, 3 band
+int corr_fft_side(int m, int R);  // smallest transform side that serves (m, R): 64 or 128
+cudaError_t launch_corr_fft(const MatchJob& one, const ItemSet& is, int L, cudaStream_t st);
+// tensor-core forms: 1 Toeplitz, 2 column, 3 band.  corr_tc_class: the
+// kernel instance a job of (m, R) takes in that form (column: G, band: NQ,
+// Toeplitz: 1 = runs, one pair per launch), 0 where the form does not run;
+// corr_tc_auto_form: the form IGEMM_TC picks (fewest MMAs), 0 = none;
+// corr_tc_maps: sets the job's tensor maps for the form.
+int corr_tc_class(int form, int m, int R);
+int corr_tc_auto_form(int m, int R);
+bool corr_tc_maps(int form, MatchJob& j);
+cudaError_t launch_corr_tc(int form, int cls, const MatchJob& one, const ItemSet& is, const int* ms, const int* Rs,
+                           int cnt, int* err_flag, cudaStream_t st);
 size_t corr_tc_smem_bytes(int m, int R);
-cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m, int R, const PointStat* stats,
-                              const float* num, int centered, float* out_maps, fastncc_result* out,
-                              cudaStream_t st);
+cudaError_t launch_ncc_argmax(const MatchJob& one, const ItemSet& is, int centered, cudaStream_t st);
 
 // block-based FAST (k_fast.cu)
 cudaError_t launch_fast_blocks(const float* img, int H, int W, size_t pitch, float t, int grid_y, int grid_x,

@@ -168,11 +168,27 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Shared-memory layout of one launch, fixed for all its items: two window
+// tile slots, TS template slab slots and the partial-sum buffer, each slot
+// as large as the largest item of the launch needs.  An item's own geometry
+// (band_geom of its m, R) sets what is copied into a slot and how the MMAs
+// read it.
+struct BandLaunch {
+    int TS;            // template slab slots
+    int tile_stride;   // bytes per window tile slot
+    int slab_stride;   // bytes per template slab slot
+    int part_off;      // partial-sum buffer
+    int smem;          // dynamic shared memory of the launch
+};
+
+// Items: the points of `one`, or (job, point) pairs of a batch; item kk goes
+// to CTA kk mod grid (a batch lists its items by decreasing cost).  The
+// window tile map is the job's tm[0] (row-major layout rm), the template
+// slab map its tm[1] (column-major layout cm).
 template <int NQ>
 __global__ void __launch_bounds__(kBandThreads, 1)
-    k_corr_tc_band(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmT,
-                   const int32_t* __restrict__ pts, int n, int m, int R, const PointStat* __restrict__ stats,
-                   float* __restrict__ maps, int* __restrict__ err) {
+    k_corr_tc_band(const __grid_constant__ MatchJob one, const MatchJob* __restrict__ jobs,
+                   const int2* __restrict__ items, int n_items, const BandLaunch BL, int* __restrict__ err) {
     constexpr int N = NQ * 16;
     constexpr int N4 = N / 4;
     constexpr int GEM = band_ge_max(NQ);
@@ -181,10 +197,8 @@ __global__ void __launch_bounds__(kBandThreads, 1)
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
 
-    const BandGeom g = band_geom(m, R);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int h = template_half(m);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bars = smem_u32(&s_bar[0]);
     auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
@@ -196,7 +210,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
             mbar_init(bar(BD_AFULL + i), 1);
             mbar_init(bar(BD_AEMPTY + i), 4);  // the four warps of the draining team
         }
-        for (int i = 0; i < g.TS; ++i) {
+        for (int i = 0; i < BL.TS; ++i) {
             mbar_init(bar(BD_TFULL + i), 1);
             mbar_init(bar(BD_TEMPTY + i), 1);
         }
@@ -220,11 +234,18 @@ __global__ void __launch_bounds__(kBandThreads, 1)
     uint32_t t_issued = 0, w_issued = 0, mma_issued = 0;
     bool ok = true;
 
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    const uint32_t TS = (uint32_t)BL.TS;
+    const uint32_t slab_off = 2u * (uint32_t)BL.tile_stride;
+    for (int kk = blockIdx.x; kk < n_items; kk += gridDim.x) {
         if (warp < 4 && *reinterpret_cast<volatile int*>(&s_abort)) break;  // the drain warps never leave early
-        const PointStat st = stats[k];
+        int k;
+        const MatchJob& J = item_job(one, jobs, items, kk, &k);
+        const PointStat st = J.stats[k];
         if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
-        const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
+        const int m = J.m, R = J.R;
+        const BandGeom g = band_geom(m, R);
+        const int h = template_half(m);
+        const int ty0 = J.pts[2 * k + 1] - h, tx0 = J.pts[2 * k] - h;
         const int wy0 = ty0 - R, wx0 = tx0 - R;
         if (warp == 0) {
             // ---------------- TMA producer ----------------
@@ -237,19 +258,19 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                         if (gp >= 2) ok = mbar_wait(bar(BD_WEMPTY + slot), ((gp >> 1) - 1) & 1, &s_abort);
                         if (!ok) break;
                         mbar_expect_tx(bar(BD_WFULL + slot), (uint32_t)g.tile_bytes);
-                        tma_load_4d(sbase + g.tile_off + slot * g.tile_bytes, &tmW, 0, wx0 + 8 * e0, wy0 + 16 * yb, 0,
+                        tma_load_4d(sbase + slot * (uint32_t)BL.tile_stride, &J.tm[0], 0, wx0 + 8 * e0, wy0 + 16 * yb, 0,
                                     bar(BD_WFULL + slot));
                         ++w_issued;
                         for (int s = 0; s < g.nS && ok; ++s, ++tp) {
-                            const uint32_t ts = tp % (uint32_t)g.TS;
-                            if (tp >= (uint32_t)g.TS)
-                                ok = mbar_wait(bar(BD_TEMPTY + ts), ((tp / g.TS) - 1) & 1, &s_abort);
+                            const uint32_t ts = tp % TS;
+                            if (tp >= TS)
+                                ok = mbar_wait(bar(BD_TEMPTY + ts), ((tp / TS) - 1) & 1, &s_abort);
                             if (!ok) break;
                             // a run of 8 rows that starts above the image is zero filled whole, so
                             // the slab starts at row 0 at the latest (the issuer compensates)
                             const int r0 = ty0 + 16 * yb - 2 * R;
                             mbar_expect_tx(bar(BD_TFULL + ts), (uint32_t)g.slab_bytes);
-                            tma_load_4d(sbase + g.slab_off + ts * g.slab_bytes, &tmT, 0, r0 < 0 ? 0 : r0,
+                            tma_load_4d(sbase + slab_off + ts * (uint32_t)BL.slab_stride, &J.tm[1], 0, r0 < 0 ? 0 : r0,
                                         tx0 + s * kBandQ, 0, bar(BD_TFULL + ts));
                             ++t_issued;
                         }
@@ -260,12 +281,12 @@ __global__ void __launch_bounds__(kBandThreads, 1)
             // ---------------- MMA issuer ----------------
             if (lane == 0) {
                 const uint32_t idesc = idesc_bf16(kM, N);
-                const uint64_t da0 = smem_desc(sbase + g.tile_off, 16u * g.Xw * 16u, (uint32_t)g.Xw * 16u);
-                const uint64_t db0 = smem_desc(sbase + g.slab_off, (uint32_t)(kBandQ * g.trows * 16), 128);
-                const uint32_t tile_step = (uint32_t)g.tile_bytes >> 4, slab_step = (uint32_t)g.slab_bytes >> 4;
+                const uint64_t da0 = smem_desc(sbase, 16u * g.Xw * 16u, (uint32_t)g.Xw * 16u);
+                const uint64_t db0 = smem_desc(sbase + slab_off, (uint32_t)(kBandQ * g.trows * 16), 128);
+                const uint32_t tile_step = (uint32_t)BL.tile_stride >> 4, slab_step = (uint32_t)BL.slab_stride >> 4;
                 const uint32_t tcol = (uint32_t)g.trows;  // slab column stride in 16-byte units
                 uint32_t gi = gc;
-                uint32_t ts = tc % (uint32_t)g.TS, tph = (tc / (uint32_t)g.TS) & 1u;
+                uint32_t ts = tc % TS, tph = (tc / TS) & 1u;
                 for (int eg = 0; eg < g.nEG && ok; ++eg) {
                     const int Gg = g.nE - eg * g.GE < g.GE ? g.nE - eg * g.GE : g.GE;
                     for (int yb = 0; yb < g.nYB && ok; ++yb, ++gi) {
@@ -298,7 +319,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                             }
                             mma_issued += (uint32_t)(nq * Gg);
                             mma_commit(bar(BD_TEMPTY + ts));
-                            if (++ts == (uint32_t)g.TS) { ts = 0; tph ^= 1u; }
+                            if (++ts == TS) { ts = 0; tph ^= 1u; }
                         }
                         if (!ok) break;
                         mma_commit(bar(BD_WEMPTY + half));
@@ -315,8 +336,8 @@ __global__ void __launch_bounds__(kBandThreads, 1)
             const int gq = lane >> 3, r = lane & 7;
             const bool b0 = (gq & 1) != 0, b1 = (gq & 2) != 0;
             const int joff = (b0 ? N / 2 : 0) + (b1 ? N4 : 0);
-            float* part = reinterpret_cast<float*>(smem + g.part_off);
-            float* out = maps + (size_t)k * g.P1 * g.P1;
+            float* part = reinterpret_cast<float*>(smem + BL.part_off);
+            float* out = J.maps + (size_t)k * g.P1 * g.P1;
             const uint32_t lbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)team * 256u;
             uint32_t gd = gc;
             for (int eg = 0; eg < g.nEG; ++eg) {
@@ -414,9 +435,9 @@ __global__ void __launch_bounds__(kBandThreads, 1)
 
     if (*reinterpret_cast<volatile int*>(&s_abort)) {
         if (warp == 0 && lane == 0) {  // let every copy in flight land
-            for (uint32_t i = 0; i < (uint32_t)g.TS && i < t_issued; ++i) {
+            for (uint32_t i = 0; i < (uint32_t)BL.TS && i < t_issued; ++i) {
                 const uint32_t ti = t_issued - 1 - i;
-                mbar_wait_short(bar(BD_TFULL + ti % g.TS), (ti / g.TS) & 1);
+                mbar_wait_short(bar(BD_TFULL + ti % BL.TS), (ti / BL.TS) & 1);
             }
             for (uint32_t i = 0; i < 2u && i < w_issued; ++i) {
                 const uint32_t wi = w_issued - 1 - i;
@@ -446,32 +467,71 @@ long long corr_band_mmas(int m, int R) {
     return (long long)b.nYB * b.nE * m;
 }
 
-cudaError_t launch_corr_band(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                             const PointStat* stats, float* maps, int* err_flag, int sms, cudaStream_t st) {
+int corr_band_class(int m, int R) { return band_supported(m, R) ? band_geom(m, R).NQ : 0; }
+
+// The job's tensor maps for the band form: window tiles of 16 rows x Xw
+// pixels of rm = [2][H][W][8] (tm[0]) and template slabs of kBandQ columns
+// x trows rows of cm = [2][W][H][8] (tm[1]), both in 128-byte runs of 8
+// pixels.
+bool corr_band_maps(MatchJob& j) {
+    const BandGeom bg = band_geom(j.m, j.R);
+    return make_map_rows8(&j.tm[0], j.rrm, (uint64_t)j.Wr, (uint64_t)j.Hr, (uint32_t)bg.Xw, 16) &&
+           make_map_rows8(&j.tm[1], j.scm, (uint64_t)j.Hs, (uint64_t)j.Ws, (uint32_t)bg.trows, kBandQ);
+}
+
+namespace {
+
+// launch layout for items whose (m, R) lie in [*, max_m] x [*, max_R] of one
+// class: every slot as large as the class's largest need
+bool band_launch(int NQ, const int* ms, const int* Rs, int cnt, BandLaunch* out) {
+    int tile = 0, slab = 0, part = 0, guard = 0;
+    for (int i = 0; i < cnt; ++i) {
+        const BandGeom g = band_geom(ms[i], Rs[i]);
+        if (g.NQ != NQ) return false;
+        tile = g.tile_bytes > tile ? g.tile_bytes : tile;
+        slab = g.slab_bytes > slab ? g.slab_bytes : slab;
+        const int pb = 8 * g.GE * g.P1 * 8 * 4;
+        part = pb > part ? pb : part;
+        const int gd = (g.N - g.trows) * 16 + 128;
+        guard = gd > guard ? gd : guard;
+    }
+    BandLaunch L;
+    const int fixed = 2 * tile + part + guard;
+    int ts = (kTcSmemMax - fixed) / (slab > 0 ? slab : 1);
+    L.TS = ts > kBandMaxTS ? kBandMaxTS : ts;
+    L.tile_stride = tile;
+    L.slab_stride = slab;
+    L.part_off = 2 * tile + L.TS * slab;
+    L.smem = L.part_off + part + guard;
+    if (L.smem < kBandSmemFloor) L.smem = kBandSmemFloor;
+    *out = L;
+    return L.TS >= 2 && L.smem <= kTcSmemMax;
+}
+
+}  // namespace
+
+// One launch over `is` (single pair: its points); every job of the launch
+// in band class NQ with its tensor maps set (corr_band_maps).  ms / Rs: the
+// distinct (m, R) of the launch's jobs (their layout bounds).
+cudaError_t launch_corr_band(const MatchJob& one, const ItemSet& is, int NQ, const int* ms, const int* Rs, int cnt,
+                             int* err_flag, int sms, cudaStream_t st) {
+    const int n = is.items ? is.n : one.n;
     if (n <= 0) return cudaSuccess;
-    if (!band_supported(m, R)) return cudaErrorNotSupported;
-    const BandGeom bg = band_geom(m, R);
-    // window tiles: 16 rows x Xw pixels of rm = [2][H][W][8]; template slabs:
-    // kBandQ columns x trows rows of cm = [2][W][H][8]; both in 128-byte runs
-    // of 8 pixels
-    alignas(64) CUtensorMap tmW, tmT;
-    if (!make_map_rows8(&tmW, ref.rm, (uint64_t)ref.W, (uint64_t)ref.H, (uint32_t)bg.Xw, 16) ||
-        !make_map_rows8(&tmT, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, (uint32_t)bg.trows, kBandQ))
-        return cudaErrorNotSupported;
+    BandLaunch BL;
+    if (!band_launch(NQ, ms, Rs, cnt, &BL)) return cudaErrorNotSupported;
     const int grid = n < sms ? n : sms;
     // one CTA per SM: the kernel allocates all 512 TMEM columns, so a second
     // CTA on the SM would block in tcgen05.alloc until the first one's whole
     // persistent loop ended; more than half of the SM's shared memory rules
-    // a second CTA out
-    const int smem = bg.smem > kBandSmemFloor ? bg.smem : kBandSmemFloor;
+    // a second CTA out (BandLaunch.smem is at least kBandSmemFloor)
     cudaError_t e = cudaErrorNotSupported;
 #define SFOC_BAND_CASE(NQV)                                                                                   \
     case NQV:                                                                                                 \
-        e = cudaFuncSetAttribute(k_corr_tc_band<NQV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);    \
+        e = cudaFuncSetAttribute(k_corr_tc_band<NQV>, cudaFuncAttributeMaxDynamicSharedMemorySize, BL.smem); \
         if (e != cudaSuccess) return e;                                                                       \
-        k_corr_tc_band<NQV><<<grid, kBandThreads, smem, st>>>(tmW, tmT, pts, n, m, R, stats, maps, err_flag); \
+        k_corr_tc_band<NQV><<<grid, kBandThreads, BL.smem, st>>>(one, is.jobs, is.items, n, BL, err_flag);     \
         return cudaGetLastError();
-    switch (bg.NQ) {
+    switch (NQ) {
         SFOC_BAND_CASE(1)
         SFOC_BAND_CASE(2)
         SFOC_BAND_CASE(3)

@@ -18,15 +18,19 @@ constexpr int kThreads = 256;
 __device__ __forceinline__ int roundup(int v, int a) { return (v + a - 1) / a * a; }
 
 template <int TPT>
-__global__ void __launch_bounds__(kThreads) k_corr_f32(const float* __restrict__ ref, size_t rpitch,
-                                                        size_t rplane, const float* __restrict__ sen, size_t spitch,
-                                                        size_t splane, const int32_t* __restrict__ pts, int m, int R,
-                                                        int z, const PointStat* __restrict__ stats,
-                                                        float* __restrict__ maps) {
+__global__ void __launch_bounds__(kThreads) k_corr_f32(const __grid_constant__ MatchJob one,
+                                                        const MatchJob* __restrict__ jobs,
+                                                        const int2* __restrict__ items) {
     extern __shared__ __align__(16) float sm[];
-    const int k = blockIdx.x;
-    const PointStat st = stats[k];
+    int k;
+    const MatchJob& J = item_job(one, jobs, items, blockIdx.x, &k);
+    const PointStat st = J.stats[k];
     if (st.status != SFOC_PT_OK) return;  // the NCC stage ignores this map
+    const float* __restrict__ ref = J.rf32;
+    const float* __restrict__ sen = J.sf32;
+    const size_t rpitch = J.rpitch, rplane = J.rplane, spitch = J.spitch, splane = J.splane;
+    const int32_t* __restrict__ pts = J.pts;
+    const int m = J.m, R = J.R, z = J.z;
     const int P1 = 2 * R + 1;
     const int Lw = m + 2 * R;
     const int mp = roundup(m, 4);
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) k_corr_f32(const float* __restrict__
             }
         }
     }
-    float* out = maps + (size_t)k * P1 * P1;
+    float* out = J.maps + (size_t)k * P1 * P1;
 #pragma unroll
     for (int j = 0; j < TPT; ++j) {
         const int t = threadIdx.x + j * kThreads;
@@ -104,21 +108,26 @@ size_t smem_bytes(int m, int R) {
 
 }  // namespace
 
-cudaError_t launch_corr_f32(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                            const PointStat* stats, float* maps, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+int corr_f32_class(int R) {
     const int P1 = 2 * R + 1;
-    const int ntile = P1 * ((P1 + 7) / 8);
-    const int tpt = (ntile + kThreads - 1) / kThreads;
+    const int tpt = (P1 * ((P1 + 7) / 8) + kThreads - 1) / kThreads;
+    return tpt <= 1 ? 1 : tpt <= 2 ? 2 : tpt <= 4 ? 4 : tpt <= 8 ? 8 : 0;
+}
+
+bool corr_f32_supported(int m, int R) { return corr_f32_class(R) > 0 && smem_bytes(m, R) <= 227 * 1024; }
+
+// tpt: threads-per-tile class, at least corr_f32_class of the largest R
+cudaError_t launch_corr_f32(const MatchJob& one, const ItemSet& is, int tpt, cudaStream_t st) {
+    const int n = is.items ? is.n : one.n;
+    if (n <= 0) return cudaSuccess;
+    const int m = is.items ? is.max_m : one.m, R = is.items ? is.max_R : one.R;
+    if (!corr_f32_supported(m, R) || tpt < corr_f32_class(R)) return cudaErrorInvalidValue;
     size_t smem = smem_bytes(m, R);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    size_t rplane = ref.pitch * ref.H, splane = sen.pitch * sen.H;
     cudaError_t e;
 #define SFOC_CORR_CASE(N)                                                                                      \
     e = cudaFuncSetAttribute(k_corr_f32<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
     if (e != cudaSuccess) return e;                                                                            \
-    k_corr_f32<N><<<n, kThreads, smem, st>>>(ref.f32, ref.pitch, rplane, sen.f32, sen.pitch, splane, pts, m, R, \
-                                             ref.z, stats, maps);
+    k_corr_f32<N><<<n, kThreads, smem, st>>>(one, is.jobs, is.items);
     if (tpt <= 1) { SFOC_CORR_CASE(1) }
     else if (tpt <= 2) { SFOC_CORR_CASE(2) }
     else if (tpt <= 4) { SFOC_CORR_CASE(4) }

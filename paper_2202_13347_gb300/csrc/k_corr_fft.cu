@@ -189,14 +189,17 @@ __device__ __forceinline__ float2 cross_spectrum(float2 a, float2 b) {
     return make_float2(0.25f * fmaf(s.x, d.y, -s.y * d.x), 0.25f * fmaf(s.x, d.x, s.y * d.y));
 }
 
+// Items: the points of `one` (items == nullptr) or (job, point) pairs of a
+// batch; with a queue the CTAs take items from an atomic counter (points of
+// uneven cost balance across the SMs), else item k goes to CTA k mod grid.
 template <int L>
 __global__ void __launch_bounds__(FftShape<L>::T, 1)
-    k_corr_fft(const float* __restrict__ Sf, size_t spitch, size_t splane, const float* __restrict__ Tf,
-               size_t tpitch, size_t tplane, const int32_t* __restrict__ pts, int n, int m, int R, int z,
-               const PointStat* __restrict__ stats, float* __restrict__ maps) {
+    k_corr_fft(const __grid_constant__ MatchJob one, const MatchJob* __restrict__ jobs,
+               const int2* __restrict__ items, int n_items, int* __restrict__ queue) {
     using Sh = FftShape<L>;
     constexpr int E = Sh::E, ZP = Sh::ZP, kFftGroups = Sh::G, kFftThreads = Sh::T;
     extern __shared__ __align__(16) float2 fsm[];
+    __shared__ int s_item;
     float2* Z = fsm;                                       // L x ZP
     float2* scr = Z + (size_t)L * ZP;                      // kFftGroups x SG
     float2* tw = scr + (size_t)kFftGroups * Sh::SG;        // 8E twiddles W_L^{t k1} at 8 k1 + t
@@ -206,8 +209,6 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
     const int grp = tid >> 3, t = tid & 7;
     const int lane = tid & 31, gbase = lane & ~7;
     float2* sc = scr + grp * Sh::SG;
-    const int P1 = 2 * R + 1, Lw = m + 2 * R;
-    const int h = template_half(m);
     const float inv_area = 1.f / ((float)L * (float)L);
     // partner of row t + 8m is row -(t + 8m): thread (8 - t) mod 8, index
     // (E - m) mod E for t = 0, E - 1 - m otherwise
@@ -218,13 +219,40 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
         sincospi(-2.0 * ((p & 7) * (p >> 3)) / L, &s, &c);
         tw[p] = make_float2((float)c, (float)s);
     }
-    for (int i = tid; i < L * ZP; i += kFftThreads) Z[i] = make_float2(0.f, 0.f);  // rows >= m + 2R stay zero
+    for (int i = tid; i < L * ZP; i += kFftThreads) Z[i] = make_float2(0.f, 0.f);
     __syncthreads();
+    // rows of Z at or past zhi are zero; an item's row passes write the rows
+    // below its m + 2R, every other row it reads must be zero
+    int zhi = 0;
 
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
-        const PointStat st = stats[k];
+    for (int next = blockIdx.x;;) {
+        int kk;
+        if (queue) {
+            if (tid == 0) s_item = atomicAdd(queue, 1);
+            __syncthreads();
+            kk = s_item;
+            __syncthreads();  // read by all before thread 0 takes the next one
+        } else {
+            kk = next;
+            next += gridDim.x;
+        }
+        if (kk >= n_items) break;
+        int k;
+        const MatchJob& J = item_job(one, jobs, items, kk, &k);
+        const PointStat st = J.stats[k];
         if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
-        const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
+        const float* __restrict__ Sf = J.rf32;
+        const float* __restrict__ Tf = J.sf32;
+        const size_t spitch = J.rpitch, splane = J.rplane, tpitch = J.spitch, tplane = J.splane;
+        const int m = J.m, R = J.R, z = J.z;
+        const int P1 = 2 * R + 1, Lw = m + 2 * R;
+        const int h = template_half(m);
+        if (zhi > Lw) {  // rows [Lw, zhi) of an earlier, taller window
+            for (int i = tid; i < (zhi - Lw) * ZP; i += kFftThreads) Z[(size_t)Lw * ZP + i] = make_float2(0.f, 0.f);
+            __syncthreads();
+        }
+        zhi = Lw;
+        const int ty0 = J.pts[2 * k + 1] - h, tx0 = J.pts[2 * k] - h;
         const int wy0 = ty0 - R, wx0 = tx0 - R;
         const float tmean = st.tmean;
         float2 acc[E];  // channel sum of X conj(Y) on column pr of this group's pair
@@ -314,7 +342,7 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
         }
         __syncthreads();
         // ---- inverse along the rows (Hermitian extension), real part
-        float* out = maps + (size_t)k * P1 * P1;
+        float* out = J.maps + (size_t)k * P1 * P1;
         for (int y0 = 0; y0 < P1; y0 += kFftGroups) {
             const int y = y0 + grp;
             const int yy = y < P1 ? y : 0;
@@ -342,15 +370,18 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
 
 bool corr_fft_supported(int m, int R) { return m + 2 * R <= 128; }
 
-cudaError_t launch_corr_fft(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                            const PointStat* stats, float* maps, cudaStream_t st) {
+int corr_fft_side(int m, int R) { return m + 2 * R <= 64 ? 64 : 128; }
+
+// L: the transform side (64 or 128, at least the largest m + 2R of the items)
+cudaError_t launch_corr_fft(const MatchJob& one, const ItemSet& is, int L, cudaStream_t st) {
+    const int n = is.items ? is.n : one.n;
     if (n <= 0) return cudaSuccess;
-    if (ref.dtype != SFOC_DTYPE_F32 || sen.dtype != SFOC_DTYPE_F32 || !corr_fft_supported(m, R))
-        return cudaErrorNotSupported;
+    const int lw = is.items ? is.max_lw : one.m + 2 * one.R;
+    if ((L != 64 && L != 128) || lw > L) return cudaErrorNotSupported;
+    if (!is.items && (one.rf32 == nullptr || one.sf32 == nullptr)) return cudaErrorNotSupported;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t rplane = ref.pitch * ref.H, splane = sen.pitch * sen.H;
     cudaError_t e;
 #define SFOC_FFT_LAUNCH(LV)                                                                                       \
     {                                                                                                             \
@@ -358,10 +389,9 @@ cudaError_t launch_corr_fft(const Cube& ref, const Cube& sen, const int32_t* pts
         e = cudaFuncSetAttribute(k_corr_fft<LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);             \
         if (e != cudaSuccess) return e;                                                                           \
         const int grid = n < sms ? n : sms;                                                                       \
-        k_corr_fft<LV><<<grid, FftShape<LV>::T, smem, st>>>(ref.f32, ref.pitch, rplane, sen.f32, sen.pitch, splane, \
-                                                        pts, n, m, R, ref.z, stats, maps);                      \
+        k_corr_fft<LV><<<grid, FftShape<LV>::T, smem, st>>>(one, is.jobs, is.items, n, is.queue);                 \
     }
-    if (m + 2 * R <= 64) {
+    if (L == 64) {
         SFOC_FFT_LAUNCH(64)
     } else {
         SFOC_FFT_LAUNCH(128)

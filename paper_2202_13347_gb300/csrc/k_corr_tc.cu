@@ -104,11 +104,18 @@ enum {
 
 // NQ = number of 16-column accumulator chunks (Npad / 16), UC = template
 // columns per column block (8, or 4 for the largest windows)
+// One pair (`one`): its window slab map tm[0], template column maps tm[1]
+// (rows [0, 256)) and tm[2] (rows past 256).
 template <int NQ, int UC>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_corr_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const __grid_constant__ CUtensorMap tmB2, const int32_t* __restrict__ pts, int n, int m, int R,
-              const PointStat* __restrict__ stats, float* __restrict__ maps, int* __restrict__ err) {
+    k_corr_tc(const __grid_constant__ MatchJob one, int* __restrict__ err) {
+    const CUtensorMap& tmA = one.tm[0];
+    const CUtensorMap& tmB = one.tm[1];
+    const CUtensorMap& tmB2 = one.tm[2];
+    const int32_t* __restrict__ pts = one.pts;
+    const int n = one.n, m = one.m, R = one.R;
+    const PointStat* __restrict__ stats = one.stats;
+    float* __restrict__ maps = one.maps;
     constexpr int U = UC;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_bar[NBAR];
@@ -453,28 +460,59 @@ enum {
     CB_N
 };
 
+// Shared-memory layout of one column-form launch, fixed for all its items:
+// TS template slab slots and WS window slab slots (both counts set by the
+// class's G), each as large as the launch's largest item needs, then the
+// band buffers and partial sums, whose number (NB) each item derives from
+// the room left (col_item).
+struct ColLaunch {
+    int WS, TS;
+    int ts_stride, ws_stride;  // bytes per template / window slab slot
+    int w_off, bk_off;
+    int smem;
+};
+
+// An item's geometry inside a launch: its own slab shapes and band buffers,
+// the launch's slots and offsets.
+__host__ __device__ inline ColGeom col_item(int m, int R, const ColLaunch& L) {
+    ColGeom c = col_geom(m, R);
+    c.WS = L.WS;
+    c.TS = L.TS;
+    c.t_off = 0;
+    c.w_off = L.w_off;
+    c.bk_off = L.bk_off;
+    const int guard = 2048 - 16 * c.wrows;
+    int nb = (L.smem - c.bk_off - guard) / (c.bk_bytes + kColDrain * 4);
+    nb = nb > c.G ? c.G : nb;
+    c.NB = nb < 1 ? 1 : nb;
+    c.part_off = c.bk_off + c.NB * c.bk_bytes;
+    c.smem = L.smem;
+    return c;
+}
+
+// Items: the points of `one`, or (job, point) pairs of a batch whose jobs
+// all have col_geom(m, R).G == G; item kk goes to CTA kk mod grid.  The
+// window slab map is the job's tm[0], the template slab map its tm[1] (both
+// over the column-major layout cm).
 template <int G>
 __global__ void __launch_bounds__(kColThreads, 1)
-    k_corr_tc_col(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmT,
-                  const int32_t* __restrict__ pts, int n, int m, int R, const PointStat* __restrict__ stats,
-                  float* __restrict__ maps, int* __restrict__ err) {
+    k_corr_tc_col(const __grid_constant__ MatchJob one, const MatchJob* __restrict__ jobs,
+                  const int2* __restrict__ items, int n_items, const ColLaunch CL, int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_bar[CB_N];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ int s_go;
 
-    const ColGeom g = col_geom(m, R);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int h = template_half(m);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bars = smem_u32(&s_bar[0]);
     auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
 
     if (tid == 0) {
-        for (int i = 0; i < g.WS; ++i) mbar_init(bar(CB_WEMPTY + i), 1);
-        for (int i = 0; i < g.TS; ++i) {
+        for (int i = 0; i < CL.WS; ++i) mbar_init(bar(CB_WEMPTY + i), 1);
+        for (int i = 0; i < CL.TS; ++i) {
             mbar_init(bar(CB_TFULL + i), 1);
             mbar_init(bar(CB_TEMPTY + i), 1);
         }
@@ -500,13 +538,18 @@ __global__ void __launch_bounds__(kColThreads, 1)
     // advanced identically by every role
     uint32_t wsc = 0, tsc = 0, grp = 0;
     uint32_t t_issued = 0, mma_issued = 0;
-    const int nstage = (m + kColQ - 1) / kColQ;  // stages (template slabs) per group
 
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    for (int kk = blockIdx.x; kk < n_items; kk += gridDim.x) {
         if (*reinterpret_cast<volatile int*>(&s_abort)) break;
-        const PointStat st = stats[k];
+        int k;
+        const MatchJob& J = item_job(one, jobs, items, kk, &k);
+        const PointStat st = J.stats[k];
         if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
-        const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
+        const int m = J.m, R = J.R;
+        const ColGeom g = col_item(m, R, CL);
+        const int nstage = (m + kColQ - 1) / kColQ;  // stages (template slabs) per group
+        const int h = template_half(m);
+        const int ty0 = J.pts[2 * k + 1] - h, tx0 = J.pts[2 * k] - h;
         const int wy0 = ty0 - R, wx0 = tx0 - R;
         bool ok = true;
         if (warp == 0) {
@@ -533,12 +576,13 @@ __global__ void __launch_bounds__(kColThreads, 1)
                         if (!ok) break;
                         const uint32_t full = bar(CB_TFULL + tslot);
                         mbar_expect_tx(full, (uint32_t)g.ts_bytes + (uint32_t)(last + 1 - wl) * (uint32_t)g.ws_bytes);
-                        tma_load_4d(sbase + g.t_off + tslot * g.ts_bytes, &tmT, 0, ty0, tx0 + s * kColQ, 0, full);
+                        tma_load_4d(sbase + g.t_off + tslot * (uint32_t)CL.ts_stride, &J.tm[1], 0, ty0, tx0 + s * kColQ, 0,
+                                    full);
                         ++tv;
                         ++t_issued;
                         for (; wl <= last; ++wl, ++wv)
-                            tma_load_4d(sbase + g.w_off + (wv % g.WS) * g.ws_bytes, &tmW, 0, wy0, wx0 + d0 + wl * kColQ,
-                                        0, full);
+                            tma_load_4d(sbase + g.w_off + (wv % g.WS) * (uint32_t)CL.ws_stride, &J.tm[0], 0, wy0,
+                                        wx0 + d0 + wl * kColQ, 0, full);
                     }
                 }
             }
@@ -550,7 +594,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 const uint32_t tcol = (uint32_t)g.trows;  // template column stride in 16-byte units
                 const uint64_t da_base = smem_desc(sbase + g.w_off, kColQ * g.wrows * 16u, 128);
                 const uint64_t db_base = smem_desc(sbase + g.t_off, kColQ * g.trows * 16u, 128);
-                const uint32_t w_step = (uint32_t)g.ws_bytes >> 4, t_step = (uint32_t)g.ts_bytes >> 4;
+                const uint32_t w_step = (uint32_t)CL.ws_stride >> 4, t_step = (uint32_t)CL.ts_stride >> 4;
                 uint32_t dD[G];
 #pragma unroll
                 for (int gi = 0; gi < G; ++gi) dD[gi] = tmem + (uint32_t)(gi * g.Npad);
@@ -683,7 +727,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
             }
             const int dummy = g.P1 * Sb + lane;  // per-lane slot for entries outside the band
             float* pbuf = reinterpret_cast<float*>(smem + g.part_off);
-            float* out = maps + (size_t)k * g.P1 * g.P1;
+            float* out = J.maps + (size_t)k * g.P1 * g.P1;
             const uint32_t lbase = tmem + ((uint32_t)(quarter * 32) << 16);
             uint32_t gg = grp;
             for (int d0 = 0; d0 < g.P1 && ok; d0 += G, ++gg) {
@@ -801,9 +845,9 @@ __global__ void __launch_bounds__(kColThreads, 1)
 
     if (*reinterpret_cast<volatile int*>(&s_abort)) {
         if (warp == 0 && lane == 0) {  // let every copy in flight land (all complete on template barriers)
-            for (uint32_t i = 0; i < (uint32_t)g.TS && i < t_issued; ++i) {
+            for (uint32_t i = 0; i < (uint32_t)CL.TS && i < t_issued; ++i) {
                 const uint32_t ti = t_issued - 1 - i;
-                mbar_wait_short(bar(CB_TFULL + ti % g.TS), (ti / g.TS) & 1);
+                mbar_wait_short(bar(CB_TFULL + ti % CL.TS), (ti / CL.TS) & 1);
             }
         }
         if (warp == 1 && lane == 0 && mma_issued > 0) {  // and every MMA issued
@@ -882,42 +926,113 @@ bool make_map_rows8(CUtensorMap* map, const void* base, uint64_t d1, uint64_t d2
 
 size_t corr_tc_smem_bytes(int m, int R) { return (size_t)tc_geom(m, R, pick_U(m, R)).smem; }
 
-cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                           const PointStat* stats, float* maps, int* err_flag, int form, cudaStream_t st) {
+namespace {
+
+bool col_ok(int m, int R) { return m + 2 * R <= kM && 2 * R + 1 <= kM && col_geom(m, R).smem <= kColSmemMax; }
+
+bool toeplitz_ok(int m, int R) {
+    if (2 * R + 1 > kM || m > kMaxTemplate) return false;
+    const TcGeom g = tc_geom(m, R, pick_U(m, R));
+    return g.NA >= 2 && g.JS <= 512 && g.AW <= 256;
+}
+
+// launch layout of a column-form class: slots as large as its largest item
+bool col_launch(int G, const int* ms, const int* Rs, int cnt, ColLaunch* out) {
+    int tsb = 0, wsb = 0, need = 0;
+    for (int i = 0; i < cnt; ++i) {
+        const ColGeom g = col_geom(ms[i], Rs[i]);
+        if (g.G != G) return false;
+        tsb = g.ts_bytes > tsb ? g.ts_bytes : tsb;
+        wsb = g.ws_bytes > wsb ? g.ws_bytes : wsb;
+    }
+    ColLaunch L;
+    L.TS = kColMaxTS;
+    L.WS = (kColQ + G - 2) / kColQ + 2;
+    L.ts_stride = tsb;
+    L.ws_stride = wsb;
+    L.w_off = L.TS * tsb;
+    L.bk_off = L.w_off + L.WS * wsb;
+    L.smem = kColSmemMax;
+    // every item needs one band buffer and its partial sums, and the read
+    // guard past the last window slab
+    for (int i = 0; i < cnt; ++i) {
+        const ColGeom g = col_geom(ms[i], Rs[i]);
+        const int n1 = L.bk_off + g.bk_bytes + kColDrain * 4 + (2048 - 16 * g.wrows);
+        need = n1 > need ? n1 : need;
+    }
+    *out = L;
+    return need <= L.smem && L.WS <= kColMaxWS;
+}
+
+}  // namespace
+
+int corr_tc_class(int form, int m, int R) {
+    switch (form) {
+        case 1: return toeplitz_ok(m, R) ? 1 : 0;  // per pair (its geometry decides the instance)
+        case 2: return col_ok(m, R) ? col_geom(m, R).G : 0;
+        case 3: return corr_band_class(m, R);
+        default: return 0;
+    }
+}
+
+int corr_tc_auto_form(int m, int R) {
+    // every form's MMAs cost about the same (M = 128, K = 16 and N <= 96 are
+    // bound by shared-memory operand reads), so the form that issues fewer
+    // per point wins: the column form (2R+1) m, the band form
+    // ceil((m+2R)/16) ceil((2R+1)/8) m; the Toeplitz form ((m+2R) m narrow
+    // ones) only when neither of the others runs
+    const bool c = col_ok(m, R), b = corr_band_supported(m, R);
+    if (b && (!c || corr_band_mmas(m, R) < (long long)(2 * R + 1) * m)) return 3;
+    if (c) return 2;
+    return toeplitz_ok(m, R) ? 1 : 0;
+}
+
+bool corr_tc_maps(int form, MatchJob& j) {
+    if (form == 3) return corr_band_maps(j);
+    if (form == 2) {
+        // slabs of 8 columns x 2 chunks, rows in 128-byte runs of 8 pixels
+        const ColGeom c = col_geom(j.m, j.R);
+        return make_map_rows8(&j.tm[0], j.rcm, (uint64_t)j.Hr, (uint64_t)j.Wr, (uint32_t)c.wrows, kColQ) &&
+               make_map_rows8(&j.tm[1], j.scm, (uint64_t)j.Hs, (uint64_t)j.Ws, (uint32_t)c.trows, kColQ);
+    }
+    if (form == 1) {
+        // A: window slab, box {8, AW, 8 rows, 2 chunks} over rm = [2][H][W][8]
+        // B: one template column, box {8, rows, 1, 1} over cm = [2][W][H][8];
+        //    rows [0, 256) through tm[1] and [256, JS) through tm[2] when JS > 256
+        const TcGeom g = tc_geom(j.m, j.R, pick_U(j.m, j.R));
+        const uint32_t brow = g.JS < 256 ? (uint32_t)g.JS : 256u;
+        const uint32_t brow2 = g.JS > 256 ? (uint32_t)(g.JS - 256) : 8u;
+        return make_map(&j.tm[0], j.rrm, (uint64_t)j.Wr, (uint64_t)j.Hr, (uint32_t)g.AW, kY, 2) &&
+               make_map(&j.tm[1], j.scm, (uint64_t)j.Hs, (uint64_t)j.Ws, brow, 1, 1) &&
+               make_map(&j.tm[2], j.scm, (uint64_t)j.Hs, (uint64_t)j.Ws, brow2, 1, 1);
+    }
+    return false;
+}
+
+// One launch of a tensor-core form over `is` (items == nullptr: the points
+// of `one`; the Toeplitz form only runs that way).  Every job of the launch
+// has class `cls` of the form and its tensor maps set (corr_tc_maps); ms /
+// Rs list the distinct (m, R) of its jobs.
+cudaError_t launch_corr_tc(int form, int cls, const MatchJob& one, const ItemSet& is, const int* ms, const int* Rs,
+                           int cnt, int* err_flag, cudaStream_t st) {
+    const int n = is.items ? is.n : one.n;
     if (n <= 0) return cudaSuccess;
-    if (ref.dtype != SFOC_DTYPE_BF16 || sen.dtype != SFOC_DTYPE_BF16 || ref.z != 12) return cudaErrorNotSupported;
-    if (2 * R + 1 > kM || m > kMaxTemplate) return cudaErrorNotSupported;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // Automatic choice: every form's MMAs cost about the same (M = 128, K = 16
-    // and N <= 96 are bound by shared-memory operand reads), so the form that
-    // issues fewer per point wins: the column form (2R+1) m, the band form
-    // ceil((m+2R)/16) ceil((2R+1)/8) m; the Toeplitz form ((m+2R) m narrow
-    // ones) only when neither of the others runs.
-    const bool col_ok = m + 2 * R <= kM && col_geom(m, R).smem <= kColSmemMax;
-    if (form == 0 && corr_band_supported(m, R) &&
-        (!col_ok || corr_band_mmas(m, R) < (long long)(2 * R + 1) * m))
-        form = 3;
-    if (form == 3) return launch_corr_band(ref, sen, pts, n, m, R, stats, maps, err_flag, sms, st);
-    if (form == 2 && !col_ok) return cudaErrorNotSupported;
-    if (col_ok && form != 1) {
-        const ColGeom c = col_geom(m, R);
-        if (c.smem > kColSmemMax) return cudaErrorNotSupported;
-        // slabs of 8 columns x 2 chunks, rows in 128-byte runs of 8 pixels
-        alignas(64) CUtensorMap tmW, tmT;
-        if (!make_map_rows8(&tmW, ref.cm, (uint64_t)ref.H, (uint64_t)ref.W, (uint32_t)c.wrows, kColQ) ||
-            !make_map_rows8(&tmT, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, (uint32_t)c.trows, kColQ))
-            return cudaErrorNotSupported;
-        const int grid = n < sms ? n : sms;
+    const int grid = n < sms ? n : sms;
+    if (form == 3) return launch_corr_band(one, is, cls, ms, Rs, cnt, err_flag, sms, st);
+    if (form == 2) {
+        ColLaunch CL;
+        if (!col_launch(cls, ms, Rs, cnt, &CL)) return cudaErrorNotSupported;
         cudaError_t e = cudaErrorNotSupported;
-#define SFOC_COL_CASE(GV)                                                                                     \
-    case GV:                                                                                                  \
-        e = cudaFuncSetAttribute(k_corr_tc_col<GV>, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);     \
-        if (e != cudaSuccess) return e;                                                                       \
-        k_corr_tc_col<GV><<<grid, kColThreads, c.smem, st>>>(tmW, tmT, pts, n, m, R, stats, maps, err_flag);  \
+#define SFOC_COL_CASE(GV)                                                                                       \
+    case GV:                                                                                                    \
+        e = cudaFuncSetAttribute(k_corr_tc_col<GV>, cudaFuncAttributeMaxDynamicSharedMemorySize, CL.smem);      \
+        if (e != cudaSuccess) return e;                                                                         \
+        k_corr_tc_col<GV><<<grid, kColThreads, CL.smem, st>>>(one, is.jobs, is.items, n, CL, err_flag);          \
         return cudaGetLastError();
-        switch (c.G) {
+        switch (cls) {
             SFOC_COL_CASE(1)
             SFOC_COL_CASE(2)
             SFOC_COL_CASE(3)
@@ -939,26 +1054,17 @@ cudaError_t launch_corr_tc(const Cube& ref, const Cube& sen, const int32_t* pts,
 #undef SFOC_COL_CASE
         return e;
     }
+    if (form != 1 || is.items || !toeplitz_ok(one.m, one.R)) return cudaErrorNotSupported;
+    const int m = one.m, R = one.R;
     const int U = pick_U(m, R);
     const TcGeom g = tc_geom(m, R, U);
-    if (g.NA < 2 || g.JS > 512 || g.AW > 256) return cudaErrorNotSupported;
-    // A: window slab, box {8, AW, 8 rows, 2 chunks} over rm = [2][H][W][8]
-    // B: one template column, box {8, rows, 1, 1} over cm = [2][W][H][8];
-    //    rows [0, 256) through tmB and [256, JS) through tmB2 when JS > 256
-    alignas(64) CUtensorMap tmA, tmB, tmB2;
-    const uint32_t brow = g.JS < 256 ? (uint32_t)g.JS : 256u;
-    const uint32_t brow2 = g.JS > 256 ? (uint32_t)(g.JS - 256) : 8u;
-    if (!make_map(&tmA, ref.rm, (uint64_t)ref.W, (uint64_t)ref.H, (uint32_t)g.AW, kY, 2)) return cudaErrorNotSupported;
-    if (!make_map(&tmB, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, brow, 1, 1)) return cudaErrorNotSupported;
-    if (!make_map(&tmB2, sen.cm, (uint64_t)sen.H, (uint64_t)sen.W, brow2, 1, 1)) return cudaErrorNotSupported;
-    const int grid = n < sms ? n : sms;
     const int nq = g.Npad / 16;
     const size_t smem = (size_t)g.smem;
     cudaError_t e;
 #define SFOC_TC_CASE(NQ, UC)                                                                               \
     e = cudaFuncSetAttribute(k_corr_tc<NQ, UC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
     if (e != cudaSuccess) return e;                                                                        \
-    k_corr_tc<NQ, UC><<<grid, kThreads, smem, st>>>(tmA, tmB, tmB2, pts, n, m, R, stats, maps, err_flag);
+    k_corr_tc<NQ, UC><<<grid, kThreads, smem, st>>>(one, err_flag);
 #define SFOC_TC_NQ(UC)                  \
     switch (nq) {                       \
         case 1: SFOC_TC_CASE(1, UC) break; \

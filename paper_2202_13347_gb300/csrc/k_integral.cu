@@ -19,6 +19,7 @@
 //   k_int_final     per tile: local 2-D prefix + the grid-line values
 // HBM traffic is ~8 B/px read twice + 16 B/px written.
 #include <math.h>
+#include <string.h>
 
 #include "internal.h"
 
@@ -56,10 +57,60 @@ IntLayout layout(int H, int W, void* scratch) {
     return L;
 }
 
-__global__ void __launch_bounds__(256) k_int_tilesums(const float* __restrict__ s1, const float* __restrict__ s2,
-                                                       size_t pitch, IntLayout L) {
+// One cube's integral images: its sum planes, scratch layout and output.
+struct IntJob {
+    IntLayout L;
+    const float* s1;
+    const float* s2;
+    size_t pitch;
+    u64* P;
+    size_t ipitch;
+};
+
+// CTAs of each of the four kernels for one cube
+struct IntCtas {
+    int tiles, carry, lines, fin;
+};
+
+IntCtas int_ctas(int H, int W) {
+    const int nty = (H + kT - 1) / kT, ntx = (W + kT - 1) / kT;
+    IntCtas c;
+    c.tiles = ntx * nty;
+    c.carry = (2 * W + 2 * H + 255) / 256;
+    c.lines = 2 * nty + 2 * ntx;
+    c.fin = 2 * ntx * nty;
+    return c;
+}
+
+// the job of this CTA (single: `one`, the CTA index as is) and the CTA's
+// index within it (binary search of the prefix `begin` of n entries)
+__device__ __forceinline__ const IntJob& int_job(const IntJob& one, const IntJob* jobs, const int* begin, int n,
+                                                 int* local) {
+    const int bid = blockIdx.x;
+    if (!jobs) {
+        *local = bid;
+        return one;
+    }
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= bid) lo = mid;
+        else hi = mid - 1;
+    }
+    *local = bid - begin[lo];
+    return jobs[lo];
+}
+
+__global__ void __launch_bounds__(256) k_int_tilesums(const __grid_constant__ IntJob one, const IntJob* __restrict__ jobs,
+                                                       const int* __restrict__ begin, int n_jobs) {
     __shared__ u64 t[kT][kT + 1];
-    const int ty = blockIdx.y, tx = blockIdx.x;
+    int local;
+    const IntJob& J = int_job(one, jobs, begin, n_jobs, &local);
+    const IntLayout& L = J.L;
+    const float* __restrict__ s1 = J.s1;
+    const float* __restrict__ s2 = J.s2;
+    const size_t pitch = J.pitch;
+    const int ty = local / L.ntx, tx = local - (local / L.ntx) * L.ntx;
     const int y0 = ty * kT, x0 = tx * kT;
     for (int p = 0; p < 2; ++p) {
         const float* s = p ? s2 : s1;
@@ -84,8 +135,12 @@ __global__ void __launch_bounds__(256) k_int_tilesums(const float* __restrict__ 
 }
 
 // Exclusive running sums over tile rows (per column) and tile columns (per row).
-__global__ void k_int_carry(IntLayout L) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+__global__ void k_int_carry(const __grid_constant__ IntJob one, const IntJob* __restrict__ jobs,
+                            const int* __restrict__ begin, int n_jobs) {
+    int local;
+    const IntJob& J = int_job(one, jobs, begin, n_jobs, &local);
+    const IntLayout& L = J.L;
+    size_t i = local * (size_t)blockDim.x + threadIdx.x;
     size_t ncol = 2 * (size_t)L.W, nrow = 2 * (size_t)L.H;
     if (i < ncol) {
         int p = (int)(i / L.W), x = (int)(i % L.W);
@@ -146,8 +201,11 @@ __device__ void block_scan_excl(const u64* in, u64* out, int n) {
 }
 
 // blocks [0, 2*nty): horizontal lines; [2*nty, 2*nty + 2*ntx): vertical lines
-__global__ void __launch_bounds__(256) k_int_lines(IntLayout L) {
-    int b = blockIdx.x;
+__global__ void __launch_bounds__(256) k_int_lines(const __grid_constant__ IntJob one, const IntJob* __restrict__ jobs,
+                                                    const int* __restrict__ begin, int n_jobs) {
+    int b;
+    const IntJob& J = int_job(one, jobs, begin, n_jobs, &b);
+    const IntLayout& L = J.L;
     if (b < 2 * L.nty) {
         int p = b / L.nty, ty = b % L.nty;
         block_scan_excl(&L.colsum[((size_t)p * L.nty + ty) * L.W], &L.top[((size_t)p * L.nty + ty) * (L.W + 1)], L.W);
@@ -158,10 +216,20 @@ __global__ void __launch_bounds__(256) k_int_lines(IntLayout L) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_int_final(const float* __restrict__ s1, const float* __restrict__ s2,
-                                                    size_t pitch, IntLayout L, u64* __restrict__ P, size_t ipitch) {
+__global__ void __launch_bounds__(256) k_int_final(const __grid_constant__ IntJob one, const IntJob* __restrict__ jobs,
+                                                    const int* __restrict__ begin, int n_jobs) {
     __shared__ u64 t[kT][kT + 1];
-    const int ty = blockIdx.y, tx = blockIdx.x, p = blockIdx.z;
+    int local;
+    const IntJob& J = int_job(one, jobs, begin, n_jobs, &local);
+    const IntLayout& L = J.L;
+    const float* __restrict__ s1 = J.s1;
+    const float* __restrict__ s2 = J.s2;
+    const size_t pitch = J.pitch, ipitch = J.ipitch;
+    u64* __restrict__ P = J.P;
+    const int ntiles = L.ntx * L.nty;
+    const int p = local >= ntiles ? 1 : 0;
+    const int tl = local - p * ntiles;
+    const int ty = tl / L.ntx, tx = tl - (tl / L.ntx) * L.ntx;
     const int y0 = ty * kT, x0 = tx * kT;
     const float* s = p ? s2 : s1;
     u64* Pp = P + (size_t)p * (L.H + 1) * ipitch;
@@ -258,16 +326,76 @@ size_t integral_scratch_bytes(int H, int W) {
     return sizeof(u64) * (2 * nty * W + 2 * ntx * H + 2 * nty * (W + 1) + 2 * ntx * (H + 1));
 }
 
+namespace {
+
+IntJob int_job_of(const Cube& c, void* scratch) {
+    IntJob j;
+    j.L = layout(c.H, c.W, scratch);
+    j.s1 = c.s1;
+    j.s2 = c.s2;
+    j.pitch = c.pitch;
+    j.P = c.integ;
+    j.ipitch = c.ipitch;
+    return j;
+}
+
+}  // namespace
+
 cudaError_t launch_integral(const Cube& c, void* scratch, cudaStream_t st, int* launches) {
-    IntLayout L = layout(c.H, c.W, scratch);
-    dim3 g2(L.ntx, L.nty);
-    k_int_tilesums<<<g2, 256, 0, st>>>(c.s1, c.s2, c.pitch, L);
-    size_t nthreads = 2 * (size_t)L.W + 2 * (size_t)L.H;
-    k_int_carry<<<(unsigned)((nthreads + 255) / 256), 256, 0, st>>>(L);
-    k_int_lines<<<2 * L.nty + 2 * L.ntx, 256, 0, st>>>(L);
-    dim3 g3(L.ntx, L.nty, 2);
-    k_int_final<<<g3, 256, 0, st>>>(c.s1, c.s2, c.pitch, L, c.integ, c.ipitch);
+    const IntJob one = int_job_of(c, scratch);
+    const IntCtas n = int_ctas(c.H, c.W);
+    k_int_tilesums<<<n.tiles, 256, 0, st>>>(one, nullptr, nullptr, 0);
+    k_int_carry<<<n.carry, 256, 0, st>>>(one, nullptr, nullptr, 0);
+    k_int_lines<<<n.lines, 256, 0, st>>>(one, nullptr, nullptr, 0);
+    k_int_final<<<n.fin, 256, 0, st>>>(one, nullptr, nullptr, 0);
     if (launches) *launches += 4;
+    return cudaGetLastError();
+}
+
+// Batched form.  The table blob holds n IntJob entries and four prefix
+// arrays (n + 1 ints each: tiles, carry, lines, final CTAs), in that order.
+size_t integral_batch_blob_bytes(int n) {
+    return ((sizeof(IntJob) * (size_t)n + 15) / 16) * 16 + 4 * sizeof(int) * (size_t)(n + 1);
+}
+
+void integral_batch_blob(const Cube* const* cubes, int n, char* scratch, void* blob, int* ctas4) {
+    IntJob* jobs = static_cast<IntJob*>(blob);
+    int* pre = reinterpret_cast<int*>(static_cast<char*>(blob) + ((sizeof(IntJob) * (size_t)n + 15) / 16) * 16);
+    int acc[4] = {0, 0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+        const Cube& c = *cubes[i];
+        jobs[i] = int_job_of(c, scratch);
+        scratch += (integral_scratch_bytes(c.H, c.W) + 255) / 256 * 256;
+        const IntCtas k = int_ctas(c.H, c.W);
+        const int v[4] = {k.tiles, k.carry, k.lines, k.fin};
+        for (int q = 0; q < 4; ++q) {
+            pre[q * (n + 1) + i] = acc[q];
+            acc[q] += v[q];
+        }
+    }
+    for (int q = 0; q < 4; ++q) {
+        pre[q * (n + 1) + n] = acc[q];
+        ctas4[q] = acc[q];
+    }
+}
+
+size_t integral_batch_scratch_bytes(const Cube* const* cubes, int n) {
+    size_t b = 0;
+    for (int i = 0; i < n; ++i) b += (integral_scratch_bytes(cubes[i]->H, cubes[i]->W) + 255) / 256 * 256;
+    return b;
+}
+
+cudaError_t launch_integral_batch(const void* d_blob, int n, const int* ctas4, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const IntJob* jobs = static_cast<const IntJob*>(d_blob);
+    const int* pre =
+        reinterpret_cast<const int*>(static_cast<const char*>(d_blob) + ((sizeof(IntJob) * (size_t)n + 15) / 16) * 16);
+    IntJob none;
+    memset(&none, 0, sizeof(none));
+    k_int_tilesums<<<ctas4[0], 256, 0, st>>>(none, jobs, pre, n);
+    k_int_carry<<<ctas4[1], 256, 0, st>>>(none, jobs, pre + (n + 1), n);
+    k_int_lines<<<ctas4[2], 256, 0, st>>>(none, jobs, pre + 2 * (n + 1), n);
+    k_int_final<<<ctas4[3], 256, 0, st>>>(none, jobs, pre + 3 * (n + 1), n);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@
 //                   of its FP32 rate, so FP64 is kept to a few operations
 //                   per offset.
 #include <math.h>
+#include <string.h>
 
 #include "internal.h"
 
@@ -36,11 +37,16 @@ __device__ __forceinline__ long long rect(const u64* P, size_t ip, int y0, int x
 constexpr int kStatThreads = 128;
 
 __global__ void __launch_bounds__(kStatThreads)
-    k_template_stats(const float* __restrict__ s1, const float* __restrict__ s2, size_t pitch, int Hs, int Ws,
-                     int Hr, int Wr, const int32_t* __restrict__ pts, int m, int R, int z,
-                     PointStat* __restrict__ stats) {
+    k_template_stats(const __grid_constant__ MatchJob one, const MatchJob* __restrict__ jobs,
+                     const int2* __restrict__ items) {
     __shared__ u64 s_acc[kStatThreads / 32][2];
-    const int k = blockIdx.x;
+    int k;
+    const MatchJob& J = item_job(one, jobs, items, blockIdx.x, &k);
+    const float* __restrict__ s1 = J.ss1;
+    const float* __restrict__ s2 = J.ss2;
+    const size_t pitch = J.spitch;
+    const int Hs = J.Hs, Ws = J.Ws, Hr = J.Hr, Wr = J.Wr, m = J.m, R = J.R, z = J.z;
+    const int32_t* __restrict__ pts = J.pts;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = template_half(m);
     const int px = pts[2 * k], py = pts[2 * k + 1];
@@ -92,7 +98,7 @@ __global__ void __launch_bounds__(kStatThreads)
             s.status = vT <= 1e-6 * N ? SFOC_PT_FLAT_TEMPLATE : SFOC_PT_OK;
         }
     }
-    stats[k] = s;
+    J.stats[k] = s;
 }
 
 // argmax key: larger value wins, ties go to the smaller index
@@ -102,19 +108,24 @@ __device__ __forceinline__ bool better(float v, int i, float bv, int bi) {
 
 constexpr int kNccThreads = 256;
 
-__global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const u64* __restrict__ Pr, int Hr, size_t ipr,
-                                                            const int32_t* __restrict__ pts, int m, int R, int z,
-                                                            const PointStat* __restrict__ stats,
-                                                            const float* __restrict__ num, int centered,
-                                                            float* __restrict__ out_maps,
-                                                            fastncc_result* __restrict__ out) {
+__global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const __grid_constant__ MatchJob one,
+                                                            const MatchJob* __restrict__ jobs,
+                                                            const int2* __restrict__ items, int centered) {
     extern __shared__ float s_map[];  // P1 * P1
     __shared__ float s_bv[kNccThreads / 32];
     __shared__ int s_bi[kNccThreads / 32];
     __shared__ int s_nan;
-    const int k = blockIdx.x;
+    int k;
+    const MatchJob& J = item_job(one, jobs, items, blockIdx.x, &k);
+    const u64* __restrict__ Pr = J.rint;
+    const int Hr = J.Hr, m = J.m, R = J.R, z = J.z;
+    const size_t ipr = J.ripitch;
+    const int32_t* __restrict__ pts = J.pts;
+    const float* __restrict__ num = J.maps;
+    float* __restrict__ out_maps = J.out_maps;
+    fastncc_result* __restrict__ out = J.out;
     const int P1 = 2 * R + 1, P = P1 * P1;
-    const PointStat st = stats[k];
+    const PointStat st = J.stats[k];
     if (threadIdx.x == 0) s_nan = 0;
     fastncc_result res;
     res.dx = res.dy = 0;
@@ -211,25 +222,57 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const u64* __restric
 
 }  // namespace
 
-cudaError_t launch_template_stats(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                                  PointStat* stats, cudaStream_t st) {
+cudaError_t launch_template_stats(const MatchJob& one, const ItemSet& is, cudaStream_t st) {
+    const int n = is.items ? is.n : one.n;
     if (n <= 0) return cudaSuccess;
-    k_template_stats<<<n, kStatThreads, 0, st>>>(sen.s1, sen.s2, sen.pitch, sen.H, sen.W, ref.H, ref.W, pts, m, R,
-                                                 sen.z, stats);
+    k_template_stats<<<n, kStatThreads, 0, st>>>(one, is.jobs, is.items);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ncc_argmax(const Cube& ref, const int32_t* pts, int n, int m, int R, const PointStat* stats,
-                              const float* num, int centered, float* out_maps, fastncc_result* out,
-                              cudaStream_t st) {
+cudaError_t launch_ncc_argmax(const MatchJob& one, const ItemSet& is, int centered, cudaStream_t st) {
+    const int n = is.items ? is.n : one.n;
     if (n <= 0) return cudaSuccess;
+    const int R = is.items ? is.max_R : one.R;
     const int P1 = 2 * R + 1;
     size_t smem = sizeof(float) * (size_t)P1 * P1;
     cudaError_t e = cudaFuncSetAttribute(k_ncc_argmax, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_ncc_argmax<<<n, kNccThreads, smem, st>>>(ref.integ, ref.H, ref.ipitch, pts, m, R, ref.z, stats, num, centered,
-                                               out_maps, out);
+    k_ncc_argmax<<<n, kNccThreads, smem, st>>>(one, is.jobs, is.items, centered);
     return cudaGetLastError();
+}
+
+MatchJob make_job(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R, PointStat* stats,
+                  float* maps, float* out_maps, fastncc_result* out) {
+    MatchJob j;
+    memset(&j, 0, sizeof(j));
+    j.rf32 = ref.f32;
+    j.rrm = ref.rm;
+    j.rcm = ref.cm;
+    j.rint = ref.integ;
+    j.rpitch = ref.pitch;
+    j.rplane = ref.pitch * (size_t)ref.H;
+    j.ripitch = ref.ipitch;
+    j.Hr = ref.H;
+    j.Wr = ref.W;
+    j.sf32 = sen.f32;
+    j.ss1 = sen.s1;
+    j.ss2 = sen.s2;
+    j.srm = sen.rm;
+    j.scm = sen.cm;
+    j.spitch = sen.pitch;
+    j.splane = sen.pitch * (size_t)sen.H;
+    j.Hs = sen.H;
+    j.Ws = sen.W;
+    j.z = ref.z;
+    j.m = m;
+    j.R = R;
+    j.n = n;
+    j.pts = pts;
+    j.stats = stats;
+    j.maps = maps;
+    j.out_maps = out_maps;
+    j.out = out;
+    return j;
 }
 
 }  // namespace sfoc

@@ -10,6 +10,7 @@
 // do the horizontal pass into shared planes, then the vertical pass per
 // output pixel.  Borders clamp to the edge in every convolution.
 #include <cuda_bf16.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -151,9 +152,12 @@ __device__ __forceinline__ float codd(const float* x, const float* t) {
 // Three CTAs per SM: the 80-register cap (a few spilled values) hides the
 // tile loads better than two CTAs at 127 registers did (0.207 -> 0.179 ms
 // per step for the two 2048 x 2048 images).
+// One image (`one`, CTA = tile in row-major tile order) or a batch (device
+// table `jobs`, CTAs of image j from begin[j]).
 template <typename T, int KA, int KB, int KC, int KS>
-__global__ void __launch_bounds__(kThreads, 3) k_sfoc_steer_ct(const T* __restrict__ img, int H, int W, size_t pitch,
-                                                             float* __restrict__ F, size_t fpitch, size_t fplane,
+__global__ void __launch_bounds__(kThreads, 3) k_sfoc_steer_ct(const __grid_constant__ ImgJob one,
+                                                             const ImgJob* __restrict__ jobs,
+                                                             const int* __restrict__ begin, int n_jobs,
                                                              SteerTaps tp) {
     constexpr int HAL = KS > KA ? (KS > KB ? (KS > KC ? KS : KC) : (KB > KC ? KB : KC))
                                 : (KA > KB ? (KA > KC ? KA : KC) : (KB > KC ? KB : KC));
@@ -165,7 +169,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_sfoc_steer_ct(const T* __restri
     extern __shared__ float4 sm4[];
     float* s_h = reinterpret_cast<float*>(sm4);          // NP x IH x kTW
     __shared__ float s_t[NP][kMaxDerivRadius + 1];        // taps of the nine 1-D factors
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    int tile;
+    const ImgJob& J = img_job(one, jobs, begin, n_jobs, &tile);
+    const T* __restrict__ img = static_cast<const T*>(J.img);
+    const int H = J.H, W = J.W;
+    const size_t pitch = J.pitch, fpitch = J.fpitch, fplane = J.fpitch * (size_t)J.H;
+    float* __restrict__ F = J.F;
+    const int ntx = (W + kTW - 1) / kTW;
+    const int tby = tile / ntx;
+    const int x0 = (tile - tby * ntx) * kTW, y0 = tby * kTH;
     if (threadIdx.x < NP * (kMaxDerivRadius + 1)) {
         const int pl = threadIdx.x / (kMaxDerivRadius + 1), q = threadIdx.x % (kMaxDerivRadius + 1);
         const float* src = pl < 6 ? ((pl & 1) ? tp.g1[pl >> 1] : tp.a1[pl >> 1])
@@ -580,12 +592,24 @@ __device__ __forceinline__ void smooth_group_123(int g, const float* __restrict_
 // instruction footprint is what limits the fully unrolled passes) and fits
 // two CTAs per SM.  The second group's launch continues the per-pixel sums
 // from the stored planes, adding in the same order as one launch would.
+// One image (`one`, CTA = tile in row-major tile order) or a batch (device
+// table `jobs`, CTAs of image j from begin[j]).
 template <int NO, int KDG>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_sfoc_smooth_grp(const float* __restrict__ F, size_t fpitch, size_t fplane, int H, int W, SmoothTaps tp, int g,
-                      float* __restrict__ c32, size_t cpitch, size_t cplane, __nv_bfloat16* __restrict__ rm,
-                      __nv_bfloat16* __restrict__ cm, float* __restrict__ s1, float* __restrict__ s2) {
+    k_sfoc_smooth_grp(const __grid_constant__ ImgJob one, const ImgJob* __restrict__ jobs,
+                      const int* __restrict__ begin, int n_jobs, SmoothTaps tp, int g) {
     extern __shared__ float sm[];
+    int tile;
+    const ImgJob& J = img_job(one, jobs, begin, n_jobs, &tile);
+    const float* __restrict__ F = J.F;
+    const size_t fpitch = J.fpitch, fplane = J.fpitch * (size_t)J.H;
+    const int H = J.H, W = J.W;
+    float* __restrict__ c32 = J.c32;
+    const size_t cpitch = J.cpitch, cplane = J.cpitch * (size_t)J.H;
+    __nv_bfloat16* __restrict__ rm = J.rm;
+    __nv_bfloat16* __restrict__ cm = J.cm;
+    float* __restrict__ s1 = J.s1;
+    float* __restrict__ s2 = J.s2;
     __shared__ float s_tap[kMaxSmoothRadius + 1];
     if (threadIdx.x == 0) {  // constant indices: the parameter block stays in the constant bank
 #pragma unroll
@@ -597,7 +621,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     float* s_F = sm;                   // HR x FW
     float* s_h = s_F + HR * FW;        // 3 x HR x kSTW
     float* s_F2 = s_h + 3 * HR * kSTW;  // second input tile buffer
-    const int x0 = blockIdx.x * kSTW, y0 = blockIdx.y * kSTH;
+    const int ntx = (W + kSTW - 1) / kSTW;
+    const int tby = tile / ntx;
+    const int x0 = (tile - tby * ntx) * kSTW, y0 = tby * kSTH;
     const int cp = threadIdx.x & 15, rb = (threadIdx.x >> 4) * kPRows;
 
     float a1[kPRows][2], a2[kPRows][2];
@@ -690,17 +716,29 @@ __global__ void k_cube_export_f32(const float* __restrict__ c32, int H, int W, i
     }
 }
 
+bool steer_is_paper(const SteerTaps& tp) {
+    return tp.ns == 3 && tp.K1[0] == 2 && tp.K1[1] == 3 && tp.K1[2] == 3 && tp.second && tp.K2 == 5 && tp.no == 6;
+}
+
 template <typename T>
 cudaError_t launch_steer_any(const T* img, int H, int W, size_t pitch, float* F, size_t fpitch, const SteerTaps& tp,
                              cudaStream_t st) {
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
     // the paper's scales (0.6, 0.8, 1.0 and 1.5 at 3 sigma: radii 2, 3, 3, 5), six orientations
-    if (tp.ns == 3 && tp.K1[0] == 2 && tp.K1[1] == 3 && tp.K1[2] == 3 && tp.second && tp.K2 == 5 && tp.no == 6) {
+    if (steer_is_paper(tp)) {
         auto kern = k_sfoc_steer_ct<T, 2, 3, 3, 5>;
         const size_t smem = sizeof(float) * 9 * (size_t)(kTH + 10) * kTW;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, kThreads, smem, st>>>(img, H, W, pitch, F, fpitch, fpitch * (size_t)H, tp);
+        ImgJob one;
+        memset(&one, 0, sizeof(one));
+        one.img = img;
+        one.pitch = pitch;
+        one.H = H;
+        one.W = W;
+        one.F = F;
+        one.fpitch = fpitch;
+        kern<<<grid.x * grid.y, kThreads, smem, st>>>(one, nullptr, nullptr, 0, tp);
         return cudaGetLastError();
     }
     const int hal = tp.halo;
@@ -727,26 +765,72 @@ cudaError_t launch_sfoc_steer(const uint16_t* img, int H, int W, size_t pitch, f
 
 int smooth_launch_count(const SmoothTaps& tp) { return smooth_is_paper(tp) ? 2 : 1; }
 
+namespace {
+
+// the two group launches of the paper's smoothing (sigma_d 1.0 / 1.5, rates
+// 1, 2, 3) over `ctas` CTAs
+cudaError_t launch_smooth_paper(const ImgJob& one, const ImgJob* jobs, const int* begin, int n_jobs, int ctas,
+                                const SmoothTaps& tp, cudaStream_t st) {
+    auto run = [&](auto kern, int g, int hal) -> cudaError_t {
+        const int HR = kSTH + 2 * hal, FW = smooth_row_stride(hal);
+        const size_t smem = sizeof(float) * (2 * (size_t)HR * FW + 3 * (size_t)HR * kSTW);
+        cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e2 == cudaSuccess)
+            e2 = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared);
+        if (e2 != cudaSuccess) return e2;
+        kern<<<ctas, kThreads, smem, st>>>(one, jobs, begin, n_jobs, tp, g);
+        return cudaGetLastError();
+    };
+    cudaError_t e = run(k_sfoc_smooth_grp<6, 3>, 0, 9);
+    if (e == cudaSuccess) e = run(k_sfoc_smooth_grp<6, 5>, 1, 15);
+    return e;
+}
+
+}  // namespace
+
+bool sfoc_batch_supported(const SteerTaps& st, const SmoothTaps& sm) { return steer_is_paper(st) && smooth_is_paper(sm); }
+
+void sfoc_batch_tiles(int H, int W, int* steer_ctas, int* smooth_ctas) {
+    *steer_ctas = ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
+    *smooth_ctas = ((W + kSTW - 1) / kSTW) * ((H + kSTH - 1) / kSTH);
+}
+
+cudaError_t launch_sfoc_batch(const ImgJob* jobs, int n_jobs, const int* steer_begin, int steer_ctas,
+                              const int* smooth_begin, int smooth_ctas, const SteerTaps& st, const SmoothTaps& sm,
+                              cudaStream_t s) {
+    if (n_jobs <= 0) return cudaSuccess;
+    if (!sfoc_batch_supported(st, sm)) return cudaErrorNotSupported;
+    ImgJob none;
+    memset(&none, 0, sizeof(none));
+    auto kern = k_sfoc_steer_ct<float, 2, 3, 3, 5>;
+    const size_t smem = sizeof(float) * 9 * (size_t)(kTH + 10) * kTW;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<steer_ctas, kThreads, smem, s>>>(none, jobs, steer_begin, n_jobs, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_smooth_paper(none, jobs, smooth_begin, n_jobs, smooth_ctas, sm, s);
+}
+
 cudaError_t launch_sfoc_smooth(const float* F, size_t fpitch, int H, int W, const SmoothTaps& tp, Cube& c,
                                cudaStream_t st) {
     dim3 grid((W + kSTW - 1) / kSTW, (H + kSTH - 1) / kSTH);
     cudaError_t e;
     if (smooth_is_paper(tp)) {  // sigma_d 1.0 / 1.5 with rates 1, 2, 3 (Sec. 2.1): one launch per group
-        auto run = [&](auto kern, int g, int hal) -> cudaError_t {
-            const int HR = kSTH + 2 * hal, FW = smooth_row_stride(hal);
-            const size_t smem = sizeof(float) * (2 * (size_t)HR * FW + 3 * (size_t)HR * kSTW);
-            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e2 == cudaSuccess)
-                e2 = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                          (int)cudaSharedmemCarveoutMaxShared);
-            if (e2 != cudaSuccess) return e2;
-            kern<<<grid, kThreads, smem, st>>>(F, fpitch, fpitch * (size_t)H, H, W, tp, g, c.f32, c.pitch,
-                                               c.pitch * (size_t)H, c.rm, c.cm, c.s1, c.s2);
-            return cudaGetLastError();
-        };
-        e = run(k_sfoc_smooth_grp<6, 3>, 0, 9);
-        if (e == cudaSuccess) e = run(k_sfoc_smooth_grp<6, 5>, 1, 15);
-        return e;
+        ImgJob one;
+        memset(&one, 0, sizeof(one));
+        one.H = H;
+        one.W = W;
+        one.F = const_cast<float*>(F);
+        one.fpitch = fpitch;
+        one.c32 = c.f32;
+        one.cpitch = c.pitch;
+        one.rm = c.rm;
+        one.cm = c.cm;
+        one.s1 = c.s1;
+        one.s2 = c.s2;
+        return launch_smooth_paper(one, nullptr, nullptr, 0, (int)(grid.x * grid.y), tp, st);
     }
     const int maxhal = tp.halo[0] > tp.halo[1] ? tp.halo[0] : tp.halo[1];
     const int HR = kSTH + 2 * maxhal, FW = smooth_row_stride(maxhal);

@@ -4,6 +4,8 @@
 // the closed forms of Eq. 2, 3, 5 and the dilated Gaussian of Sec. 2.1),
 // workspace management and kernel dispatch on the context's stream.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -13,58 +15,17 @@
 #include <string>
 #include <vector>
 
-#include "internal.h"
+#include "host.h"
 
 using namespace sfoc;
 
-struct sfoc_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    std::string err;
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
-    int64_t launches = 0;
-    int* d_err = nullptr;  // device error word set by bounded waits
-    // cached cubes and staging for the pair pipeline
-    sfoc_cube* pair_ref = nullptr;
-    sfoc_cube* pair_sen = nullptr;
-    void* stage = nullptr;
-    size_t stage_bytes = 0;
-    // second stream for the sensed image's host copy (overlaps the reference cube)
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_copied = nullptr;
-    cudaEvent_t ev_switch = nullptr;  // orders a new stream after the previous one
-    // per-stage timing
-    bool timing = false;
-    struct Ev {
-        int stage, launches;
-        cudaEvent_t a, b;
-    };
-    std::vector<Ev> evs;
-    std::vector<cudaEvent_t> pool;
-    double acc_ms[SFOC_NUM_STAGES] = {0};
-    int64_t acc_n[SFOC_NUM_STAGES] = {0};
-};
-
-struct sfoc_cube {
-    Cube c;
-};
 
 namespace {
-
 const double kPi = 3.14159265358979323846;
+int radius_of(double sigma, double mult) { return (int)ceil(mult * sigma - 1e-9); }
+}  // namespace
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+namespace sfoc {
 
 sfoc_status fail(sfoc_ctx* ctx, sfoc_status s, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -82,13 +43,19 @@ sfoc_status cuda_fail(sfoc_ctx* ctx, cudaError_t e, const char* what) {
     return fail(ctx, SFOC_ERR_CUDA, m);
 }
 
-int radius_of(double sigma, double mult) { return (int)ceil(mult * sigma - 1e-9); }
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    return cs != cudaStreamCaptureStatusNone;
+}
 
-size_t roundup(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int sm_count(int device) {
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return sms;
+}
 
-enum { ST_STEER = 0, ST_SMOOTH = 1, ST_INTEGRAL = 2, ST_STATS = 3, ST_CORR = 4, ST_NCC = 5, ST_OTHER = 6 };
-
-cudaEvent_t pool_event(sfoc_ctx* c) {
+static cudaEvent_t pool_event(sfoc_ctx* c) {
     if (!c->pool.empty()) {
         cudaEvent_t e = c->pool.back();
         c->pool.pop_back();
@@ -99,39 +66,29 @@ cudaEvent_t pool_event(sfoc_ctx* c) {
     return e;
 }
 
-// Brackets the launches of one stage with events (when timing is on) and
-// counts them.
-struct StageScope {
-    sfoc_ctx* c;
-    int stage, launches;
-    cudaEvent_t a = nullptr;
-    StageScope(sfoc_ctx* ctx, int st, int nl) : c(ctx), stage(st), launches(nl) {
-        c->launches += nl;
-        if (!c->timing) return;
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        cudaStreamIsCapturing(c->stream, &cs);
-        if (cs != cudaStreamCaptureStatusNone) return;
-        a = pool_event(c);
-        if (a) cudaEventRecord(a, c->stream);
-    }
-    ~StageScope() {
-        if (!a) return;
-        cudaEvent_t b = pool_event(c);
-        if (!b) return;
-        cudaEventRecord(b, c->stream);
-        c->evs.push_back({stage, launches, a, b});
-    }
-};
+StageScope::StageScope(sfoc_ctx* ctx, int st, int nl) : c(ctx), stage(st), launches(nl) {
+    c->launches += nl;
+    if (!c->timing || capturing(c->stream)) return;
+    a = pool_event(c);
+    if (a) cudaEventRecord(a, c->stream);
+}
 
-// Grows the workspace (never inside a stream capture).
+StageScope::~StageScope() {
+    if (!a) return;
+    cudaEvent_t b = pool_event(c);
+    if (!b) return;
+    cudaEventRecord(b, c->stream);
+    c->evs.push_back({stage, launches, a, b});
+}
+
 sfoc_status ensure_ws(sfoc_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->ws_bytes) return SFOC_OK;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(ctx->stream, &cs);
-    if (cs != cudaStreamCaptureStatusNone)
+    if (capturing(ctx->stream))
         return fail(ctx, SFOC_ERR_INVALID_ARG, "workspace too small inside a stream capture; call sfoc_ctx_reserve first");
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    for (BatchPlan* p : ctx->plans) destroy_plan(p);  // their tables point into the old workspace
+    ctx->plans.clear();
     if (ctx->ws) cudaFree(ctx->ws);
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
@@ -308,9 +265,110 @@ sfoc_status build_integral(sfoc_ctx* ctx, Cube& c) {
     return SFOC_OK;
 }
 
-size_t align256(size_t v) { return roundup(v, 256); }
+}  // namespace sfoc
 
-}  // namespace
+namespace sfoc {
+
+cudaError_t launch_corr_path(sfoc_ctx* ctx, int path, int option, MatchJob& one) {
+    const ItemSet none;
+    const int m = one.m, R = one.R;
+    switch (path) {
+        case SFOC_CORR_DIRECT_F32: {
+            const int c = corr_f32_class(R);
+            if (!c || !corr_f32_supported(m, R) || !one.rf32) return cudaErrorNotSupported;
+            return launch_corr_f32(one, none, c, ctx->stream);
+        }
+        case SFOC_CORR_FFT: {
+            if (!corr_fft_supported(m, R) || !one.rf32) return cudaErrorNotSupported;
+            return launch_corr_fft(one, none, option ? option : corr_fft_side(m, R), ctx->stream);
+        }
+        case SFOC_CORR_TC_TOEPLITZ:
+        case SFOC_CORR_TC_COLUMN:
+        case SFOC_CORR_TC_BAND: {
+            const int form = path == SFOC_CORR_TC_TOEPLITZ ? 1 : path == SFOC_CORR_TC_COLUMN ? 2 : 3;
+            const int cls = corr_tc_class(form, m, R);
+            if (!cls || !one.rrm || one.z != 12 || !corr_tc_maps(form, one)) return cudaErrorNotSupported;
+            return launch_corr_tc(form, cls, one, none, &m, &R, 1, ctx->d_err, ctx->stream);
+        }
+        default:
+            return cudaErrorNotSupported;
+    }
+}
+
+int auto_rule(int dtype, int m, int R) {
+    if (dtype == SFOC_DTYPE_BF16) {
+        switch (corr_tc_auto_form(m, R)) {
+            case 3: return SFOC_CORR_TC_BAND;
+            case 2: return SFOC_CORR_TC_COLUMN;
+            case 1: return SFOC_CORR_TC_TOEPLITZ;
+            default: return -1;
+        }
+    }
+    if (corr_fft_supported(m, R)) return SFOC_CORR_FFT;
+    return corr_f32_supported(m, R) ? SFOC_CORR_DIRECT_F32 : -1;
+}
+
+const TuneEntry* autotune_pair(sfoc_ctx* ctx, int dtype, MatchJob one) {
+    const int m = one.m, R = one.R;
+    TuneEntry t;
+    memset(&t, 0, sizeof(t));
+    if (dtype == SFOC_DTYPE_F32) {
+        if (corr_fft_supported(m, R)) {
+            const int side = corr_fft_side(m, R);
+            t.cand_path[t.n_cand] = SFOC_CORR_FFT;
+            t.cand_option[t.n_cand++] = side;
+            if (side == 64) {  // the larger transform as a tile option
+                t.cand_path[t.n_cand] = SFOC_CORR_FFT;
+                t.cand_option[t.n_cand++] = 128;
+            }
+        }
+        if (corr_f32_supported(m, R)) t.cand_path[t.n_cand++] = SFOC_CORR_DIRECT_F32;
+    } else {
+        const int forms[3] = {3, 2, 1}, paths[3] = {SFOC_CORR_TC_BAND, SFOC_CORR_TC_COLUMN, SFOC_CORR_TC_TOEPLITZ};
+        for (int i = 0; i < 3; ++i)
+            if (corr_tc_class(forms[i], m, R) > 0) t.cand_path[t.n_cand++] = paths[i];
+    }
+    if (t.n_cand == 0) return nullptr;
+    // a sample of up to two waves of points, timed per candidate: one
+    // warm-up launch, then the better of two
+    const int sms = sm_count(ctx->device);
+    one.n = one.n < 2 * sms ? one.n : 2 * sms;
+    t.sample = one.n;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) e = nullptr;
+    int best = -1;
+    for (int c = 0; c < t.n_cand; ++c) {
+        t.cand_ms[c] = -1.f;
+        if (!ev[0] || !ev[1] || !ev[2]) continue;
+        bool ok = launch_corr_path(ctx, t.cand_path[c], t.cand_option[c], one) == cudaSuccess;
+        ok = ok && cudaEventRecord(ev[0], ctx->stream) == cudaSuccess;
+        ok = ok && launch_corr_path(ctx, t.cand_path[c], t.cand_option[c], one) == cudaSuccess;
+        ok = ok && cudaEventRecord(ev[1], ctx->stream) == cudaSuccess;
+        ok = ok && launch_corr_path(ctx, t.cand_path[c], t.cand_option[c], one) == cudaSuccess;
+        ok = ok && cudaEventRecord(ev[2], ctx->stream) == cudaSuccess;
+        ok = ok && cudaEventSynchronize(ev[2]) == cudaSuccess;
+        ctx->launches += 3;
+        float a = 0.f, b = 0.f;
+        if (ok && cudaEventElapsedTime(&a, ev[0], ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, ev[1], ev[2]) == cudaSuccess) {
+            t.cand_ms[c] = a < b ? a : b;
+            if (best < 0 || t.cand_ms[c] < t.cand_ms[best]) best = c;
+        } else {
+            (void)cudaGetLastError();  // a refused candidate leaves no error behind
+        }
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (best < 0) return nullptr;
+    t.path = t.cand_path[best];
+    t.option = t.cand_option[best];
+    auto& slot = ctx->tune[TuneKey{dtype, m, R}];
+    slot = t;
+    return &slot;
+}
+
+}  // namespace sfoc
 
 namespace {
 
@@ -420,6 +478,8 @@ sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx) {
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
     if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
     if (ctx->ev_switch) cudaEventDestroy(ctx->ev_switch);
+    for (BatchPlan* p : ctx->plans) destroy_plan(p);
+    cudaFree(ctx->hstage);
     delete ctx;
     return SFOC_OK;
 }
@@ -713,18 +773,22 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
     if (ref->c.z != sen->c.z) return fail(ctx, SFOC_ERR_SHAPE, "cubes have different channel counts");
     if (ref->c.dtype != sen->c.dtype) return fail(ctx, SFOC_ERR_SHAPE, "cubes have different dtypes");
     int path = opts ? opts->corr_path : SFOC_CORR_AUTO;
-    if (path == SFOC_CORR_AUTO)
-        path = ref->c.dtype == SFOC_DTYPE_BF16                       ? SFOC_CORR_IGEMM_TC
-               : corr_fft_supported(template_size, search_radius) ? SFOC_CORR_FFT
-                                                                    : SFOC_CORR_DIRECT_F32;
-    if (path != SFOC_CORR_DIRECT_F32 && path != SFOC_CORR_IGEMM_TC && path != SFOC_CORR_TC_TOEPLITZ &&
-        path != SFOC_CORR_TC_COLUMN && path != SFOC_CORR_TC_BAND && path != SFOC_CORR_FFT)
-        return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown corr_path");
-    const bool f32_path = path == SFOC_CORR_DIRECT_F32 || path == SFOC_CORR_FFT;
-    if (f32_path && ref->c.dtype != SFOC_DTYPE_F32)
-        return fail(ctx, SFOC_ERR_UNSUPPORTED, "DIRECT_F32 and FFT need F32 cubes");
-    if (!f32_path && ref->c.dtype != SFOC_DTYPE_BF16)
-        return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
+    if (path < SFOC_CORR_AUTO || path > SFOC_CORR_FFT) return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown corr_path");
+    const int dtype = ref->c.dtype;
+    const bool f32_cube = dtype == SFOC_DTYPE_F32;
+    const int m = template_size, R = search_radius;
+    if (path == SFOC_CORR_IGEMM_TC) {
+        if (f32_cube) return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
+        path = auto_rule(SFOC_DTYPE_BF16, m, R);
+        if (path < 0) return fail(ctx, SFOC_ERR_UNSUPPORTED, "no tensor-core form runs for this m / R");
+    }
+    if (path != SFOC_CORR_AUTO) {
+        const bool f32_path = path == SFOC_CORR_DIRECT_F32 || path == SFOC_CORR_FFT;
+        if (f32_path && !f32_cube) return fail(ctx, SFOC_ERR_UNSUPPORTED, "DIRECT_F32 and FFT need F32 cubes");
+        if (!f32_path && f32_cube) return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
+    } else if (auto_rule(dtype, m, R) < 0) {
+        return fail(ctx, SFOC_ERR_UNSUPPORTED, "no correlation form runs for this m / R");
+    }
     DeviceGuard g(ctx->device);
     if (n == 0) return SFOC_OK;
 
@@ -737,36 +801,42 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
     char* w = static_cast<char*>(ctx->ws);
     PointStat* stats = reinterpret_cast<PointStat*>(w);
     float* maps = reinterpret_cast<float*>(w + align256(sizeof(PointStat) * (size_t)n));
-    const int m = template_size, R = search_radius;
+    MatchJob one = make_job(ref->c, sen->c, d_points, n, m, R, stats, maps, opts ? opts->d_maps : nullptr, d_out);
+    const ItemSet none;
     cudaError_t e;
     {
         StageScope sc(ctx, ST_STATS, 1);
-        e = launch_template_stats(ref->c, sen->c, d_points, n, m, R, stats, ctx->stream);
+        e = launch_template_stats(one, none, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "template stats launch");
+    int option = 0;
+    if (path == SFOC_CORR_AUTO) {
+        // the measured choice for (dtype, m, R): looked up, or measured now on
+        // this call's points (not inside a capture: the measurement waits
+        // for its events); the fixed rule where there is neither
+        auto it = ctx->tune.find(TuneKey{dtype, m, R});
+        const TuneEntry* te = it != ctx->tune.end() ? &it->second : nullptr;
+        if (!te && ctx->autotune && !capturing(ctx->stream)) te = autotune_pair(ctx, dtype, one);
+        if (te) {
+            path = te->path;
+            option = te->option;
+        } else {
+            path = auto_rule(dtype, m, R);
+        }
+    }
     {
         StageScope sc(ctx, ST_CORR, 1);
-        if (path == SFOC_CORR_DIRECT_F32)
-            e = launch_corr_f32(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->stream);
-        else if (path == SFOC_CORR_FFT)
-            e = launch_corr_fft(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->stream);
-        else
-            e = launch_corr_tc(ref->c, sen->c, d_points, n, m, R, stats, maps, ctx->d_err,
-                               path == SFOC_CORR_TC_TOEPLITZ  ? 1
-                               : path == SFOC_CORR_TC_COLUMN ? 2
-                               : path == SFOC_CORR_TC_BAND   ? 3
-                                                             : 0,
-                               ctx->stream);
+        e = launch_corr_path(ctx, path, option, one);
     }
     if (e == cudaErrorInvalidValue || e == cudaErrorNotSupported) {
         (void)cudaGetLastError();  // a refused attribute or launch leaves no error for later calls
         return fail(ctx, SFOC_ERR_UNSUPPORTED, "correlation kernel does not support this m / R");
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "correlation launch");
+    const bool centered = path == SFOC_CORR_DIRECT_F32 || path == SFOC_CORR_FFT;
     {
         StageScope sc(ctx, ST_NCC, 1);
-        e = launch_ncc_argmax(ref->c, d_points, n, m, R, stats, maps, f32_path ? 1 : 0,
-                              opts ? opts->d_maps : nullptr, d_out, ctx->stream);
+        e = launch_ncc_argmax(one, none, centered ? 1 : 0, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ncc launch");
     return SFOC_OK;
@@ -856,32 +926,114 @@ sfoc_status fastncc_register_pair_host(sfoc_ctx* ctx, const float* h_ref, int Hr
     return SFOC_OK;
 }
 
-sfoc_status sfoc_build_batch(sfoc_ctx* ctx, int n_img, const float* const* d_images, const int* H, const int* W,
-                             const size_t* pitch_elems, const sfoc_params* p, sfoc_cube** outs) {
+sfoc_status sfoc_ctx_set_autotune(sfoc_ctx* ctx, int enable) {
     if (!ctx) return SFOC_ERR_INVALID_ARG;
-    if (n_img < 0 || (n_img > 0 && (!d_images || !H || !W || !outs)))
-        return fail(ctx, SFOC_ERR_INVALID_ARG, "bad batch arguments");
-    for (int i = 0; i < n_img; ++i) {
-        sfoc_status s = sfoc_build(ctx, d_images[i], H[i], W[i], pitch_elems ? pitch_elems[i] : (size_t)W[i], nullptr, 0,
-                                   0, p, &outs[i]);
-        if (s != SFOC_OK) return s;
+    ctx->autotune = enable != 0;
+    return SFOC_OK;
+}
+
+sfoc_status sfoc_ctx_autotune_entry(const sfoc_ctx* ctx, int dtype, int m, int R, int* corr_path, int* option,
+                                    int* n_cand, int* cand_path, int* cand_option, float* cand_ms, int* sample) {
+    if (!ctx || !corr_path) return SFOC_ERR_INVALID_ARG;
+    auto it = ctx->tune.find(TuneKey{dtype, m, R});
+    if (it == ctx->tune.end()) {
+        *corr_path = -1;
+        if (n_cand) *n_cand = 0;
+        return SFOC_OK;
+    }
+    const TuneEntry& t = it->second;
+    *corr_path = t.path;
+    if (option) *option = t.option;
+    if (n_cand) *n_cand = t.n_cand;
+    if (sample) *sample = t.sample;
+    for (int i = 0; i < t.n_cand; ++i) {
+        if (cand_path) cand_path[i] = t.cand_path[i];
+        if (cand_option) cand_option[i] = t.cand_option[i];
+        if (cand_ms) cand_ms[i] = t.cand_ms[i];
     }
     return SFOC_OK;
 }
 
-sfoc_status fastncc_match_batch(sfoc_ctx* ctx, int n_pairs, sfoc_cube* const* refs, sfoc_cube* const* sens,
-                                const int32_t* const* d_points, const int* n_points, const int* template_size,
-                                const int* search_radius, const fastncc_opts* opts, fastncc_result* const* d_outs) {
-    if (!ctx) return SFOC_ERR_INVALID_ARG;
-    if (n_pairs < 0 || (n_pairs > 0 && (!refs || !sens || !d_points || !n_points || !template_size || !search_radius ||
-                                        !d_outs)))
-        return fail(ctx, SFOC_ERR_INVALID_ARG, "bad batch arguments");
-    for (int i = 0; i < n_pairs; ++i) {
-        fastncc_opts o = {opts ? opts->corr_path : SFOC_CORR_AUTO, nullptr};
-        sfoc_status s = fastncc_match(ctx, refs[i], sens[i], d_points[i], n_points[i], template_size[i],
-                                      search_radius[i], &o, d_outs[i]);
-        if (s != SFOC_OK) return s;
+sfoc_status sfoc_ctx_autotune_export(const sfoc_ctx* ctx, char* buf, size_t cap, size_t* len) {
+    if (!ctx || !len) return SFOC_ERR_INVALID_ARG;
+    std::string j = "{\"sfoc_autotune\": 1, \"entries\": [";
+    bool first = true;
+    char tmp[256];
+    for (const auto& kv : ctx->tune) {
+        const TuneEntry& t = kv.second;
+        snprintf(tmp, sizeof(tmp), "%s{\"dtype\": %d, \"m\": %d, \"R\": %d, \"path\": %d, \"option\": %d, \"sample\": %d, "
+                 "\"candidates\": [", first ? "" : ", ", kv.first.dtype, kv.first.m, kv.first.R, t.path, t.option,
+                 t.sample);
+        j += tmp;
+        for (int i = 0; i < t.n_cand; ++i) {
+            snprintf(tmp, sizeof(tmp), "%s[%d, %d, %.6g]", i ? ", " : "", t.cand_path[i], t.cand_option[i],
+                     (double)t.cand_ms[i]);
+            j += tmp;
+        }
+        j += "]}";
+        first = false;
     }
+    j += "]}";
+    *len = j.size() + 1;
+    if (!buf) return SFOC_OK;
+    if (cap < j.size() + 1) return SFOC_ERR_INVALID_ARG;
+    memcpy(buf, j.c_str(), j.size() + 1);
+    return SFOC_OK;
+}
+
+namespace {
+
+// the integer after `"key":` inside [p, end); false when absent
+bool json_int(const char* p, const char* end, const char* key, int* out) {
+    std::string k = std::string("\"") + key + "\"";
+    const char* q = std::search(p, end, k.begin(), k.end());
+    if (q == end) return false;
+    q += k.size();
+    while (q < end && (*q == ' ' || *q == ':')) ++q;
+    char* e = nullptr;
+    long v = strtol(q, &e, 10);
+    if (e == q) return false;
+    *out = (int)v;
+    return true;
+}
+
+}  // namespace
+
+sfoc_status sfoc_ctx_autotune_import(sfoc_ctx* ctx, const char* text) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!text) return fail(ctx, SFOC_ERR_INVALID_ARG, "null text");
+    const char* p = strstr(text, "\"entries\"");
+    if (!p) return fail(ctx, SFOC_ERR_INVALID_ARG, "no entries in the autotune text");
+    std::map<TuneKey, TuneEntry> got;
+    // each entry is an object from "{" to the "]}" that closes its candidates
+    while ((p = strstr(p, "{\"dtype\"")) != nullptr) {
+        const char* end = strstr(p, "]}");
+        if (!end) return fail(ctx, SFOC_ERR_INVALID_ARG, "unterminated autotune entry");
+        TuneEntry t;
+        memset(&t, 0, sizeof(t));
+        int dtype, m, R;
+        if (!json_int(p, end, "dtype", &dtype) || !json_int(p, end, "m", &m) || !json_int(p, end, "R", &R) ||
+            !json_int(p, end, "path", &t.path) || !json_int(p, end, "option", &t.option))
+            return fail(ctx, SFOC_ERR_INVALID_ARG, "autotune entry without dtype, m, R, path or option");
+        json_int(p, end, "sample", &t.sample);
+        const bool ok_path = t.path == SFOC_CORR_DIRECT_F32 || t.path == SFOC_CORR_FFT || t.path == SFOC_CORR_TC_TOEPLITZ ||
+                             t.path == SFOC_CORR_TC_COLUMN || t.path == SFOC_CORR_TC_BAND;
+        const bool f32 = t.path == SFOC_CORR_DIRECT_F32 || t.path == SFOC_CORR_FFT;
+        if (!ok_path || (dtype != SFOC_DTYPE_F32 && dtype != SFOC_DTYPE_BF16) || f32 != (dtype == SFOC_DTYPE_F32) ||
+            m < 1 || m > kMaxTemplate || R < 0 || R > kMaxRadius)
+            return fail(ctx, SFOC_ERR_INVALID_ARG, "autotune entry out of range");
+        const int opt = t.path == SFOC_CORR_FFT ? t.option : 0;
+        if (t.path == SFOC_CORR_FFT && (opt != 64 && opt != 128)) return fail(ctx, SFOC_ERR_INVALID_ARG, "bad FFT side");
+        // the entry must name a form that runs for (m, R)
+        if (t.path == SFOC_CORR_FFT ? (!corr_fft_supported(m, R) || m + 2 * R > opt)
+            : t.path == SFOC_CORR_DIRECT_F32 ? !corr_f32_supported(m, R)
+                                             : corr_tc_class(t.path == SFOC_CORR_TC_TOEPLITZ ? 1
+                                                             : t.path == SFOC_CORR_TC_COLUMN ? 2 : 3, m, R) == 0)
+            return fail(ctx, SFOC_ERR_INVALID_ARG, "autotune entry names a form that does not run for its m / R");
+        got[TuneKey{dtype, m, R}] = t;
+        p = end + 2;
+    }
+    for (const auto& kv : got) ctx->tune[kv.first] = kv.second;
     return SFOC_OK;
 }
 

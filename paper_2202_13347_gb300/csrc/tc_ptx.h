@@ -134,10 +134,13 @@ bool make_map_rows8(CUtensorMap* map, const void* base, uint64_t d1, uint64_t d2
 }  // namespace tcx
 
 // band form of the tensor-core correlation (k_corr_band.cu): whether it
-// runs for (m, R), and the MMAs it issues per point
+// runs for (m, R), the MMAs it issues per point, its class (kernel
+// instance NQ, 0 = unsupported), the job's tensor maps, and the launch
 bool corr_band_supported(int m, int R);
 long long corr_band_mmas(int m, int R);
-cudaError_t launch_corr_band(const Cube& ref, const Cube& sen, const int32_t* pts, int n, int m, int R,
-                             const PointStat* stats, float* maps, int* err_flag, int sms, cudaStream_t st);
+int corr_band_class(int m, int R);
+bool corr_band_maps(MatchJob& j);
+cudaError_t launch_corr_band(const MatchJob& one, const ItemSet& is, int NQ, const int* ms, const int* Rs, int cnt,
+                             int* err_flag, int sms, cudaStream_t st);
 
 }  // namespace sfoc

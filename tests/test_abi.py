@@ -79,7 +79,7 @@ def test_null_context_is_rejected_everywhere(b):
     other arguments are (here all zero / NULL)."""
     L = b.lib()
     host_only = {"sfoc_ctx_create", "sfoc_match_workspace_bytes", "sfoc_params_default", "sfoc_last_error_string",
-                 "sfoc_ctx_launch_count"}
+                 "sfoc_ctx_launch_count", "sfoc_ctx_plan_count"}
     checked = 0
     for name, (res, args) in b._SIGS.items():
         if name in host_only:
@@ -89,7 +89,7 @@ def test_null_context_is_rejected_everywhere(b):
         assert getattr(L, name)(*vals) == -1, name
         checked += 1
     assert checked >= 24
-    assert L.sfoc_ctx_launch_count(None) == 0
+    assert L.sfoc_ctx_launch_count(None) == 0 and L.sfoc_ctx_plan_count(None) == 0
     assert L.sfoc_ctx_create(None, 0, None) == -1
 
 
