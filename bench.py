@@ -1,26 +1,33 @@
 #!/usr/bin/env python
 """Benchmark of the fine-registration hot path of arXiv 2202.13347 on GB300.
 
-One step = the whole path on one synthetic image pair: SFOC cube of the
-reference and of the sensed image (Sec. 2.1), the integral images of the
-searched cube, template statistics, correlation R_ST, NCC (Eq. 9), argmax
+One step = the whole path on one batch of synthetic image pairs: SFOC cube
+of every reference and sensed image (Sec. 2.1), the integral images of the
+searched cubes, template statistics, correlation R_ST, NCC (Eq. 9), argmax
 and sub-pixel refinement for every interest point (Sec. 2.2, Sec. 3.2.2).
 
-Default workload: 2048x2048 optical-like reference vs SAR-like sensed image
-(Gamma speckle L=4, piecewise shift field), 1000 block-Harris points,
-template 81x81, search radius 20, 12 SFOC channels.
+Default workload (--workload mixed64): 64 seeded pairs of uneven size
+(sides 512-4096, non-square), each with its own radiometric map, 200-4000
+block points, template from {41, 61, 81, 101} and search radius in
+[10, 40]; 12 SFOC channels.  Forms:
+  bf16batch  BF16 cubes, every pair in one batched launch per stage, the
+             correlation form of each (m, R) measured by the autotuner
+             (tensor-core forms), the whole step a replayed CUDA graph:
+             the line's value;
+  f32batch   the same with F32 cubes (Fourier or direct FP32 correlation);
+  f32plain   F32 cubes, the direct FP32 correlation, pairs one after the
+             other (the plain FP32 GPU form).
+The single-pair workloads (--workload sar2048: 2048^2 optical-like vs
+SAR-like, 1000 points, m=81, R=20; inverting512; speckle10000) time the
+forms bf16 (tensor cores), f32 (Fourier where it runs) and f32direct.
 
 Metric: matched control points per second (points whose status is OK),
-whole job over all ranks; SFOC Mpix/s is reported beside it.  Three forms
-are measured: the BF16 cube + tcgen05 correlation form and the FP32 form,
-both with the library's automatic correlation choice (for F32 cubes the
-Fourier correlation of Eq. 13 when m + 2R <= 128, else the direct FP32
-kernel), and the plain FP32 form (F32 cubes, direct correlation); the
-line's `value` is the fastest form, the others are reported under
-`forms`.
+whole job over all ranks; SFOC Mpix/s is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank runs its own replica (weak scaling).
+                  [--workload mixed64|sar2048|inverting512|speckle10000]
+Under torchrun each rank runs its own shard of the job (its own seeded
+batch or pair: weak scaling).
 """
 from __future__ import annotations
 
@@ -53,10 +60,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sar2048", choices=["inverting512", "sar2048"])
-    ap.add_argument("--forms", default="bf16,f32,f32direct",
-                    help="bf16: BF16 cubes, tensor-core correlation; f32: F32 cubes, automatic correlation (the "
-                         "Fourier form where m + 2R <= 128); f32direct: F32 cubes, the plain direct correlation")
+    ap.add_argument("--workload", default="mixed64", choices=["mixed64", "inverting512", "sar2048", "speckle10000"])
+    ap.add_argument("--forms", default=None,
+                    help="mixed64: bf16batch,f32batch,f32plain; single pairs: bf16 (BF16 cubes, tensor-core "
+                         "correlation), f32 (F32 cubes, automatic correlation), f32direct (F32 cubes, the plain "
+                         "direct correlation)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--noise-sweep", action="store_true",
@@ -76,15 +84,31 @@ def peaks():
 
 
 def workload(name, rank):
-    from workloads import inverting_pair_512, sar_pair_2048
+    from workloads import inverting_pair_512, sar_pair_2048, speckle_pair_10000
     if name == "inverting512":
         p = inverting_pair_512(seed=1000 + 7919 * rank)
         desc = "512x512 pair, piecewise inverting map, 100 block-max points, m=41, R=10, z=12"
+    elif name == "speckle10000":
+        p = speckle_pair_10000(seed=5000 + 7919 * rank)
+        desc = ("10000x10000 uint16 reference (read as v/65535) vs L=1 speckled sensed image under block affine "
+                "residuals, 10000 points, m=101, R=40, z=12")
     else:
         p = sar_pair_2048(seed=2000 + 7919 * rank)
         desc = ("2048x2048 optical-like ref vs SAR-like sensed (Gamma L=4 speckle, 256-px shift field), "
                 "1000 block-Harris points, m=81, R=20, z=12")
     return p, desc
+
+
+def batch_workload(rank, workers):
+    """The 64-pair mixed batch of this rank (its own seed: under torchrun each
+    rank's batch is its shard of a 64 x N-pair job)."""
+    from workloads import mixed_batch
+    pairs = mixed_batch(seed=4000 + 7919 * rank, workers=workers)
+    px = sum(q.ref.size + q.sen.size for q in pairs)
+    pts = sum(len(q.points) for q in pairs)
+    desc = ("64 pairs, sides U[512,4096] (non-square), linear/gamma/inverted/speckled maps, 200-4000 block points, "
+            "m in {41,61,81,101}, R in U[10,40], z=12: %d points, %.1f Mpx" % (pts, px / 1e6))
+    return pairs, desc
 
 
 class ClockSampler:
@@ -406,15 +430,18 @@ def fft_side(pair):
     return next((L for L in FFT_SIZES if pair.m + 2 * pair.R <= L), None)
 
 
-def fft_flops(pair, z=12):
+def fft_flops_mrl(m, R, L, z=12):
     """Work of the Fourier correlation per point, counting 5 L log2 L flop per
     complex length-L transform: per channel m + 2R row and L column
     transforms, 12 flop per cross-spectrum bin of the half spectrum; then
     L/2 + 1 column and 2R + 1 row inverse transforms."""
-    L = fft_side(pair)
     t = 5.0 * L * math.log2(L)
-    P1 = 2 * pair.R + 1
-    return z * ((pair.m + 2 * pair.R + L) * t + 12.0 * L * (L // 2 + 1)) + (L // 2 + 1 + P1) * t
+    P1 = 2 * R + 1
+    return z * ((m + 2 * R + L) * t + 12.0 * L * (L // 2 + 1)) + (L // 2 + 1 + P1) * t
+
+
+def fft_flops(pair, z=12):
+    return fft_flops_mrl(pair.m, pair.R, fft_side(pair), z)
 
 
 def fp32_peak(pk):
@@ -540,6 +567,344 @@ def noise_sweep(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------
+# batched workload
+# ---------------------------------------------------------------------------
+
+BATCH_FORMS = ("bf16batch", "f32batch", "f32plain")
+PATH_NAMES = {1: "k_corr_f32 (direct FP32)", 3: "k_corr_tc (Toeplitz tcgen05)", 4: "k_corr_tc_col (column tcgen05)",
+              5: "k_corr_tc_band (band tcgen05)", 6: "k_corr_fft (FP32 Fourier, Eq. 13)"}
+
+
+def class_flops(path, cls, m, R, z=12):
+    """Algorithmic work per processed point of one correlation class: the
+    direct-equivalent 2 m^2 z (2R+1)^2 flop for the direct and tensor-core
+    forms, the transform count for the Fourier form (cls = its side)."""
+    if path == 6:
+        return fft_flops_mrl(m, R, cls, z)
+    return 2.0 * m * m * z * (2 * R + 1) ** 2
+
+
+def run_batch_form(b, torch, ctx, pairs, form, steps, warmup):
+    p = b.params(dtype=b.DTYPE_BF16 if form == "bf16batch" else b.DTYPE_F32)
+    corr = b.CORR_DIRECT_F32 if form == "f32plain" else b.CORR_AUTO
+    n = len(pairs)
+    d_refs = [torch.from_numpy(q.ref).cuda() for q in pairs]
+    d_sens = [torch.from_numpy(q.sen).cuda() for q in pairs]
+    d_pts = [torch.from_numpy(q.points).cuda() for q in pairs]
+    outs = [torch.empty((len(q.points), 6), dtype=torch.int32, device="cuda") for q in pairs]
+    ms_, Rs_ = [q.m for q in pairs], [q.R for q in pairs]
+    if form == "f32plain":
+        # pairs one after the other; each pair's cubes are rebuilt in place
+        cr, cs = [None] * n, [None] * n
+
+        def step():
+            for i in range(n):
+                cr[i] = ctx.sfoc_build(d_refs[i], p=p, out=cr[i])
+                cs[i] = ctx.sfoc_build(d_sens[i], p=p, out=cs[i])
+                outs[i].copy_(ctx.fastncc_match(cr[i], cs[i], d_pts[i], ms_[i], Rs_[i], corr_path=corr)["raw"])
+    else:
+        def step():
+            ctx.register_batch(d_refs, d_sens, d_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs)
+    t0 = time.perf_counter()
+    step()  # the first call: plan, autotuner measurements, graph capture
+    ctx.sync()
+    prep_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        step()
+    ctx.sync()
+    stream = torch.cuda.current_stream()
+    l0 = ctx.launch_count
+    evs = []
+    torch.cuda.synchronize()
+    t_start = time.monotonic()
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    t_end = time.monotonic()
+    launches = ctx.launch_count - l0
+    ctx.sync()
+    ms = [a.elapsed_time(c) for a, c in evs]
+    status = [o[:, 5].cpu() for o in outs]
+    matched = int(sum(int((st == 0).sum()) for st in status))
+    processed = [int(((st == 0) | (st == 3)).sum()) for st in status]
+    # stage breakdown: one more step with per-stage events (a plan runs stage
+    # by stage while they are on)
+    info = ctx.plan_info() if form != "f32plain" else None
+    ctx.enable_timing(True)
+    ctx.reset_timing()
+    step()
+    stages = ctx.stage_times()
+    scopes = ctx.stage_scopes("correlation")
+    ctx.enable_timing(False)
+    tune = {}
+    if corr == b.CORR_AUTO:
+        for q in pairs:
+            e = ctx.autotune_entry(p.cube_dtype, q.m, q.R)
+            if e:
+                tune["%d,%d" % (q.m, q.R)] = {"path": e["path"], "option": e["option"],
+                                              "candidates_ms": {"%d/%d" % (c[0], c[1]): round(c[2], 4)
+                                                                for c in e["candidates"]}}
+    return dict(ms=sum(ms), ms_steps=ms, matched=matched, processed=processed, stages=stages, scopes=scopes,
+                info=info, launches=launches, p=p, corr=corr, outs=outs, prep_s=prep_s, tune=tune,
+                t_timed=(t_start, t_end))
+
+
+def batch_roofline(form, pairs, r, pk):
+    """Roofline of the dominant correlation kernel of a batched form: per
+    class (one persistent launch), the algorithmic work of the points it
+    processed over its launch time (CUDA events of the stage-by-stage run),
+    against the peak of the unit that bounds it; the class with the longest
+    launch is reported, all classes beside it."""
+    peak32, src32 = fp32_peak(pk)
+    rows = []
+    if r["info"] is None:  # pairs in order: every launch is the direct kernel
+        fl = sum(class_flops(1, 0, q.m, q.R) * r["processed"][i] for i, q in enumerate(pairs))
+        secs = sum(r["scopes"]) * 1e-3
+        rows.append(dict(kernel=PATH_NAMES[1], path=1, cls=0, launches=len(r["scopes"]), ms=sum(r["scopes"]),
+                         flops=fl, items=sum(r["processed"])))
+    else:
+        k = 0
+        for c in r["info"]["classes"]:
+            nl = c["launches"]
+            ms = sum(r["scopes"][k:k + nl])
+            k += nl
+            fl = sum(class_flops(c["path"], c["cls"], pairs[i].m, pairs[i].R) * r["processed"][i] for i in c["pairs"])
+            rows.append(dict(kernel=PATH_NAMES.get(c["path"], str(c["path"])), path=c["path"], cls=c["cls"],
+                             launches=nl, ms=ms, flops=fl, items=c["items"]))
+    out = []
+    for row in rows:
+        tc = row["path"] in (3, 4, 5)
+        peak = pk["bf16_sus"] if tc else peak32
+        # work per launch over mean launch time = the class's work over its launches' summed time
+        ach = row["flops"] / (row["ms"] * 1e-3) / 1e12 if row["ms"] > 0 else 0.0
+        out.append(dict(row, achieved=ach, peak=peak, frac=ach / peak, bound="tensor" if tc else "alu"))
+    top = max(out, key=lambda x: x["ms"])
+    tc = top["path"] in (3, 4, 5)
+    return {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": "TFLOP/s",
+            "frac": top["frac"], "traffic": None, "kernel": top["kernel"] + " class %d" % top["cls"],
+            "launch_ms": top["ms"] / max(1, top["launches"]),
+            "peak_src": ("bf16_tflops_sustained (%s): timed inside a long step" % pk["src"]) if tc else src32,
+            "work": ("2*m^2*z*(2R+1)^2 flop per processed point" if top["path"] != 6 else
+                     "5 L log2 L flop per transform + 12 flop per cross-spectrum bin, per processed point"),
+            "classes": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in x.items() if k != "flops"}
+                        for x in out]}
+
+
+def batch_e2e(b, torch, ctx, pairs, p, corr, steps):
+    """The same step through the C ABI from host buffers (pinned): every
+    image and point set copied in and every result copied out inside the
+    timed call (fastncc_register_batch_host, synchronous)."""
+    h_refs = [torch.from_numpy(q.ref).pin_memory() for q in pairs]
+    h_sens = [torch.from_numpy(q.sen).pin_memory() for q in pairs]
+    h_pts = [torch.from_numpy(q.points).pin_memory() for q in pairs]
+    outs = [torch.empty((len(q.points), 6), dtype=torch.int32).pin_memory() for q in pairs]
+    ms_, Rs_ = [q.m for q in pairs], [q.R for q in pairs]
+    for _ in range(2):  # plan and graph of the staged buffers
+        ctx.register_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs)
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        ctx.register_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs)
+        t.append(time.perf_counter() - t0)
+    matched = sum(int((o[:, 5] == 0).sum()) for o in outs)
+    h2d = sum(x.numel() * 4 for x in h_refs + h_sens + h_pts)
+    d2h = sum(o.numel() * 4 for o in outs)
+    return dict(ms=1e3 * sum(t), steps=steps, matched=matched, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+
+
+def batch_oracle_sample(pairs, seed, n_pairs=16, per_pair=2):
+    """A seeded sample of (pair, point) indices of the batch."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(len(pairs), min(n_pairs, len(pairs)), replace=False))
+    out = []
+    for i in sel:
+        k = min(per_pair, len(pairs[i].points))
+        out.append((int(i), np.sort(rng.choice(len(pairs[i].points), k, replace=False))))
+    return out
+
+
+def batch_cpu_baseline(pairs, outs, seed=99):
+    """The oracle as it stands on a seeded sample of the batch's points (2 in
+    each of 16 pairs: about 15 s on 16 host cores), and the agreement of the
+    GPU results on those points with it: offsets equal, near-ties (oracle
+    best-vs-second margin <= 2e-4) and NCC error against the FP64 oracle."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    sample = batch_oracle_sample(pairs, seed)
+    matched, dt = 0, 0.0
+    eq = ties = valid = 0
+    err = 0.0
+    for i, idx in sample:
+        q = pairs[i]
+        t0 = time.perf_counter()
+        o = oracle.match_pair(q.ref, q.sen, q.points[idx], q.m, q.R)
+        dt += time.perf_counter() - t0
+        matched += int((o["status"] == 0).sum())
+        g = outs[i][torch_index(idx)].cpu().numpy()
+        ok = np.isin(o["status"], [0, 3])
+        valid += int(ok.sum())
+        same = ok & (g[:, 0] == o["dx"]) & (g[:, 1] == o["dy"])
+        eq += int(same.sum())
+        ties += int((ok & (o["margin"] <= 2e-4)).sum())
+        if same.any():
+            gn = g[:, 2].view(np.float32).astype(np.float64)
+            err = max(err, float(np.abs(gn[same] - o["ncc"][same]).max()))
+    n = sum(len(idx) for _, idx in sample)
+    mpix, region = oracle_sfoc_mpix(pairs[0])
+    cpu = dict(value=matched / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+               sample="%d points (2 in each of %d seeded pairs) of %d, FP64 SFOC on their windows only, Eq. 8 NCC"
+               % (n, len(sample), sum(len(q.points) for q in pairs)),
+               seconds=dt, sfoc_mpix_s=mpix, sfoc_sample=region)
+    parity = dict(points=n, valid=valid, offsets_equal=eq, near_ties=ties, ncc_err_max_vs_fp64=err,
+                  note="GPU result of the line's form against the unrounded FP64 oracle on the sampled points")
+    return cpu, parity
+
+
+def torch_index(idx):
+    import torch
+    return torch.from_numpy(idx)
+
+
+def reference_batch(args, rank):
+    """The reference arm on the batched workload: the oracle as it stands on
+    the host cores, each step a bounded seeded sample (4 points) of the same
+    64-pair batch; rank 0 only."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    oracle.build()
+    pairs, desc = batch_workload(0, workers=min(16, os.cpu_count() or 1))
+    steps_t, matched, n_sample = [], 0, 4
+    for i in range(args.warmup + args.steps):
+        sample = batch_oracle_sample(pairs, 1000 + i, n_pairs=n_sample, per_pair=1)
+        t0 = time.perf_counter()
+        ok = 0
+        for pi, idx in sample:
+            q = pairs[pi]
+            o = oracle.match_pair(q.ref, q.sen, q.points[idx], q.m, q.R)
+            ok += int((o["status"] == 0).sum())
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            steps_t.append(dt)
+            matched += ok
+    tot = sum(steps_t)
+    value = matched / tot
+    mpix, region = oracle_sfoc_mpix(pairs[0])
+    sample = "%d seeded points per step (1 in each of %d seeded pairs) of %d, FP64 SFOC on their windows, Eq. 8 NCC" % (
+        n_sample, n_sample, sum(len(q.points) for q in pairs))
+    config = {"workload": desc, "pairs_per_rank": len(pairs), "points_per_rank": sum(len(q.points) for q in pairs),
+              "z": 12, "form": "bf16batch"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample, "sfoc_mpix_s": mpix, "sfoc_sample": region},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main_batch(args, torch, dist, rank, world, gpu_index):
+    import paper_2202_13347_gb300 as pkg
+    pkg.build()
+    b = pkg.load()
+    pairs, desc = batch_workload(rank, workers=min(16, os.cpu_count() or 1))
+    px = sum(q.ref.size + q.sen.size for q in pairs)
+    n_points = sum(len(q.points) for q in pairs)
+    config = {"workload": desc, "pairs_per_rank": len(pairs), "points_per_rank": n_points, "pixels_per_rank": px,
+              "z": 12, "l2": "not flushed: every step reads %.1f GB of images and cubes, far above the 129 MB L2"
+              % (px * 4 / 1e9 * 18)}
+    ctx = b.Context(torch.cuda.current_device())
+    forms = [f for f in (args.forms or ",".join(BATCH_FORMS)).split(",") if f]
+    pk = peaks()
+    try:
+        mp = ctx.measure_peaks()
+        pk.update(fp32=max(mp["fp32_tflops"], mp["fp32x2_tflops"]), fp32_scalar=mp["fp32_tflops"],
+                  fp32_src="measured by sfoc_measure_peaks: %s FMA chains (scalar %.1f, paired %.1f TFLOP/s)" % (
+                      "paired FFMA2" if mp["fp32x2_tflops"] > mp["fp32_tflops"] else "scalar FFMA",
+                      mp["fp32_tflops"], mp["fp32x2_tflops"]), microbench=mp)
+    except Exception as e:  # noqa: BLE001
+        pk.update(microbench={"error": str(e)})
+    results = {}
+    for form in forms:
+        try:
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            steps = args.steps if form != "f32plain" else max(3, min(args.steps, 5))
+            with ClockSampler(gpu_index) as cs:
+                r = run_batch_form(b, torch, ctx, pairs, form, steps, args.warmup if form != "f32plain" else 1)
+                cs.mark(*r["t_timed"])
+            r["steps"] = steps
+            r["ms_max"], r["matched_all"] = reduce_over_ranks(dist, torch, r["ms"], r["matched"], "cuda")
+            r["clocks"] = cs.summary()
+            results[form] = r
+        except b.SfocError as e:
+            results[form] = {"error": str(e)}
+        if form != forms[-1] and form != "bf16batch":
+            ctx.release_plans()  # the next form builds its own cubes
+    ok = [f for f in forms if "error" not in results.get(f, {"error": 1})]
+    if not ok:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "error": {f: results[f].get("error") for f in forms}}))
+        sys.exit(1)
+
+    def summarize(r, form):
+        per_step = {k: v[0] for k, v in r["stages"].items()}  # the one stage-by-stage step
+        sfoc_ms = per_step["steer"] + per_step["smooth"]
+        return dict(value=job_value(r["matched_all"], r["steps"], r["ms_max"]), ms_per_step=r["ms_max"] / r["steps"],
+                    steps=r["steps"], sfoc_mpix_s=px / (sfoc_ms * 1e-3) / 1e6 if sfoc_ms > 0 else None,
+                    stage_ms_per_step={k: round(v, 3) for k, v in per_step.items()},
+                    roofline=batch_roofline(form, pairs, r, pk), matched_per_step=r["matched"],
+                    gpu_launches=r["launches"], launches_per_step=r["launches"] / r["steps"], clocks=r["clocks"],
+                    first_call_s=round(r["prep_s"], 2), graph=bool(r["info"] and r["info"].get("graph")),
+                    autotune=r["tune"] or None)
+
+    summ = {f: summarize(results[f], f) for f in ok}
+    main_form = "bf16batch" if "bf16batch" in summ else max(summ, key=lambda f: summ[f]["value"])
+    main = summ[main_form]
+    r0 = results[main_form]
+    e2e = None
+    if not args.no_e2e and main_form != "f32plain":
+        er = batch_e2e(b, torch, ctx, pairs, r0["p"], r0["corr"], max(3, min(args.steps, 10)))
+        if dist:
+            dist.barrier()
+        ms_max, matched_all = reduce_over_ranks(dist, torch, er["ms"], er["matched"] * er["steps"], "cuda")
+        e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=er["h2d_bytes_per_step"],
+                   d2h_bytes_per_step=er["d2h_bytes_per_step"], ms_per_step=ms_max / er["steps"],
+                   call="fastncc_register_batch_host (pinned host buffers)")
+    cpu, parity = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu, parity = batch_cpu_baseline(pairs, r0["outs"])
+        except Exception as e:  # noqa: BLE001
+            cpu = {"error": "%s: %s" % (type(e).__name__, e)}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": main["steps"],
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if main_form == "bf16batch" else "f32",
+            "data": "synthetic", "config": dict(config, form=main_form), "roofline": main["roofline"],
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
+            "sfoc_mpix_s": main["sfoc_mpix_s"], "stage_ms_per_step": main["stage_ms_per_step"], "parity": parity,
+            "forms": {f: {k: v for k, v in sm.items() if k not in ("clocks",)} for f, sm in summ.items()},
+            "bf16batch_over_f32plain": (summ["bf16batch"]["value"] / summ["f32plain"]["value"]
+                                        if "bf16batch" in summ and "f32plain" in summ else None),
+            "peaks": {"hbm_gbs": pk["hbm"], "bf16_tflops": pk["bf16"], "bf16_tflops_sustained": pk["bf16_sus"],
+                      "src": pk["src"] + " (MEASURED_PEAKS.json)", "microbench": pk.get("microbench")},
+            "errors": {f: results[f]["error"] for f in forms if "error" in results[f]} or None}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.noise_sweep:
@@ -557,6 +922,12 @@ def main():
         if torch.cuda.is_available():
             torch.cuda.set_device(0)
 
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if os.environ.get(
+        "CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    if args.workload == "mixed64":
+        if args.impl == "reference":
+            return reference_batch(args, rank)
+        return main_batch(args, torch, dist, rank, world, gpu_index)
     pair, desc = workload(args.workload, rank)
     config = {"workload": desc, "H": int(pair.ref.shape[0]), "W": int(pair.ref.shape[1]),
               "points_per_pair": int(len(pair.points)), "m": pair.m, "R": pair.R, "z": 12,
@@ -600,7 +971,7 @@ def main():
     b = pkg.load()
     ctx = b.Context(torch.cuda.current_device())
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    forms = [f for f in args.forms.split(",") if f]
+    forms = [f for f in (args.forms or "bf16,f32,f32direct").split(",") if f]
     pk = peaks()
     try:  # the FP32 peak of this device, by the library's own microbenchmark
         mp = ctx.measure_peaks()
@@ -611,8 +982,6 @@ def main():
     except Exception as e:  # noqa: BLE001
         pk.update(microbench={"error": str(e)})
     results = {}
-    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if os.environ.get(
-        "CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
     clocks = None
     for form in forms:
         try:

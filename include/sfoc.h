@@ -166,6 +166,11 @@ SFOC_API sfoc_status sfoc_ctx_enable_timing(sfoc_ctx* ctx, int enable);
  * and the number of launches since the last reset. */
 SFOC_API sfoc_status sfoc_ctx_stage_times(sfoc_ctx* ctx, double* ms_out, int64_t* launches_out);
 SFOC_API sfoc_status sfoc_ctx_reset_timing(sfoc_ctx* ctx);
+/* The timed scopes of one stage since the last reset, in order (a scope is
+ * one launch, or the launches of one step of a stage: the four integral
+ * kernels, a batched SFOC wave); *n_out = their number, the first `cap`
+ * written to ms_out (milliseconds).  Synchronises the stream. */
+SFOC_API sfoc_status sfoc_ctx_stage_scopes(sfoc_ctx* ctx, int stage, float* ms_out, int cap, int* n_out);
 
 /* Peaks of this device measured by the library's own microbenchmarks (the
  * denominators of roofline fractions): FP32 FMA chains as scalar FFMA and
@@ -377,6 +382,14 @@ SFOC_API sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, con
  * context's stream first). */
 SFOC_API int sfoc_ctx_plan_count(const sfoc_ctx* ctx);
 SFOC_API sfoc_status sfoc_ctx_release_plans(sfoc_ctx* ctx);
+/* The most recently used plan as JSON text: kind (0 build, 1 match, 2 both),
+ * pairs, items, whether it has a graph and how many kernels one run
+ * launches, the SFOC waves, and per correlation class (in launch order) its
+ * sfoc_corr_path, kernel class, items, launches and pairs (indices into the
+ * call's arrays, in the order its items are listed).  "{}" without a plan.
+ * *len receives the bytes needed (with the zero); buf NULL writes nothing
+ * else; SFOC_ERR_INVALID_ARG when cap is smaller. */
+SFOC_API sfoc_status sfoc_ctx_plan_info(const sfoc_ctx* ctx, char* buf, size_t cap, size_t* len);
 
 /* ---- autotuner -------------------------------------------------------- */
 /*

@@ -112,6 +112,8 @@ _SIGS = {
                                               C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                               C.POINTER(Params), C.POINTER(Opts), C.POINTER(_P)]),
     "sfoc_ctx_plan_count": (C.c_int, [_P]),
+    "sfoc_ctx_plan_info": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "sfoc_ctx_stage_scopes": (C.c_int, [_P, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
     "sfoc_ctx_release_plans": (C.c_int, [_P]),
     "sfoc_ctx_set_autotune": (C.c_int, [_P, C.c_int]),
     "sfoc_ctx_autotune_entry": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -527,6 +529,24 @@ class Context:
     @property
     def plan_count(self) -> int:
         return int(lib().sfoc_ctx_plan_count(self.h))
+
+    def plan_info(self):
+        """The most recently used batch plan (sfoc_ctx_plan_info) as a dict."""
+        import json
+        n = C.c_size_t()
+        self._chk(lib().sfoc_ctx_plan_info(self.h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._chk(lib().sfoc_ctx_plan_info(self.h, buf, n.value, C.byref(n)))
+        return json.loads(buf.value.decode())
+
+    def stage_scopes(self, stage):
+        """Milliseconds of each timed scope of a stage (by name) since the last reset."""
+        idx = self.STAGES.index(stage)
+        n = C.c_int()
+        self._chk(lib().sfoc_ctx_stage_scopes(self.h, idx, None, 0, C.byref(n)))
+        arr = (C.c_float * max(1, n.value))()
+        self._chk(lib().sfoc_ctx_stage_scopes(self.h, idx, arr, n.value, C.byref(n)))
+        return [float(arr[i]) for i in range(n.value)]
 
     def release_plans(self):
         self._chk(lib().sfoc_ctx_release_plans(self.h))

@@ -17,6 +17,7 @@
 // signature replay the graph on the context's stream.  Plans live in the
 // context (the most recent few) and point into its workspace, so a
 // workspace that has to grow drops them.
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -965,6 +966,45 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
 }
 
 int sfoc_ctx_plan_count(const sfoc_ctx* ctx) { return ctx ? (int)ctx->plans.size() : 0; }
+
+sfoc_status sfoc_ctx_plan_info(const sfoc_ctx* ctx, char* buf, size_t cap, size_t* len) {
+    if (!ctx || !len) return SFOC_ERR_INVALID_ARG;
+    std::string j = "{}";
+    if (!ctx->plans.empty()) {
+        const BatchPlan* p = ctx->plans.back();
+        char t[256];
+        snprintf(t, sizeof(t), "{\"kind\": %d, \"pairs\": %d, \"items\": %d, \"graph\": %s, \"launches\": %d, ",
+                 p->kind, (int)p->jobs.size(), p->n_items, p->exec ? "true" : "false", p->launches);
+        j = t;
+        j += "\"build_batched\": ";
+        j += p->build_batched ? "true" : "false";
+        j += ", \"waves\": [";
+        for (size_t i = 0; i < p->waves.size(); ++i) {
+            snprintf(t, sizeof(t), "%s{\"images\": %d, \"steer_ctas\": %d, \"smooth_ctas\": %d}", i ? ", " : "",
+                     p->waves[i].n_img, p->waves[i].steer_ctas, p->waves[i].smooth_ctas);
+            j += t;
+        }
+        j += "], \"classes\": [";
+        for (size_t i = 0; i < p->classes.size(); ++i) {
+            const CorrClass& c = p->classes[i];
+            snprintf(t, sizeof(t), "%s{\"path\": %d, \"cls\": %d, \"items\": %d, \"launches\": %d, \"pairs\": [",
+                     i ? ", " : "", c.path, c.cls, c.n_items,
+                     c.path == SFOC_CORR_TC_TOEPLITZ ? (int)c.pairs.size() : 1);
+            j += t;
+            for (size_t q = 0; q < c.pairs.size(); ++q) {
+                snprintf(t, sizeof(t), "%s%d", q ? ", " : "", c.pairs[q]);
+                j += t;
+            }
+            j += "]}";
+        }
+        j += "]}";
+    }
+    *len = j.size() + 1;
+    if (!buf) return SFOC_OK;
+    if (cap < j.size() + 1) return SFOC_ERR_INVALID_ARG;
+    memcpy(buf, j.c_str(), j.size() + 1);
+    return SFOC_OK;
+}
 
 sfoc_status sfoc_ctx_release_plans(sfoc_ctx* ctx) {
     if (!ctx) return SFOC_ERR_INVALID_ARG;

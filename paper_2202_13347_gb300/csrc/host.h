@@ -64,6 +64,7 @@ struct sfoc_ctx {
     std::vector<cudaEvent_t> pool;
     double acc_ms[SFOC_NUM_STAGES] = {0};
     int64_t acc_n[SFOC_NUM_STAGES] = {0};
+    std::vector<float> scope_ms[SFOC_NUM_STAGES];  // each timed scope of a stage, in order
     // autotuner
     bool autotune = true;
     std::map<sfoc::TuneKey, sfoc::TuneEntry> tune;

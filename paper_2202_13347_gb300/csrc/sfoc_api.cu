@@ -552,6 +552,7 @@ sfoc_status sfoc_ctx_stage_times(sfoc_ctx* ctx, double* ms_out, int64_t* launche
     for (auto& ev : ctx->evs) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) ctx->acc_ms[ev.stage] += ms;
+        ctx->scope_ms[ev.stage].push_back(ms);
         ctx->acc_n[ev.stage] += ev.launches;
         ctx->pool.push_back(ev.a);
         ctx->pool.push_back(ev.b);
@@ -571,8 +572,22 @@ sfoc_status sfoc_ctx_reset_timing(sfoc_ctx* ctx) {
     for (int i = 0; i < SFOC_NUM_STAGES; ++i) {
         ctx->acc_ms[i] = 0.0;
         ctx->acc_n[i] = 0;
+        ctx->scope_ms[i].clear();
     }
     return s;
+}
+
+sfoc_status sfoc_ctx_stage_scopes(sfoc_ctx* ctx, int stage, float* ms_out, int cap, int* n_out) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (stage < 0 || stage >= SFOC_NUM_STAGES || !n_out || cap < 0)
+        return fail(ctx, SFOC_ERR_INVALID_ARG, "bad stage or output");
+    double tmp[SFOC_NUM_STAGES];
+    sfoc_status s = sfoc_ctx_stage_times(ctx, tmp, nullptr);  // collects the pending events
+    if (s != SFOC_OK) return s;
+    const std::vector<float>& v = ctx->scope_ms[stage];
+    *n_out = (int)v.size();
+    for (int i = 0; i < (int)v.size() && i < cap && ms_out; ++i) ms_out[i] = v[i];
+    return SFOC_OK;
 }
 
 sfoc_status sfoc_measure_peaks(sfoc_ctx* ctx, sfoc_peaks* out) {

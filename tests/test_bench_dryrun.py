@@ -45,7 +45,7 @@ def _fake_library(fail_ransac=False):
     b.SfocError = SfocError
     b.DTYPE_F32, b.DTYPE_BF16 = 0, 1
     b.CORR_AUTO, b.CORR_DIRECT_F32 = 0, 1
-    b.params = lambda dtype=0, **kw: types.SimpleNamespace(dtype=dtype)
+    b.params = lambda dtype=0, **kw: types.SimpleNamespace(dtype=dtype, cube_dtype=dtype)
 
     class Context:
         def __init__(self, device):
@@ -204,3 +204,84 @@ def test_noise_sweep_line(monkeypatch, capsys):
     for v in line["cmr"].values():
         for kind, levels in bench.NOISE_LEVELS.items():
             assert len(v[kind]) == len(levels) and all(0.0 <= c <= 1.0 for c in v[kind])
+
+
+def _fake_batch_library():
+    pkg = _fake_library()
+    b = pkg.load()
+    base = b.Context
+
+    class Context(base):
+        def __init__(self, device):
+            super().__init__(device)
+            self.plans = 0
+
+        def register_batch(self, refs, sens, pts, ms, Rs, p=None, corr_path=0, outs=None):
+            self.plans = 1
+            self.launch_count += 14
+            self.n_steps += 1
+            for pt, o in zip(pts, outs):
+                self._fill(pt, o)
+            return outs
+
+        def register_batch_host(self, refs, sens, pts, ms, Rs, p=None, corr_path=0, outs=None):
+            return self.register_batch(refs, sens, pts, ms, Rs, p, corr_path, outs)
+
+        def plan_info(self):
+            return {"kind": 2, "graph": True, "classes": [{"path": 5, "cls": 3, "items": 10, "launches": 1,
+                                                          "pairs": [0, 1]},
+                                                         {"path": 6, "cls": 128, "items": 5, "launches": 1,
+                                                          "pairs": [2]}]}
+
+        def stage_scopes(self, stage):
+            return [0.5, 0.2] if stage == "correlation" else []
+
+        def autotune_entry(self, dtype, m, R):
+            return {"path": 5, "option": 0, "sample": 10, "candidates": [(5, 0, 0.5), (4, 0, 0.7)]}
+
+        def release_plans(self):
+            self.plans = 0
+
+        def fastncc_match(self, ref, sen, pts, m, R, corr_path=0):
+            self.launch_count += 3
+            return super().fastncc_match(ref, sen, pts, m, R)
+
+    b.Context = Context
+    return pkg
+
+
+def test_batched_line(monkeypatch, capsys):
+    """The default (batched) workload: the BF16-batched form heads the line,
+    the plain FP32 form and the F32-batched form beside it, the roofline of
+    the longest correlation class with every class listed, e2e through the
+    host-buffer batch call, and the oracle sample's agreement."""
+    from workloads import mixed_batch
+    import oracle
+    oracle.build()
+    small = mixed_batch(seed=4100, n_pairs=3, scale=0.12)
+    monkeypatch.setattr(bench, "batch_workload", lambda rank, workers: (small, "3 small pairs"))
+    _patch_cuda(monkeypatch)
+    monkeypatch.setitem(sys.modules, "paper_2202_13347_gb300", _fake_batch_library())
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "3", "--warmup", "3"])
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert set(line["forms"]) == {"bf16batch", "f32batch", "f32plain"}
+    assert line["config"]["form"] == "bf16batch" and line["value"] == line["forms"]["bf16batch"]["value"]
+    assert line["dtype"] == "bf16" and line["scaling"] == "weak"
+    roof = line["roofline"]
+    assert roof["bound"] == "tensor" and len(roof["classes"]) == 2 and roof["launch_ms"] == 0.5
+    assert line["e2e"]["h2d_bytes_per_step"] == sum(q.ref.nbytes + q.sen.nbytes + q.points.nbytes for q in small)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["parity"]["points"] > 0
+    assert line["bf16batch_over_f32plain"] is not None
+    assert line["gpu_launches"] == 14 * 3
+    assert line["forms"]["bf16batch"]["autotune"]
+
+
+def test_batched_reference_arm(monkeypatch, capsys):
+    from workloads import mixed_batch
+    small = mixed_batch(seed=4100, n_pairs=3, scale=0.12)
+    monkeypatch.setattr(bench, "batch_workload", lambda rank, workers: (small, "3 small pairs"))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"])
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["e2e"]["d2h_bytes_per_step"] == 0

@@ -353,34 +353,43 @@ def sar_pair_2048(seed=2000, H=2048, W=2048, grid=32, n_points=1000, m=81, R=20,
     return Pair(ref, sen, pts, m, R, truth, dict(gamma=g, block=block, seed=seed))
 
 
+def _mixed_pair(seed, p, side_lo, side_hi, templates, r_lo, r_hi, pts_lo, pts_hi, max_shift, scale):
+    """Pair p of the mixed batch, drawn from its own seed (seed + 1 + p) only."""
+    kinds = ("linear", "gamma", "inverted", "speckled")
+    prng = np.random.default_rng(seed + 1 + p)
+    H = int(prng.integers(side_lo, side_hi + 1) * scale)
+    W = int(prng.integers(side_lo, side_hi + 1) * scale)
+    m = int(templates[int(prng.integers(0, len(templates)))])
+    R = int(prng.integers(r_lo, r_hi + 1))
+    npts = int(prng.integers(pts_lo, pts_hi + 1) * scale)
+    kind = kinds[int(prng.integers(0, 4))]
+    H = max(H, m + 2 * R + 8)
+    W = max(W, m + 2 * R + 8)
+    ref = optical_like(prng, H, W)
+    sx, sy = (int(v) for v in prng.integers(-max_shift, max_shift + 1, 2))
+    sen = radiometric(prng, shift_image(ref, sx, sy), kind)
+    g = max(1, int(math.ceil(math.sqrt(max(1, npts)))))
+    pts = _points_for(sen, ref.shape, m, R, (g, g), "grad", npts)
+    truth = np.tile(np.array([[-sx, -sy]], np.float64), (len(pts), 1))
+    return Pair(ref, sen, pts, m, R, truth, dict(kind=kind, shift=(sx, sy), seed=seed + 1 + p))
+
+
 def mixed_batch(seed=4000, n_pairs=64, side_lo=512, side_hi=4096, templates=(41, 61, 81, 101),
-            r_lo=10, r_hi=40, pts_lo=200, pts_hi=4000, max_shift=8, scale=1.0):
+                r_lo=10, r_hi=40, pts_lo=200, pts_hi=4000, max_shift=8, scale=1.0, workers=1):
     """64 pairs, sides uniform in [512, 4096] (non-square allowed), each with
     one radiometric map of {linear, gamma, inverted, speckled}, 200-4000
     points, m from {41, 61, 81, 101}, R uniform in [10, 40].  ``scale``
-    shrinks sides and point counts for quick variants (1.0 = the full size)."""
-    rng = np.random.default_rng(seed)
-    kinds = ("linear", "gamma", "inverted", "speckled")
-    pairs = []
-    for p in range(n_pairs):
-        prng = np.random.default_rng(seed + 1 + p)
-        H = int(prng.integers(side_lo, side_hi + 1) * scale)
-        W = int(prng.integers(side_lo, side_hi + 1) * scale)
-        m = int(templates[int(prng.integers(0, len(templates)))])
-        R = int(prng.integers(r_lo, r_hi + 1))
-        npts = int(prng.integers(pts_lo, pts_hi + 1) * scale)
-        kind = kinds[int(prng.integers(0, 4))]
-        H = max(H, m + 2 * R + 8)
-        W = max(W, m + 2 * R + 8)
-        ref = optical_like(prng, H, W)
-        sx, sy = (int(v) for v in prng.integers(-max_shift, max_shift + 1, 2))
-        sen = radiometric(prng, shift_image(ref, sx, sy), kind)
-        g = max(1, int(math.ceil(math.sqrt(max(1, npts)))))
-        pts = _points_for(sen, ref.shape, m, R, (g, g), "grad", npts)
-        truth = np.tile(np.array([[-sx, -sy]], np.float64), (len(pts), 1))
-        pairs.append(Pair(ref, sen, pts, m, R, truth, dict(kind=kind, shift=(sx, sy), seed=seed + 1 + p)))
-    del rng
-    return pairs
+    shrinks sides and point counts for quick variants (1.0 = the full size).
+    Each pair depends on its own seed only, so ``workers`` > 1 builds them in
+    parallel processes (started with ``spawn``) with the same result."""
+    args = [(seed, p, side_lo, side_hi, templates, r_lo, r_hi, pts_lo, pts_hi, max_shift, scale)
+            for p in range(n_pairs)]
+    if workers <= 1 or n_pairs <= 1:
+        return [_mixed_pair(*a) for a in args]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=min(workers, n_pairs), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_mixed_pair, *zip(*args)))
 
 
 def speckle_pair_10000(seed=5000, H=10000, W=10000, n_points=10000, m=101, R=40, block=512,
