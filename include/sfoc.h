@@ -61,16 +61,16 @@ typedef enum {
     SFOC_CORR_AUTO = 0,       /* the form the autotuner measured fastest for (cube dtype, m, R)
                                * (see the autotuner section below) */
     SFOC_CORR_DIRECT_F32 = 1, /* FP32 CUDA-core direct correlation (F32 cubes) */
-    SFOC_CORR_IGEMM_TC = 2,   /* tcgen05 BF16 implicit GEMM, FP32 accumulate (BF16 cubes):
-                               * the column or band form, whichever issues fewer MMAs for
-                               * (m, R); the Toeplitz form when neither runs */
+    SFOC_CORR_IGEMM_TC = 2,   /* tcgen05 BF16 implicit GEMM, FP32 accumulate (BF16 cubes): the
+                               * tensor-core form the autotuner measured fastest (family 1) */
     SFOC_CORR_TC_TOEPLITZ = 3, /* the Toeplitz form of the tcgen05 kernel for any m, R */
     SFOC_CORR_TC_COLUMN = 4,  /* the column form: m + 2R <= 128, else SFOC_ERR_UNSUPPORTED */
     SFOC_CORR_TC_BAND = 5,    /* the band form (bands of 16 window rows x 8 offsets):
                                * R <= 40 and its shared memory fits, else SFOC_ERR_UNSUPPORTED */
     SFOC_CORR_FFT = 6         /* Eq. 13: FP32 Fourier transforms of the zero-padded window and
-                               * zero-mean template, summed over channels (F32 cubes,
-                               * m + 2R <= 128, else SFOC_ERR_UNSUPPORTED) */
+                               * zero-mean template, summed over channels (F32 cubes, or BF16
+                               * cubes widened to FP32 as they are read; m + 2R <= 128, else
+                               * SFOC_ERR_UNSUPPORTED) */
 } sfoc_corr_path;
 
 /*
@@ -293,7 +293,7 @@ SFOC_API sfoc_status sfoc_cube_free(sfoc_cube* cube);
  * n > 0, n < 0, m < 1, R < 0 or an unknown corr_path; SFOC_ERR_SHAPE when
  * the cubes' channel counts or dtypes differ; SFOC_ERR_UNSUPPORTED beyond
  * m <= 128, R <= 63, for a path the cube dtype does not serve (DIRECT_F32
- * and FFT need F32 cubes, the tensor-core paths BF16 cubes) or a forced
+ * needs F32 cubes, the tensor-core paths BF16 cubes) or a forced
  * form outside its limits; SFOC_ERR_OOM when the workspace cannot grow.
  * Points whose template or windows leave an image get status OUT_OF_BOUNDS.
  */
@@ -393,19 +393,22 @@ SFOC_API sfoc_status sfoc_ctx_plan_info(const sfoc_ctx* ctx, char* buf, size_t c
 
 /* ---- autotuner -------------------------------------------------------- */
 /*
- * With SFOC_CORR_AUTO the correlation form of a (cube dtype, m, R) is
- * measured, not ruled: on the first match of that key (outside a stream
- * capture) every form that runs for it is launched on the first
- * min(n, 2 x SMs) points of that call (one warm-up launch, then the better
- * of two timed with CUDA events): for F32 cubes the Fourier correlation
- * (and, where m + 2R <= 64, also its 128-point transform) and the direct
- * kernel; for BF16 cubes the band, column and Toeplitz tensor-core forms.
- * The fastest is kept in the context and used from then on.  The paper
- * weighs its FFT against spatial correlation by operation counts (Eq.
- * 17-19); on this device the choice is made by measurement.  Without an
- * entry (autotuning off, or inside a capture) AUTO takes the fixed rule: F32
- * cubes the Fourier form when m + 2R <= 128, else the direct kernel; BF16
- * cubes the tensor-core form with the fewest MMAs.
+ * With SFOC_CORR_AUTO (family 0) and SFOC_CORR_IGEMM_TC (family 1) the
+ * correlation form of a (cube dtype, m, R) is measured, not ruled: on the
+ * first match of that key (outside a stream capture) every form of the
+ * family that runs for it is launched on the first min(n, 2 x SMs) points
+ * of that call (one warm-up launch, then the better of two timed with CUDA
+ * events), and the fastest is kept in the context and used from then on.
+ *   family 0, F32 cubes:  the Fourier correlation (where m + 2R <= 64 also
+ *                         with its 128-point transform) and the direct kernel;
+ *   family 0, BF16 cubes: the band, column and Toeplitz tensor-core forms and
+ *                         the Fourier correlation (reading the bf16 cube);
+ *   family 1 (BF16):      the tensor-core forms only.
+ * The paper weighs its FFT against spatial correlation by operation counts
+ * (Eq. 17-19); on this device the choice is made by measurement.  Without
+ * an entry (autotuning off, or inside a capture) the fixed rule: F32 cubes
+ * the Fourier form when m + 2R <= 128, else the direct kernel; BF16 cubes
+ * the tensor-core form with the fewest MMAs.
  */
 SFOC_API sfoc_status sfoc_ctx_set_autotune(sfoc_ctx* ctx, int enable);
 /* The entry of (dtype, m, R): *corr_path = the chosen sfoc_corr_path (-1 when
@@ -413,9 +416,9 @@ SFOC_API sfoc_status sfoc_ctx_set_autotune(sfoc_ctx* ctx, int enable);
  * (*n_cand <= 6) its path, option and milliseconds (-1 = it failed to run);
  * *sample = the points timed.  Output pointers other than corr_path may be
  * NULL. */
-SFOC_API sfoc_status sfoc_ctx_autotune_entry(const sfoc_ctx* ctx, int dtype, int m, int R, int* corr_path,
-                                             int* option, int* n_cand, int* cand_path, int* cand_option,
-                                             float* cand_ms, int* sample);
+SFOC_API sfoc_status sfoc_ctx_autotune_entry(const sfoc_ctx* ctx, int dtype, int m, int R, int family,
+                                             int* corr_path, int* option, int* n_cand, int* cand_path,
+                                             int* cand_option, float* cand_ms, int* sample);
 /* The context's entries as JSON text ({"sfoc_autotune": 1, "entries":
  * [...]}).  *len receives the bytes needed including the terminating zero;
  * with buf NULL nothing else is written; SFOC_ERR_INVALID_ARG when cap is

@@ -116,7 +116,8 @@ _SIGS = {
     "sfoc_ctx_stage_scopes": (C.c_int, [_P, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
     "sfoc_ctx_release_plans": (C.c_int, [_P]),
     "sfoc_ctx_set_autotune": (C.c_int, [_P, C.c_int]),
-    "sfoc_ctx_autotune_entry": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+    "sfoc_ctx_autotune_entry": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                           C.POINTER(C.c_float), C.POINTER(C.c_int)]),
     "sfoc_ctx_autotune_export": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -554,13 +555,14 @@ class Context:
     def set_autotune(self, on=True):
         self._chk(lib().sfoc_ctx_set_autotune(self.h, 1 if on else 0))
 
-    def autotune_entry(self, dtype, m, R):
+    def autotune_entry(self, dtype, m, R, family=0):
         """{path, option, sample, candidates: [(path, option, ms)]} of the
-        autotuner's entry for (dtype, m, R), or None."""
+        autotuner's entry for (dtype, m, R) in a family (0: AUTO, every form;
+        1: IGEMM_TC, the tensor-core forms), or None."""
         path, opt, nc, smp = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         cp, co, cm = (C.c_int * 6)(), (C.c_int * 6)(), (C.c_float * 6)()
-        self._chk(lib().sfoc_ctx_autotune_entry(self.h, int(dtype), int(m), int(R), C.byref(path), C.byref(opt),
-                                                 C.byref(nc), cp, co, cm, C.byref(smp)))
+        self._chk(lib().sfoc_ctx_autotune_entry(self.h, int(dtype), int(m), int(R), int(family), C.byref(path),
+                                                 C.byref(opt), C.byref(nc), cp, co, cm, C.byref(smp)))
         if path.value < 0:
             return None
         return dict(path=path.value, option=opt.value, sample=smp.value,

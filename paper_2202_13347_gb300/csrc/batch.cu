@@ -71,7 +71,7 @@ struct BatchPlan {
     size_t d_jobs = 0, d_items = 0, d_queues = 0;
     int n_items = 0, max_R = 0, n_queues = 0;
     std::vector<CorrClass> classes;
-    int centered = 1;
+    int dtype = 0;                   // the cubes' dtype (every pair alike)
     // graph of the whole call
     cudaGraphExec_t exec = nullptr;
     int launches = 0;                // kernel launches per run
@@ -234,7 +234,7 @@ cudaError_t enqueue_match_tail(sfoc_ctx* ctx, BatchPlan* p, cudaStream_t s) {
             continue;
         }
         StageScope sc(ctx, ST_CORR, 1);
-        if (c.path == SFOC_CORR_FFT) e = launch_corr_fft(none, is, c.cls, s);
+        if (c.path == SFOC_CORR_FFT) e = launch_corr_fft(none, is, c.cls, p->dtype == SFOC_DTYPE_BF16, s);
         else if (c.path == SFOC_CORR_DIRECT_F32) e = launch_corr_f32(none, is, c.cls, s);
         else e = launch_corr_tc(tc_form(c.path), c.cls, none, is, c.ms.data(), c.Rs.data(), (int)c.ms.size(),
                                 ctx->d_err, s);
@@ -246,7 +246,7 @@ cudaError_t enqueue_match_tail(sfoc_ctx* ctx, BatchPlan* p, cudaStream_t s) {
     all.n = p->n_items;
     all.max_R = p->max_R;
     StageScope sc(ctx, ST_NCC, 1);
-    return launch_ncc_argmax(none, all, p->centered, s);
+    return launch_ncc_argmax(none, all, s);
 }
 
 cudaError_t enqueue_all(sfoc_ctx* ctx, BatchPlan* p, cudaStream_t s) {
@@ -429,15 +429,15 @@ sfoc_status check_match(sfoc_ctx* ctx, const MatchIn& in, int path) {
         } else if (r->c.dtype != dtype || r->c.z != z) {
             return fail(ctx, SFOC_ERR_SHAPE, "every pair of a batch has the same cube dtype and channels");
         }
-        if (path != SFOC_CORR_AUTO) {
-            const int pp = path == SFOC_CORR_IGEMM_TC ? auto_rule(SFOC_DTYPE_BF16, in.m[i], in.R[i]) : path;
-            const bool f32 = pp == SFOC_CORR_DIRECT_F32 || pp == SFOC_CORR_FFT;
-            if (pp < 0 || f32 != (dtype == SFOC_DTYPE_F32) || (path == SFOC_CORR_IGEMM_TC && dtype != SFOC_DTYPE_BF16))
-                return fail(ctx, SFOC_ERR_UNSUPPORTED, "the correlation path does not serve a pair of the batch");
-            if (class_of(pp, 0, in.m[i], in.R[i]) == 0)
+        if (path == SFOC_CORR_AUTO || path == SFOC_CORR_IGEMM_TC) {
+            const int family = path == SFOC_CORR_AUTO ? 0 : 1;
+            if (auto_rule(dtype, in.m[i], in.R[i], family) < 0)
+                return fail(ctx, SFOC_ERR_UNSUPPORTED, "no correlation form of the path runs for a pair's m / R");
+        } else {
+            if (!path_serves(path, dtype))
+                return fail(ctx, SFOC_ERR_UNSUPPORTED, "the correlation path does not serve the batch's cubes");
+            if (class_of(path, 0, in.m[i], in.R[i]) == 0)
                 return fail(ctx, SFOC_ERR_UNSUPPORTED, "the correlation form does not run for a pair's m / R");
-        } else if (auto_rule(r->c.dtype, in.m[i], in.R[i]) < 0) {
-            return fail(ctx, SFOC_ERR_UNSUPPORTED, "no correlation form runs for a pair's m / R");
         }
     }
     return SFOC_OK;
@@ -498,19 +498,12 @@ bool plan_classes(sfoc_ctx* ctx, BatchPlan* p, int path, int dtype, Layout& lay)
         int path, cls;
     };
     std::vector<Pick> pick(p->jobs.size());
+    p->dtype = dtype;
     for (size_t i = 0; i < p->jobs.size(); ++i) {
-        const MatchJob& j = p->jobs[i];
-        int pp = path, opt = 0;
-        if (pp == SFOC_CORR_IGEMM_TC) pp = auto_rule(SFOC_DTYPE_BF16, j.m, j.R);
-        if (pp == SFOC_CORR_AUTO) {
-            auto te = ctx->tune.find(TuneKey{dtype, j.m, j.R});
-            if (te != ctx->tune.end()) {
-                pp = te->second.path;
-                opt = te->second.option;
-            } else {
-                pp = auto_rule(dtype, j.m, j.R);
-            }
-        }
+        MatchJob& j = p->jobs[i];
+        int opt = 0;
+        const int pp = resolve_path(ctx, path, dtype, &j, false, &opt);
+        j.centered = centered_path(pp) ? 1 : 0;
         pick[i] = {pp, class_of(pp, opt, j.m, j.R)};
     }
     p->classes.clear();
@@ -551,7 +544,6 @@ bool plan_classes(sfoc_ctx* ctx, BatchPlan* p, int path, int dtype, Layout& lay)
         if (c.path == SFOC_CORR_FFT) c.queue = p->n_queues++;
     }
     p->d_queues = lay.add(sizeof(int) * (size_t)(p->n_queues > 0 ? p->n_queues : 1));
-    p->centered = dtype == SFOC_DTYPE_F32 ? 1 : 0;
     return true;
 }
 
@@ -640,9 +632,10 @@ sfoc_status make_and_run(sfoc_ctx* ctx, int kind, std::vector<uint64_t>&& key, c
     // the stages the autotuner needs
     const int dtype = min ? mi.refs[0]->c.dtype : 0;
     bool need_tune = false;
-    if (min && path == SFOC_CORR_AUTO && ctx->autotune)
+    const int family = path == SFOC_CORR_AUTO ? 0 : 1;
+    if (min && (path == SFOC_CORR_AUTO || path == SFOC_CORR_IGEMM_TC) && ctx->autotune)
         for (int i = 0; i < mi.n; ++i)
-            if (mi.npts[i] > 0 && !ctx->tune.count(TuneKey{dtype, mi.m[i], mi.R[i]})) need_tune = true;
+            if (mi.npts[i] > 0 && !ctx->tune.count(TuneKey{dtype, mi.m[i], mi.R[i], family})) need_tune = true;
     std::vector<char> host;
     if (min) {
         // classes need the forms, which may need measurements: lay them out after
@@ -670,8 +663,8 @@ sfoc_status make_and_run(sfoc_ctx* ctx, int kind, std::vector<uint64_t>&& key, c
             }
             // measure each (m, R) without an entry on the first pair that has it
             for (int i = 0; i < mi.n; ++i) {
-                if (mi.npts[i] == 0 || ctx->tune.count(TuneKey{dtype, mi.m[i], mi.R[i]})) continue;
-                if (!autotune_pair(ctx, dtype, p->jobs[i])) {
+                if (mi.npts[i] == 0 || ctx->tune.count(TuneKey{dtype, mi.m[i], mi.R[i], family})) continue;
+                if (!autotune_pair(ctx, dtype, family, p->jobs[i])) {
                     destroy_plan(p);
                     return fail(ctx, SFOC_ERR_UNSUPPORTED, "no correlation form ran for a pair's m / R");
                 }

@@ -14,11 +14,14 @@ namespace sfoc {
 
 struct BatchPlan;  // batch.cu
 
-// Autotuner: the correlation form measured fastest for (cube dtype, m, R).
+// Autotuner: the correlation form measured fastest for (cube dtype, m, R)
+// among a family of forms: 0 = every form that runs on the dtype (AUTO),
+// 1 = the tensor-core forms only (IGEMM_TC, BF16 cubes).
 struct TuneKey {
-    int dtype, m, R;
+    int dtype, m, R, family;
     bool operator<(const TuneKey& o) const {
         if (dtype != o.dtype) return dtype < o.dtype;
+        if (family != o.family) return family < o.family;
         if (m != o.m) return m < o.m;
         return R < o.R;
     }
@@ -128,10 +131,24 @@ int sm_count(int device);
 // TC_BAND), `option` the FFT side (0 = the smallest that serves).  Returns
 // cudaErrorNotSupported where the form does not run for the job.
 cudaError_t launch_corr_path(sfoc_ctx* ctx, int path, int option, MatchJob& one);
-// The concrete form AUTO takes for (dtype, m, R) without a tuned entry.
-int auto_rule(int dtype, int m, int R);
-// Measures every eligible form on the first points of `one` (its template
-// statistics already computed) and stores the winner; returns it.
-const TuneEntry* autotune_pair(sfoc_ctx* ctx, int dtype, MatchJob one);
+// The concrete form a family takes for (dtype, m, R) without a tuned entry
+// (-1: none runs).
+int auto_rule(int dtype, int m, int R, int family);
+// Measures every form of the family that runs for `one` on its first points
+// (their template statistics already computed) and stores the winner;
+// returns it.
+const TuneEntry* autotune_pair(sfoc_ctx* ctx, int dtype, int family, MatchJob one);
+// The concrete form for a match with corr_path `path` (AUTO, IGEMM_TC or a
+// concrete one): the tuned entry, measured now when allowed, else the rule.
+// *option receives the FFT side (0 otherwise); -1 when no form runs.
+int resolve_path(sfoc_ctx* ctx, int path, int dtype, const MatchJob* one, bool may_measure, int* option);
+// whether a concrete path computes the zero-mean numerator of Eq. 9
+inline bool centered_path(int path) { return path == SFOC_CORR_DIRECT_F32 || path == SFOC_CORR_FFT; }
+// whether a concrete path runs on cubes of this dtype
+inline bool path_serves(int path, int dtype) {
+    if (path == SFOC_CORR_FFT) return true;
+    if (path == SFOC_CORR_DIRECT_F32) return dtype == SFOC_DTYPE_F32;
+    return dtype == SFOC_DTYPE_BF16;
+}
 
 }  // namespace sfoc

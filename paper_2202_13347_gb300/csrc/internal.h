@@ -199,6 +199,7 @@ struct MatchJob {  // aligned as its tensor maps (128 bytes)
     size_t spitch, splane;
     int Hs, Ws;
     int z, m, R, n;
+    int centered;           // 1: the correlation gives the zero-mean numerator of Eq. 9 (FP32 forms)
     const int32_t* pts;     // n x (x, y)
     PointStat* stats;       // n
     float* maps;            // n x (2R+1)^2 correlation maps (scratch)
@@ -240,7 +241,8 @@ bool corr_f32_supported(int m, int R);
 cudaError_t launch_corr_f32(const MatchJob& one, const ItemSet& is, int tpt, cudaStream_t st);
 bool corr_fft_supported(int m, int R);
 int corr_fft_side(int m, int R);  // smallest transform side that serves (m, R): 64 or 128
-cudaError_t launch_corr_fft(const MatchJob& one, const ItemSet& is, int L, cudaStream_t st);
+// bf16: the jobs' cubes are BF16 (read from the row-major chunk layout rm)
+cudaError_t launch_corr_fft(const MatchJob& one, const ItemSet& is, int L, bool bf16, cudaStream_t st);
 // tensor-core forms: 1 Toeplitz, 2 column, 3 band.  corr_tc_class: the
 // kernel instance a job of (m, R) takes in that form (column: G, band: NQ,
 // Toeplitz: 1 = runs, one pair per launch), 0 where the form does not run;
@@ -252,7 +254,7 @@ bool corr_tc_maps(int form, MatchJob& j);
 cudaError_t launch_corr_tc(int form, int cls, const MatchJob& one, const ItemSet& is, const int* ms, const int* Rs,
                            int cnt, int* err_flag, cudaStream_t st);
 size_t corr_tc_smem_bytes(int m, int R);
-cudaError_t launch_ncc_argmax(const MatchJob& one, const ItemSet& is, int centered, cudaStream_t st);
+cudaError_t launch_ncc_argmax(const MatchJob& one, const ItemSet& is, cudaStream_t st);
 
 // block-based FAST (k_fast.cu)
 cudaError_t launch_fast_blocks(const float* img, int H, int W, size_t pitch, float t, int grid_y, int grid_x,

@@ -23,6 +23,8 @@
 // 2R + 1 wanted rows the Hermitian-extended row.
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace sfoc {
@@ -189,10 +191,32 @@ __device__ __forceinline__ float2 cross_spectrum(float2 a, float2 b) {
     return make_float2(0.25f * fmaf(s.x, d.y, -s.y * d.x), 0.25f * fmaf(s.x, d.x, s.y * d.y));
 }
 
+// One value of channel c at (row y, column x) of a cube: the F32 planes, or
+// the BF16 row-major chunks (chunk c / 6, lane c % 6 of a pixel's 8),
+// widened to FP32.
+struct CubeF32 {
+    const float* p;
+    size_t pitch, plane;
+    __device__ __forceinline__ const float* row(int c, int y, int x0) const {
+        return p + (size_t)c * plane + (size_t)y * pitch + x0;
+    }
+    __device__ __forceinline__ static float at(const float* r, int x) { return r[x]; }
+};
+struct CubeBF16 {
+    const __nv_bfloat16* p;
+    int H, W;
+    __device__ __forceinline__ const __nv_bfloat16* row(int c, int y, int x0) const {
+        const int g = c / 6;
+        return p + (((size_t)g * H + y) * W + x0) * 8 + (c - 6 * g);
+    }
+    __device__ __forceinline__ static float at(const __nv_bfloat16* r, int x) { return __bfloat162float(r[8 * x]); }
+};
+
 // Items: the points of `one` (items == nullptr) or (job, point) pairs of a
 // batch; with a queue the CTAs take items from an atomic counter (points of
 // uneven cost balance across the SMs), else item k goes to CTA k mod grid.
-template <int L>
+// BF: the jobs' cubes are BF16 (12 channels), read from the row-major layout.
+template <int L, bool BF>
 __global__ void __launch_bounds__(FftShape<L>::T, 1)
     k_corr_fft(const __grid_constant__ MatchJob one, const MatchJob* __restrict__ jobs,
                const int2* __restrict__ items, int n_items, int* __restrict__ queue) {
@@ -241,9 +265,15 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
         const MatchJob& J = item_job(one, jobs, items, kk, &k);
         const PointStat st = J.stats[k];
         if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
-        const float* __restrict__ Sf = J.rf32;
-        const float* __restrict__ Tf = J.sf32;
-        const size_t spitch = J.rpitch, splane = J.rplane, tpitch = J.spitch, tplane = J.splane;
+        typedef typename std::conditional<BF, CubeBF16, CubeF32>::type Src;
+        Src Sc, Tc;
+        if constexpr (BF) {
+            Sc = CubeBF16{J.rrm, J.Hr, J.Wr};
+            Tc = CubeBF16{J.srm, J.Hs, J.Ws};
+        } else {
+            Sc = CubeF32{J.rf32, J.rpitch, J.rplane};
+            Tc = CubeF32{J.sf32, J.spitch, J.splane};
+        }
         const int m = J.m, R = J.R, z = J.z;
         const int P1 = 2 * R + 1, Lw = m + 2 * R;
         const int h = template_half(m);
@@ -261,20 +291,18 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
         for (int i = tid; i < L; i += kFftThreads) P64[i] = make_float2(0.f, 0.f);
 
         for (int c = 0; c < z; ++c) {
-            const float* Sp = Sf + (size_t)c * splane;
-            const float* Tp = Tf + (size_t)c * tplane;
             // ---- rows: z = S + i (T - mean), zero outside the window / template
             for (int y0 = 0; y0 < Lw; y0 += kFftGroups) {
                 const int y = y0 + grp;
                 const bool rs = y < Lw, rt = y < m;
-                const float* srow = Sp + (size_t)(wy0 + (rs ? y : 0)) * spitch + wx0;
-                const float* trow = Tp + (size_t)(ty0 + (rt ? y : 0)) * tpitch + tx0;
+                const auto srow = Sc.row(c, wy0 + (rs ? y : 0), wx0);
+                const auto trow = Tc.row(c, ty0 + (rt ? y : 0), tx0);
                 float2 v[E];
 #pragma unroll
                 for (int j = 0; j < E; ++j) {
                     const int x = t + 8 * j;
-                    v[j].x = (rs && x < Lw) ? srow[x] : 0.f;
-                    v[j].y = (rt && x < m) ? trow[x] - tmean : 0.f;
+                    v[j].x = (rs && x < Lw) ? Src::at(srow, x) : 0.f;
+                    v[j].y = (rt && x < m) ? Src::at(trow, x) - tmean : 0.f;
                 }
                 group_fft<E, -1>(v, t, sc, tw);
                 if (rs) {
@@ -373,28 +401,30 @@ bool corr_fft_supported(int m, int R) { return m + 2 * R <= 128; }
 int corr_fft_side(int m, int R) { return m + 2 * R <= 64 ? 64 : 128; }
 
 // L: the transform side (64 or 128, at least the largest m + 2R of the items)
-cudaError_t launch_corr_fft(const MatchJob& one, const ItemSet& is, int L, cudaStream_t st) {
+cudaError_t launch_corr_fft(const MatchJob& one, const ItemSet& is, int L, bool bf16, cudaStream_t st) {
     const int n = is.items ? is.n : one.n;
     if (n <= 0) return cudaSuccess;
     const int lw = is.items ? is.max_lw : one.m + 2 * one.R;
     if ((L != 64 && L != 128) || lw > L) return cudaErrorNotSupported;
-    if (!is.items && (one.rf32 == nullptr || one.sf32 == nullptr)) return cudaErrorNotSupported;
+    if (!is.items && (bf16 ? (one.rrm == nullptr || one.srm == nullptr || one.z != 12)
+                           : (one.rf32 == nullptr || one.sf32 == nullptr)))
+        return cudaErrorNotSupported;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
-#define SFOC_FFT_LAUNCH(LV)                                                                                       \
+#define SFOC_FFT_LAUNCH(LV, BV)                                                                                   \
     {                                                                                                             \
         const int smem = (int)FftShape<LV>::smem;                                                                 \
-        e = cudaFuncSetAttribute(k_corr_fft<LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);             \
+        e = cudaFuncSetAttribute(k_corr_fft<LV, BV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);         \
         if (e != cudaSuccess) return e;                                                                           \
         const int grid = n < sms ? n : sms;                                                                       \
-        k_corr_fft<LV><<<grid, FftShape<LV>::T, smem, st>>>(one, is.jobs, is.items, n, is.queue);                 \
+        k_corr_fft<LV, BV><<<grid, FftShape<LV>::T, smem, st>>>(one, is.jobs, is.items, n, is.queue);             \
     }
     if (L == 64) {
-        SFOC_FFT_LAUNCH(64)
+        if (bf16) SFOC_FFT_LAUNCH(64, true) else SFOC_FFT_LAUNCH(64, false)
     } else {
-        SFOC_FFT_LAUNCH(128)
+        if (bf16) SFOC_FFT_LAUNCH(128, true) else SFOC_FFT_LAUNCH(128, false)
     }
 #undef SFOC_FFT_LAUNCH
     return cudaGetLastError();

@@ -110,7 +110,7 @@ constexpr int kNccThreads = 256;
 
 __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const __grid_constant__ MatchJob one,
                                                             const MatchJob* __restrict__ jobs,
-                                                            const int2* __restrict__ items, int centered) {
+                                                            const int2* __restrict__ items) {
     extern __shared__ float s_map[];  // P1 * P1
     __shared__ float s_bv[kNccThreads / 32];
     __shared__ int s_bi[kNccThreads / 32];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const __grid_constan
     int k;
     const MatchJob& J = item_job(one, jobs, items, blockIdx.x, &k);
     const u64* __restrict__ Pr = J.rint;
-    const int Hr = J.Hr, m = J.m, R = J.R, z = J.z;
+    const int Hr = J.Hr, m = J.m, R = J.R, z = J.z, centered = J.centered;
     const size_t ipr = J.ripitch;
     const int32_t* __restrict__ pts = J.pts;
     const float* __restrict__ num = J.maps;
@@ -229,7 +229,7 @@ cudaError_t launch_template_stats(const MatchJob& one, const ItemSet& is, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_ncc_argmax(const MatchJob& one, const ItemSet& is, int centered, cudaStream_t st) {
+cudaError_t launch_ncc_argmax(const MatchJob& one, const ItemSet& is, cudaStream_t st) {
     const int n = is.items ? is.n : one.n;
     if (n <= 0) return cudaSuccess;
     const int R = is.items ? is.max_R : one.R;
@@ -237,7 +237,7 @@ cudaError_t launch_ncc_argmax(const MatchJob& one, const ItemSet& is, int center
     size_t smem = sizeof(float) * (size_t)P1 * P1;
     cudaError_t e = cudaFuncSetAttribute(k_ncc_argmax, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_ncc_argmax<<<n, kNccThreads, smem, st>>>(one, is.jobs, is.items, centered);
+    k_ncc_argmax<<<n, kNccThreads, smem, st>>>(one, is.jobs, is.items);
     return cudaGetLastError();
 }
 

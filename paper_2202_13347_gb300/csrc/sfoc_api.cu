@@ -279,8 +279,9 @@ cudaError_t launch_corr_path(sfoc_ctx* ctx, int path, int option, MatchJob& one)
             return launch_corr_f32(one, none, c, ctx->stream);
         }
         case SFOC_CORR_FFT: {
-            if (!corr_fft_supported(m, R) || !one.rf32) return cudaErrorNotSupported;
-            return launch_corr_fft(one, none, option ? option : corr_fft_side(m, R), ctx->stream);
+            if (!corr_fft_supported(m, R)) return cudaErrorNotSupported;
+            return launch_corr_fft(one, none, option ? option : corr_fft_side(m, R), one.rf32 == nullptr,
+                                   ctx->stream);
         }
         case SFOC_CORR_TC_TOEPLITZ:
         case SFOC_CORR_TC_COLUMN:
@@ -295,39 +296,39 @@ cudaError_t launch_corr_path(sfoc_ctx* ctx, int path, int option, MatchJob& one)
     }
 }
 
-int auto_rule(int dtype, int m, int R) {
+int auto_rule(int dtype, int m, int R, int family) {
     if (dtype == SFOC_DTYPE_BF16) {
         switch (corr_tc_auto_form(m, R)) {
             case 3: return SFOC_CORR_TC_BAND;
             case 2: return SFOC_CORR_TC_COLUMN;
             case 1: return SFOC_CORR_TC_TOEPLITZ;
-            default: return -1;
+            default: return family == 0 && corr_fft_supported(m, R) ? SFOC_CORR_FFT : -1;
         }
     }
+    if (family != 0) return -1;
     if (corr_fft_supported(m, R)) return SFOC_CORR_FFT;
     return corr_f32_supported(m, R) ? SFOC_CORR_DIRECT_F32 : -1;
 }
 
-const TuneEntry* autotune_pair(sfoc_ctx* ctx, int dtype, MatchJob one) {
+const TuneEntry* autotune_pair(sfoc_ctx* ctx, int dtype, int family, MatchJob one) {
     const int m = one.m, R = one.R;
     TuneEntry t;
     memset(&t, 0, sizeof(t));
-    if (dtype == SFOC_DTYPE_F32) {
-        if (corr_fft_supported(m, R)) {
-            const int side = corr_fft_side(m, R);
-            t.cand_path[t.n_cand] = SFOC_CORR_FFT;
-            t.cand_option[t.n_cand++] = side;
-            if (side == 64) {  // the larger transform as a tile option
-                t.cand_path[t.n_cand] = SFOC_CORR_FFT;
-                t.cand_option[t.n_cand++] = 128;
-            }
-        }
-        if (corr_f32_supported(m, R)) t.cand_path[t.n_cand++] = SFOC_CORR_DIRECT_F32;
-    } else {
-        const int forms[3] = {3, 2, 1}, paths[3] = {SFOC_CORR_TC_BAND, SFOC_CORR_TC_COLUMN, SFOC_CORR_TC_TOEPLITZ};
-        for (int i = 0; i < 3; ++i)
-            if (corr_tc_class(forms[i], m, R) > 0) t.cand_path[t.n_cand++] = paths[i];
+    auto add = [&](int path, int option) {
+        t.cand_path[t.n_cand] = path;
+        t.cand_option[t.n_cand++] = option;
+    };
+    if (dtype == SFOC_DTYPE_BF16) {
+        if (corr_tc_class(3, m, R) > 0) add(SFOC_CORR_TC_BAND, 0);
+        if (corr_tc_class(2, m, R) > 0) add(SFOC_CORR_TC_COLUMN, 0);
+        if (corr_tc_class(1, m, R) > 0) add(SFOC_CORR_TC_TOEPLITZ, 0);
     }
+    if (family == 0 && corr_fft_supported(m, R)) {
+        const int side = corr_fft_side(m, R);
+        add(SFOC_CORR_FFT, side);
+        if (side == 64) add(SFOC_CORR_FFT, 128);  // the larger transform as a tile option
+    }
+    if (family == 0 && dtype == SFOC_DTYPE_F32 && corr_f32_supported(m, R)) add(SFOC_CORR_DIRECT_F32, 0);
     if (t.n_cand == 0) return nullptr;
     // a sample of up to two waves of points, timed per candidate: one
     // warm-up launch, then the better of two
@@ -363,9 +364,25 @@ const TuneEntry* autotune_pair(sfoc_ctx* ctx, int dtype, MatchJob one) {
     if (best < 0) return nullptr;
     t.path = t.cand_path[best];
     t.option = t.cand_option[best];
-    auto& slot = ctx->tune[TuneKey{dtype, m, R}];
+    auto& slot = ctx->tune[TuneKey{dtype, m, R, family}];
     slot = t;
     return &slot;
+}
+
+int resolve_path(sfoc_ctx* ctx, int path, int dtype, const MatchJob* one, bool may_measure, int* option) {
+    *option = 0;
+    if (path != SFOC_CORR_AUTO && path != SFOC_CORR_IGEMM_TC) return path_serves(path, dtype) ? path : -1;
+    const int family = path == SFOC_CORR_AUTO ? 0 : 1;
+    if (family == 1 && dtype != SFOC_DTYPE_BF16) return -1;
+    const int m = one->m, R = one->R;
+    auto it = ctx->tune.find(TuneKey{dtype, m, R, family});
+    const TuneEntry* te = it != ctx->tune.end() ? &it->second : nullptr;
+    if (!te && may_measure && ctx->autotune && !capturing(ctx->stream)) te = autotune_pair(ctx, dtype, family, *one);
+    if (te) {
+        *option = te->option;
+        return te->path;
+    }
+    return auto_rule(dtype, m, R, family);
 }
 
 }  // namespace sfoc
@@ -794,15 +811,13 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
     const int m = template_size, R = search_radius;
     if (path == SFOC_CORR_IGEMM_TC) {
         if (f32_cube) return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
-        path = auto_rule(SFOC_DTYPE_BF16, m, R);
-        if (path < 0) return fail(ctx, SFOC_ERR_UNSUPPORTED, "no tensor-core form runs for this m / R");
-    }
-    if (path != SFOC_CORR_AUTO) {
-        const bool f32_path = path == SFOC_CORR_DIRECT_F32 || path == SFOC_CORR_FFT;
-        if (f32_path && !f32_cube) return fail(ctx, SFOC_ERR_UNSUPPORTED, "DIRECT_F32 and FFT need F32 cubes");
-        if (!f32_path && f32_cube) return fail(ctx, SFOC_ERR_UNSUPPORTED, "tensor-core paths need BF16 cubes");
-    } else if (auto_rule(dtype, m, R) < 0) {
-        return fail(ctx, SFOC_ERR_UNSUPPORTED, "no correlation form runs for this m / R");
+        if (auto_rule(SFOC_DTYPE_BF16, m, R, 1) < 0)
+            return fail(ctx, SFOC_ERR_UNSUPPORTED, "no tensor-core form runs for this m / R");
+    } else if (path == SFOC_CORR_AUTO) {
+        if (auto_rule(dtype, m, R, 0) < 0) return fail(ctx, SFOC_ERR_UNSUPPORTED, "no correlation form runs for this m / R");
+    } else if (!path_serves(path, dtype)) {
+        return fail(ctx, SFOC_ERR_UNSUPPORTED,
+                    f32_cube ? "tensor-core paths need BF16 cubes" : "DIRECT_F32 needs F32 cubes");
     }
     DeviceGuard g(ctx->device);
     if (n == 0) return SFOC_OK;
@@ -824,21 +839,13 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
         e = launch_template_stats(one, none, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "template stats launch");
+    // AUTO / IGEMM_TC: the measured choice for (dtype, m, R), looked up or
+    // measured now on this call's points (not inside a capture: the
+    // measurement waits for its events); the fixed rule where there is neither
     int option = 0;
-    if (path == SFOC_CORR_AUTO) {
-        // the measured choice for (dtype, m, R): looked up, or measured now on
-        // this call's points (not inside a capture: the measurement waits
-        // for its events); the fixed rule where there is neither
-        auto it = ctx->tune.find(TuneKey{dtype, m, R});
-        const TuneEntry* te = it != ctx->tune.end() ? &it->second : nullptr;
-        if (!te && ctx->autotune && !capturing(ctx->stream)) te = autotune_pair(ctx, dtype, one);
-        if (te) {
-            path = te->path;
-            option = te->option;
-        } else {
-            path = auto_rule(dtype, m, R);
-        }
-    }
+    path = resolve_path(ctx, path, dtype, &one, true, &option);
+    if (path < 0) return fail(ctx, SFOC_ERR_UNSUPPORTED, "no correlation form runs for this m / R");
+    one.centered = centered_path(path) ? 1 : 0;
     {
         StageScope sc(ctx, ST_CORR, 1);
         e = launch_corr_path(ctx, path, option, one);
@@ -848,10 +855,9 @@ sfoc_status fastncc_match(sfoc_ctx* ctx, sfoc_cube* ref, sfoc_cube* sen, const i
         return fail(ctx, SFOC_ERR_UNSUPPORTED, "correlation kernel does not support this m / R");
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "correlation launch");
-    const bool centered = path == SFOC_CORR_DIRECT_F32 || path == SFOC_CORR_FFT;
     {
         StageScope sc(ctx, ST_NCC, 1);
-        e = launch_ncc_argmax(one, none, centered ? 1 : 0, ctx->stream);
+        e = launch_ncc_argmax(one, none, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ncc launch");
     return SFOC_OK;
@@ -947,10 +953,11 @@ sfoc_status sfoc_ctx_set_autotune(sfoc_ctx* ctx, int enable) {
     return SFOC_OK;
 }
 
-sfoc_status sfoc_ctx_autotune_entry(const sfoc_ctx* ctx, int dtype, int m, int R, int* corr_path, int* option,
-                                    int* n_cand, int* cand_path, int* cand_option, float* cand_ms, int* sample) {
+sfoc_status sfoc_ctx_autotune_entry(const sfoc_ctx* ctx, int dtype, int m, int R, int family, int* corr_path,
+                                    int* option, int* n_cand, int* cand_path, int* cand_option, float* cand_ms,
+                                    int* sample) {
     if (!ctx || !corr_path) return SFOC_ERR_INVALID_ARG;
-    auto it = ctx->tune.find(TuneKey{dtype, m, R});
+    auto it = ctx->tune.find(TuneKey{dtype, m, R, family});
     if (it == ctx->tune.end()) {
         *corr_path = -1;
         if (n_cand) *n_cand = 0;
@@ -976,9 +983,9 @@ sfoc_status sfoc_ctx_autotune_export(const sfoc_ctx* ctx, char* buf, size_t cap,
     char tmp[256];
     for (const auto& kv : ctx->tune) {
         const TuneEntry& t = kv.second;
-        snprintf(tmp, sizeof(tmp), "%s{\"dtype\": %d, \"m\": %d, \"R\": %d, \"path\": %d, \"option\": %d, \"sample\": %d, "
-                 "\"candidates\": [", first ? "" : ", ", kv.first.dtype, kv.first.m, kv.first.R, t.path, t.option,
-                 t.sample);
+        snprintf(tmp, sizeof(tmp), "%s{\"dtype\": %d, \"family\": %d, \"m\": %d, \"R\": %d, \"path\": %d, "
+                 "\"option\": %d, \"sample\": %d, \"candidates\": [", first ? "" : ", ", kv.first.dtype,
+                 kv.first.family, kv.first.m, kv.first.R, t.path, t.option, t.sample);
         j += tmp;
         for (int i = 0; i < t.n_cand; ++i) {
             snprintf(tmp, sizeof(tmp), "%s[%d, %d, %.6g]", i ? ", " : "", t.cand_path[i], t.cand_option[i],
@@ -1026,15 +1033,16 @@ sfoc_status sfoc_ctx_autotune_import(sfoc_ctx* ctx, const char* text) {
         if (!end) return fail(ctx, SFOC_ERR_INVALID_ARG, "unterminated autotune entry");
         TuneEntry t;
         memset(&t, 0, sizeof(t));
-        int dtype, m, R;
+        int dtype, m, R, family = 0;
         if (!json_int(p, end, "dtype", &dtype) || !json_int(p, end, "m", &m) || !json_int(p, end, "R", &R) ||
             !json_int(p, end, "path", &t.path) || !json_int(p, end, "option", &t.option))
             return fail(ctx, SFOC_ERR_INVALID_ARG, "autotune entry without dtype, m, R, path or option");
         json_int(p, end, "sample", &t.sample);
+        json_int(p, end, "family", &family);
         const bool ok_path = t.path == SFOC_CORR_DIRECT_F32 || t.path == SFOC_CORR_FFT || t.path == SFOC_CORR_TC_TOEPLITZ ||
                              t.path == SFOC_CORR_TC_COLUMN || t.path == SFOC_CORR_TC_BAND;
-        const bool f32 = t.path == SFOC_CORR_DIRECT_F32 || t.path == SFOC_CORR_FFT;
-        if (!ok_path || (dtype != SFOC_DTYPE_F32 && dtype != SFOC_DTYPE_BF16) || f32 != (dtype == SFOC_DTYPE_F32) ||
+        if (!ok_path || (dtype != SFOC_DTYPE_F32 && dtype != SFOC_DTYPE_BF16) || !path_serves(t.path, dtype) ||
+            (family != 0 && family != 1) || (family == 1 && (dtype != SFOC_DTYPE_BF16 || centered_path(t.path))) ||
             m < 1 || m > kMaxTemplate || R < 0 || R > kMaxRadius)
             return fail(ctx, SFOC_ERR_INVALID_ARG, "autotune entry out of range");
         const int opt = t.path == SFOC_CORR_FFT ? t.option : 0;
@@ -1045,7 +1053,7 @@ sfoc_status sfoc_ctx_autotune_import(sfoc_ctx* ctx, const char* text) {
                                              : corr_tc_class(t.path == SFOC_CORR_TC_TOEPLITZ ? 1
                                                              : t.path == SFOC_CORR_TC_COLUMN ? 2 : 3, m, R) == 0)
             return fail(ctx, SFOC_ERR_INVALID_ARG, "autotune entry names a form that does not run for its m / R");
-        got[TuneKey{dtype, m, R}] = t;
+        got[TuneKey{dtype, m, R, family}] = t;
         p = end + 2;
     }
     for (const auto& kv : got) ctx->tune[kv.first] = kv.second;

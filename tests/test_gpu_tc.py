@@ -53,12 +53,14 @@ def gpu_bf16(ctx, b, pair, want_maps=False, path=None):
                              corr_path=b.CORR_IGEMM_TC if path is None else path, want_maps=want_maps)
 
 
-FORMS = ["auto", "toeplitz", "column", "band"]
+# "auto": IGEMM_TC, the measured fastest tensor-core form; "fft": the Fourier
+# correlation reading the bf16 cube; "any": AUTO, the fastest of all of them
+FORMS = ["auto", "toeplitz", "column", "band", "fft", "any"]
 
 
 def form_path(b, form):
     return {"auto": None, "toeplitz": b.CORR_TC_TOEPLITZ, "column": b.CORR_TC_COLUMN,
-            "band": b.CORR_TC_BAND}[form]
+            "band": b.CORR_TC_BAND, "fft": b.CORR_FFT, "any": b.CORR_AUTO}[form]
 
 
 SMALL = [
@@ -75,8 +77,9 @@ SMALL = [
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("H,W,m,R,npts,seed", SMALL)
 def test_tc_small_cases(b, ctx, orc, H, W, m, R, npts, seed, form):
-    """Every tensor-core form on the same inputs: the column form (m + 2R
-    <= 128), the Toeplitz form and the band form."""
+    """Every correlation form of BF16 cubes on the same inputs: the column
+    form (m + 2R <= 128), the Toeplitz form, the band form and the Fourier
+    correlation of the bf16 values, and the two measured choices."""
     pair = tiny_pair(seed, H, W, m, R, npts, shift=(2, -1))
     g = gpu_bf16(ctx, b, pair, want_maps=True, path=form_path(b, form))
     ctx.sync()
@@ -127,7 +130,7 @@ def test_tc_inverting_pair_512(b, ctx, orc, form):
     assert rep["bf16_vs_fp64_offsets_equal"] >= 95
 
 
-@pytest.mark.parametrize("form", ["auto", "band"])
+@pytest.mark.parametrize("form", ["auto", "band", "fft"])
 def test_tc_sar_pair_2048_full_size_sampled(b, ctx, orc, form):
     """2048^2, 1000 points, m=81, R=20 in the benchmark's launch
     configuration; a seeded sample of 64 points against the oracle (shared by
