@@ -65,6 +65,12 @@ def parse():
                     help="mixed64: bf16batch,f32batch,f32plain; single pairs: bf16 (BF16 cubes, tensor-core "
                          "correlation), f32 (F32 cubes, automatic correlation), f32direct (F32 cubes, the plain "
                          "direct correlation)")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="mixed64 under torchrun: weak = every rank its own seeded 64-pair batch (its shard of a "
+                         "64 x N-pair job); strong = one 64-pair job whose pairs are balanced over the ranks by "
+                         "cost, results gathered on rank 0")
+    ap.add_argument("--pairs", type=int, default=64, help="mixed64: pairs per batch (fewer for small profiling cases)")
+    ap.add_argument("--scale", type=float, default=1.0, help="mixed64: side and point-count scale (1 = full size)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--noise-sweep", action="store_true",
@@ -99,15 +105,17 @@ def workload(name, rank):
     return p, desc
 
 
-def batch_workload(rank, workers):
-    """The 64-pair mixed batch of this rank (its own seed: under torchrun each
+def batch_workload(rank, workers, n_pairs=64, scale=1.0):
+    """The mixed batch of this rank (its own seed: under torchrun each
     rank's batch is its shard of a 64 x N-pair job)."""
     from workloads import mixed_batch
-    pairs = mixed_batch(seed=4000 + 7919 * rank, workers=workers)
+    pairs = mixed_batch(seed=4000 + 7919 * rank, n_pairs=n_pairs, scale=scale, workers=workers)
     px = sum(q.ref.size + q.sen.size for q in pairs)
     pts = sum(len(q.points) for q in pairs)
-    desc = ("64 pairs, sides U[512,4096] (non-square), linear/gamma/inverted/speckled maps, 200-4000 block points, "
-            "m in {41,61,81,101}, R in U[10,40], z=12: %d points, %.1f Mpx" % (pts, px / 1e6))
+    desc = ("%d pairs, sides U[512,4096]%s (non-square), linear/gamma/inverted/speckled maps, 200-4000%s block "
+            "points, m in {41,61,81,101}, R in U[10,40], z=12: %d points, %.1f Mpx"
+            % (n_pairs, "" if scale == 1.0 else " x %g" % scale, "" if scale == 1.0 else " x %g" % scale, pts,
+               px / 1e6))
     return pairs, desc
 
 
@@ -782,7 +790,7 @@ def reference_batch(args, rank):
     import numpy as np
     import oracle
     oracle.build()
-    pairs, desc = batch_workload(0, workers=min(16, os.cpu_count() or 1))
+    pairs, desc = batch_workload(0, min(16, os.cpu_count() or 1), args.pairs, args.scale)
     steps_t, matched, n_sample = [], 0, 4
     for i in range(args.warmup + args.steps):
         sample = batch_oracle_sample(pairs, 1000 + i, n_pairs=n_sample, per_pair=1)
@@ -817,7 +825,16 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
     import paper_2202_13347_gb300 as pkg
     pkg.build()
     b = pkg.load()
-    pairs, desc = batch_workload(rank, workers=min(16, os.cpu_count() or 1))
+    strong = args.scaling == "strong" and world > 1
+    pairs, desc = batch_workload(0 if strong else rank, min(16, os.cpu_count() or 1), args.pairs, args.scale)
+    mine = list(range(len(pairs)))
+    if strong:  # one job, its pairs balanced over the ranks
+        from paper_2202_13347_gb300 import shard
+        job = pairs
+        costs = [shard.pair_cost(len(q.points), q.m, q.R, q.ref.size + q.sen.size) for q in job]
+        mine = shard.shard_pairs(costs, world)[rank]
+        pairs = [job[i] for i in mine]
+        desc += "; pairs of one job balanced over %d ranks by cost" % world
     px = sum(q.ref.size + q.sen.size for q in pairs)
     n_points = sum(len(q.points) for q in pairs)
     config = {"workload": desc, "pairs_per_rank": len(pairs), "points_per_rank": n_points, "pixels_per_rank": px,
@@ -882,6 +899,16 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
         e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=er["h2d_bytes_per_step"],
                    d2h_bytes_per_step=er["d2h_bytes_per_step"], ms_per_step=ms_max / er["steps"],
                    call="fastncc_register_batch_host (pinned host buffers)")
+    gathered = None
+    if strong:  # the final collective: every rank's results to rank 0, in the job's order
+        import numpy as np
+        from paper_2202_13347_gb300 import shard
+        offs = np.cumsum([0] + [len(q.points) for q in job])
+        idx = np.concatenate([np.arange(offs[i], offs[i + 1]) for i in mine]) if mine else np.zeros(0, np.int64)
+        rows = (np.concatenate([o.cpu().numpy() for o in r0["outs"]]) if mine else np.zeros((0, 6), np.int32))
+        full = shard.gather_results(dist, rank, world, int(offs[-1]), idx, rows)
+        if rank == 0:
+            gathered = {"points": int(full.shape[0]), "matched": int((full[:, 5] == 0).sum())}
     cpu, parity = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -892,10 +919,12 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
         return
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": main["steps"],
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if main_form == "bf16batch" else "f32",
+            "scaling": "strong" if strong else "weak", "vs_baseline": None,
+            "dtype": "bf16" if main_form == "bf16batch" else "f32",
             "data": "synthetic", "config": dict(config, form=main_form), "roofline": main["roofline"],
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
             "sfoc_mpix_s": main["sfoc_mpix_s"], "stage_ms_per_step": main["stage_ms_per_step"], "parity": parity,
+            "gathered": gathered,
             "forms": {f: {k: v for k, v in sm.items() if k not in ("clocks",)} for f, sm in summ.items()},
             "bf16batch_over_f32plain": (summ["bf16batch"]["value"] / summ["f32plain"]["value"]
                                         if "bf16batch" in summ and "f32plain" in summ else None),

@@ -145,6 +145,14 @@ SFOC_API sfoc_status sfoc_ctx_set_stream(sfoc_ctx* ctx, void* stream);
 /* Blocks until the context's stream is idle; reports deferred device errors
  * (SFOC_ERR_CUDA, or SFOC_ERR_TIMEOUT when a bounded device wait expired). */
 SFOC_API sfoc_status sfoc_ctx_sync(sfoc_ctx* ctx);
+/* Self-test of the failure path (not part of the paper's method): enqueues
+ * one kernel that allocates tensor memory, waits on a barrier nothing
+ * arrives on with the bounded wait the tensor-core kernels use, limited to
+ * limit_us microseconds (1..100000), and then takes their abort path (frees
+ * the tensor memory, sets the context's device error word, returns).  The
+ * next sfoc_ctx_sync returns SFOC_ERR_TIMEOUT and clears the word; the
+ * context stays usable.  SFOC_ERR_INVALID_ARG for a limit out of range. */
+SFOC_API sfoc_status sfoc_ctx_selftest_timeout(sfoc_ctx* ctx, int limit_us);
 /* Grows the workspace to hold at least `bytes` (so later calls, e.g. inside
  * a CUDA-graph capture, allocate nothing). */
 SFOC_API sfoc_status sfoc_ctx_reserve(sfoc_ctx* ctx, size_t bytes);

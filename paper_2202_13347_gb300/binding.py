@@ -73,6 +73,7 @@ _SIGS = {
     "sfoc_ctx_destroy": (C.c_int, [_P]),
     "sfoc_ctx_set_stream": (C.c_int, [_P, _P]),
     "sfoc_ctx_sync": (C.c_int, [_P]),
+    "sfoc_ctx_selftest_timeout": (C.c_int, [_P, C.c_int]),
     "sfoc_ctx_reserve": (C.c_int, [_P, C.c_size_t]),
     "sfoc_match_workspace_bytes": (C.c_size_t, [C.c_int, C.c_int]),
     "sfoc_last_error_string": (C.c_char_p, [_P]),
@@ -293,6 +294,11 @@ class Context:
 
     def sync(self):
         self._chk(lib().sfoc_ctx_sync(self.h))
+
+    def selftest_timeout(self, limit_us=1000):
+        """Enqueues the failure-path self-test (sfoc_ctx_selftest_timeout);
+        the next sync() raises SfocError with code -5 (SFOC_ERR_TIMEOUT)."""
+        self._chk(lib().sfoc_ctx_selftest_timeout(self.h, int(limit_us)))
 
     def reserve(self, nbytes):
         self._chk(lib().sfoc_ctx_reserve(self.h, int(nbytes)))

@@ -274,6 +274,10 @@ cudaError_t launch_results_to_points(const int32_t* pts, const fastncc_result* r
 // HBM copy GB/s; synchronous
 cudaError_t measure_peaks(cudaStream_t st, int sms, double* fp32, double* fp32x2, double* fp64, double* hbm);
 
+// failure-path self-test (k_selftest.cu): one bounded wait that expires after
+// limit_us microseconds and sets *err
+cudaError_t launch_wait_selftest(int* err, int limit_us, cudaStream_t st);
+
 // template half-width: rows before the centre
 __host__ __device__ inline int template_half(int m) { return (m % 2) ? (m - 1) / 2 : m / 2; }
 

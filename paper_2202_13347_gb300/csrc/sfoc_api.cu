@@ -622,6 +622,19 @@ sfoc_status sfoc_measure_peaks(sfoc_ctx* ctx, sfoc_peaks* out) {
     return SFOC_OK;
 }
 
+sfoc_status sfoc_ctx_selftest_timeout(sfoc_ctx* ctx, int limit_us) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (limit_us < 1 || limit_us > 100000) return fail(ctx, SFOC_ERR_INVALID_ARG, "limit_us must be in [1, 100000]");
+    DeviceGuard g(ctx->device);
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_OTHER, 1);
+        e = launch_wait_selftest(ctx->d_err, limit_us, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "self-test launch");
+    return SFOC_OK;
+}
+
 sfoc_status sfoc_params_default(sfoc_params* p) {
     if (!p) return SFOC_ERR_INVALID_ARG;
     memset(p, 0, sizeof(*p));

@@ -44,18 +44,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; on expiry (or once another role aborted) returns false.
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, int* s_abort) {
+// Bounded wait of at most limit_ns; on expiry it sets *s_abort and returns
+// false, as it does once another role has aborted.
+__device__ inline bool mbar_wait_limit(uint32_t bar, uint32_t parity, int* s_abort, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*reinterpret_cast<volatile int*>(s_abort)) return false;
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             atomicExch(s_abort, 1);
             return false;
         }
     }
+}
+
+// The kernels' bounded wait (about 2 s).
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, int* s_abort) {
+    return mbar_wait_limit(bar, parity, s_abort, kWaitNs);
 }
 
 // Bounded wait that ignores the abort flag (used to let copies land).

@@ -259,7 +259,7 @@ def test_batched_line(monkeypatch, capsys):
     import oracle
     oracle.build()
     small = mixed_batch(seed=4100, n_pairs=3, scale=0.12)
-    monkeypatch.setattr(bench, "batch_workload", lambda rank, workers: (small, "3 small pairs"))
+    monkeypatch.setattr(bench, "batch_workload", lambda rank, workers, n_pairs=64, scale=1.0: (small, "3 small pairs"))
     _patch_cuda(monkeypatch)
     monkeypatch.setitem(sys.modules, "paper_2202_13347_gb300", _fake_batch_library())
     monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "3", "--warmup", "3"])
@@ -280,7 +280,7 @@ def test_batched_line(monkeypatch, capsys):
 def test_batched_reference_arm(monkeypatch, capsys):
     from workloads import mixed_batch
     small = mixed_batch(seed=4100, n_pairs=3, scale=0.12)
-    monkeypatch.setattr(bench, "batch_workload", lambda rank, workers: (small, "3 small pairs"))
+    monkeypatch.setattr(bench, "batch_workload", lambda rank, workers, n_pairs=64, scale=1.0: (small, "3 small pairs"))
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"])
     bench.main()
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])

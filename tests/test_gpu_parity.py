@@ -357,3 +357,25 @@ def test_cube_view_layouts(b, ctx):
             chans = torch.cat([raw[0, :, :, :6], raw[1, :, :, :6]], dim=-1).permute(2, 0, 1).float()
             assert torch.equal(chans, exp)
             assert torch.all(raw[:, :, :, 6:] == 0)
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_recovers(b, ctx):
+    """The failure path of the tensor-core kernels on a GPU: a bounded wait
+    (1 ms) on a barrier nothing arrives on expires, the kernel frees its
+    tensor memory, sets the context's error word and returns; sync reports
+    SFOC_ERR_TIMEOUT once, the word is cleared, and a BF16 tensor-core match
+    on the same context then runs normally."""
+    ctx.sync()
+    ctx.selftest_timeout(1000)
+    with pytest.raises(b.SfocError) as e:
+        ctx.sync()
+    assert e.value.code == -5
+    ctx.sync()  # the error word was cleared
+    pair = tiny_pair(45, 90, 96, 15, 4, 6, shift=(1, 1))
+    p = b.params(dtype=b.DTYPE_BF16)
+    rc, sc = ctx.sfoc_build(dev(pair.ref), p=p), ctx.sfoc_build(dev(pair.sen), p=p)
+    res = ctx.fastncc_match(rc, sc, dev(pair.points), pair.m, pair.R, corr_path=b.CORR_TC_BAND)
+    ctx.sync()
+    assert int((res["status"] == 0).sum()) + int((res["status"] == 3).sum()) > 0
+    with pytest.raises(b.SfocError):
+        ctx.selftest_timeout(0)  # a limit out of range is refused before any launch
