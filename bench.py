@@ -69,6 +69,8 @@ def parse():
                     help="mixed64 under torchrun: weak = every rank its own seeded 64-pair batch (its shard of a "
                          "64 x N-pair job); strong = one 64-pair job whose pairs are balanced over the ranks by "
                          "cost, results gathered on rank 0")
+    ap.add_argument("--corr", default="auto", choices=["auto", "igemm_tc", "band", "column", "fft", "direct"],
+                    help="mixed64: correlation path of the batched forms (auto: the autotuner's measured choice)")
     ap.add_argument("--pairs", type=int, default=64, help="mixed64: pairs per batch (fewer for small profiling cases)")
     ap.add_argument("--scale", type=float, default=1.0, help="mixed64: side and point-count scale (1 = full size)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -593,9 +595,14 @@ def class_flops(path, cls, m, R, z=12):
     return 2.0 * m * m * z * (2 * R + 1) ** 2
 
 
-def run_batch_form(b, torch, ctx, pairs, form, steps, warmup):
+def corr_option(b, name):
+    return {"auto": b.CORR_AUTO, "igemm_tc": b.CORR_IGEMM_TC, "band": b.CORR_TC_BAND, "column": b.CORR_TC_COLUMN,
+            "fft": b.CORR_FFT, "direct": b.CORR_DIRECT_F32}[name]
+
+
+def run_batch_form(b, torch, ctx, pairs, form, steps, warmup, corr_name="auto"):
     p = b.params(dtype=b.DTYPE_BF16 if form == "bf16batch" else b.DTYPE_F32)
-    corr = b.CORR_DIRECT_F32 if form == "f32plain" else b.CORR_AUTO
+    corr = b.CORR_DIRECT_F32 if form == "f32plain" else corr_option(b, corr_name)
     n = len(pairs)
     d_refs = [torch.from_numpy(q.ref).cuda() for q in pairs]
     d_sens = [torch.from_numpy(q.sen).cuda() for q in pairs]
@@ -651,9 +658,9 @@ def run_batch_form(b, torch, ctx, pairs, form, steps, warmup):
     scopes = ctx.stage_scopes("correlation")
     ctx.enable_timing(False)
     tune = {}
-    if corr == b.CORR_AUTO:
+    if corr in (b.CORR_AUTO, b.CORR_IGEMM_TC):
         for q in pairs:
-            e = ctx.autotune_entry(p.cube_dtype, q.m, q.R)
+            e = ctx.autotune_entry(p.cube_dtype, q.m, q.R, 0 if corr == b.CORR_AUTO else 1)
             if e:
                 tune["%d,%d" % (q.m, q.R)] = {"path": e["path"], "option": e["option"],
                                               "candidates_ms": {"%d/%d" % (c[0], c[1]): round(c[2], 4)
@@ -859,7 +866,8 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
             torch.cuda.synchronize()
             steps = args.steps if form != "f32plain" else max(3, min(args.steps, 5))
             with ClockSampler(gpu_index) as cs:
-                r = run_batch_form(b, torch, ctx, pairs, form, steps, args.warmup if form != "f32plain" else 1)
+                r = run_batch_form(b, torch, ctx, pairs, form, steps, args.warmup if form != "f32plain" else 1,
+                                   args.corr)
                 cs.mark(*r["t_timed"])
             r["steps"] = steps
             r["ms_max"], r["matched_all"] = reduce_over_ranks(dist, torch, r["ms"], r["matched"], "cuda")

@@ -45,6 +45,7 @@ struct CorrClass {
     int n_items = 0;
     int max_m = 0, max_R = 0, max_lw = 0;
     int queue = -1;                 // its counter (Fourier form), or -1
+    int msplit = 0;                 // tensor-core forms: the template size of its pairs
 };
 
 }  // namespace
@@ -506,17 +507,22 @@ bool plan_classes(sfoc_ctx* ctx, BatchPlan* p, int path, int dtype, Layout& lay)
         j.centered = centered_path(pp) ? 1 : 0;
         pick[i] = {pp, class_of(pp, opt, j.m, j.R)};
     }
+    // a tensor-core launch lays its shared memory out for its largest item,
+    // so its classes are split by template size too: a launch of smaller
+    // templates keeps smaller window tiles and a deeper template-slab ring
     p->classes.clear();
     for (size_t i = 0; i < p->jobs.size(); ++i) {
         if (p->jobs[i].n == 0) continue;
+        const int msplit = tc_form(pick[i].path) ? p->jobs[i].m : 0;
         CorrClass* c = nullptr;
         for (CorrClass& cc : p->classes)
-            if (cc.path == pick[i].path && cc.cls == pick[i].cls) c = &cc;
+            if (cc.path == pick[i].path && cc.cls == pick[i].cls && cc.msplit == msplit) c = &cc;
         if (!c) {
             p->classes.push_back(CorrClass());
             c = &p->classes.back();
             c->path = pick[i].path;
             c->cls = pick[i].cls;
+            c->msplit = msplit;
         }
         c->pairs.push_back((int)i);
     }
@@ -567,10 +573,9 @@ sfoc_status upload(sfoc_ctx* ctx, BatchPlan* p, const std::vector<char>& host, s
 
 // Makes a plan for a match over `in` (and, kind 2, the build of its images
 // first): tables, eager first run with the autotuner, graph.
-sfoc_status make_and_run(sfoc_ctx* ctx, int kind, std::vector<uint64_t>&& key, const BuildIn* bin,
-                         const sfoc_params* prm, sfoc_cube** build_cubes, const MatchIn* min, int path,
-                         BatchPlan** out) {
-    // workspace: [stats][maps][scratch: SFOC waves / integral scratch]
+// Workspace of a plan: [stats][maps][scratch: SFOC waves / integral scratch].
+// *scratch_out (may be null) receives the scratch part.
+size_t plan_ws_bytes(const BuildIn* bin, const sfoc_params* prm, const MatchIn* min, size_t* scratch_out) {
     size_t ws_match = 0, maps_off = 0;
     int total_items = 0;
     if (min) ws_match = match_ws_bytes(*min, &maps_off, &total_items);
@@ -593,9 +598,21 @@ sfoc_status make_and_run(sfoc_ctx* ctx, int kind, std::vector<uint64_t>&& key, c
         }
         int_need = integral_batch_scratch_bytes(rc.data(), (int)rc.size());
     }
-    size_t f_bytes = std::min(f_need, std::max(f_max, kFBudget));
+    const size_t f_bytes = std::min(f_need, std::max(f_max, kFBudget));
     const size_t scratch = std::max(f_bytes, int_need);
-    const size_t ws_total = align256(ws_match) + scratch;
+    if (scratch_out) *scratch_out = scratch;
+    return align256(ws_match) + scratch;
+}
+
+sfoc_status make_and_run(sfoc_ctx* ctx, int kind, std::vector<uint64_t>&& key, const BuildIn* bin,
+                         const sfoc_params* prm, sfoc_cube** build_cubes, const MatchIn* min, int path,
+                         BatchPlan** out) {
+    // workspace: [stats][maps][scratch: SFOC waves / integral scratch]
+    size_t ws_match = 0, maps_off = 0;
+    int total_items = 0;
+    if (min) ws_match = match_ws_bytes(*min, &maps_off, &total_items);
+    size_t scratch = 0;
+    const size_t ws_total = plan_ws_bytes(bin, prm, min, &scratch);
     sfoc_status s = ensure_ws(ctx, ws_total);
     if (s != SFOC_OK) return s;
     char* ws = static_cast<char*>(ctx->ws);
@@ -888,14 +905,18 @@ sfoc_status fastncc_register_batch(sfoc_ctx* ctx, int n_pairs, const float* cons
 sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs, const int* Hr,
                                         const int* Wr, const float* const* h_sens, const int* Hs, const int* Ws,
                                         const int32_t* const* h_points, const int* n_points, const int* template_size,
-                                        const int* search_radius, const sfoc_params* p, const fastncc_opts* opts,
+                                        const int* search_radius, const sfoc_params* pin, const fastncc_opts* opts,
                                         fastncc_result* const* h_outs) {
     if (!ctx) return SFOC_ERR_INVALID_ARG;
     if (n_pairs < 0 || (n_pairs > 0 && (!h_refs || !Hr || !Wr || !h_sens || !Hs || !Ws || !h_points || !n_points ||
                                         !template_size || !search_radius || !h_outs)))
         return fail(ctx, SFOC_ERR_INVALID_ARG, "bad batch arguments");
     if (n_pairs == 0) return SFOC_OK;
+    sfoc_params prm;
+    sfoc_status s = resolve_params(ctx, pin, &prm);
+    if (s != SFOC_OK) return s;
     size_t need = 0;
+    double px_all = 0.0;
     for (int i = 0; i < n_pairs; ++i) {
         if (!h_refs[i] || !h_sens[i] || n_points[i] < 0 || (n_points[i] > 0 && (!h_points[i] || !h_outs[i])))
             return fail(ctx, SFOC_ERR_INVALID_ARG, "null host buffer in the batch");
@@ -903,8 +924,69 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
         need += align256(sizeof(float) * (size_t)Hr[i] * Wr[i]) + align256(sizeof(float) * (size_t)Hs[i] * Ws[i]) +
                 align256(sizeof(int32_t) * 2 * (size_t)n_points[i]) +
                 align256(sizeof(fastncc_result) * (size_t)n_points[i]);
+        px_all += (double)Hr[i] * Wr[i] + (double)Hs[i] * Ws[i];
+    }
+    // chunks of consecutive pairs with about equal pixel counts: the images of
+    // chunk k + 1 are copied on a second stream while chunk k is processed
+    constexpr int kMaxChunks = 4;
+    const int K = n_pairs < kMaxChunks ? n_pairs : kMaxChunks;
+    int lo[kMaxChunks + 1];
+    {
+        // chunk k starts after the first pair at which the running pixel count
+        // reaches k / K of the total, kept strictly increasing and leaving at
+        // least one pair for every later chunk
+        lo[0] = 0;
+        double acc = 0.0;
+        int i = 0;
+        for (int k = 1; k < K; ++k) {
+            const double target = px_all * k / K;
+            while (i < n_pairs && acc < target) {
+                acc += (double)Hr[i] * Wr[i] + (double)Hs[i] * Ws[i];
+                ++i;
+            }
+            int b = i;
+            if (b < lo[k - 1] + 1) b = lo[k - 1] + 1;
+            if (b > n_pairs - (K - k)) b = n_pairs - (K - k);
+            lo[k] = b;
+        }
+        lo[K] = n_pairs;
     }
     DeviceGuard g(ctx->device);
+    // the workspace of the largest chunk first, so no chunk's plan is dropped
+    // by another one's growth
+    {
+        const int z = prm.first_order_only ? prm.n_orient : 2 * prm.n_orient;
+        size_t ws_max = 0;
+        for (int k = 0; k < K; ++k) {
+            const int n = lo[k + 1] - lo[k];
+            std::vector<const float*> imgs(2 * (size_t)n, nullptr);
+            std::vector<int> H(2 * (size_t)n), W(2 * (size_t)n);
+            std::vector<sfoc_cube> shape(2 * (size_t)n);
+            std::vector<sfoc_cube*> rp(n), sp(n);
+            for (int i = 0; i < n; ++i) {
+                const int j = lo[k] + i;
+                H[2 * i] = Hr[j];
+                W[2 * i] = Wr[j];
+                H[2 * i + 1] = Hs[j];
+                W[2 * i + 1] = Ws[j];
+                for (int q = 0; q < 2; ++q) {
+                    Cube& c = shape[2 * i + q].c;
+                    c.H = H[2 * i + q];
+                    c.W = W[2 * i + q];
+                    c.z = z;
+                    c.dtype = prm.cube_dtype;
+                }
+                rp[i] = &shape[2 * i];
+                sp[i] = &shape[2 * i + 1];
+            }
+            BuildIn bin{2 * n, imgs.data(), H.data(), W.data(), nullptr};
+            MatchIn mi{n, rp.data(), sp.data(), h_points + lo[k], n_points + lo[k], template_size + lo[k],
+                       search_radius + lo[k], h_outs + lo[k]};
+            ws_max = std::max(ws_max, plan_ws_bytes(&bin, &prm, &mi, nullptr));
+        }
+        s = ensure_ws(ctx, ws_max);
+        if (s != SFOC_OK) return s;
+    }
     if (need > ctx->hstage_bytes) {
         // the staging buffer moves: plans keyed on the old one are dropped
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -918,41 +1000,59 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch staging)");
         ctx->hstage_bytes = need;
     }
+    if (ctx->max_plans < (size_t)K + 2) ctx->max_plans = (size_t)K + 2;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->ev_start) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+    for (int k = 0; k < kMaxChunks && e == cudaSuccess; ++k)
+        if (!ctx->ev_chunk[k]) e = cudaEventCreateWithFlags(&ctx->ev_chunk[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
     std::vector<const float*> dr(n_pairs), ds(n_pairs);
     std::vector<const int32_t*> dp(n_pairs);
     std::vector<fastncc_result*> dout(n_pairs);
-    char* b = static_cast<char*>(ctx->hstage);
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < n_pairs && e == cudaSuccess; ++i) {
-        const size_t br = sizeof(float) * (size_t)Hr[i] * Wr[i], bs = sizeof(float) * (size_t)Hs[i] * Ws[i];
-        const size_t bp = sizeof(int32_t) * 2 * (size_t)n_points[i];
-        dr[i] = reinterpret_cast<const float*>(b);
-        e = cudaMemcpyAsync(b, h_refs[i], br, cudaMemcpyHostToDevice, ctx->stream);
-        b += align256(br);
-        ds[i] = reinterpret_cast<const float*>(b);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(b, h_sens[i], bs, cudaMemcpyHostToDevice, ctx->stream);
-        b += align256(bs);
-        dp[i] = reinterpret_cast<const int32_t*>(b);
-        if (e == cudaSuccess && bp) e = cudaMemcpyAsync(b, h_points[i], bp, cudaMemcpyHostToDevice, ctx->stream);
-        b += align256(bp);
-        dout[i] = reinterpret_cast<fastncc_result*>(b);
-        b += align256(sizeof(fastncc_result) * (size_t)n_points[i]);
-    }
     // synchronous on every path: copies from the caller's buffers are waited for
     auto drained = [&](sfoc_status st) {
+        cudaStreamSynchronize(ctx->copy_stream);
         cudaStreamSynchronize(ctx->stream);
         (void)cudaGetLastError();
         return st;
     };
+    // every copy after the work already queued on the context stream
+    e = cudaEventRecord(ctx->ev_start, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_start, 0);
+    char* b = static_cast<char*>(ctx->hstage);
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        for (int i = lo[k]; i < lo[k + 1] && e == cudaSuccess; ++i) {
+            const size_t br = sizeof(float) * (size_t)Hr[i] * Wr[i], bs = sizeof(float) * (size_t)Hs[i] * Ws[i];
+            const size_t bp = sizeof(int32_t) * 2 * (size_t)n_points[i];
+            dr[i] = reinterpret_cast<const float*>(b);
+            e = cudaMemcpyAsync(b, h_refs[i], br, cudaMemcpyHostToDevice, ctx->copy_stream);
+            b += align256(br);
+            ds[i] = reinterpret_cast<const float*>(b);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(b, h_sens[i], bs, cudaMemcpyHostToDevice, ctx->copy_stream);
+            b += align256(bs);
+            dp[i] = reinterpret_cast<const int32_t*>(b);
+            if (e == cudaSuccess && bp) e = cudaMemcpyAsync(b, h_points[i], bp, cudaMemcpyHostToDevice, ctx->copy_stream);
+            b += align256(bp);
+            dout[i] = reinterpret_cast<fastncc_result*>(b);
+            b += align256(sizeof(fastncc_result) * (size_t)n_points[i]);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_chunk[k], ctx->copy_stream);
+    }
     if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "host to device copy"));
-    sfoc_status s = fastncc_register_batch(ctx, n_pairs, dr.data(), Hr, Wr, ds.data(), Hs, Ws, dp.data(), n_points,
-                                           template_size, search_radius, p, opts, dout.data());
-    if (s != SFOC_OK) return drained(s);
-    for (int i = 0; i < n_pairs && e == cudaSuccess; ++i)
-        if (n_points[i] > 0)
-            e = cudaMemcpyAsync(h_outs[i], dout[i], sizeof(fastncc_result) * (size_t)n_points[i],
-                                cudaMemcpyDeviceToHost, ctx->stream);
-    if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "device to host copy"));
+    for (int k = 0; k < K; ++k) {
+        const int j = lo[k], n = lo[k + 1] - lo[k];
+        e = cudaStreamWaitEvent(ctx->stream, ctx->ev_chunk[k], 0);
+        if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "cudaStreamWaitEvent"));
+        s = fastncc_register_batch(ctx, n, dr.data() + j, Hr + j, Wr + j, ds.data() + j, Hs + j, Ws + j, dp.data() + j,
+                                   n_points + j, template_size + j, search_radius + j, &prm, opts, dout.data() + j);
+        if (s != SFOC_OK) return drained(s);
+        for (int i = j; i < j + n && e == cudaSuccess; ++i)
+            if (n_points[i] > 0)
+                e = cudaMemcpyAsync(h_outs[i], dout[i], sizeof(fastncc_result) * (size_t)n_points[i],
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "device to host copy"));
+    }
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
     return SFOC_OK;

@@ -93,7 +93,7 @@ __host__ __device__ inline BandGeom band_geom(int m, int R) {
     b.slab_bytes = 2 * kBandQ * b.trows * 16;
     b.tile_off = 0;
     b.slab_off = 2 * b.tile_bytes;
-    const int part_bytes = 8 * b.GE * b.P1 * 8 * 4;
+    const int part_bytes = 4 * b.GE * b.P1 * 8 * 4;  // per quarter q: GE x P1 x 8 offsets
     // an MMA on the last column of a slab reads N - trows rows past it; the
     // partial-sum buffer follows the slabs, plus a guard for the last slot
     const int guard = (b.N - b.trows) * 16 + 128;
@@ -280,7 +280,6 @@ __global__ void __launch_bounds__(kBandThreads, 1)
         } else if (warp == 1) {
             // ---------------- MMA issuer ----------------
             if (lane == 0) {
-                const uint32_t idesc = idesc_bf16(kM, N);
                 const uint64_t da0 = smem_desc(sbase, 16u * g.Xw * 16u, (uint32_t)g.Xw * 16u);
                 const uint64_t db0 = smem_desc(sbase + slab_off, (uint32_t)(kBandQ * g.trows * 16), 128);
                 const uint32_t tile_step = (uint32_t)BL.tile_stride >> 4, slab_step = (uint32_t)BL.slab_stride >> 4;
@@ -302,20 +301,30 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                         // template rows i < 0, which the drain drops)
                         const int r0 = ty0 + 16 * yb - 2 * R;
                         const uint32_t clamp = r0 < 0 ? (uint32_t)(-r0) : 0u;
+                        // the band meets template rows [nlo, nhi) of its N; its MMAs cover only
+                        // the 16-row-aligned span around them (accumulator columns outside it
+                        // keep an earlier group's values, which the drain zeroes)
+                        const int ilo = 16 * yb - 2 * R;
+                        const int nlo = ilo < 0 ? -ilo : 0;
+                        const int nhi = m - ilo < N ? m - ilo : N;
+                        const int n0 = nlo & ~15;
+                        const int n1 = ((nhi + 15) & ~15) < N ? ((nhi + 15) & ~15) : N;
+                        const uint32_t idesc_b = idesc_bf16(kM, n1 - n0);
+                        const uint32_t dacc_b = dacc + (uint32_t)n0;
                         for (int s = 0; s < g.nS; ++s) {
                             ok = mbar_wait(bar(BD_TFULL + ts), tph, &s_abort);
                             if (!ok) break;
                             tc_fence_after();
-                            const uint64_t dB = db0 + (uint64_t)(ts * slab_step) - (uint64_t)clamp;
+                            const uint64_t dB = db0 + (uint64_t)(ts * slab_step) - (uint64_t)clamp + (uint64_t)n0;
                             const int u0 = s * kBandQ;
                             const int nq = m - u0 < kBandQ ? m - u0 : kBandQ;
                             const uint64_t dAu = dA + (uint64_t)u0;
                             switch (Gg) {  // outside the run of MMAs
-                                case 1: band_stage_any<N, 1>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
-                                case 2: band_stage_any<N, 2>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
-                                case 3: band_stage_any<N, GEM < 3 ? GEM : 3>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
-                                case 4: band_stage_any<N, GEM < 4 ? GEM : 4>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
-                                default: band_stage_any<N, GEM < 5 ? GEM : 5>(s == 0, dacc, dAu, dB, tcol, idesc, nq); break;
+                                case 1: band_stage_any<N, 1>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
+                                case 2: band_stage_any<N, 2>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
+                                case 3: band_stage_any<N, GEM < 3 ? GEM : 3>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
+                                case 4: band_stage_any<N, GEM < 4 ? GEM : 4>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
+                                default: band_stage_any<N, GEM < 5 ? GEM : 5>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
                             }
                             mma_issued += (uint32_t)(nq * Gg);
                             mma_commit(bar(BD_TEMPTY + ts));
@@ -332,7 +341,6 @@ __global__ void __launch_bounds__(kBandThreads, 1)
             const int t = tid - 128;  // 0 .. kBandDrain-1
             const int team = t >> 7;
             const int q = warp & 3;
-            const int w8 = warp - 4;
             const int gq = lane >> 3, r = lane & 7;
             const bool b0 = (gq & 1) != 0, b1 = (gq & 2) != 0;
             const int joff = (b0 ? N / 2 : 0) + (b1 ? N4 : 0);
@@ -401,18 +409,28 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                         }
                     }
                 }
-                // sums of this offset-group set: column j = joff + p is dy = 2R + 4q - j
+                // sums of this offset-group set: column j = joff + p is dy = 2R + 4q - j.
+                // The two teams hold the same entries (each over its own bands): team 0
+                // writes them per quarter q, team 1 adds its own in place (a fixed
+                // order), then the four quarters are summed
+                for (int tm = 0; tm < 2; ++tm) {
+                    if (team == tm) {
 #pragma unroll
-                for (int e = 0; e < GEM; ++e) {
-                    if (e < Gg) {
+                        for (int e = 0; e < GEM; ++e) {
+                            if (e < Gg) {
 #pragma unroll
-                        for (int p = 0; p < N4; ++p) {
-                            const int dy = 2 * R + 4 * q - joff - p;
-                            if ((unsigned)dy < (unsigned)g.P1) part[((w8 * g.GE + e) * g.P1 + dy) * 8 + r] = sums[e][p];
+                                for (int p = 0; p < N4; ++p) {
+                                    const int dy = 2 * R + 4 * q - joff - p;
+                                    if ((unsigned)dy < (unsigned)g.P1) {
+                                        float* slot = &part[((q * g.GE + e) * g.P1 + dy) * 8 + r];
+                                        *slot = tm == 0 ? sums[e][p] : *slot + sums[e][p];
+                                    }
+                                }
+                            }
                         }
                     }
+                    asm volatile("bar.sync 1, %0;" ::"r"(kBandDrain) : "memory");
                 }
-                asm volatile("bar.sync 1, %0;" ::"r"(kBandDrain) : "memory");
                 for (int idx = t; idx < Gg * g.P1 * 8; idx += kBandDrain) {
                     const int e = idx / (g.P1 * 8);
                     const int rem = idx - e * g.P1 * 8;
@@ -421,7 +439,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                     if (dx < g.P1) {
                         float s = 0.f;
 #pragma unroll
-                        for (int w = 0; w < 8; ++w) s += part[((w * g.GE + e) * g.P1 + dy) * 8 + rr];
+                        for (int w = 0; w < 4; ++w) s += part[((w * g.GE + e) * g.P1 + dy) * 8 + rr];
                         out[dy * g.P1 + dx] = s;
                     }
                 }
@@ -490,7 +508,7 @@ bool band_launch(int NQ, const int* ms, const int* Rs, int cnt, BandLaunch* out)
         if (g.NQ != NQ) return false;
         tile = g.tile_bytes > tile ? g.tile_bytes : tile;
         slab = g.slab_bytes > slab ? g.slab_bytes : slab;
-        const int pb = 8 * g.GE * g.P1 * 8 * 4;
+        const int pb = 4 * g.GE * g.P1 * 8 * 4;
         part = pb > part ? pb : part;
         const int gd = (g.N - g.trows) * 16 + 128;
         guard = gd > guard ? gd : guard;

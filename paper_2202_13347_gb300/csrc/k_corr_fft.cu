@@ -191,23 +191,28 @@ __device__ __forceinline__ float2 cross_spectrum(float2 a, float2 b) {
     return make_float2(0.25f * fmaf(s.x, d.y, -s.y * d.x), 0.25f * fmaf(s.x, d.x, s.y * d.y));
 }
 
-// One value of channel c at (row y, column x) of a cube: the F32 planes, or
-// the BF16 row-major chunks (chunk c / 6, lane c % 6 of a pixel's 8),
-// widened to FP32.
+// Rows of one item's window (or template) in a cube: `p` points at channel
+// 0, row 0, column 0 of the region; row(c, y) is channel c, region row y.
+// F32 cubes: planar, `pitch` elements per row, `plane` per channel.  BF16
+// cubes: the row-major chunks (chunk c / 6, lane c % 6 of a pixel's 8),
+// widened to FP32 as read; `pitch` = 8 W elements per row, `plane` = 8 H W
+// per chunk.
 struct CubeF32 {
     const float* p;
-    size_t pitch, plane;
-    __device__ __forceinline__ const float* row(int c, int y, int x0) const {
-        return p + (size_t)c * plane + (size_t)y * pitch + x0;
+    size_t plane;
+    unsigned pitch;
+    __device__ __forceinline__ const float* row(int c, int y) const {
+        return p + (size_t)c * plane + (size_t)y * pitch;
     }
     __device__ __forceinline__ static float at(const float* r, int x) { return r[x]; }
 };
 struct CubeBF16 {
     const __nv_bfloat16* p;
-    int H, W;
-    __device__ __forceinline__ const __nv_bfloat16* row(int c, int y, int x0) const {
+    size_t plane;
+    unsigned pitch;
+    __device__ __forceinline__ const __nv_bfloat16* row(int c, int y) const {
         const int g = c / 6;
-        return p + (((size_t)g * H + y) * W + x0) * 8 + (c - 6 * g);
+        return p + (size_t)g * plane + (size_t)y * pitch + (c - 6 * g);
     }
     __device__ __forceinline__ static float at(const __nv_bfloat16* r, int x) { return __bfloat162float(r[8 * x]); }
 };
@@ -224,6 +229,11 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
     constexpr int E = Sh::E, ZP = Sh::ZP, kFftGroups = Sh::G, kFftThreads = Sh::T;
     extern __shared__ __align__(16) float2 fsm[];
     __shared__ int s_item;
+    typedef typename std::conditional<BF, CubeBF16, CubeF32>::type SrcT;
+    __shared__ SrcT s_src[2];  // the item's window and template rows
+    __shared__ float* s_out;
+    __shared__ int s_par[4];   // the item's m, m + 2R, 2R + 1, channels
+    __shared__ float s_tmean;  // the item's template mean
     float2* Z = fsm;                                       // L x ZP
     float2* scr = Z + (size_t)L * ZP;                      // kFftGroups x SG
     float2* tw = scr + (size_t)kFftGroups * Sh::SG;        // 8E twiddles W_L^{t k1} at 8 k1 + t
@@ -234,6 +244,11 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
     const int lane = tid & 31, gbase = lane & ~7;
     float2* sc = scr + grp * Sh::SG;
     const float inv_area = 1.f / ((float)L * (float)L);
+    // the row a group transforms in the row passes: within a block of 8 rows
+    // per warp pair, the two groups of a half-warp take rows 4 apart, so their
+    // 64-bit accesses to Z rows (pitch ZP = L + 2: 4 banks apart per row)
+    // fall on disjoint banks
+    const int yrow = 8 * (grp >> 3) + 2 * ((grp >> 2) & 1) + ((grp >> 1) & 1) + 4 * (grp & 1);
     // partner of row t + 8m is row -(t + 8m): thread (8 - t) mod 8, index
     // (E - m) mod E for t = 0, E - 1 - m otherwise
     const int tpart = gbase + ((8 - t) & 7);
@@ -266,14 +281,6 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
         const PointStat st = J.stats[k];
         if (st.status != SFOC_PT_OK) continue;  // uniform across the CTA
         typedef typename std::conditional<BF, CubeBF16, CubeF32>::type Src;
-        Src Sc, Tc;
-        if constexpr (BF) {
-            Sc = CubeBF16{J.rrm, J.Hr, J.Wr};
-            Tc = CubeBF16{J.srm, J.Hs, J.Ws};
-        } else {
-            Sc = CubeF32{J.rf32, J.rpitch, J.rplane};
-            Tc = CubeF32{J.sf32, J.spitch, J.splane};
-        }
         const int m = J.m, R = J.R, z = J.z;
         const int P1 = 2 * R + 1, Lw = m + 2 * R;
         const int h = template_half(m);
@@ -282,21 +289,43 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
             __syncthreads();
         }
         zhi = Lw;
-        const int ty0 = J.pts[2 * k + 1] - h, tx0 = J.pts[2 * k] - h;
-        const int wy0 = ty0 - R, wx0 = tx0 - R;
-        const float tmean = st.tmean;
+        // the item's window and template rows and its output, in shared memory:
+        // read again after each barrier, they hold no registers across the
+        // column passes (whose transforms set the kernel's register peak)
+        if (tid == 0) {
+            const int ty0 = J.pts[2 * k + 1] - h, tx0 = J.pts[2 * k] - h;
+            const int wy0 = ty0 - R, wx0 = tx0 - R;
+            if constexpr (BF) {
+                s_src[0] = CubeBF16{J.rrm + ((size_t)wy0 * J.Wr + wx0) * 8, (size_t)8 * J.Hr * J.Wr, 8u * (unsigned)J.Wr};
+                s_src[1] = CubeBF16{J.srm + ((size_t)ty0 * J.Ws + tx0) * 8, (size_t)8 * J.Hs * J.Ws, 8u * (unsigned)J.Ws};
+            } else {
+                s_src[0] = CubeF32{J.rf32 + (size_t)wy0 * J.rpitch + wx0, J.rplane, (unsigned)J.rpitch};
+                s_src[1] = CubeF32{J.sf32 + (size_t)ty0 * J.spitch + tx0, J.splane, (unsigned)J.spitch};
+            }
+            s_out = J.maps + (size_t)k * P1 * P1;
+            s_par[0] = m;
+            s_par[1] = Lw;
+            s_par[2] = P1;
+            s_par[3] = z;
+            s_tmean = st.tmean;
+        }
+        __syncthreads();
+
         float2 acc[E];  // channel sum of X conj(Y) on column pr of this group's pair
 #pragma unroll
         for (int j = 0; j < E; ++j) acc[j] = make_float2(0.f, 0.f);
         for (int i = tid; i < L; i += kFftThreads) P64[i] = make_float2(0.f, 0.f);
 
-        for (int c = 0; c < z; ++c) {
+        for (int c = 0; c < s_par[3]; ++c) {
+            const Src Sc = s_src[0], Tc = s_src[1];
+            const int m = s_par[0], Lw = s_par[1];
+            const float tmean = s_tmean;
             // ---- rows: z = S + i (T - mean), zero outside the window / template
             for (int y0 = 0; y0 < Lw; y0 += kFftGroups) {
-                const int y = y0 + grp;
+                const int y = y0 + yrow;
                 const bool rs = y < Lw, rt = y < m;
-                const auto srow = Sc.row(c, wy0 + (rs ? y : 0), wx0);
-                const auto trow = Tc.row(c, ty0 + (rt ? y : 0), tx0);
+                const auto srow = Sc.row(c, rs ? y : 0);
+                const auto trow = Tc.row(c, rt ? y : 0);
                 float2 v[E];
 #pragma unroll
                 for (int j = 0; j < E; ++j) {
@@ -349,13 +378,14 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
             __syncthreads();
         }
 
+        const int P1i = s_par[2];
         // ---- inverse along the columns kx in [0, L/2]: rows y < 2R + 1 of Q in Z
         {
             const int pr = grp;
             group_fft<E, 1>(acc, t, sc, tw);
 #pragma unroll
             for (int j = 0; j < E; ++j)
-                if (t + 8 * j < P1) Z[(size_t)(t + 8 * j) * ZP + pr] = acc[j];
+                if (t + 8 * j < P1i) Z[(size_t)(t + 8 * j) * ZP + pr] = acc[j];
         }
         {
             float2 v[E];
@@ -365,15 +395,15 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
             if (grp == 0) {
 #pragma unroll
                 for (int j = 0; j < E; ++j)
-                    if (t + 8 * j < P1) Z[(size_t)(t + 8 * j) * ZP + L / 2] = v[j];
+                    if (t + 8 * j < P1i) Z[(size_t)(t + 8 * j) * ZP + L / 2] = v[j];
             }
         }
         __syncthreads();
         // ---- inverse along the rows (Hermitian extension), real part
-        float* out = J.maps + (size_t)k * P1 * P1;
-        for (int y0 = 0; y0 < P1; y0 += kFftGroups) {
-            const int y = y0 + grp;
-            const int yy = y < P1 ? y : 0;
+        float* out = s_out;
+        for (int y0 = 0; y0 < P1i; y0 += kFftGroups) {
+            const int y = y0 + yrow;
+            const int yy = y < P1i ? y : 0;
             float2 v[E];
 #pragma unroll
             for (int j = 0; j < E; ++j) {
@@ -382,11 +412,11 @@ __global__ void __launch_bounds__(FftShape<L>::T, 1)
                 v[j] = kx <= L / 2 ? q : make_float2(q.x, -q.y);
             }
             group_fft<E, 1>(v, t, sc, tw);
-            if (y < P1) {
+            if (y < P1i) {
 #pragma unroll
                 for (int j = 0; j < E; ++j) {
                     const int x = t + 8 * j;
-                    if (x < P1) out[(size_t)y * P1 + x] = v[j].x * inv_area;
+                    if (x < P1i) out[(size_t)y * P1i + x] = v[j].x * inv_area;
                 }
             }
         }

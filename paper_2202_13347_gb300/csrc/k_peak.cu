@@ -117,7 +117,7 @@ cudaError_t measure_peaks(cudaStream_t st, int sms, double* fp32, double* fp32x2
     cudaError_t e = cudaMalloc(&sink, sizeof(double) * (size_t)blocks * kPeakThreads);
     if (e != cudaSuccess) return e;
     float ms = 0.f;
-    const int it32 = 4096, it64 = 256;
+    const int it32 = 4096, it64 = 64;
     e = best_ms([&] { k_fma_f32<CH><<<blocks, kPeakThreads, 0, st>>>(sink, it32, 0.999f, 1e-4f); }, st, 5, &ms);
     if (e == cudaSuccess) *fp32 = 2.0 * threads * CH * kUnroll * it32 / (ms * 1e-3) / 1e12;
     if (e == cudaSuccess)

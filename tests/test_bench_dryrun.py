@@ -44,7 +44,7 @@ def _fake_library(fail_ransac=False):
 
     b.SfocError = SfocError
     b.DTYPE_F32, b.DTYPE_BF16 = 0, 1
-    b.CORR_AUTO, b.CORR_DIRECT_F32 = 0, 1
+    b.CORR_AUTO, b.CORR_DIRECT_F32, b.CORR_IGEMM_TC, b.CORR_TC_BAND, b.CORR_TC_COLUMN, b.CORR_FFT = 0, 1, 2, 5, 4, 6
     b.params = lambda dtype=0, **kw: types.SimpleNamespace(dtype=dtype, cube_dtype=dtype)
 
     class Context:
@@ -236,7 +236,7 @@ def _fake_batch_library():
         def stage_scopes(self, stage):
             return [0.5, 0.2] if stage == "correlation" else []
 
-        def autotune_entry(self, dtype, m, R):
+        def autotune_entry(self, dtype, m, R, family=0):
             return {"path": 5, "option": 0, "sample": 10, "candidates": [(5, 0, 0.5), (4, 0, 0.7)]}
 
         def release_plans(self):

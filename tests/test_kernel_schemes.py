@@ -76,8 +76,9 @@ def _band_form(S, T, m, R):
     g = 4q + l/8, r = l % 8.  Template rows outside [0, m) are zeroed, the
     row is shifted left by g' = l/8 in two select steps (1, then 2), then two
     butterflies over the lanes 8 and 16 apart add the four rows g' and leave
-    each lane a quarter of the columns; those sums run over the bands and the
-    drain warps' partial sums are added in a fixed order at the end."""
+    each lane a quarter of the columns; those sums run over the bands, and at
+    the end the two teams' sums per quarter and then the quarters are added in a
+    fixed order."""
     z = S.shape[0]
     Lw, P1 = m + 2 * R, 2 * R + 1
     N = (16 + 2 * R + 15) // 16 * 16
@@ -125,8 +126,10 @@ def _band_form(S, T, m, R):
                     mine = W[l, N // 4:] if keep_hi else W[l, :N // 4]
                     theirs = W[l ^ 16, N // 4:] if keep_hi else W[l ^ 16, :N // 4]
                     sums[team, q, l] += mine + theirs
-        # each (team, quarter) is one drain warp; its lanes map back to (dy, dx)
-        part = np.zeros((8, P1, 8))
+        # each (team, quarter) is one drain warp; its lanes map back to (dy, dx).
+        # Team 0 writes the quarter's entries, team 1 adds its own to them, then
+        # the four quarters are summed in order
+        part = np.zeros((4, P1, 8))
         for team in range(2):
             for q in range(4):
                 for l in range(32):
@@ -135,10 +138,10 @@ def _band_form(S, T, m, R):
                     for p in range(N // 4):
                         dy = 2 * R + 4 * q - joff - p
                         if 0 <= dy < P1:
-                            part[4 * team + q, dy, r] = sums[team, q, l, p]
+                            part[q, dy, r] = sums[team, q, l, p] if team == 0 else part[q, dy, r] + sums[team, q, l, p]
         for r in range(8):
             if 8 * e + r < P1:
-                out[:, 8 * e + r] = sum(part[w, :, r] for w in range(8))   # fixed order over the warps
+                out[:, 8 * e + r] = sum(part[w, :, r] for w in range(4))   # fixed order over the quarters
     return out
 
 
