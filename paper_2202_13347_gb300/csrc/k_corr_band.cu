@@ -48,14 +48,19 @@ using namespace tcx;
 // before the shift; window rows past m + 2R only reach dy > 2R.  After the
 // last band the eight drain warps' sums meet in shared memory and are added
 // in a fixed order, so the result does not depend on timing.
-// Teams: warps 4-7 drain the even groups (TMEM half 0), warps 8-11 the odd
-// ones (half 1).  Each accumulator spans m MMAs, like the column form's.
+// Roles: warp 0 copies, warps 1 and 2 issue the MMAs (accumulators e of a
+// group alternate between them: an issuing thread stalls for a few hundred
+// clocks at every stage's barrier, and with the short N <= 96 MMAs the
+// tensor pipe's queue runs dry meanwhile unless the other thread has MMAs
+// queued), warps 4-7 drain the even groups (TMEM half 0), warps 8-11 the
+// odd ones (half 1).  Each accumulator spans m MMAs, like the column form's.
 // ---------------------------------------------------------------------------
 constexpr int kBandQ = 8;  // template columns per stage
 constexpr int kBandMaxTS = 4;
 constexpr int kBandThreads = 384;
 constexpr int kBandDrain = 256;
 constexpr int kBandMaxNQ = 6;  // N <= 96, i.e. R <= 40
+constexpr int kBandIssuers = 2;  // MMA-issuing warps (1 .. kBandIssuers)
 constexpr int kBandSmemFloor = 120 * 1024;  // dynamic shared memory of a launch: at least this
 
 __host__ __device__ constexpr int band_ge_max(int nq) { return nq <= 3 ? 5 : 16 / nq; }
@@ -121,7 +126,8 @@ enum {
 };
 
 // One stage of the band form: template columns u0 + q (q < nq) of the slab
-// at dB against the window tile at dAu = tile + u0, for GG accumulators,
+// at dB against the window tile at dAu = tile + u0, for GG accumulators
+// kBandIssuers apart (one issuer's share of the group),
 // as straight-line code (an MMA that is predicated off still costs about
 // as much issue time as one that runs).  FIRST: the stage of u0 = 0, whose
 // first MMA per accumulator overwrites it.
@@ -133,7 +139,8 @@ __device__ __forceinline__ void band_stage(uint32_t dacc, uint64_t dAu, uint64_t
         for (int q = 0; q < kBandQ; ++q)
 #pragma unroll
             for (int e = 0; e < GG; ++e)
-                mma_bf16(dacc + (uint32_t)(e * N), dAu + (uint64_t)(q + 8 * e), dB + (uint64_t)(q * tcol), idesc,
+                mma_bf16(dacc + (uint32_t)(e * kBandIssuers * N), dAu + (uint64_t)(q + 8 * kBandIssuers * e),
+                         dB + (uint64_t)(q * tcol), idesc,
                          (FIRST && q == 0) ? 0u : 1u);
     } else {
 #pragma unroll
@@ -141,7 +148,8 @@ __device__ __forceinline__ void band_stage(uint32_t dacc, uint64_t dAu, uint64_t
             if (q < nq) {
 #pragma unroll
                 for (int e = 0; e < GG; ++e)
-                    mma_bf16(dacc + (uint32_t)(e * N), dAu + (uint64_t)(q + 8 * e), dB + (uint64_t)(q * tcol), idesc,
+                    mma_bf16(dacc + (uint32_t)(e * kBandIssuers * N), dAu + (uint64_t)(q + 8 * kBandIssuers * e),
+                         dB + (uint64_t)(q * tcol), idesc,
                              (FIRST && q == 0) ? 0u : 1u);
             }
     }
@@ -192,6 +200,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
     constexpr int N = NQ * 16;
     constexpr int N4 = N / 4;
     constexpr int GEM = band_ge_max(NQ);
+    constexpr int GEI = (GEM + kBandIssuers - 1) / kBandIssuers;  // accumulators per issuer
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_bar[BD_N];
     __shared__ uint32_t s_tmem;
@@ -206,15 +215,15 @@ __global__ void __launch_bounds__(kBandThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(bar(BD_WFULL + i), 1);
-            mbar_init(bar(BD_WEMPTY + i), 1);
-            mbar_init(bar(BD_AFULL + i), 1);
+            mbar_init(bar(BD_WEMPTY + i), kBandIssuers);
+            mbar_init(bar(BD_AFULL + i), kBandIssuers);
             mbar_init(bar(BD_AEMPTY + i), 4);  // the four warps of the draining team
         }
         for (int i = 0; i < BL.TS; ++i) {
             mbar_init(bar(BD_TFULL + i), 1);
-            mbar_init(bar(BD_TEMPTY + i), 1);
+            mbar_init(bar(BD_TEMPTY + i), kBandIssuers);
         }
-        mbar_init(bar(BD_FIN), 1);
+        mbar_init(bar(BD_FIN), kBandIssuers);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
 
     // per-CTA running counts of groups and stages, advanced alike by every role
     uint32_t gc = 0, tc = 0;
-    uint32_t t_issued = 0, w_issued = 0, mma_issued = 0;
+    uint32_t t_issued = 0, w_issued = 0;
     bool ok = true;
 
     const uint32_t TS = (uint32_t)BL.TS;
@@ -277,9 +286,14 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                     }
                 }
             }
-        } else if (warp == 1) {
-            // ---------------- MMA issuer ----------------
+        } else if (warp >= 1 && warp <= kBandIssuers) {
+            // ---------------- MMA issuers ----------------
+            // issuer i (warp 1 + i) owns the accumulators e of the group with
+            // e mod kBandIssuers == i, so every accumulator's MMAs come from one
+            // thread in a fixed order; both issuers take every stage's waits
+            // and commit every barrier a stage or group releases
             if (lane == 0) {
+                const int iss = warp - 1;
                 const uint64_t da0 = smem_desc(sbase, 16u * g.Xw * 16u, (uint32_t)g.Xw * 16u);
                 const uint64_t db0 = smem_desc(sbase + slab_off, (uint32_t)(kBandQ * g.trows * 16), 128);
                 const uint32_t tile_step = (uint32_t)BL.tile_stride >> 4, slab_step = (uint32_t)BL.slab_stride >> 4;
@@ -310,7 +324,9 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                         const int n0 = nlo & ~15;
                         const int n1 = ((nhi + 15) & ~15) < N ? ((nhi + 15) & ~15) : N;
                         const uint32_t idesc_b = idesc_bf16(kM, n1 - n0);
-                        const uint32_t dacc_b = dacc + (uint32_t)n0;
+                        // this issuer's accumulators e = iss, iss + kBandIssuers, ...
+                        const int Gi = Gg > iss ? (Gg - iss + kBandIssuers - 1) / kBandIssuers : 0;
+                        const uint32_t dacc_i = dacc + (uint32_t)n0 + (uint32_t)(iss * N);
                         for (int s = 0; s < g.nS; ++s) {
                             ok = mbar_wait(bar(BD_TFULL + ts), tph, &s_abort);
                             if (!ok) break;
@@ -319,14 +335,12 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                             const int u0 = s * kBandQ;
                             const int nq = m - u0 < kBandQ ? m - u0 : kBandQ;
                             const uint64_t dAu = dA + (uint64_t)u0;
-                            switch (Gg) {  // outside the run of MMAs
-                                case 1: band_stage_any<N, 1>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
-                                case 2: band_stage_any<N, 2>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
-                                case 3: band_stage_any<N, GEM < 3 ? GEM : 3>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
-                                case 4: band_stage_any<N, GEM < 4 ? GEM : 4>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
-                                default: band_stage_any<N, GEM < 5 ? GEM : 5>(s == 0, dacc_b, dAu, dB, tcol, idesc_b, nq); break;
+                            switch (Gi) {  // outside the run of MMAs
+                                case 0: break;
+                                case 1: band_stage_any<N, 1>(s == 0, dacc_i, dAu + (uint64_t)(8 * iss), dB, tcol, idesc_b, nq); break;
+                                case 2: band_stage_any<N, GEI < 2 ? GEI : 2>(s == 0, dacc_i, dAu + (uint64_t)(8 * iss), dB, tcol, idesc_b, nq); break;
+                                default: band_stage_any<N, GEI < 3 ? GEI : 3>(s == 0, dacc_i, dAu + (uint64_t)(8 * iss), dB, tcol, idesc_b, nq); break;
                             }
-                            mma_issued += (uint32_t)(nq * Gg);
                             mma_commit(bar(BD_TEMPTY + ts));
                             if (++ts == TS) { ts = 0; tph ^= 1u; }
                         }
@@ -462,7 +476,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
                 mbar_wait_short(bar(BD_WFULL + (wi & 1u)), (wi >> 1) & 1);
             }
         }
-        if (warp == 1 && lane == 0 && mma_issued > 0) {  // and every MMA issued
+        if (warp >= 1 && warp <= kBandIssuers && lane == 0) {  // and every MMA issued
             mma_commit(bar(BD_FIN));
             mbar_wait_short(bar(BD_FIN), 0);
         }
