@@ -48,10 +48,10 @@ using namespace tcx;
 // before the shift; window rows past m + 2R only reach dy > 2R.  After the
 // last band the eight drain warps' sums meet in shared memory and are added
 // in a fixed order, so the result does not depend on timing.
-// Roles: warp 0 copies, warps 1 and 2 issue the MMAs (accumulators e of a
-// group alternate between them: an issuing thread stalls for a few hundred
+// Roles: warp 0 copies, warps 1-3 issue the MMAs (accumulator e of a group
+// goes to warp 1 + e mod 3: an issuing thread stalls for a few hundred
 // clocks at every stage's barrier, and with the short N <= 96 MMAs the
-// tensor pipe's queue runs dry meanwhile unless the other thread has MMAs
+// tensor pipe's queue runs dry meanwhile unless another thread has MMAs
 // queued), warps 4-7 drain the even groups (TMEM half 0), warps 8-11 the
 // odd ones (half 1).  Each accumulator spans m MMAs, like the column form's.
 // ---------------------------------------------------------------------------
@@ -60,7 +60,7 @@ constexpr int kBandMaxTS = 4;
 constexpr int kBandThreads = 384;
 constexpr int kBandDrain = 256;
 constexpr int kBandMaxNQ = 6;  // N <= 96, i.e. R <= 40
-constexpr int kBandIssuers = 2;  // MMA-issuing warps (1 .. kBandIssuers)
+constexpr int kBandIssuers = 3;  // MMA-issuing warps (1 .. kBandIssuers)
 constexpr int kBandSmemFloor = 120 * 1024;  // dynamic shared memory of a launch: at least this
 
 __host__ __device__ constexpr int band_ge_max(int nq) { return nq <= 3 ? 5 : 16 / nq; }
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kBandThreads, 1)
             // ---------------- MMA issuers ----------------
             // issuer i (warp 1 + i) owns the accumulators e of the group with
             // e mod kBandIssuers == i, so every accumulator's MMAs come from one
-            // thread in a fixed order; both issuers take every stage's waits
+            // thread in a fixed order; every issuer takes every stage's waits
             // and commit every barrier a stage or group releases
             if (lane == 0) {
                 const int iss = warp - 1;

@@ -43,6 +43,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
+#include <type_traits>
 
 #include "internal.h"
 #include "tc_ptx.h"
@@ -393,7 +394,7 @@ constexpr int kColSmemMax = kTcSmemMax;
 // seen the first phase.
 constexpr int kColNS = 8;
 constexpr int kColDB = 4;  // TMEM chunks of 16 columns per drain load batch
-// 12 warps: 0 TMA producer, 1 MMA issuer, 2 release relay, 3 idle,
+// 12 warps: 0 TMA producer, 1 and 3 MMA issuers, 2 release relay,
 // 4..11 drain (two teams of four, one warp per TMEM lane quarter each)
 constexpr int kColThreads = 384;
 constexpr int kColDrain = 256;
@@ -516,10 +517,10 @@ __global__ void __launch_bounds__(kColThreads, 1)
             mbar_init(bar(CB_TFULL + i), 1);
             mbar_init(bar(CB_TEMPTY + i), 1);
         }
-        for (int i = 0; i < kColNS; ++i) mbar_init(bar(CB_STG + i), 1);
-        mbar_init(bar(CB_AFULL), 1);
+        for (int i = 0; i < kColNS; ++i) mbar_init(bar(CB_STG + i), 2);  // both issuers
+        mbar_init(bar(CB_AFULL), 2);
         for (int i = 0; i < kColMaxG; ++i) mbar_init(bar(CB_AEMPTY + i), kColDrain / 32);  // every drain warp
-        mbar_init(bar(CB_FIN), 1);
+        mbar_init(bar(CB_FIN), 2);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
     // per-CTA running counts (window slabs, template slabs = stages, groups),
     // advanced identically by every role
     uint32_t wsc = 0, tsc = 0, grp = 0;
-    uint32_t t_issued = 0, mma_issued = 0;
+    uint32_t t_issued = 0;
 
     for (int kk = blockIdx.x; kk < n_items; kk += gridDim.x) {
         if (*reinterpret_cast<volatile int*>(&s_abort)) break;
@@ -586,9 +587,15 @@ __global__ void __launch_bounds__(kColThreads, 1)
                     }
                 }
             }
-        } else if (warp == 1) {
-            // ---------------- MMA issuer ----------------
-            if (lane == 0) {
+        } else if (warp == 1 || warp == 3) {
+            // ---------------- MMA issuers ----------------
+            // warp 1 issues the even accumulators gi of a group, warp 3 the odd
+            // ones: each accumulator's MMAs come from one thread in a fixed
+            // order, and while one thread stalls at a stage barrier the other
+            // keeps the tensor pipe's queue fed.  Both take every wait and
+            // commit every stage and group barrier.
+            auto issue = [&](auto iss_c) {
+                constexpr int ISS = decltype(iss_c)::value;
                 const uint32_t idesc = idesc_bf16(kM, g.Npad);
                 const uint32_t wcol = (uint32_t)g.wrows;  // window column stride in 16-byte units
                 const uint32_t tcol = (uint32_t)g.trows;  // template column stride in 16-byte units
@@ -632,7 +639,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
                             // contents of it (the drain releases them one by one)
 #pragma unroll
                             for (int gi = 0; gi < G; ++gi) {
-                                if (gi < Gg) {
+                                if ((gi & 1) == ISS && gi < Gg) {
                                     if (gg >= 1) {
                                         ok = mbar_wait(bar(CB_AEMPTY + gi), (gg - 1) & 1, &s_abort);
                                         if (!ok) break;
@@ -652,21 +659,21 @@ __global__ void __launch_bounds__(kColThreads, 1)
                             for (int q = 0; q < kColQ; ++q)
 #pragma unroll
                                 for (int gi = 0; gi < G; ++gi)
-                                    mma_bf16(dD[gi], dW[(q + gi) / kColQ] + (uint64_t)(((q + gi) % kColQ) * wcol),
-                                             dT + (uint64_t)(q * tcol), idesc, q > 0 ? 1u : acc0);
+                                    if ((gi & 1) == ISS)
+                                        mma_bf16(dD[gi], dW[(q + gi) / kColQ] + (uint64_t)(((q + gi) % kColQ) * wcol),
+                                                 dT + (uint64_t)(q * tcol), idesc, q > 0 ? 1u : acc0);
                         } else {
 #pragma unroll
                             for (int q = 0; q < kColQ; ++q)
                                 if (q < nq) {
 #pragma unroll
                                     for (int gi = 0; gi < G; ++gi)
-                                        if (gi < Gg)
+                                        if ((gi & 1) == ISS && gi < Gg)
                                             mma_bf16(dD[gi],
                                                      dW[(q + gi) / kColQ] + (uint64_t)(((q + gi) % kColQ) * wcol),
                                                      dT + (uint64_t)(q * tcol), idesc, q > 0 ? 1u : acc0);
                                 }
                         }
-                        mma_issued += (uint32_t)(nq * Gg);
                         if (s == nstage - 1) mma_commit(bar(CB_AFULL));
                         mma_commit(bar(CB_STG + stg));
                         if (++stg == (uint32_t)kColNS) stg = 0;
@@ -677,6 +684,12 @@ __global__ void __launch_bounds__(kColThreads, 1)
                     for (int b2 = 0; b2 < nws; ++b2)
                         if (++ws == (uint32_t)g.WS) { ws = 0; wph ^= 1u; }
                 }
+            };
+            if (lane == 0) {
+                if (warp == 1)
+                    issue(std::integral_constant<int, 0>{});
+                else
+                    issue(std::integral_constant<int, 1>{});
             }
         } else if (warp == 2) {
             // ---------------- slab release relay ----------------
@@ -850,7 +863,7 @@ __global__ void __launch_bounds__(kColThreads, 1)
                 mbar_wait_short(bar(CB_TFULL + ti % CL.TS), (ti / CL.TS) & 1);
             }
         }
-        if (warp == 1 && lane == 0 && mma_issued > 0) {  // and every MMA issued
+        if ((warp == 1 || warp == 3) && lane == 0) {  // and every MMA issued
             mma_commit(bar(CB_FIN));
             mbar_wait_short(bar(CB_FIN), 0);
         }
