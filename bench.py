@@ -48,10 +48,10 @@ METRIC = "matched CPs/sec and SFOC Mpix/sec on 1 GB300, BF16-batched vs plain FP
 UNIT = "CP/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 FFT_SIZES = (64, 128)  # transform sides of the Fourier correlation (the smallest with m + 2R <= L)
-# DRAM bytes (read + write) per launch of each form's correlation kernel on
-# the 2048x2048 workload, from one ncu capture of the kernel as it stands;
-# None where the kernel has changed since its capture.
-CORR_TRAFFIC_SAR2048 = {"bf16": None, "f32": 407.75e6}
+# DRAM bytes (read + write) per launch of a correlation kernel on the
+# 2048x2048 workload, keyed by (cube dtype form, correlation path), from one
+# ncu capture of the kernel as it stands; absent where none is current.
+CORR_TRAFFIC_SAR2048 = {}
 
 
 def parse():
@@ -244,9 +244,16 @@ def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
     ctx.enable_timing(False)
     ms = [a.elapsed_time(c) for a, c in evs]
     status = raw[:, 5].cpu()
+    # the concrete correlation form the steps ran: the autotuner's entry for
+    # an AUTO form, the forced form otherwise
+    path, option = int(corr), 0
+    if corr == b.CORR_AUTO:
+        ent = ctx.autotune_entry(p.cube_dtype, pair.m, pair.R)
+        if ent is not None:
+            path, option = ent["path"], ent["option"]
     return dict(ms=sum(ms), ms_steps=ms, matched=int((status == 0).sum()), valid=int(((status == 0) | (status == 3)).sum()),
                 stages=st, launches=launches, p=p, corr=corr, d=(d_ref, d_sen, d_pts), raw=raw,
-                t_timed=(t_start, t_end))
+                t_timed=(t_start, t_end), path=path, option=option)
 
 
 # FP32 operations of one FAST-9 score as k_fast_blocks computes it: 16
@@ -424,18 +431,6 @@ def corr_flops(pair, z=12):
     return 2.0 * pair.m * pair.m * z * P
 
 
-def tc_kernel(pair):
-    """The tensor-core form the library picks: the column or the band form,
-    whichever issues fewer MMAs per point; the Toeplitz form otherwise."""
-    m, R = pair.m, pair.R
-    col = m + 2 * R <= 128
-    band = R <= 40
-    band_mmas = -(-(m + 2 * R) // 16) * -(-(2 * R + 1) // 8) * m
-    if band and (not col or band_mmas < (2 * R + 1) * m):
-        return "k_corr_tc_band"
-    return "k_corr_tc_col" if col else "k_corr_tc (Toeplitz form)"
-
-
 def fft_side(pair):
     return next((L for L in FFT_SIZES if pair.m + 2 * pair.R <= L), None)
 
@@ -463,29 +458,30 @@ def fp32_peak(pk):
     return FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal: the microbenchmark did not run)"
 
 
-def form_roofline(form, pair, per_launch_ms, processed, pk, workload):
-    """Roofline of a form's correlation kernel: the algorithmic work of the
-    points it processed over its mean launch time (CUDA events), against the
-    peak of the unit that bounds it."""
-    traffic = CORR_TRAFFIC_SAR2048.get(form) if workload == "sar2048" else None
+def form_roofline(form, pair, per_launch_ms, processed, pk, workload, path, option=0):
+    """Roofline of a form's correlation kernel (the concrete form `path` the
+    steps ran): the algorithmic work of the points it processed over its mean
+    launch time (CUDA events), against the peak of the unit that bounds it."""
+    traffic = CORR_TRAFFIC_SAR2048.get((form, path)) if workload == "sar2048" else None
     secs = per_launch_ms * 1e-3
-    if form == "bf16":
-        ach = corr_flops(pair) * processed / secs / 1e12
-        return {"bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
-                "frac": ach / pk["bf16"], "traffic": traffic,
-                "kernel": tc_kernel(pair) + " (tcgen05 bf16, fp32 accumulate)",
-                "peak_src": "bf16_tflops burst, %s" % pk["src"],
-                "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
     peak32, fp32_src = fp32_peak(pk)
-    if form == "f32" and fft_side(pair):
-        ach = fft_flops(pair) * processed / secs / 1e12
+    if path == 6:  # the Fourier correlation, on F32 cubes or BF16 cubes widened as read
+        L = option or fft_side(pair)
+        ach = fft_flops_mrl(pair.m, pair.R, L) * processed / secs / 1e12
         return {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
                 "frac": ach / peak32, "traffic": traffic,
-                "kernel": "k_corr_fft<%d> (FP32 Fourier correlation, Eq. 13)" % fft_side(pair),
+                "kernel": "k_corr_fft<%d> (FP32 Fourier correlation, Eq. 13, %s cubes)" % (
+                    L, "BF16" if form == "bf16" else "F32"),
                 "peak_src": fp32_src,
                 "work": "5 L log2 L flop per length-L transform (z (m+2R+L) forward, L/2+1+2R+1 inverse) "
                         "+ 12 flop per cross-spectrum bin, per processed point"}
     ach = corr_flops(pair) * processed / secs / 1e12
+    if path in (3, 4, 5):
+        return {"bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
+                "frac": ach / pk["bf16"], "traffic": traffic,
+                "kernel": PATH_NAMES[path] + " (bf16 operands, fp32 accumulate)",
+                "peak_src": "bf16_tflops burst, %s" % pk["src"],
+                "work": "2*m^2*z*(2R+1)^2 flop per processed point"}
     return {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
             "frac": ach / peak32, "traffic": traffic,
             "kernel": "k_corr_f32 (direct FP32 FMA)", "peak_src": fp32_src,
@@ -1045,7 +1041,7 @@ def main():
         sfoc_ms = per_step["steer"] + per_step["smooth"]
         corr_ms, corr_n = st["correlation"]
         per_launch = corr_ms / max(1, corr_n)
-        roof = form_roofline(form, pair, per_launch, r["valid"], pk, args.workload)
+        roof = form_roofline(form, pair, per_launch, r["valid"], pk, args.workload, r["path"], r["option"])
         return dict(value=job_value(r["matched_all"], args.steps, r["ms_max"]), ms_per_step=r["ms_max"] / args.steps,
                     sfoc_mpix_s=2 * pair.ref.size / (sfoc_ms * 1e-3) / 1e6 if sfoc_ms > 0 else None,
                     stage_ms_per_step={k: round(v, 4) for k, v in per_step.items()}, roofline=roof,

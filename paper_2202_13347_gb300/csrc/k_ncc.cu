@@ -10,13 +10,16 @@
 //                   building them.
 // k_ncc_argmax      per point (one CTA): for every offset, R_S and R_SS from
 //                   the reference integral images (4 lookups each, exact
-//                   64-bit fixed point), the variance R_SS - R_S^2/mnz and
-//                   the numerator in FP64 (the only steps that cancel), then
-//                   NCC = num / sqrt(vS vT) in FP32; a warp-shuffle argmax
-//                   with the (NCC desc, dy asc, dx asc) order and a 3-point
-//                   parabola per axis.  GB300 runs FP64 at a small fraction
-//                   of its FP32 rate, so FP64 is kept to a few operations
-//                   per offset.
+//                   64-bit fixed point); the two steps that cancel are taken
+//                   in exact 128-bit integers: mnz R_SS - R_S^2 (the
+//                   variance times mnz) and, for the uncentred correlation
+//                   forms, R_S R_T (the mean correction of the numerator);
+//                   each is rounded to FP32 once, then NCC = num / sqrt(vS vT)
+//                   in FP32; a warp-shuffle argmax with the (NCC desc, dy
+//                   asc, dx asc) order and a 3-point parabola per axis.  No
+//                   FP64 per offset: GB300 runs it at a small fraction of its
+//                   FP32 rate, and 64 x 64-bit integer products cost a few
+//                   integer multiply-adds.
 #include <math.h>
 #include <string.h>
 
@@ -27,6 +30,13 @@ namespace sfoc {
 namespace {
 
 typedef unsigned long long u64;
+
+// a non-negative 128-bit integer to FP32 (two roundings: relative error
+// below 2^-23)
+__device__ __forceinline__ float u128_to_float(unsigned __int128 v) {
+    const u64 hi = (u64)(v >> 64), lo = (u64)v;
+    return fmaf(__ull2float_rn(hi), 18446744073709551616.f, __ull2float_rn(lo));
+}
 
 // window sum (Eq. 16) in 2^-28 units; exact (the planes wrap modulo 2^64)
 __device__ __forceinline__ long long rect(const u64* P, size_t ip, int y0, int x0, int y1, int x1) {
@@ -139,9 +149,13 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const __grid_constan
         return;
     }
     __syncthreads();
-    const double N = (double)m * m * z, invN = 1.0 / N, flat = 1e-6 * N;
-    const float vTf = (float)(st.RTT - st.RT * st.RT * invN);
-    const double rt_n = st.RT * invN;
+    const long long Ni = (long long)m * m * z;
+    const double N = (double)Ni;
+    const float flat = (float)(1e-6 * N);
+    const float vTf = (float)(st.RTT - st.RT * st.RT / N);
+    // 2^-56 / mnz: a product of two window sums in 2^-28 units, divided by mnz
+    const float sc = (float)(1.0 / (72057594037927936.0 * N));
+    const long long rt = (long long)(st.RT * 268435456.0);  // R_T in 2^-28 units (exact)
     const int h = template_half(m);
     const int ty0 = pts[2 * k + 1] - h, tx0 = pts[2 * k] - h;
     const u64* P1p = Pr;
@@ -160,10 +174,17 @@ __global__ void __launch_bounds__(kNccThreads) k_ncc_argmax(const __grid_constan
         if (rs >= kIntNonFiniteMin || rss >= kIntNonFiniteMin || n32 != n32) {
             v = NAN;
         } else {
-            const double RS = int_units_to_double(rs), RSS = int_units_to_double(rss);
-            const double vS = fma(-RS, RS * invN, RSS);
-            const double nm = centered ? (double)n32 : fma(-RS, rt_n, (double)n32);
-            v = vS <= flat ? 0.f : (float)nm / sqrtf((float)vS * vTf);
+            // mnz R_SS - R_S^2, exact (units 2^-56); negative only through the
+            // per-pixel rounding of a flat window
+            const __int128 d = ((__int128)(Ni * rss) << 28) - (__int128)rs * rs;
+            const float vS = d > 0 ? u128_to_float((unsigned __int128)d) * sc : 0.f;
+            float nm = n32;
+            if (!centered) {
+                const __int128 p = (__int128)rs * rt;  // R_S R_T, exact
+                const float pf = p >= 0 ? u128_to_float((unsigned __int128)p) : -u128_to_float((unsigned __int128)(-p));
+                nm = fmaf(-pf, sc, n32);
+            }
+            v = vS <= flat ? 0.f : nm / sqrtf(vS * vTf);
         }
         s_map[i] = v;
         if (out_maps) out_maps[(size_t)k * P + i] = v;

@@ -29,18 +29,6 @@ def test_fourier_flop_per_point():
     assert bench.fft_side(_pair(101, 40)) is None      # m + 2R = 181 > 128: no Fourier form
 
 
-@pytest.mark.parametrize("m,R,kernel", [
-    (81, 20, "k_corr_tc_col"),                 # column 41 * 81 = 3321 MMAs, band 8 * 6 * 81 = 3888
-    (41, 10, "k_corr_tc_band"),                # band 4 * 3 * 41 = 492, column 21 * 41 = 861
-    (101, 40, "k_corr_tc_band"),               # m + 2R = 181 > 128: no column form
-    (101, 45, "k_corr_tc (Toeplitz form)"),    # neither: R > 40 and m + 2R > 128
-])
-def test_tensor_form_choice(m, R, kernel):
-    """The bench names the tensor-core kernel the library picks: the column
-    or band form with fewer MMAs per point, else the Toeplitz form."""
-    assert bench.tc_kernel(_pair(m, R)) == kernel
-
-
 def test_job_value():
     """934 matched points per step, 20 steps in 35.95 ms: 519.6 K CP/s."""
     assert bench.job_value(934, 20, 35.95) == pytest.approx(519610.6, rel=1e-6)
@@ -97,22 +85,25 @@ def test_noise_series_are_the_papers():
 
 def test_form_rooflines_reproduce_the_last_line():
     """form_roofline against the figures of a GB300 run of the 2048^2
-    workload: 999 processed points, 0.79 ms per Fourier launch, 1.1598 ms per
-    column-form launch, the measured bf16 peak 1921.3 TFLOP/s."""
+    workload (999 processed points, the measured bf16 peak 1921.3 TFLOP/s),
+    for the concrete form each step ran: 0.79 ms per Fourier launch (on F32
+    or BF16 cubes: the same transform count), 1.1598 ms per column-form
+    launch, 7.51 ms per direct launch."""
     p = _pair(81, 20)
     pk = {"bf16": 1921.3, "src": "measured"}
-    f = bench.form_roofline("f32", p, 0.79, 999, pk, "sar2048")
-    assert f["bound"] == "alu" and f["kernel"].startswith("k_corr_fft<128>")
+    f = bench.form_roofline("f32", p, 0.79, 999, pk, "sar2048", 6, 128)
+    assert f["bound"] == "alu" and f["kernel"].startswith("k_corr_fft<128>") and "F32 cubes" in f["kernel"]
     assert f["achieved"] == pytest.approx(19.04, rel=2e-3) and f["frac"] == pytest.approx(0.2364, rel=2e-3)
-    assert f["traffic"] == 407.75e6
-    t = bench.form_roofline("bf16", p, 1.1598, 999, pk, "sar2048")
+    assert f["traffic"] is None  # no capture of the kernel as it stands
+    fb = bench.form_roofline("bf16", p, 0.79, 999, pk, "sar2048", 6, 0)
+    assert fb["bound"] == "alu" and "BF16 cubes" in fb["kernel"] and fb["achieved"] == pytest.approx(19.04, rel=2e-3)
+    t = bench.form_roofline("bf16", p, 1.1598, 999, pk, "sar2048", 4)
     assert t["bound"] == "tensor" and t["kernel"].startswith("k_corr_tc_col")
     assert t["achieved"] == pytest.approx(228.0, rel=2e-3) and t["traffic"] is None
-    d = bench.form_roofline("f32direct", p, 7.51, 999, pk, "sar2048")
+    assert bench.form_roofline("bf16", p, 1.1598, 999, pk, "sar2048", 5)["kernel"].startswith("k_corr_tc_band")
+    d = bench.form_roofline("f32direct", p, 7.51, 999, pk, "sar2048", 1)
     assert d["kernel"].startswith("k_corr_f32") and d["achieved"] == pytest.approx(35.2, rel=5e-3)
     assert d["traffic"] is None
-    # the f32 form without a transform size falls back to the direct kernel's roofline
-    assert bench.form_roofline("f32", _pair(101, 40), 7.0, 10, pk, "inverting512")["kernel"].startswith("k_corr_f32")
 
 
 def test_fast_roofline():

@@ -75,6 +75,11 @@ def _fake_library(fail_ransac=False):
         def measure_peaks(self):
             return {"fp32_tflops": 70.0, "fp32x2_tflops": 75.0, "fp64_tflops": 1.2, "hbm_copy_gbs": 6500.0}
 
+        def autotune_entry(self, dtype, m, R, family=0):
+            # F32 cubes: the Fourier form; BF16 cubes: the column form
+            path, opt = (6, 128) if dtype == 0 else (4, 0)
+            return {"path": path, "option": opt, "sample": 10, "candidates": [(path, opt, 0.5)]}
+
         def enable_timing(self, on=True):
             pass
 

@@ -9,6 +9,8 @@ arranges it, and check that it reproduces the plain definition exactly (up
 to rounding).  They pin the design of the kernels; the GPU parity tests pin
 the kernels themselves.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -303,6 +305,46 @@ def test_fixed_point_headroom():
     assert 128 * 128 * 5.7 * 2 ** 28 < 2 ** 45
     assert 128 * 128 * 2.0 * 2 ** 28 < 2 ** 45
     assert 128 * 128 * NON_FINITE + (1 << 45) < 1 << 63
+
+
+def _u128_to_f32(v):
+    """k_ncc_argmax's conversion of a non-negative 128-bit integer: FP32 of
+    the high and low 64-bit halves, then one fused multiply-add (exact
+    scaling by 2^64, one rounding of the sum)."""
+    hi, lo = v >> 64, v & ((1 << 64) - 1)
+    a, b = int(np.float32(float(hi))), int(np.float32(float(lo)))
+    return np.float32(float(Fraction(a * (1 << 64) + b)))
+
+
+def test_ncc_variance_in_exact_integers():
+    """Per offset the NCC kernel forms mnz R_SS - R_S^2 (and R_S R_T) from
+    the exact window sums in 128-bit integers and rounds once to FP32.  The
+    products fit (|R_S|, R_SS, R_T < 2^45 units, mnz < 2^18: mnz R_SS < 2^63,
+    shifted by 28 < 2^91, R_S^2 < 2^90), and the FP32 variance is within
+    2^-21 (relative: the conversion's two roundings, the rounded scale
+    2^-56 / mnz and the product) of the exact one, on windows of quantised
+    pixel sums."""
+    assert (128 * 128 * 12) < 1 << 18
+    assert (1 << 18) * (1 << 45) <= 1 << 63
+    rng = np.random.default_rng(11)
+    for trial in range(200):
+        m = int(rng.choice([1, 9, 41, 81, 101, 128]))
+        z = 12
+        n = m * m
+        scale = rng.choice([1.0, 1e-3, 1e-6])
+        g = (rng.random(n) * scale + rng.random() * 0.5).astype(np.float32)  # per-pixel channel sums s1
+        g2 = (g * g / z + rng.random(n).astype(np.float32) * scale * scale).astype(np.float32)  # s2 >= s1^2 / z
+        rs = int(_quant(g).sum())
+        rss = int(_quant(g2).sum())
+        assert abs(rs) < 1 << 45 and rss < 1 << 45
+        N = n * z
+        d = ((N * rss) << 28) - rs * rs
+        assert abs(d) < 1 << 127 and (N * rss) < 1 << 63
+        exact = Fraction(d, N << 56)
+        if d <= 0:
+            continue
+        vf = np.float32(_u128_to_f32(d) * np.float32(1.0 / (2.0 ** 56 * N)))
+        assert abs(Fraction(float(vf)) - exact) <= exact * Fraction(1, 1 << 21), (m, scale, trial)
 
 
 # --------------------------------------------------------------------------
