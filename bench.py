@@ -70,7 +70,12 @@ def parse():
                          "64 x N-pair job); strong = one 64-pair job whose pairs are balanced over the ranks by "
                          "cost, results gathered on rank 0")
     ap.add_argument("--corr", default="auto", choices=["auto", "igemm_tc", "band", "column", "fft", "direct"],
-                    help="mixed64: correlation path of the batched forms (auto: the autotuner's measured choice)")
+                    help="correlation path of the batched forms and of the single-pair bf16 / f32 forms (auto: "
+                         "the autotuner's measured choice)")
+    ap.add_argument("--template", type=int, default=0,
+                    help="single-pair workloads: template side m instead of the workload's (profiling cases)")
+    ap.add_argument("--radius", type=int, default=-1,
+                    help="single-pair workloads: search radius R instead of the workload's (profiling cases)")
     ap.add_argument("--pairs", type=int, default=64, help="mixed64: pairs per batch (fewer for small profiling cases)")
     ap.add_argument("--scale", type=float, default=1.0, help="mixed64: side and point-count scale (1 = full size)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -207,9 +212,9 @@ class ClockSampler:
                 "samples": len(sm), "scope": scope}
 
 
-def run_form(b, torch, ctx, pair, form, steps, warmup, flush):
+def run_form(b, torch, ctx, pair, form, steps, warmup, flush, corr_name="auto"):
     p = b.params(dtype=b.DTYPE_BF16 if form == "bf16" else b.DTYPE_F32)
-    corr = b.CORR_DIRECT_F32 if form == "f32direct" else b.CORR_AUTO
+    corr = b.CORR_DIRECT_F32 if form == "f32direct" else corr_option(b, corr_name)
     d_ref = torch.from_numpy(pair.ref).cuda()
     d_sen = torch.from_numpy(pair.sen).cuda()
     d_pts = torch.from_numpy(pair.points).cuda()
@@ -962,6 +967,10 @@ def main():
             return reference_batch(args, rank)
         return main_batch(args, torch, dist, rank, world, gpu_index)
     pair, desc = workload(args.workload, rank)
+    if args.template > 0 or args.radius >= 0:
+        pair.m = args.template if args.template > 0 else pair.m
+        pair.R = args.radius if args.radius >= 0 else pair.R
+        desc = "%s, with m=%d, R=%d instead" % (desc, pair.m, pair.R)
     config = {"workload": desc, "H": int(pair.ref.shape[0]), "W": int(pair.ref.shape[1]),
               "points_per_pair": int(len(pair.points)), "m": pair.m, "R": pair.R, "z": 12,
               "pairs_per_rank": 1, "l2": "flushed between timed steps (256 MB write)"}
@@ -1022,7 +1031,7 @@ def main():
                 dist.barrier()
             torch.cuda.synchronize()
             with ClockSampler(gpu_index) as cs:
-                r = run_form(b, torch, ctx, pair, form, args.steps, args.warmup, flush)
+                r = run_form(b, torch, ctx, pair, form, args.steps, args.warmup, flush, args.corr)
                 cs.mark(*r["t_timed"])
             r["ms_max"], r["matched_all"] = reduce_over_ranks(dist, torch, r["ms"], r["matched"], "cuda")
             r["clocks"] = cs.summary()
