@@ -48,10 +48,12 @@ METRIC = "matched CPs/sec and SFOC Mpix/sec on 1 GB300, BF16-batched vs plain FP
 UNIT = "CP/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 FFT_SIZES = (64, 128)  # transform sides of the Fourier correlation (the smallest with m + 2R <= L)
-# DRAM bytes (read + write) per launch of a correlation kernel on the
-# 2048x2048 workload, keyed by (cube dtype form, correlation path), from one
-# ncu capture of the kernel as it stands; absent where none is current.
-CORR_TRAFFIC_SAR2048 = {}
+# DRAM bytes (read + write) per processed point of a correlation kernel on
+# the 2048x2048 workload (m = 81, R = 20), keyed by (form, correlation path),
+# from one ncu capture of the kernel as it stands (the band form: 87.12 MB
+# read + 4.61 MB written for the autotuner's 304-point launch); absent where
+# none is current.  A launch's traffic is this times the points it processed.
+CORR_TRAFFIC_PER_POINT_SAR2048 = {("bf16", 5): (87.118848e6 + 4.611072e6) / 304}
 
 
 def parse():
@@ -467,7 +469,8 @@ def form_roofline(form, pair, per_launch_ms, processed, pk, workload, path, opti
     """Roofline of a form's correlation kernel (the concrete form `path` the
     steps ran): the algorithmic work of the points it processed over its mean
     launch time (CUDA events), against the peak of the unit that bounds it."""
-    traffic = CORR_TRAFFIC_SAR2048.get((form, path)) if workload == "sar2048" else None
+    per_point = CORR_TRAFFIC_PER_POINT_SAR2048.get((form, path)) if workload == "sar2048" else None
+    traffic = per_point * processed if per_point and (pair.m, pair.R) == (81, 20) else None
     secs = per_launch_ms * 1e-3
     peak32, fp32_src = fp32_peak(pk)
     if path == 6:  # the Fourier correlation, on F32 cubes or BF16 cubes widened as read

@@ -100,7 +100,9 @@ def test_form_rooflines_reproduce_the_last_line():
     t = bench.form_roofline("bf16", p, 1.1598, 999, pk, "sar2048", 4)
     assert t["bound"] == "tensor" and t["kernel"].startswith("k_corr_tc_col")
     assert t["achieved"] == pytest.approx(228.0, rel=2e-3) and t["traffic"] is None
-    assert bench.form_roofline("bf16", p, 1.1598, 999, pk, "sar2048", 5)["kernel"].startswith("k_corr_tc_band")
+    bb = bench.form_roofline("bf16", p, 1.1598, 999, pk, "sar2048", 5)
+    assert bb["kernel"].startswith("k_corr_tc_band")
+    assert bb["traffic"] == pytest.approx(91.73e6 / 304 * 999, rel=1e-3)  # the capture's bytes per point x points
     d = bench.form_roofline("f32direct", p, 7.51, 999, pk, "sar2048", 1)
     assert d["kernel"].startswith("k_corr_f32") and d["achieved"] == pytest.approx(35.2, rel=5e-3)
     assert d["traffic"] is None
