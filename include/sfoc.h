@@ -378,11 +378,14 @@ SFOC_API sfoc_status fastncc_register_batch(sfoc_ctx* ctx, int n_pairs, const fl
 /* fastncc_register_batch from host buffers: copies every image and point
  * set into a device staging buffer kept by the context, runs the batch and
  * copies every pair's results to h_outs[i] before returning (synchronous).
- * The pairs are taken in up to four chunks of consecutive pairs with about
- * equal pixel counts, each with its own plan: the copies of chunk k + 1 run
- * on a second stream while chunk k is processed.  (Pinned host buffers let
- * the copies overlap.)  A staging buffer that has to grow drops the
- * context's plans. */
+ * The first call with a signature copies everything, then builds the plan
+ * (as fastncc_register_batch does); later calls copy the point sets, then
+ * the images in the order of the plan's SFOC waves on a second stream, and
+ * each wave's SFOC launch waits only for its own images, so the copies of
+ * the later waves run while the earlier waves are built.  (Pinned host
+ * buffers let the copies overlap.)  These runs launch the plan's kernels
+ * one by one rather than replaying its graph.  A staging buffer that has to
+ * grow drops the context's plans. */
 SFOC_API sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs,
                                                  const int* Hr, const int* Wr, const float* const* h_sens,
                                                  const int* Hs, const int* Ws, const int32_t* const* h_points,

@@ -137,13 +137,6 @@ struct Layout {
     }
 };
 
-int concrete_path(int path) {
-    return path == SFOC_CORR_DIRECT_F32 || path == SFOC_CORR_FFT || path == SFOC_CORR_TC_TOEPLITZ ||
-                   path == SFOC_CORR_TC_COLUMN || path == SFOC_CORR_TC_BAND
-               ? path
-               : -1;
-}
-
 // per-point cost of a pair in its form (a relative figure: items are sorted
 // by it, largest first)
 double point_cost(int m, int R) { return (double)m * m * (2.0 * R + 1) * (2.0 * R + 1); }
@@ -738,6 +731,27 @@ sfoc_status resolve_params(sfoc_ctx* ctx, const sfoc_params* pin, sfoc_params* p
     return check_params(ctx, *p);
 }
 
+// the signature of a fastncc_register_batch call (its plan's key)
+void register_key(KeyWriter& k, int n_pairs, int path, const sfoc_params& prm, const float* const* d_refs,
+                  const int* Hr, const int* Wr, const float* const* d_sens, const int* Hs, const int* Ws,
+                  const int32_t* const* d_points, const int* n_points, const int* template_size,
+                  const int* search_radius, fastncc_result* const* d_outs) {
+    k.u(2);
+    k.u((uint64_t)n_pairs);
+    k.u((uint64_t)path);
+    key_params(k, prm);
+    for (int i = 0; i < n_pairs; ++i) {
+        k.p(d_refs[i]);
+        k.p(d_sens[i]);
+        k.u((uint64_t)(uint32_t)Hr[i] << 32 | (uint32_t)Wr[i]);
+        k.u((uint64_t)(uint32_t)Hs[i] << 32 | (uint32_t)Ws[i]);
+        k.p(d_points[i]);
+        k.p(d_outs[i]);
+        k.u((uint64_t)(uint32_t)n_points[i] << 32 | (uint32_t)template_size[i]);
+        k.u((uint64_t)search_radius[i]);
+    }
+}
+
 }  // namespace
 
 }  // namespace sfoc
@@ -881,20 +895,8 @@ sfoc_status fastncc_register_batch(sfoc_ctx* ctx, int n_pairs, const float* cons
     if (s != SFOC_OK) return s;
     DeviceGuard g(ctx->device);
     KeyWriter k;
-    k.u(2);
-    k.u((uint64_t)n_pairs);
-    k.u((uint64_t)path);
-    key_params(k, prm);
-    for (int i = 0; i < n_pairs; ++i) {
-        k.p(d_refs[i]);
-        k.p(d_sens[i]);
-        k.u((uint64_t)(uint32_t)Hr[i] << 32 | (uint32_t)Wr[i]);
-        k.u((uint64_t)(uint32_t)Hs[i] << 32 | (uint32_t)Ws[i]);
-        k.p(d_points[i]);
-        k.p(d_outs[i]);
-        k.u((uint64_t)(uint32_t)n_points[i] << 32 | (uint32_t)template_size[i]);
-        k.u((uint64_t)search_radius[i]);
-    }
+    register_key(k, n_pairs, path, prm, d_refs, Hr, Wr, d_sens, Hs, Ws, d_points, n_points, template_size,
+                 search_radius, d_outs);
     BatchPlan* p = find_plan(ctx, k.k);
     if (p) return run_plan(ctx, p);
     std::vector<sfoc_cube*> cubes(2 * (size_t)n_pairs, nullptr);
@@ -912,11 +914,12 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
                                         !template_size || !search_radius || !h_outs)))
         return fail(ctx, SFOC_ERR_INVALID_ARG, "bad batch arguments");
     if (n_pairs == 0) return SFOC_OK;
+    const int path = opts ? opts->corr_path : SFOC_CORR_AUTO;
+    if (path < SFOC_CORR_AUTO || path > SFOC_CORR_FFT) return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown corr_path");
     sfoc_params prm;
     sfoc_status s = resolve_params(ctx, pin, &prm);
     if (s != SFOC_OK) return s;
     size_t need = 0;
-    double px_all = 0.0;
     for (int i = 0; i < n_pairs; ++i) {
         if (!h_refs[i] || !h_sens[i] || n_points[i] < 0 || (n_points[i] > 0 && (!h_points[i] || !h_outs[i])))
             return fail(ctx, SFOC_ERR_INVALID_ARG, "null host buffer in the batch");
@@ -924,67 +927,34 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
         need += align256(sizeof(float) * (size_t)Hr[i] * Wr[i]) + align256(sizeof(float) * (size_t)Hs[i] * Ws[i]) +
                 align256(sizeof(int32_t) * 2 * (size_t)n_points[i]) +
                 align256(sizeof(fastncc_result) * (size_t)n_points[i]);
-        px_all += (double)Hr[i] * Wr[i] + (double)Hs[i] * Ws[i];
-    }
-    // chunks of consecutive pairs with about equal pixel counts: the images of
-    // chunk k + 1 are copied on a second stream while chunk k is processed
-    constexpr int kMaxChunks = 4;
-    const int K = n_pairs < kMaxChunks ? n_pairs : kMaxChunks;
-    int lo[kMaxChunks + 1];
-    {
-        // chunk k starts after the first pair at which the running pixel count
-        // reaches k / K of the total, kept strictly increasing and leaving at
-        // least one pair for every later chunk
-        lo[0] = 0;
-        double acc = 0.0;
-        int i = 0;
-        for (int k = 1; k < K; ++k) {
-            const double target = px_all * k / K;
-            while (i < n_pairs && acc < target) {
-                acc += (double)Hr[i] * Wr[i] + (double)Hs[i] * Ws[i];
-                ++i;
-            }
-            int b = i;
-            if (b < lo[k - 1] + 1) b = lo[k - 1] + 1;
-            if (b > n_pairs - (K - k)) b = n_pairs - (K - k);
-            lo[k] = b;
-        }
-        lo[K] = n_pairs;
     }
     DeviceGuard g(ctx->device);
-    // the workspace of the largest chunk first, so no chunk's plan is dropped
-    // by another one's growth
+    // the whole batch's workspace before the staging buffer, so a later
+    // growth of either does not drop the plan built below
     {
         const int z = prm.first_order_only ? prm.n_orient : 2 * prm.n_orient;
-        size_t ws_max = 0;
-        for (int k = 0; k < K; ++k) {
-            const int n = lo[k + 1] - lo[k];
-            std::vector<const float*> imgs(2 * (size_t)n, nullptr);
-            std::vector<int> H(2 * (size_t)n), W(2 * (size_t)n);
-            std::vector<sfoc_cube> shape(2 * (size_t)n);
-            std::vector<sfoc_cube*> rp(n), sp(n);
-            for (int i = 0; i < n; ++i) {
-                const int j = lo[k] + i;
-                H[2 * i] = Hr[j];
-                W[2 * i] = Wr[j];
-                H[2 * i + 1] = Hs[j];
-                W[2 * i + 1] = Ws[j];
-                for (int q = 0; q < 2; ++q) {
-                    Cube& c = shape[2 * i + q].c;
-                    c.H = H[2 * i + q];
-                    c.W = W[2 * i + q];
-                    c.z = z;
-                    c.dtype = prm.cube_dtype;
-                }
-                rp[i] = &shape[2 * i];
-                sp[i] = &shape[2 * i + 1];
+        std::vector<const float*> imgs(2 * (size_t)n_pairs, nullptr);
+        std::vector<int> H(2 * (size_t)n_pairs), W(2 * (size_t)n_pairs);
+        std::vector<sfoc_cube> shape(2 * (size_t)n_pairs);
+        std::vector<sfoc_cube*> rp(n_pairs), sp(n_pairs);
+        for (int i = 0; i < n_pairs; ++i) {
+            H[2 * i] = Hr[i];
+            W[2 * i] = Wr[i];
+            H[2 * i + 1] = Hs[i];
+            W[2 * i + 1] = Ws[i];
+            for (int q = 0; q < 2; ++q) {
+                Cube& c = shape[2 * i + q].c;
+                c.H = H[2 * i + q];
+                c.W = W[2 * i + q];
+                c.z = z;
+                c.dtype = prm.cube_dtype;
             }
-            BuildIn bin{2 * n, imgs.data(), H.data(), W.data(), nullptr};
-            MatchIn mi{n, rp.data(), sp.data(), h_points + lo[k], n_points + lo[k], template_size + lo[k],
-                       search_radius + lo[k], h_outs + lo[k]};
-            ws_max = std::max(ws_max, plan_ws_bytes(&bin, &prm, &mi, nullptr));
+            rp[i] = &shape[2 * i];
+            sp[i] = &shape[2 * i + 1];
         }
-        s = ensure_ws(ctx, ws_max);
+        BuildIn bin{2 * n_pairs, imgs.data(), H.data(), W.data(), nullptr};
+        MatchIn mi{n_pairs, rp.data(), sp.data(), h_points, n_points, template_size, search_radius, h_outs};
+        s = ensure_ws(ctx, plan_ws_bytes(&bin, &prm, &mi, nullptr));
         if (s != SFOC_OK) return s;
     }
     if (need > ctx->hstage_bytes) {
@@ -1000,16 +970,39 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch staging)");
         ctx->hstage_bytes = need;
     }
-    if (ctx->max_plans < (size_t)K + 2) ctx->max_plans = (size_t)K + 2;
     cudaError_t e = cudaSuccess;
     if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !ctx->ev_start) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
-    for (int k = 0; k < kMaxChunks && e == cudaSuccess; ++k)
-        if (!ctx->ev_chunk[k]) e = cudaEventCreateWithFlags(&ctx->ev_chunk[k], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+    // staging layout, pair by pair: reference image, sensed image, points, results
     std::vector<const float*> dr(n_pairs), ds(n_pairs);
     std::vector<const int32_t*> dp(n_pairs);
     std::vector<fastncc_result*> dout(n_pairs);
+    {
+        char* b = static_cast<char*>(ctx->hstage);
+        for (int i = 0; i < n_pairs; ++i) {
+            dr[i] = reinterpret_cast<const float*>(b);
+            b += align256(sizeof(float) * (size_t)Hr[i] * Wr[i]);
+            ds[i] = reinterpret_cast<const float*>(b);
+            b += align256(sizeof(float) * (size_t)Hs[i] * Ws[i]);
+            dp[i] = reinterpret_cast<const int32_t*>(b);
+            b += align256(sizeof(int32_t) * 2 * (size_t)n_points[i]);
+            dout[i] = reinterpret_cast<fastncc_result*>(b);
+            b += align256(sizeof(fastncc_result) * (size_t)n_points[i]);
+        }
+    }
+    KeyWriter k;
+    register_key(k, n_pairs, path, prm, dr.data(), Hr, Wr, ds.data(), Hs, Ws, dp.data(), n_points, template_size,
+                 search_radius, dout.data());
+    BatchPlan* plan = find_plan(ctx, k.k);
+    const bool by_wave = plan && plan->build_batched && plan->kind == 2;
+    const size_t n_ev = by_wave ? plan->waves.size() : 1;
+    while (ctx->ev_wave.size() < n_ev && e == cudaSuccess) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) ctx->ev_wave.push_back(ev);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy events");
     // synchronous on every path: copies from the caller's buffers are waited for
     auto drained = [&](sfoc_status st) {
         cudaStreamSynchronize(ctx->copy_stream);
@@ -1020,39 +1013,61 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
     // every copy after the work already queued on the context stream
     e = cudaEventRecord(ctx->ev_start, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_start, 0);
-    char* b = static_cast<char*>(ctx->hstage);
-    for (int k = 0; k < K && e == cudaSuccess; ++k) {
-        for (int i = lo[k]; i < lo[k + 1] && e == cudaSuccess; ++i) {
-            const size_t br = sizeof(float) * (size_t)Hr[i] * Wr[i], bs = sizeof(float) * (size_t)Hs[i] * Ws[i];
-            const size_t bp = sizeof(int32_t) * 2 * (size_t)n_points[i];
-            dr[i] = reinterpret_cast<const float*>(b);
-            e = cudaMemcpyAsync(b, h_refs[i], br, cudaMemcpyHostToDevice, ctx->copy_stream);
-            b += align256(br);
-            ds[i] = reinterpret_cast<const float*>(b);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(b, h_sens[i], bs, cudaMemcpyHostToDevice, ctx->copy_stream);
-            b += align256(bs);
-            dp[i] = reinterpret_cast<const int32_t*>(b);
-            if (e == cudaSuccess && bp) e = cudaMemcpyAsync(b, h_points[i], bp, cudaMemcpyHostToDevice, ctx->copy_stream);
-            b += align256(bp);
-            dout[i] = reinterpret_cast<fastncc_result*>(b);
-            b += align256(sizeof(fastncc_result) * (size_t)n_points[i]);
+    // the point sets first (small, and the matching needs all of them), then
+    // the images in the plan's image order (reference of pair i = image 2i,
+    // sensed = 2i + 1), with an event after each SFOC wave's last image
+    for (int i = 0; i < n_pairs && e == cudaSuccess; ++i)
+        if (n_points[i] > 0)
+            e = cudaMemcpyAsync(const_cast<int32_t*>(dp[i]), h_points[i], sizeof(int32_t) * 2 * (size_t)n_points[i],
+                                cudaMemcpyHostToDevice, ctx->copy_stream);
+    auto copy_image = [&](int im) {
+        const int i = im >> 1;
+        if (im & 1)
+            return cudaMemcpyAsync(const_cast<float*>(ds[i]), h_sens[i], sizeof(float) * (size_t)Hs[i] * Ws[i],
+                                   cudaMemcpyHostToDevice, ctx->copy_stream);
+        return cudaMemcpyAsync(const_cast<float*>(dr[i]), h_refs[i], sizeof(float) * (size_t)Hr[i] * Wr[i],
+                               cudaMemcpyHostToDevice, ctx->copy_stream);
+    };
+    if (by_wave) {
+        for (size_t w = 0; w < plan->waves.size() && e == cudaSuccess; ++w) {
+            const Wave& wv = plan->waves[w];
+            for (int im = wv.img0; im < wv.img0 + wv.n_img && e == cudaSuccess; ++im) e = copy_image(im);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_wave[w], ctx->copy_stream);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_chunk[k], ctx->copy_stream);
+    } else {
+        for (int im = 0; im < 2 * n_pairs && e == cudaSuccess; ++im) e = copy_image(im);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_wave[0], ctx->copy_stream);
     }
     if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "host to device copy"));
-    for (int k = 0; k < K; ++k) {
-        const int j = lo[k], n = lo[k + 1] - lo[k];
-        e = cudaStreamWaitEvent(ctx->stream, ctx->ev_chunk[k], 0);
+    if (by_wave) {
+        // the plan's stages launched one by one, each SFOC wave after its images
+        for (size_t w = 0; w < plan->waves.size() && e == cudaSuccess; ++w) {
+            const Wave& wv = plan->waves[w];
+            e = cudaStreamWaitEvent(ctx->stream, ctx->ev_wave[w], 0);
+            if (e != cudaSuccess) break;
+            StageScope sc(ctx, ST_STEER, 3);
+            e = launch_sfoc_batch(reinterpret_cast<const ImgJob*>(plan->dbuf + wv.tab), wv.n_img,
+                                  reinterpret_cast<const int*>(plan->dbuf + wv.steer_begin), wv.steer_ctas,
+                                  reinterpret_cast<const int*>(plan->dbuf + wv.smooth_begin), wv.smooth_ctas,
+                                  plan->st, plan->sm, ctx->stream);
+        }
+        if (e == cudaSuccess) e = enqueue_match_head(ctx, plan, ctx->stream);
+        if (e == cudaSuccess) e = enqueue_match_tail(ctx, plan, ctx->stream);
+        if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "batch launch"));
+    } else {
+        // first call with this signature: everything copied, then the plan is
+        // built and run (and its graph captured) as fastncc_register_batch does
+        e = cudaStreamWaitEvent(ctx->stream, ctx->ev_wave[0], 0);
         if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "cudaStreamWaitEvent"));
-        s = fastncc_register_batch(ctx, n, dr.data() + j, Hr + j, Wr + j, ds.data() + j, Hs + j, Ws + j, dp.data() + j,
-                                   n_points + j, template_size + j, search_radius + j, &prm, opts, dout.data() + j);
+        s = fastncc_register_batch(ctx, n_pairs, dr.data(), Hr, Wr, ds.data(), Hs, Ws, dp.data(), n_points,
+                                   template_size, search_radius, &prm, opts, dout.data());
         if (s != SFOC_OK) return drained(s);
-        for (int i = j; i < j + n && e == cudaSuccess; ++i)
-            if (n_points[i] > 0)
-                e = cudaMemcpyAsync(h_outs[i], dout[i], sizeof(fastncc_result) * (size_t)n_points[i],
-                                    cudaMemcpyDeviceToHost, ctx->stream);
-        if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "device to host copy"));
     }
+    for (int i = 0; i < n_pairs && e == cudaSuccess; ++i)
+        if (n_points[i] > 0)
+            e = cudaMemcpyAsync(h_outs[i], dout[i], sizeof(fastncc_result) * (size_t)n_points[i],
+                                cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "device to host copy"));
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
     return SFOC_OK;

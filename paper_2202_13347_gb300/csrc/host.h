@@ -57,7 +57,7 @@ struct sfoc_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_copied = nullptr;
     cudaEvent_t ev_switch = nullptr;  // orders a new stream after the previous one
-    cudaEvent_t ev_chunk[4] = {nullptr, nullptr, nullptr, nullptr};  // host batch: chunk k's copies done
+    std::vector<cudaEvent_t> ev_wave;  // host batch: the images of SFOC wave w copied (last: every copy)
     // per-stage timing
     bool timing = false;
     struct Ev {

@@ -495,7 +495,7 @@ sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx) {
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
     if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
     if (ctx->ev_switch) cudaEventDestroy(ctx->ev_switch);
-    for (auto ev : ctx->ev_chunk)
+    for (auto ev : ctx->ev_wave)
         if (ev) cudaEventDestroy(ev);
     for (BatchPlan* p : ctx->plans) destroy_plan(p);
     cudaFree(ctx->hstage);
