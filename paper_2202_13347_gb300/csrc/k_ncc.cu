@@ -65,11 +65,29 @@ __global__ void __launch_bounds__(kStatThreads)
                     ty0 + m + R <= Hr && tx0 + m + R <= Wr;
     u64 a1 = 0, a2 = 0;  // modulo 2^64, like the integral images
     if (ok) {
-        for (int r = warp; r < m; r += kStatThreads / 32) {
-            const size_t row = (size_t)(ty0 + r) * pitch + tx0;
-            for (int c = lane; c < m; c += 32) {
-                a1 += int_quant(s1[row + c]);
-                a2 += int_quant(s2[row + c]);
+        // (row, column) pairs of the template taken 4 at a time per thread, so
+        // that several loads are in flight before the first sum needs one
+        const int ncol = (m + 31) >> 5;          // column blocks of 32 per row
+        const int ntask = m * ncol;               // (row, column block) tasks
+        for (int t0 = warp; t0 < ntask; t0 += 4 * (kStatThreads / 32)) {
+            float v1[4], v2[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u * (kStatThreads / 32);
+                const int r = t / ncol, c = (t - r * ncol) * 32 + lane;
+                const bool in = t < ntask && c < m;
+                const size_t at = (size_t)(ty0 + (in ? r : 0)) * pitch + tx0 + (in ? c : 0);
+                v1[u] = in ? s1[at] : 0.f;
+                v2[u] = in ? s2[at] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u * (kStatThreads / 32);
+                const int r = t / ncol, c = (t - r * ncol) * 32 + lane;
+                if (t < ntask && c < m) {
+                    a1 += int_quant(v1[u]);
+                    a2 += int_quant(v2[u]);
+                }
             }
         }
     }
