@@ -142,25 +142,29 @@ __global__ void k_int_carry(const __grid_constant__ IntJob one, const IntJob* __
     const IntLayout& L = J.L;
     size_t i = local * (size_t)blockDim.x + threadIdx.x;
     size_t ncol = 2 * (size_t)L.W, nrow = 2 * (size_t)L.H;
-    if (i < ncol) {
-        int p = (int)(i / L.W), x = (int)(i % L.W);
+    // a line's values in groups of 8 loaded before any of them is replaced,
+    // so the loads of a group overlap (one memory latency per group)
+    auto carry = [](u64* __restrict__ base, size_t stride, int n) {
         u64 run = 0;
-        for (int ty = 0; ty < L.nty; ++ty) {
-            u64* q = &L.colsum[((size_t)p * L.nty + ty) * L.W + x];
-            u64 v = *q;
-            *q = run;
-            run += v;
+        for (int t0 = 0; t0 < n; t0 += 8) {
+            u64 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = t0 + k < n ? base[(size_t)(t0 + k) * stride] : 0ull;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (t0 + k < n) {
+                    base[(size_t)(t0 + k) * stride] = run;
+                    run += v[k];
+                }
         }
+    };
+    if (i < ncol) {
+        const int p = (int)(i / L.W), x = (int)(i % L.W);
+        carry(&L.colsum[(size_t)p * L.nty * L.W + x], (size_t)L.W, L.nty);
     } else if (i < ncol + nrow) {
         i -= ncol;
-        int p = (int)(i / L.H), y = (int)(i % L.H);
-        u64 run = 0;
-        for (int tx = 0; tx < L.ntx; ++tx) {
-            u64* q = &L.rowsum[((size_t)p * L.ntx + tx) * L.H + y];
-            u64 v = *q;
-            *q = run;
-            run += v;
-        }
+        const int p = (int)(i / L.H), y = (int)(i % L.H);
+        carry(&L.rowsum[(size_t)p * L.ntx * L.H + y], (size_t)L.H, L.ntx);
     }
 }
 
