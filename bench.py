@@ -674,6 +674,15 @@ def run_batch_form(b, torch, ctx, pairs, form, steps, warmup, corr_name="auto"):
                 t_timed=(t_start, t_end))
 
 
+# DRAM bytes per processed point of a band-form class, by (template side,
+# band instance NQ), from one ncu capture of the kernel as it stands: the
+# 2048x2048 pair's 1000 points matched at m = 101, R = 40 (851 processed;
+# 745.06 MB read + 44.46 MB written per launch).  A batched class of the same
+# template side and instance gets this times its processed points (its radii
+# range over R 33-40).
+BAND_TRAFFIC_PER_POINT = {(101, 6): (745.062144e6 + 44.461312e6) / 851}
+
+
 def batch_roofline(form, pairs, r, pk):
     """Roofline of the dominant correlation kernel of a batched form: per
     class (one persistent launch), the algorithmic work of the points it
@@ -694,8 +703,13 @@ def batch_roofline(form, pairs, r, pk):
             ms = sum(r["scopes"][k:k + nl])
             k += nl
             fl = sum(class_flops(c["path"], c["cls"], pairs[i].m, pairs[i].R) * r["processed"][i] for i in c["pairs"])
+            tm = sorted({pairs[i].m for i in c["pairs"]})
+            tr = sorted({pairs[i].R for i in c["pairs"]})
+            per_pt = BAND_TRAFFIC_PER_POINT.get((tm[0], c["cls"])) if c["path"] == 5 and len(tm) == 1 else None
+            npts = sum(r["processed"][i] for i in c["pairs"])
             rows.append(dict(kernel=PATH_NAMES.get(c["path"], str(c["path"])), path=c["path"], cls=c["cls"],
-                             launches=nl, ms=ms, flops=fl, items=c["items"]))
+                             launches=nl, ms=ms, flops=fl, items=c["items"], m=tm, R=[tr[0], tr[-1]],
+                             traffic=per_pt * npts / nl if per_pt else None))
     out = []
     for row in rows:
         tc = row["path"] in (3, 4, 5)
@@ -706,7 +720,7 @@ def batch_roofline(form, pairs, r, pk):
     top = max(out, key=lambda x: x["ms"])
     tc = top["path"] in (3, 4, 5)
     return {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": "TFLOP/s",
-            "frac": top["frac"], "traffic": None, "kernel": top["kernel"] + " class %d" % top["cls"],
+            "frac": top["frac"], "traffic": top.get("traffic"), "kernel": top["kernel"] + " class %d" % top["cls"],
             "launch_ms": top["ms"] / max(1, top["launches"]),
             "peak_src": ("bf16_tflops_sustained (%s): timed inside a long step" % pk["src"]) if tc else src32,
             "work": ("2*m^2*z*(2R+1)^2 flop per processed point" if top["path"] != 6 else

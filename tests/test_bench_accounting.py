@@ -116,3 +116,21 @@ def test_fast_roofline():
     assert r["bound"] == "alu" and r["peak"] == pytest.approx(40.28, rel=1e-3)
     assert r["achieved"] == pytest.approx(8.906, rel=2e-3) and r["frac"] == pytest.approx(0.2211, rel=3e-3)
     assert r["hbm_gbs"] == pytest.approx(199.0, rel=2e-3)
+
+
+def test_batch_roofline_scales_the_band_capture_to_a_class():
+    """The batched line's `traffic`: a band-form class of one template side
+    with a capture of its instance gets the capture's bytes per processed
+    point times the class's processed points (per launch); classes of other
+    sizes, or of several template sides, get none."""
+    pairs = [_pair(101, 40), _pair(101, 35), _pair(81, 20)]
+    info = {"classes": [{"path": 5, "cls": 6, "launches": 1, "pairs": [0, 1], "items": 30},
+                        {"path": 5, "cls": 4, "launches": 1, "pairs": [2], "items": 10}]}
+    r = {"info": info, "scopes": [20.0, 2.0], "processed": [20, 10, 10]}
+    pk = {"bf16": 1957.5, "bf16_sus": 1761.3, "src": "measured"}
+    line = bench.batch_roofline("bf16batch", pairs, r, pk)
+    per_pt = bench.BAND_TRAFFIC_PER_POINT[(101, 6)]
+    assert per_pt == pytest.approx(789.52e6 / 851, rel=1e-4)
+    assert line["kernel"].endswith("class 6") and line["traffic"] == pytest.approx(per_pt * 30)
+    small = [c for c in line["classes"] if c["cls"] == 4][0]
+    assert small["traffic"] is None and small["m"] == [81] and small["R"] == [20, 20]
