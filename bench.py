@@ -398,9 +398,27 @@ def cpu_baseline(pair, n_sample=64, seed=99):
     dt = time.perf_counter() - t0
     matched = int((o["status"] == 0).sum())
     mpix, region = oracle_sfoc_mpix(pair)
-    return dict(value=matched / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
-                sample="%d of %d points (seeded), FP64 SFOC on their windows only, Eq. 8 NCC" % (len(idx), len(pair.points)),
-                seconds=dt, sfoc_mpix_s=mpix, sfoc_sample=region)
+    cpu = dict(value=matched / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+               sample="%d of %d points (seeded), FP64 SFOC on their windows only, Eq. 8 NCC" % (len(idx), len(pair.points)),
+               seconds=dt, sfoc_mpix_s=mpix, sfoc_sample=region)
+    return cpu, (idx, o)
+
+
+def form_parity(raw, idx, o):
+    """A form's results on the oracle's sampled points against the unrounded
+    FP64 oracle: valid points, offsets equal, near ties (the oracle's
+    best-vs-second margin <= 2e-4) and the largest NCC difference where the
+    offsets agree."""
+    import numpy as np
+    g = raw.cpu().numpy()[idx]
+    ok = np.isin(o["status"], [0, 3])
+    same = ok & (g[:, 0] == o["dx"]) & (g[:, 1] == o["dy"])
+    err = 0.0
+    if same.any():
+        gn = g[:, 2].view(np.float32).astype(np.float64)
+        err = float(np.abs(gn[same] - o["ncc"][same]).max())
+    return dict(points=int(len(idx)), valid=int(ok.sum()), offsets_equal=int(same.sum()),
+                near_ties=int((ok & (o["margin"] <= 2e-4)).sum()), ncc_err_max_vs_fp64=err)
 
 
 def oracle_sfoc_mpix(pair, side=512):
@@ -1100,7 +1118,13 @@ def main():
         ransac, quality = (rq, None) if isinstance(rq, dict) else rq
         fast = aux(run_fast, torch, ctx, pair, pk["hbm"], 10, 32, 0.05, pk)
         if world == 1 and not args.no_cpu_baseline:
-            cpu = aux(cpu_baseline, pair)
+            cb = aux(cpu_baseline, pair)
+            if isinstance(cb, tuple):
+                cpu, (idx, o) = cb
+                for f in summ:
+                    summ[f]["parity"] = aux(form_parity, results[f]["raw"], idx, o)
+            else:
+                cpu = cb
     if rank != 0:
         return
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1109,6 +1133,7 @@ def main():
             "data": "synthetic", "config": dict(config, form=main_form), "roofline": main["roofline"],
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
             "sfoc_mpix_s": main["sfoc_mpix_s"], "stage_ms_per_step": main["stage_ms_per_step"],
+            "parity": main.get("parity"),
             "forms": {f: {k: v for k, v in s.items() if k not in ("clocks",)} for f, s in summ.items()},
             "ransac": ransac, "match_quality": quality, "fast": fast, "peaks": {
                 "hbm_gbs": pk["hbm"], "bf16_tflops": pk["bf16"], "src": pk["src"] + " (MEASURED_PEAKS.json)",

@@ -171,7 +171,14 @@ def test_line_has_every_contract_key(monkeypatch, capsys):
         assert k in line["e2e"], k
     assert line["e2e"]["h2d_bytes_per_step"] > 0
     assert set(line["forms"]) == {"bf16", "f32", "f32direct"}
+    # every form's results on the oracle's sampled points against the FP64 oracle
+    for f in line["forms"]:
+        par = line["forms"][f]["parity"]
+        for k in ("points", "valid", "offsets_equal", "near_ties", "ncc_err_max_vs_fp64"):
+            assert k in par, (f, k)
+        assert par["points"] > 0
     best = max(line["forms"], key=lambda f: line["forms"][f]["value"])
+    assert line["parity"] == line["forms"][best]["parity"]
     assert line["value"] == line["forms"][best]["value"] and line["config"]["form"] == best
     assert line["forms"]["f32direct"]["roofline"]["kernel"].startswith("k_corr_f32")
     assert line["gpu_launches"] == 13 * 3
