@@ -766,7 +766,21 @@ def batch_e2e(b, torch, ctx, pairs, p, corr, steps):
     matched = sum(int((o[:, 5] == 0).sum()) for o in outs)
     h2d = sum(x.numel() * 4 for x in h_refs + h_sens + h_pts)
     d2h = sum(o.numel() * 4 for o in outs)
-    return dict(ms=1e3 * sum(t), steps=steps, matched=matched, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+    # the copy rate these host buffers get on their own (outside the timed calls)
+    gbs = None
+    try:
+        dev = [torch.empty_like(x, device="cuda") for x in h_refs + h_sens]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d, x in zip(dev, h_refs + h_sens):
+            d.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        gbs = round(sum(x.numel() * 4 for x in h_refs + h_sens) / (time.perf_counter() - t0) / 1e9, 1)
+        del dev
+    except RuntimeError:  # a side figure: no device copy, no rate
+        pass
+    return dict(ms=1e3 * sum(t), steps=steps, matched=matched, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                call_ms=[round(1e3 * x, 1) for x in t], h2d_gbs_alone=gbs)
 
 
 def batch_oracle_sample(pairs, seed, n_pairs=16, per_pair=2):
@@ -942,7 +956,8 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
         ms_max, matched_all = reduce_over_ranks(dist, torch, er["ms"], er["matched"] * er["steps"], "cuda")
         e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=er["h2d_bytes_per_step"],
                    d2h_bytes_per_step=er["d2h_bytes_per_step"], ms_per_step=ms_max / er["steps"],
-                   call="fastncc_register_batch_host (pinned host buffers)")
+                   call="fastncc_register_batch_host (pinned host buffers)", call_ms=er["call_ms"],
+                   h2d_gbs_alone=er["h2d_gbs_alone"])
     gathered = None
     if strong:  # the final collective: every rank's results to rank 0, in the job's order
         import numpy as np
