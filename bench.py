@@ -758,11 +758,13 @@ def batch_e2e(b, torch, ctx, pairs, p, corr, steps):
     ms_, Rs_ = [q.m for q in pairs], [q.R for q in pairs]
     for _ in range(2):  # plan and graph of the staged buffers
         ctx.register_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs)
+    built0 = ctx.plan_info().get("plans_built")
     t = []
     for _ in range(steps):
         t0 = time.perf_counter()
         ctx.register_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs)
         t.append(time.perf_counter() - t0)
+    built1 = ctx.plan_info().get("plans_built")
     matched = sum(int((o[:, 5] == 0).sum()) for o in outs)
     h2d = sum(x.numel() * 4 for x in h_refs + h_sens + h_pts)
     d2h = sum(o.numel() * 4 for o in outs)
@@ -780,7 +782,8 @@ def batch_e2e(b, torch, ctx, pairs, p, corr, steps):
     except RuntimeError:  # a side figure: no device copy, no rate
         pass
     return dict(ms=1e3 * sum(t), steps=steps, matched=matched, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
-                call_ms=[round(1e3 * x, 1) for x in t], h2d_gbs_alone=gbs)
+                call_ms=[round(1e3 * x, 1) for x in t], h2d_gbs_alone=gbs,
+                plans_built_in_timed_calls=(built1 - built0) if built0 is not None and built1 is not None else None)
 
 
 def batch_oracle_sample(pairs, seed, n_pairs=16, per_pair=2):
@@ -957,7 +960,7 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
         e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=er["h2d_bytes_per_step"],
                    d2h_bytes_per_step=er["d2h_bytes_per_step"], ms_per_step=ms_max / er["steps"],
                    call="fastncc_register_batch_host (pinned host buffers)", call_ms=er["call_ms"],
-                   h2d_gbs_alone=er["h2d_gbs_alone"])
+                   h2d_gbs_alone=er["h2d_gbs_alone"], plans_built_in_timed_calls=er["plans_built_in_timed_calls"])
     gathered = None
     if strong:  # the final collective: every rank's results to rank 0, in the job's order
         import numpy as np

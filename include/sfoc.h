@@ -401,7 +401,8 @@ SFOC_API sfoc_status sfoc_ctx_release_plans(sfoc_ctx* ctx);
  * pairs, items, whether it has a graph and how many kernels one run
  * launches, the SFOC waves, and per correlation class (in launch order) its
  * sfoc_corr_path, kernel class, items, launches and pairs (indices into the
- * call's arrays, in the order its items are listed).  "{}" without a plan.
+ * call's arrays, in the order its items are listed); plans_built: the batch
+ * plans the context has built so far.  Without a plan only plans_built.
  * *len receives the bytes needed (with the zero); buf NULL writes nothing
  * else; SFOC_ERR_INVALID_ARG when cap is smaller. */
 SFOC_API sfoc_status sfoc_ctx_plan_info(const sfoc_ctx* ctx, char* buf, size_t cap, size_t* len);

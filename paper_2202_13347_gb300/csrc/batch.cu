@@ -94,14 +94,6 @@ struct KeyWriter {
     std::vector<uint64_t> k;
     void u(uint64_t v) { k.push_back(v); }
     void p(const void* v) { k.push_back((uint64_t)(uintptr_t)v); }
-    void bytes(const void* b, size_t n) {
-        const unsigned char* c = static_cast<const unsigned char*>(b);
-        for (size_t i = 0; i < n; i += 8) {
-            uint64_t w = 0;
-            memcpy(&w, c + i, n - i < 8 ? n - i : 8);
-            k.push_back(w);
-        }
-    }
 };
 
 BatchPlan* find_plan(sfoc_ctx* ctx, const std::vector<uint64_t>& key) {
@@ -614,6 +606,7 @@ sfoc_status make_and_run(sfoc_ctx* ctx, int kind, std::vector<uint64_t>&& key, c
     BatchPlan* p = new (std::nothrow) BatchPlan();
     if (!p) return fail(ctx, SFOC_ERR_OOM, "host allocation");
     p->kind = kind;
+    ++ctx->plans_built;
     p->key = std::move(key);
     Layout lay;
     if (bin) {
@@ -710,7 +703,27 @@ sfoc_status make_and_run(sfoc_ctx* ctx, int kind, std::vector<uint64_t>&& key, c
     return run_plan(ctx, p);
 }
 
-void key_params(KeyWriter& k, const sfoc_params& p) { k.bytes(&p, sizeof(p)); }
+// field by field: the struct's padding bytes (and the unused tails of its
+// arrays) hold whatever the caller's copy left there, so hashing its raw
+// bytes could key two equal parameter sets apart
+void key_params(KeyWriter& k, const sfoc_params& p) {
+    auto dbl = [&](double v) {
+        uint64_t w;
+        memcpy(&w, &v, sizeof(w));
+        k.u(w);
+    };
+    k.u((uint64_t)(uint32_t)p.n_scales);
+    for (int i = 0; i < p.n_scales && i < 8; ++i) dbl(p.scales[i]);
+    dbl(p.sigma2);
+    k.u((uint64_t)(uint32_t)p.n_orient << 32 | (uint32_t)p.n_dil);
+    for (int i = 0; i < p.n_dil && i < 4; ++i) k.u((uint64_t)(uint32_t)p.dil[i]);
+    dbl(p.sigma_d1);
+    dbl(p.sigma_d2);
+    dbl(p.eps);
+    dbl(p.radius_mult);
+    k.u((uint64_t)(uint32_t)p.rectify << 32 | (uint32_t)p.first_order_only);
+    k.u((uint64_t)(uint32_t)p.cube_dtype);
+}
 
 void key_cube(KeyWriter& k, const sfoc_cube* c) {
     k.p(c);
@@ -1077,12 +1090,15 @@ int sfoc_ctx_plan_count(const sfoc_ctx* ctx) { return ctx ? (int)ctx->plans.size
 
 sfoc_status sfoc_ctx_plan_info(const sfoc_ctx* ctx, char* buf, size_t cap, size_t* len) {
     if (!ctx || !len) return SFOC_ERR_INVALID_ARG;
-    std::string j = "{}";
+    std::string j = "{\"plans_built\": " + std::to_string((long long)ctx->plans_built) + "}";
     if (!ctx->plans.empty()) {
         const BatchPlan* p = ctx->plans.back();
         char t[256];
-        snprintf(t, sizeof(t), "{\"kind\": %d, \"pairs\": %d, \"items\": %d, \"graph\": %s, \"launches\": %d, ",
-                 p->kind, (int)p->jobs.size(), p->n_items, p->exec ? "true" : "false", p->launches);
+        snprintf(t, sizeof(t),
+                 "{\"plans_built\": %lld, \"kind\": %d, \"pairs\": %d, \"items\": %d, \"graph\": %s, "
+                 "\"launches\": %d, ",
+                 (long long)ctx->plans_built, p->kind, (int)p->jobs.size(), p->n_items, p->exec ? "true" : "false",
+                 p->launches);
         j = t;
         j += "\"build_batched\": ";
         j += p->build_batched ? "true" : "false";

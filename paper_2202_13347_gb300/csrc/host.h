@@ -75,6 +75,7 @@ struct sfoc_ctx {
     // batch plans (tables, owned cubes, captured graphs), most recent last
     std::vector<sfoc::BatchPlan*> plans;
     size_t max_plans = 2;
+    int64_t plans_built = 0;  // batch plans built over the context's life
     // device staging of fastncc_register_batch_host (images, points, results)
     void* hstage = nullptr;
     size_t hstage_bytes = 0;
