@@ -138,6 +138,27 @@ def test_register_batch_host_equals_device(b, ctx, small_batch):
     ctx.release_plans()
 
 
+def test_register_batch_host_keeps_its_plan(b, ctx, small_batch):
+    """Repeated host-buffer calls with the same buffers find the plan the
+    first one built (no plan is built again; the parameters are passed as a
+    fresh struct each time, so the plan key must not depend on its padding),
+    and give the same results every time."""
+    batch = small_batch[:4]
+    ms, Rs = [q.m for q in batch], [q.R for q in batch]
+    h_refs = [torch.from_numpy(q.ref).pin_memory() for q in batch]
+    h_sens = [torch.from_numpy(q.sen).pin_memory() for q in batch]
+    h_pts = [torch.from_numpy(q.points).pin_memory() for q in batch]
+    first = ctx.register_batch_host(h_refs, h_sens, h_pts, ms, Rs, p=b.params(dtype=b.DTYPE_BF16))
+    first = [o.clone() for o in first]
+    built = ctx.plan_info()["plans_built"]
+    for _ in range(3):
+        outs = ctx.register_batch_host(h_refs, h_sens, h_pts, ms, Rs, p=b.params(dtype=b.DTYPE_BF16))
+        for a, c in zip(first, outs):
+            assert torch.equal(a, c)
+    assert ctx.plan_info()["plans_built"] == built
+    ctx.release_plans()
+
+
 @pytest.mark.parametrize("dt", ["f32", "bf16"])
 def test_register_batch_against_oracle(b, ctx, orc, small_batch, dt):
     """A seeded sample of 6 points per pair against the FP64 oracle (BF16:
