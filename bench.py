@@ -748,16 +748,22 @@ def batch_roofline(form, pairs, r, pk):
 
 
 def batch_e2e(b, torch, ctx, pairs, p, corr, steps):
-    """The same step through the C ABI from host buffers (pinned): every
-    image and point set copied in and every result copied out inside the
-    timed call (fastncc_register_batch_host, synchronous)."""
+    """The same step through the C ABI from host buffers (pinned): each
+    step's images and point sets are copied in and its results copied out
+    inside the timed region.  The steps are a stream of submissions
+    (fastncc_submit_batch_host): step k + 1 is submitted before step k's
+    results are waited for (fastncc_wait_batch_host), so its copies run
+    while step k is matched; the region ends when the last step's results
+    are on the host.  Alternate steps write alternate result buffers.  The
+    synchronous call (fastncc_register_batch_host, one step per call) is
+    timed afterwards as a side figure."""
     h_refs = [torch.from_numpy(q.ref).pin_memory() for q in pairs]
     h_sens = [torch.from_numpy(q.sen).pin_memory() for q in pairs]
     h_pts = [torch.from_numpy(q.points).pin_memory() for q in pairs]
-    outs = [torch.empty((len(q.points), 6), dtype=torch.int32).pin_memory() for q in pairs]
+    outs = [[torch.empty((len(q.points), 6), dtype=torch.int32).pin_memory() for q in pairs] for _ in range(2)]
     ms_, Rs_ = [q.m for q in pairs], [q.R for q in pairs]
     for _ in range(2):  # plan and graph of the staged buffers
-        ctx.register_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs)
+        ctx.register_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs[0])
     built0 = ctx.plan_info().get("plans_built")
     # Python's cyclic garbage collector stays off while the calls are timed (as
     # timeit does): a full collection over the benchmark's own objects is not
@@ -765,33 +771,49 @@ def batch_e2e(b, torch, ctx, pairs, p, corr, steps):
     import gc
     gc.collect()
     gc.disable()
-    t = []
+    done = []
     try:
+        tickets = []
+        t0 = time.perf_counter()
+        for k in range(steps):
+            t, _ = ctx.submit_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs[k % 2])
+            tickets.append(t)
+            if k >= 1:
+                ctx.wait_batch_host(tickets[k - 1])
+                done.append(time.perf_counter())
+        ctx.wait_batch_host(tickets[-1])
+        done.append(time.perf_counter())
+        total = done[-1] - t0
+        sync_t = []
         for _ in range(steps):
-            t0 = time.perf_counter()
-            ctx.register_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs)
-            t.append(time.perf_counter() - t0)
+            s0 = time.perf_counter()
+            ctx.register_batch_host(h_refs, h_sens, h_pts, ms_, Rs_, p=p, corr_path=corr, outs=outs[0])
+            sync_t.append(time.perf_counter() - s0)
     finally:
         gc.enable()
     built1 = ctx.plan_info().get("plans_built")
-    matched = sum(int((o[:, 5] == 0).sum()) for o in outs)
+    last = outs[(steps - 1) % 2]
+    matched = sum(int((o[:, 5] == 0).sum()) for o in last)
+    same = all(torch.equal(x, y) for x, y in zip(outs[0], outs[1])) if steps >= 2 else None
     h2d = sum(x.numel() * 4 for x in h_refs + h_sens + h_pts)
-    d2h = sum(o.numel() * 4 for o in outs)
+    d2h = sum(o.numel() * 4 for o in last)
     # the copy rate these host buffers get on their own (outside the timed calls)
     gbs = None
     try:
         dev = [torch.empty_like(x, device="cuda") for x in h_refs + h_sens]
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        c0 = time.perf_counter()
         for d, x in zip(dev, h_refs + h_sens):
             d.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
-        gbs = round(sum(x.numel() * 4 for x in h_refs + h_sens) / (time.perf_counter() - t0) / 1e9, 1)
+        gbs = round(sum(x.numel() * 4 for x in h_refs + h_sens) / (time.perf_counter() - c0) / 1e9, 1)
         del dev
     except RuntimeError:  # a side figure: no device copy, no rate
         pass
-    return dict(ms=1e3 * sum(t), steps=steps, matched=matched, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
-                call_ms=[round(1e3 * x, 1) for x in t], h2d_gbs_alone=gbs,
+    return dict(ms=1e3 * total, steps=steps, matched=matched, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                step_done_ms=[round(1e3 * (done[i] - (done[i - 1] if i else t0)), 1) for i in range(len(done))],
+                sync_call_ms=[round(1e3 * x, 1) for x in sync_t], results_equal_across_steps=same,
+                h2d_gbs_alone=gbs,
                 plans_built_in_timed_calls=(built1 - built0) if built0 is not None and built1 is not None else None)
 
 
@@ -974,7 +996,10 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
         ms_max, matched_all = reduce_over_ranks(dist, torch, er["ms"], er["matched"] * er["steps"], "cuda")
         e2e = dict(value=matched_all / (ms_max * 1e-3), unit=UNIT, h2d_bytes_per_step=er["h2d_bytes_per_step"],
                    d2h_bytes_per_step=er["d2h_bytes_per_step"], ms_per_step=ms_max / er["steps"],
-                   call="fastncc_register_batch_host (pinned host buffers)", call_ms=er["call_ms"],
+                   call="fastncc_submit_batch_host + fastncc_wait_batch_host (pinned host buffers; step k+1 "
+                        "submitted before step k is waited for)",
+                   step_done_ms=er["step_done_ms"], results_equal_across_steps=er["results_equal_across_steps"],
+                   sync_call="fastncc_register_batch_host", sync_call_ms=er["sync_call_ms"],
                    h2d_gbs_alone=er["h2d_gbs_alone"], plans_built_in_timed_calls=er["plans_built_in_timed_calls"])
     gathered = None
     if strong:  # the final collective: every rank's results to rank 0, in the job's order

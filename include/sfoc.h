@@ -377,21 +377,52 @@ SFOC_API sfoc_status fastncc_register_batch(sfoc_ctx* ctx, int n_pairs, const fl
 
 /* fastncc_register_batch from host buffers: copies every image and point
  * set into a device staging buffer kept by the context, runs the batch and
- * copies every pair's results to h_outs[i] before returning (synchronous).
+ * copies every pair's results to h_outs[i] before returning (synchronous:
+ * fastncc_submit_batch_host, then fastncc_wait_batch_host).
  * The first call with a signature copies everything, then builds the plan
- * (as fastncc_register_batch does); later calls copy the point sets, then
- * the images in the order of the plan's SFOC waves on a second stream, and
- * each wave's SFOC launch waits only for its own images, so the copies of
- * the later waves run while the earlier waves are built.  (Pinned host
+ * (as fastncc_register_batch does); later calls copy the images in the
+ * order of the plan's SFOC waves on a second stream, then the point sets,
+ * and each wave's SFOC launch waits only for its own images, so the copies
+ * of the later waves run while the earlier waves are built.  (Pinned host
  * buffers let the copies overlap.)  These runs launch the plan's kernels
  * one by one rather than replaying its graph.  A staging buffer that has to
- * grow drops the context's plans. */
+ * grow waits for every submission in flight and drops the context's plans. */
 SFOC_API sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs,
                                                  const int* Hr, const int* Wr, const float* const* h_sens,
                                                  const int* Hs, const int* Ws, const int32_t* const* h_points,
                                                  const int* n_points, const int* template_size,
                                                  const int* search_radius, const sfoc_params* p,
                                                  const fastncc_opts* opts, fastncc_result* const* h_outs);
+
+/* The same batch, enqueued without waiting, for a stream of batches (the
+ * paper's per-point loop of Sec. 3.2.2 over many image pairs, fed from host
+ * memory).  Arguments as fastncc_register_batch_host; *ticket receives the
+ * submission's number (1, 2, ...; 0 for an empty batch, which enqueues
+ * nothing).  The submission is ordered against the previous one by events
+ * only: its images are copied in once the previous submission's SFOC
+ * launches have read the staged ones, its point sets once the previous
+ * results are out, so its copies run while the previous batch is still
+ * being matched.  The host buffers (inputs unchanged, outputs unread) must
+ * stay valid until fastncc_wait_batch_host(ticket) returns; they must be
+ * pinned for the call to return before the copies end (pageable buffers
+ * make the runtime copy synchronously).  The first submission with a
+ * signature builds its plan and runs as the synchronous call does.
+ * Errors: as fastncc_register_batch_host, SFOC_ERR_INVALID_ARG for a NULL
+ * ticket; on an error every copy and launch in flight has ended and no
+ * ticket is issued. */
+SFOC_API sfoc_status fastncc_submit_batch_host(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs,
+                                               const int* Hr, const int* Wr, const float* const* h_sens,
+                                               const int* Hs, const int* Ws, const int32_t* const* h_points,
+                                               const int* n_points, const int* template_size,
+                                               const int* search_radius, const sfoc_params* p,
+                                               const fastncc_opts* opts, fastncc_result* const* h_outs,
+                                               int64_t* ticket);
+/* Blocks until submission `ticket` has copied its results to its h_outs
+ * (when more than four submissions are outstanding it may also wait for a
+ * later one).  Ticket 0 returns at once; a ticket not yet issued by this
+ * context is SFOC_ERR_INVALID_ARG.  A bounded device wait that expired is
+ * reported by sfoc_ctx_sync, as for the other calls. */
+SFOC_API sfoc_status fastncc_wait_batch_host(sfoc_ctx* ctx, int64_t ticket);
 
 /* Number of batch plans the context holds; frees them all (waits for the
  * context's stream first). */

@@ -112,6 +112,12 @@ _SIGS = {
                                               C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_P),
                                               C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                               C.POINTER(Params), C.POINTER(Opts), C.POINTER(_P)]),
+    "fastncc_submit_batch_host": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                            C.POINTER(_P), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_P),
+                                            C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                            C.POINTER(Params), C.POINTER(Opts), C.POINTER(_P),
+                                            C.POINTER(C.c_int64)]),
+    "fastncc_wait_batch_host": (C.c_int, [_P, C.c_int64]),
     "sfoc_ctx_plan_count": (C.c_int, [_P]),
     "sfoc_ctx_plan_info": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "sfoc_ctx_stage_scopes": (C.c_int, [_P, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
@@ -503,10 +509,9 @@ class Context:
             C.byref(p) if p is not None else None, C.byref(o), (C.c_void_p * n)(*[t.data_ptr() for t in outs])))
         return outs
 
-    def register_batch_host(self, refs, sens, points, template_sizes, search_radii, p: Params = None,
-                            corr_path=CORR_AUTO, outs=None):
-        """fastncc_register_batch_host: host (ideally pinned) tensors in,
-        host result tensors out (synchronous)."""
+    def _host_batch_args(self, refs, sens, points, template_sizes, search_radii, p, corr_path, outs):
+        """The C arguments of the host-buffer batch calls (after the context),
+        and the result tensors."""
         n = len(refs)
         if not (len(sens) == len(points) == len(template_sizes) == len(search_radii) == n):
             raise ValueError("refs, sens, points, template_sizes and search_radii must have the same length")
@@ -524,14 +529,45 @@ class Context:
                 _check_host(o, "outs[%d]" % i, torch.int32)
                 _check_shape(o, "outs[%d]" % i, (points[i].shape[0], 6))
         o = Opts(int(corr_path), None)
-        self._chk(lib().fastncc_register_batch_host(
-            self.h, n, (C.c_void_p * n)(*[t.data_ptr() for t in refs]), (C.c_int * n)(*[t.shape[0] for t in refs]),
-            (C.c_int * n)(*[t.shape[1] for t in refs]), (C.c_void_p * n)(*[t.data_ptr() for t in sens]),
-            (C.c_int * n)(*[t.shape[0] for t in sens]), (C.c_int * n)(*[t.shape[1] for t in sens]),
-            (C.c_void_p * n)(*[t.data_ptr() for t in points]), (C.c_int * n)(*[t.shape[0] for t in points]),
-            (C.c_int * n)(*[int(v) for v in template_sizes]), (C.c_int * n)(*[int(v) for v in search_radii]),
-            C.byref(p) if p is not None else None, C.byref(o), (C.c_void_p * n)(*[t.data_ptr() for t in outs])))
+        args = (n, (C.c_void_p * n)(*[t.data_ptr() for t in refs]), (C.c_int * n)(*[t.shape[0] for t in refs]),
+                (C.c_int * n)(*[t.shape[1] for t in refs]), (C.c_void_p * n)(*[t.data_ptr() for t in sens]),
+                (C.c_int * n)(*[t.shape[0] for t in sens]), (C.c_int * n)(*[t.shape[1] for t in sens]),
+                (C.c_void_p * n)(*[t.data_ptr() for t in points]), (C.c_int * n)(*[t.shape[0] for t in points]),
+                (C.c_int * n)(*[int(v) for v in template_sizes]), (C.c_int * n)(*[int(v) for v in search_radii]),
+                C.byref(p) if p is not None else None, C.byref(o),
+                (C.c_void_p * n)(*[t.data_ptr() for t in outs]))
+        return args, outs
+
+    def register_batch_host(self, refs, sens, points, template_sizes, search_radii, p: Params = None,
+                            corr_path=CORR_AUTO, outs=None):
+        """fastncc_register_batch_host: host (ideally pinned) tensors in,
+        host result tensors out (synchronous)."""
+        args, outs = self._host_batch_args(refs, sens, points, template_sizes, search_radii, p, corr_path, outs)
+        self._chk(lib().fastncc_register_batch_host(self.h, *args))
         return outs
+
+    def submit_batch_host(self, refs, sens, points, template_sizes, search_radii, p: Params = None,
+                          corr_path=CORR_AUTO, outs=None):
+        """fastncc_submit_batch_host: enqueues the batch and returns
+        (ticket, outs) without waiting; the tensors are held until
+        wait_batch_host(ticket), and outs are valid only after it."""
+        args, outs = self._host_batch_args(refs, sens, points, template_sizes, search_radii, p, corr_path, outs)
+        t = C.c_int64()
+        self._chk(lib().fastncc_submit_batch_host(self.h, *args, C.byref(t)))
+        if t.value:
+            if not hasattr(self, "_held"):
+                self._held = {}
+            self._held[t.value] = (list(refs), list(sens), list(points), outs)
+        return t.value, outs
+
+    def wait_batch_host(self, ticket):
+        """fastncc_wait_batch_host: blocks until the submission's results are
+        in its outs; releases the tensors held for it (and for every earlier
+        submission, which ends before it)."""
+        self._chk(lib().fastncc_wait_batch_host(self.h, int(ticket)))
+        held = getattr(self, "_held", {})
+        for k in [k for k in held if k <= ticket]:
+            del held[k]
 
     @property
     def plan_count(self) -> int:

@@ -917,12 +917,22 @@ sfoc_status fastncc_register_batch(sfoc_ctx* ctx, int n_pairs, const float* cons
     return make_and_run(ctx, 2, std::move(k.k), &bin, &prm, cubes.data(), &mi, path, &p);
 }
 
-sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs, const int* Hr,
-                                        const int* Wr, const float* const* h_sens, const int* Hs, const int* Ws,
-                                        const int32_t* const* h_points, const int* n_points, const int* template_size,
-                                        const int* search_radius, const sfoc_params* pin, const fastncc_opts* opts,
-                                        fastncc_result* const* h_outs) {
-    if (!ctx) return SFOC_ERR_INVALID_ARG;
+namespace {
+
+// The host-buffer batch, enqueued without waiting: the point sets and images
+// copied into the context's staging buffer on the copy stream, the batch's
+// launches and the copies of the results into h_outs on the context stream.
+// Against the previous submission it is ordered by events alone: its images
+// are overwritten once that submission's SFOC launches are done with them,
+// its point sets once its results are out, so a submission's copies run
+// while the one before it is still matching.  *ticket = the submission's
+// number (0 when nothing was enqueued: an empty batch).
+sfoc_status host_batch_enqueue(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs, const int* Hr, const int* Wr,
+                               const float* const* h_sens, const int* Hs, const int* Ws,
+                               const int32_t* const* h_points, const int* n_points, const int* template_size,
+                               const int* search_radius, const sfoc_params* pin, const fastncc_opts* opts,
+                               fastncc_result* const* h_outs, int64_t* ticket) {
+    *ticket = 0;
     if (n_pairs < 0 || (n_pairs > 0 && (!h_refs || !Hr || !Wr || !h_sens || !Hs || !Ws || !h_points || !n_points ||
                                         !template_size || !search_radius || !h_outs)))
         return fail(ctx, SFOC_ERR_INVALID_ARG, "bad batch arguments");
@@ -971,8 +981,10 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
         if (s != SFOC_OK) return s;
     }
     if (need > ctx->hstage_bytes) {
-        // the staging buffer moves: plans keyed on the old one are dropped
+        // the staging buffer moves: every submission in flight ends first, and
+        // plans keyed on the old buffer are dropped
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess && ctx->copy_stream) e = cudaStreamSynchronize(ctx->copy_stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
         for (BatchPlan* bp : ctx->plans) destroy_plan(bp);
         ctx->plans.clear();
@@ -985,7 +997,10 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
     }
     cudaError_t e = cudaSuccess;
     if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !ctx->ev_start) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->ev_hsfoc) e = cudaEventCreateWithFlags(&ctx->ev_hsfoc, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->ev_hpts) e = cudaEventCreateWithFlags(&ctx->ev_hpts, cudaEventDisableTiming);
+    for (int r = 0; r < sfoc_ctx::kHostRing && e == cudaSuccess; ++r)
+        if (!ctx->ev_hdone[r]) e = cudaEventCreateWithFlags(&ctx->ev_hdone[r], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
     // staging layout, pair by pair: reference image, sensed image, points, results
     std::vector<const float*> dr(n_pairs), ds(n_pairs);
@@ -1016,23 +1031,19 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
         if (e == cudaSuccess) ctx->ev_wave.push_back(ev);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy events");
-    // synchronous on every path: copies from the caller's buffers are waited for
+    // on a failure after the first copy: everything in flight ends before the
+    // caller's buffers go back to it
     auto drained = [&](sfoc_status st) {
         cudaStreamSynchronize(ctx->copy_stream);
         cudaStreamSynchronize(ctx->stream);
         (void)cudaGetLastError();
         return st;
     };
-    // every copy after the work already queued on the context stream
-    e = cudaEventRecord(ctx->ev_start, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_start, 0);
-    // the point sets first (small, and the matching needs all of them), then
-    // the images in the plan's image order (reference of pair i = image 2i,
-    // sensed = 2i + 1), with an event after each SFOC wave's last image
-    for (int i = 0; i < n_pairs && e == cudaSuccess; ++i)
-        if (n_points[i] > 0)
-            e = cudaMemcpyAsync(const_cast<int32_t*>(dp[i]), h_points[i], sizeof(int32_t) * 2 * (size_t)n_points[i],
-                                cudaMemcpyHostToDevice, ctx->copy_stream);
+    const int64_t prev = ctx->host_ticket;  // the previous submission (0: none)
+    // the images, in the plan's image order (reference of pair i = image 2i,
+    // sensed = 2i + 1) with an event after each SFOC wave's last image, once
+    // the previous submission's SFOC launches have read the staged images
+    if (prev > 0) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_hsfoc, 0);
     auto copy_image = [&](int im) {
         const int i = im >> 1;
         if (im & 1)
@@ -1049,8 +1060,16 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
         }
     } else {
         for (int im = 0; im < 2 * n_pairs && e == cudaSuccess; ++im) e = copy_image(im);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_wave[0], ctx->copy_stream);
     }
+    // then the point sets, once the previous submission's results are out
+    // (its matching is the last to read them)
+    if (prev > 0 && e == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_hdone[prev % sfoc_ctx::kHostRing], 0);
+    for (int i = 0; i < n_pairs && e == cudaSuccess; ++i)
+        if (n_points[i] > 0)
+            e = cudaMemcpyAsync(const_cast<int32_t*>(dp[i]), h_points[i], sizeof(int32_t) * 2 * (size_t)n_points[i],
+                                cudaMemcpyHostToDevice, ctx->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_hpts, ctx->copy_stream);
     if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "host to device copy"));
     if (by_wave) {
         // the plan's stages launched one by one, each SFOC wave after its images
@@ -1064,26 +1083,69 @@ sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float*
                                   reinterpret_cast<const int*>(plan->dbuf + wv.smooth_begin), wv.smooth_ctas,
                                   plan->st, plan->sm, ctx->stream);
         }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_hsfoc, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_hpts, 0);
         if (e == cudaSuccess) e = enqueue_match_head(ctx, plan, ctx->stream);
         if (e == cudaSuccess) e = enqueue_match_tail(ctx, plan, ctx->stream);
         if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "batch launch"));
     } else {
         // first call with this signature: everything copied, then the plan is
         // built and run (and its graph captured) as fastncc_register_batch does
-        e = cudaStreamWaitEvent(ctx->stream, ctx->ev_wave[0], 0);
+        e = cudaStreamWaitEvent(ctx->stream, ctx->ev_hpts, 0);
         if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "cudaStreamWaitEvent"));
-        s = fastncc_register_batch(ctx, n_pairs, dr.data(), Hr, Wr, ds.data(), Hs, Ws, dp.data(), n_points,
-                                   template_size, search_radius, &prm, opts, dout.data());
-        if (s != SFOC_OK) return drained(s);
+        sfoc_status s2 = fastncc_register_batch(ctx, n_pairs, dr.data(), Hr, Wr, ds.data(), Hs, Ws, dp.data(),
+                                                n_points, template_size, search_radius, &prm, opts, dout.data());
+        if (s2 != SFOC_OK) return drained(s2);
+        e = cudaEventRecord(ctx->ev_hsfoc, ctx->stream);
+        if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "cudaEventRecord"));
     }
     for (int i = 0; i < n_pairs && e == cudaSuccess; ++i)
         if (n_points[i] > 0)
             e = cudaMemcpyAsync(h_outs[i], dout[i], sizeof(fastncc_result) * (size_t)n_points[i],
                                 cudaMemcpyDeviceToHost, ctx->stream);
+    const int64_t t = prev + 1;
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_hdone[t % sfoc_ctx::kHostRing], ctx->stream);
     if (e != cudaSuccess) return drained(cuda_fail(ctx, e, "device to host copy"));
-    e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    ctx->host_ticket = t;
+    *ticket = t;
     return SFOC_OK;
+}
+
+}  // namespace
+
+sfoc_status fastncc_submit_batch_host(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs, const int* Hr,
+                                      const int* Wr, const float* const* h_sens, const int* Hs, const int* Ws,
+                                      const int32_t* const* h_points, const int* n_points, const int* template_size,
+                                      const int* search_radius, const sfoc_params* p, const fastncc_opts* opts,
+                                      fastncc_result* const* h_outs, int64_t* ticket) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (!ticket) return fail(ctx, SFOC_ERR_INVALID_ARG, "ticket is NULL");
+    return host_batch_enqueue(ctx, n_pairs, h_refs, Hr, Wr, h_sens, Hs, Ws, h_points, n_points, template_size,
+                              search_radius, p, opts, h_outs, ticket);
+}
+
+sfoc_status fastncc_wait_batch_host(sfoc_ctx* ctx, int64_t ticket) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    if (ticket == 0) return SFOC_OK;  // an empty batch
+    if (ticket < 0 || ticket > ctx->host_ticket) return fail(ctx, SFOC_ERR_INVALID_ARG, "unknown batch ticket");
+    DeviceGuard g(ctx->device);
+    // a later submission in the same ring slot ends after this one
+    cudaError_t e = cudaEventSynchronize(ctx->ev_hdone[ticket % sfoc_ctx::kHostRing]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventSynchronize");
+    return SFOC_OK;
+}
+
+sfoc_status fastncc_register_batch_host(sfoc_ctx* ctx, int n_pairs, const float* const* h_refs, const int* Hr,
+                                        const int* Wr, const float* const* h_sens, const int* Hs, const int* Ws,
+                                        const int32_t* const* h_points, const int* n_points, const int* template_size,
+                                        const int* search_radius, const sfoc_params* p, const fastncc_opts* opts,
+                                        fastncc_result* const* h_outs) {
+    if (!ctx) return SFOC_ERR_INVALID_ARG;
+    int64_t t = 0;
+    sfoc_status s = host_batch_enqueue(ctx, n_pairs, h_refs, Hr, Wr, h_sens, Hs, Ws, h_points, n_points,
+                                       template_size, search_radius, p, opts, h_outs, &t);
+    if (s != SFOC_OK) return s;
+    return fastncc_wait_batch_host(ctx, t);
 }
 
 int sfoc_ctx_plan_count(const sfoc_ctx* ctx) { return ctx ? (int)ctx->plans.size() : 0; }

@@ -79,6 +79,15 @@ struct sfoc_ctx {
     // device staging of fastncc_register_batch_host (images, points, results)
     void* hstage = nullptr;
     size_t hstage_bytes = 0;
+    // host-buffer batch submissions (fastncc_submit_batch_host): their count,
+    // and events on the context stream: the last submission's images read by
+    // its SFOC launches, and submission t's results copied out (slot t mod
+    // kHostRing)
+    static constexpr int kHostRing = 4;
+    int64_t host_ticket = 0;
+    cudaEvent_t ev_hsfoc = nullptr;
+    cudaEvent_t ev_hpts = nullptr;  // the point sets of the submission being enqueued copied
+    cudaEvent_t ev_hdone[kHostRing] = {};
 };
 
 struct sfoc_cube {

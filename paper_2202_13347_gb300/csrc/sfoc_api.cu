@@ -497,6 +497,10 @@ sfoc_status sfoc_ctx_destroy(sfoc_ctx* ctx) {
     if (ctx->ev_switch) cudaEventDestroy(ctx->ev_switch);
     for (auto ev : ctx->ev_wave)
         if (ev) cudaEventDestroy(ev);
+    if (ctx->ev_hsfoc) cudaEventDestroy(ctx->ev_hsfoc);
+    if (ctx->ev_hpts) cudaEventDestroy(ctx->ev_hpts);
+    for (auto ev : ctx->ev_hdone)
+        if (ev) cudaEventDestroy(ev);
     for (BatchPlan* p : ctx->plans) destroy_plan(p);
     cudaFree(ctx->hstage);
     delete ctx;
@@ -917,12 +921,11 @@ sfoc_status fastncc_register_pair_host(sfoc_ctx* ctx, const float* h_ref, int Hr
     int32_t* d_pts = reinterpret_cast<int32_t*>(b + b_ref + b_sen);
     fastncc_result* d_out = reinterpret_cast<fastncc_result*>(b + b_ref + b_sen + b_pts);
     cudaError_t e = cudaSuccess;
-    if (!ctx->copy_stream) {
-        e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
-    }
+    // each created on first use (the batched host path shares the stream)
+    if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->ev_start) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->ev_copied) e = cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
     // the reference image on the context stream, the sensed image and the
     // points on the copy stream (after everything queued before this call):
     // the sensed copy lands while the reference cube is built

@@ -239,6 +239,13 @@ def _fake_batch_library():
         def register_batch_host(self, refs, sens, pts, ms, Rs, p=None, corr_path=0, outs=None):
             return self.register_batch(refs, sens, pts, ms, Rs, p, corr_path, outs)
 
+        def submit_batch_host(self, refs, sens, pts, ms, Rs, p=None, corr_path=0, outs=None):
+            self.tickets = getattr(self, "tickets", 0) + 1
+            return self.tickets, self.register_batch(refs, sens, pts, ms, Rs, p, corr_path, outs)
+
+        def wait_batch_host(self, ticket):
+            assert 0 < ticket <= self.tickets
+
         def plan_info(self):
             return {"kind": 2, "graph": True, "classes": [{"path": 5, "cls": 3, "items": 10, "launches": 1,
                                                           "pairs": [0, 1]},
@@ -283,6 +290,9 @@ def test_batched_line(monkeypatch, capsys):
     roof = line["roofline"]
     assert roof["bound"] == "tensor" and len(roof["classes"]) == 2 and roof["launch_ms"] == 0.5
     assert line["e2e"]["h2d_bytes_per_step"] == sum(q.ref.nbytes + q.sen.nbytes + q.points.nbytes for q in small)
+    # the timed steps are submissions, each waited for after the next one is in
+    assert line["e2e"]["call"].startswith("fastncc_submit_batch_host") and len(line["e2e"]["step_done_ms"]) == 3
+    assert line["e2e"]["results_equal_across_steps"] is True and len(line["e2e"]["sync_call_ms"]) == 3
     assert line["cpu_baseline"]["kind"] == "oracle" and line["parity"]["points"] > 0
     assert line["bf16batch_over_f32plain"] is not None
     assert line["gpu_launches"] == 14 * 3

@@ -159,6 +159,71 @@ def test_register_batch_host_keeps_its_plan(b, ctx, small_batch):
     ctx.release_plans()
 
 
+def _pinned_sets(batch):
+    """Two input sets of the same shapes: the batch, and its images mirrored
+    left to right with the points mirrored too."""
+    a = ([torch.from_numpy(q.ref).pin_memory() for q in batch], [torch.from_numpy(q.sen).pin_memory() for q in batch],
+         [torch.from_numpy(q.points).pin_memory() for q in batch])
+    mirror = []
+    for q in batch:
+        pts = q.points.copy()
+        pts[:, 0] = q.sen.shape[1] - 1 - pts[:, 0]
+        mirror.append(pts)
+    b_ = ([torch.from_numpy(np.ascontiguousarray(q.ref[:, ::-1])).pin_memory() for q in batch],
+          [torch.from_numpy(np.ascontiguousarray(q.sen[:, ::-1])).pin_memory() for q in batch],
+          [torch.from_numpy(np.ascontiguousarray(pt)).pin_memory() for pt in mirror])
+    return a, b_
+
+
+def test_submitted_batches_overlap_and_match(b, ctx, small_batch):
+    """fastncc_submit_batch_host / fastncc_wait_batch_host: submissions that
+    alternate between two input sets through the one staging buffer, with
+    up to six outstanding (more than the four-slot event ring), each give
+    the synchronous call's results for its own inputs; the plan is built
+    once; an empty batch gets ticket 0; an unissued ticket is an error."""
+    p = b.params(dtype=b.DTYPE_BF16)
+    batch = small_batch[:4]
+    ms, Rs = [q.m for q in batch], [q.R for q in batch]
+    sets = _pinned_sets(batch)
+    want = [[o.clone() for o in ctx.register_batch_host(*st, ms, Rs, p=p)] for st in sets]
+    assert any(not torch.equal(x, y) for x, y in zip(*want))  # the two sets differ
+    built = ctx.plan_info()["plans_built"]
+    # two in flight at a time
+    outs, tickets = [], []
+    for k in range(6):
+        o = [torch.empty_like(x).pin_memory() for x in want[k % 2]]
+        t, o = ctx.submit_batch_host(*sets[k % 2], ms, Rs, p=p, outs=o)
+        tickets.append(t)
+        outs.append(o)
+        if k >= 1:
+            ctx.wait_batch_host(tickets[k - 1])
+            assert all(torch.equal(x, y) for x, y in zip(outs[k - 1], want[(k - 1) % 2])), k - 1
+    ctx.wait_batch_host(tickets[-1])
+    assert all(torch.equal(x, y) for x, y in zip(outs[-1], want[1]))
+    assert tickets == list(range(tickets[0], tickets[0] + 6))
+    # six outstanding, then one wait for the last
+    outs, tickets = [], []
+    for k in range(6):
+        t, o = ctx.submit_batch_host(*sets[k % 2], ms, Rs, p=p,
+                                     outs=[torch.empty_like(x).pin_memory() for x in want[k % 2]])
+        tickets.append(t)
+        outs.append(o)
+    ctx.wait_batch_host(tickets[-1])
+    for k in range(6):
+        assert all(torch.equal(x, y) for x, y in zip(outs[k], want[k % 2])), k
+    assert ctx.plan_info()["plans_built"] == built
+    # a synchronous call after submissions still matches
+    again = ctx.register_batch_host(*sets[0], ms, Rs, p=p)
+    assert all(torch.equal(x, y) for x, y in zip(again, want[0]))
+    t0, _ = ctx.submit_batch_host([], [], [], [], [], p=p, outs=[])
+    assert t0 == 0
+    ctx.wait_batch_host(0)
+    with pytest.raises(b.SfocError):
+        ctx.wait_batch_host(tickets[-1] + 100)
+    ctx.sync()
+    ctx.release_plans()
+
+
 @pytest.mark.parametrize("dt", ["f32", "bf16"])
 def test_register_batch_against_oracle(b, ctx, orc, small_batch, dt):
     """A seeded sample of 6 points per pair against the FP64 oracle (BF16:
