@@ -693,12 +693,14 @@ def run_batch_form(b, torch, ctx, pairs, form, steps, warmup, corr_name="auto"):
 
 
 # DRAM bytes per processed point of a band-form class, by (template side,
-# band instance NQ), from one ncu capture of the kernel as it stands: the
-# 2048x2048 pair's 1000 points matched at m = 101, R = 40 (851 processed;
-# 745.06 MB read + 44.46 MB written per launch).  A batched class of the same
-# template side and instance gets this times its processed points (its radii
-# range over R 33-40).
-BAND_TRAFFIC_PER_POINT = {(101, 6): (745.062144e6 + 44.461312e6) / 851}
+# band instance NQ), from ncu captures of the kernel as it stands, each of the
+# 2048x2048 pair's 1000 points matched with forced band form at one (m, R):
+# m = 101, R = 40 (851 processed; 745.06 MB read + 44.46 MB written per
+# launch) and m = 81, R = 36 (879 points in bounds; 359.81 MB + 30.00 MB).  A
+# batched class of the same template side and instance gets this times its
+# processed points (its radii range over R 33-40).
+BAND_TRAFFIC_PER_POINT = {(101, 6): (745.062144e6 + 44.461312e6) / 851,
+                          (81, 6): (359.80928e6 + 29.997056e6) / 879}
 
 
 def batch_roofline(form, pairs, r, pk):
