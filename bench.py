@@ -964,7 +964,7 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
             # FP32 work) the host copies of alternate calls were seen to run at a
             # tenth of their rate, with no kernel running beside them
             if form == "bf16batch" and not args.no_e2e:
-                r["e2e_raw"] = batch_e2e(b, torch, ctx, pairs, r["p"], r["corr"], max(3, min(args.steps, 10)))
+                r["e2e_raw"] = batch_e2e(b, torch, ctx, pairs, r["p"], r["corr"], max(3, args.steps))
         except b.SfocError as e:
             results[form] = {"error": str(e)}
         if form != forms[-1] and form != "bf16batch":
@@ -992,7 +992,7 @@ def main_batch(args, torch, dist, rank, world, gpu_index):
     r0 = results[main_form]
     e2e = None
     if not args.no_e2e and main_form != "f32plain":
-        er = r0.get("e2e_raw") or batch_e2e(b, torch, ctx, pairs, r0["p"], r0["corr"], max(3, min(args.steps, 10)))
+        er = r0.get("e2e_raw") or batch_e2e(b, torch, ctx, pairs, r0["p"], r0["corr"], max(3, args.steps))
         if dist:
             dist.barrier()
         ms_max, matched_all = reduce_over_ranks(dist, torch, er["ms"], er["matched"] * er["steps"], "cuda")
@@ -1157,7 +1157,7 @@ def main():
     r0 = results[main_form]
     e2e = None
     if not args.no_e2e:
-        r = run_e2e(b, torch, ctx, pair, r0["p"], r0["corr"], max(3, min(args.steps, 10)))
+        r = run_e2e(b, torch, ctx, pair, r0["p"], r0["corr"], max(3, args.steps))
         if dist:
             dist.barrier()
         ms_max, matched_all = reduce_over_ranks(dist, torch, r["ms"], r["matched"] * r["steps"], "cuda")
