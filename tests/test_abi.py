@@ -137,3 +137,51 @@ def test_binding_shape_checks(b):
         b._check_host(torch.zeros(3, dtype=torch.float64), "h", torch.float32)
     with pytest.raises(ValueError):
         b._check_host(torch.zeros((4, 4), dtype=torch.float32).t(), "h", torch.float32)
+
+
+def test_submitted_batch_keeps_its_tensors_until_waited(b, monkeypatch):
+    """submit_batch_host hands the library raw pointers and returns at once,
+    so the binding holds each submission's tensors until wait_batch_host
+    returns for its ticket or a later one; the pointers and shapes passed are
+    the tensors' own.  (The library is stubbed: no device.)"""
+    import torch
+    seen = []
+
+    class Stub:
+        def fastncc_submit_batch_host(self, h, n, refs, Hr, Wr, sens, Hs, Ws, pts, npts, ms, Rs, p, o, outs, t):
+            seen.append((n, [refs[i] for i in range(n)], [Hr[i] for i in range(n)], [Ws[i] for i in range(n)],
+                         [npts[i] for i in range(n)], [ms[i] for i in range(n)], o._obj.corr_path))
+            t._obj.value = len(seen)
+            return 0
+
+        def fastncc_wait_batch_host(self, h, t):
+            return 0 if 0 <= t <= len(seen) else -1
+
+        def sfoc_last_error_string(self, h):
+            return b"unknown batch ticket"
+
+    monkeypatch.setattr(b, "lib", lambda: Stub())
+    ctx = object.__new__(b.Context)
+    ctx.h, ctx.device = C.c_void_p(1), torch.device("cuda", 0)
+    try:
+        refs = [torch.zeros((30, 40)), torch.zeros((50, 20))]
+        sens = [torch.zeros((31, 41)), torch.zeros((51, 21))]
+        pts = [torch.zeros((3, 2), dtype=torch.int32), torch.zeros((5, 2), dtype=torch.int32)]
+        t1, o1 = ctx.submit_batch_host(refs, sens, pts, [9, 11], [2, 3], corr_path=b.CORR_TC_BAND)
+        t2, o2 = ctx.submit_batch_host(refs, sens, pts, [9, 11], [2, 3])
+        assert (t1, t2) == (1, 2)
+        assert [tuple(o.shape) for o in o1] == [(3, 6), (5, 6)]
+        n, ptr, H, W, npt, m, corr = seen[0]
+        assert n == 2 and ptr == [r.data_ptr() for r in refs] and H == [30, 50] and W == [41, 21]
+        assert npt == [3, 5] and m == [9, 11] and corr == b.CORR_TC_BAND
+        assert set(ctx._held) == {1, 2} and ctx._held[1][3] is o1
+        ctx.wait_batch_host(1)
+        assert set(ctx._held) == {2}
+        ctx.wait_batch_host(2)
+        assert not ctx._held
+        with pytest.raises(b.SfocError):
+            ctx.wait_batch_host(7)
+        with pytest.raises(ValueError):  # images must be float32
+            ctx.submit_batch_host([torch.zeros((3, 3), dtype=torch.float64)], sens[:1], pts[:1], [1], [0])
+    finally:
+        ctx.h = None  # nothing to destroy: the handle is the stub's
